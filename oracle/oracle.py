@@ -1,0 +1,194 @@
+"""ctypes front end of the FP64 oracle (``bte_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+State layout: ``e[k][d][z][y][x]`` as a float64 array of shape (nb, nd, nz, ny, nx).
+Boundary codes: 0 isothermal, 1 diffuse, 2 specular, 3 periodic; walls ordered
+-x, +x, -y, +y, -z, +z.  Limiter codes: 0 first order, 1 minmod, 2 van Albada.
+"""
+import ctypes as ct
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bte_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle_bte.so")
+_lock = threading.Lock()
+_lib = None
+
+BC_ISOTHERMAL, BC_DIFFUSE, BC_SPECULAR, BC_PERIODIC = 0, 1, 2, 3
+LIM_FIRST_ORDER, LIM_MINMOD, LIM_VANALBADA = 0, 1, 2
+
+
+def build_oracle(force=False):
+    """Compile ``bte_oracle.c`` into ``liboracle_bte.so`` next to it (gcc, OpenMP)."""
+    srcs = [_SRC, os.path.join(_HERE, "bte_oracle_adjoint.c")]
+    srcs = [s for s in srcs if os.path.exists(s)]
+    newest = max(os.path.getmtime(s) for s in srcs)
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
+        return _LIB
+    tmp = _LIB + ".tmp.%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c99", "-o", tmp] + srcs + ["-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Prob(ct.Structure):
+    _fields_ = [
+        ("dim", ct.c_int), ("nx", ct.c_int), ("ny", ct.c_int), ("nz", ct.c_int),
+        ("dx", ct.c_double), ("dy", ct.c_double), ("dz", ct.c_double),
+        ("nb", ct.c_int), ("nd", ct.c_int),
+        ("C", ct.POINTER(ct.c_double)), ("v", ct.POINTER(ct.c_double)), ("tau", ct.POINTER(ct.c_double)),
+        ("s", ct.POINTER(ct.c_double)), ("w", ct.POINTER(ct.c_double)),
+        ("mirror", ct.POINTER(ct.c_int)),
+        ("bc", ct.c_int * 6), ("Tw", ct.c_double * 6),
+        ("dt", ct.c_double), ("limiter", ct.c_int),
+    ]
+
+
+def load_oracle():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build_oracle()
+            _lib = ct.CDLL(_LIB)
+            dp = ct.POINTER(ct.c_double)
+            fp = ct.POINTER(ct.c_float)
+            pp = ct.POINTER(_Prob)
+            _lib.orc_step.argtypes = [pp, dp, dp, fp, ct.c_double]
+            _lib.orc_run.argtypes = [pp, dp, fp, dp, ct.c_int, ct.c_long, ct.c_int]
+            _lib.orc_moments.argtypes = [pp, dp, dp, dp, dp]
+            _lib.orc_lattice_temperature.argtypes = [pp, dp, dp]
+            _lib.orc_energy.argtypes = [pp, dp, dp, dp]
+            _lib.orc_step_points.argtypes = [pp, dp, fp, ct.c_double, ct.c_long, ct.POINTER(ct.c_long), dp]
+            if hasattr(_lib, "orc_adjoint"):
+                _lib.orc_adjoint.argtypes = [pp, dp, fp, dp, ct.c_int, ct.c_int, dp, dp, dp, ct.c_int]
+                _lib.orc_adjoint_step.argtypes = [pp, dp, dp, dp, dp]
+                _lib.orc_adjoint.restype = ct.c_int
+        return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ct.POINTER(ct.c_double))
+
+
+def _fp(a):
+    return None if a is None else a.ctypes.data_as(ct.POINTER(ct.c_float))
+
+
+class Problem:
+    """One discretised problem: grid, bands, quadrature, walls, time step and limiter."""
+
+    def __init__(self, dim, n, h, C, v, tau, s, w, mirror, bc, Tw, dt, limiter=LIM_VANALBADA):
+        self.dim = int(dim)
+        self.nx, self.ny, self.nz = (int(t) for t in n)
+        self.dx, self.dy, self.dz = (float(t) for t in h)
+        self.C = np.ascontiguousarray(C, dtype=np.float64)
+        self.v = np.ascontiguousarray(v, dtype=np.float64)
+        self.tau = np.ascontiguousarray(tau, dtype=np.float64)
+        self.s = np.ascontiguousarray(s, dtype=np.float64).reshape(-1, 3)
+        self.w = np.ascontiguousarray(w, dtype=np.float64)
+        self.mirror = np.ascontiguousarray(mirror, dtype=np.int32).reshape(3, -1)
+        self.nb, self.nd = self.C.size, self.w.size
+        self.bc = [int(b) for b in bc]
+        self.Tw = [float(t) for t in Tw]
+        self.dt = float(dt)
+        self.limiter = int(limiter)
+        self._lib = load_oracle()
+        self._p = _Prob(self.dim, self.nx, self.ny, self.nz, self.dx, self.dy, self.dz, self.nb, self.nd,
+                        _dp(self.C), _dp(self.v), _dp(self.tau), _dp(self.s), _dp(self.w),
+                        self.mirror.ctypes.data_as(ct.POINTER(ct.c_int)),
+                        (ct.c_int * 6)(*self.bc), (ct.c_double * 6)(*self.Tw), self.dt, self.limiter)
+
+    # -- sizes ---------------------------------------------------------------------------
+    @property
+    def shape(self):
+        return (self.nb, self.nd, self.nz, self.ny, self.nx)
+
+    @property
+    def ncell(self):
+        return self.nx * self.ny * self.nz
+
+    @property
+    def W(self):
+        # sequential sum, the same order as the C code's total weight
+        W = 0.0
+        for x in self.w:
+            W += float(x)
+        return W
+
+    def _src(self, Q):
+        if Q is None:
+            return None
+        Q = np.ascontiguousarray(Q, dtype=np.float32).reshape(-1)
+        assert Q.size == self.ncell
+        return Q
+
+    # -- state ---------------------------------------------------------------------------
+    def equilibrium(self, dT):
+        """e_{k,d,i} = C_k dT_i / W, the equilibrium energy density of Eq. (BTE_get_e0)."""
+        dT = np.broadcast_to(np.asarray(dT, dtype=np.float64), (self.nz, self.ny, self.nx))
+        e = self.C[:, None, None, None, None] * dT[None, None] / self.W
+        return np.ascontiguousarray(np.broadcast_to(e, self.shape), dtype=np.float64)
+
+    def step(self, e, Q=None, amp=1.0):
+        e = np.ascontiguousarray(e, dtype=np.float64)
+        out = np.empty_like(e)
+        Qc = self._src(Q)
+        self._lib.orc_step(ct.byref(self._p), _dp(e), _dp(out), _fp(Qc), float(amp))
+        return out
+
+    def run(self, e, nsteps, Q=None, amps=None, n0=0):
+        """nsteps steps; amps[n] is the source amplitude at step n (None: 1; past the end: 0)."""
+        e = np.array(e, dtype=np.float64, order="C", copy=True)
+        Qc = self._src(Q)
+        if amps is None:
+            ap, na = None, 0
+        else:
+            amps = np.ascontiguousarray(amps, dtype=np.float64)
+            ap, na = _dp(amps), amps.size
+        self._lib.orc_run(ct.byref(self._p), _dp(e), _fp(Qc), ap, na, int(n0), int(nsteps))
+        return e
+
+    def lattice_temperature(self, e):
+        e = np.ascontiguousarray(e, dtype=np.float64)
+        TL = np.empty(self.ncell)
+        self._lib.orc_lattice_temperature(ct.byref(self._p), _dp(e), _dp(TL))
+        return TL.reshape(self.nz, self.ny, self.nx)
+
+    def moments(self, e):
+        """(T, T_L, q) of Eq. (getTQ) and Eq. (BTE_get_e0); q has shape (3, nz, ny, nx)."""
+        e = np.ascontiguousarray(e, dtype=np.float64)
+        T = np.empty(self.ncell)
+        TL = np.empty(self.ncell)
+        q = np.empty(3 * self.ncell)
+        self._lib.orc_moments(ct.byref(self._p), _dp(e), _dp(T), _dp(TL), _dp(q))
+        g = (self.nz, self.ny, self.nx)
+        return T.reshape(g), TL.reshape(g), q.reshape((3,) + g)
+
+    def energy(self, e):
+        """(E_total, wall_flux[6]): the global energy and the outward wall heat flows."""
+        e = np.ascontiguousarray(e, dtype=np.float64)
+        E = np.zeros(1)
+        F = np.zeros(6)
+        self._lib.orc_energy(ct.byref(self._p), _dp(e), _dp(E), _dp(F))
+        return float(E[0]), F
+
+    def step_points(self, e, pts, Q=None, amp=1.0):
+        """e^{n+1} at the given (k, d, cell) triples, from e^n."""
+        e = np.ascontiguousarray(e, dtype=np.float64)
+        pts = np.ascontiguousarray(pts, dtype=np.int64).reshape(-1, 3)
+        out = np.empty(pts.shape[0])
+        Qc = self._src(Q)
+        self._lib.orc_step_points(ct.byref(self._p), _dp(e), _fp(Qc), float(amp), pts.shape[0],
+                                  pts.ctypes.data_as(ct.POINTER(ct.c_long)), _dp(out))
+        return out
+
+    @property
+    def cell_volume(self):
+        L = [self.dx, self.dy, self.dz]
+        return float(np.prod([L[a] if a < self.dim else 1.0 for a in range(3)]))

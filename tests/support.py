@@ -1,0 +1,41 @@
+"""Shared helpers for the tests: turn a workload dict into an oracle problem."""
+import numpy as np
+
+from oracle import Problem
+from oracle import quadrature as oq
+from oracle.oracle import LIM_VANALBADA
+
+
+def oracle_quadrature(quad):
+    if quad[0] == "gl1d":
+        return oq.polar_1d(quad[1])
+    return oq.octant_rule(quad[1], quad[2])
+
+
+def oracle_problem(cfg, limiter=LIM_VANALBADA, **over):
+    c = dict(cfg)
+    c.update(over)
+    s, w, mirror = oracle_quadrature(c["quad"])
+    return Problem(c["dim"], c["n"], c["h"], c["C"], c["v"], c["tau"], s, w, mirror, c["bc"], c["Tw"], c["dt"],
+                   limiter)
+
+
+def small_cfg(dim, n, bc, Tw=(0, 0, 0, 0, 0, 0), nb=3, quad=None, h=2e-9, seed=7, beta=0.5, tau=None, v=None):
+    """A small synthetic problem for pins."""
+    from paper_2306_14181_gb300 import inputs
+    C, vv, tt = inputs.bands(seed, nb)
+    if tau is not None:
+        tt = np.full(nb, float(tau)) if np.isscalar(tau) else np.asarray(tau, float)
+    if v is not None:
+        vv = np.full(nb, float(v)) if np.isscalar(v) else np.asarray(v, float)
+    if quad is None:
+        quad = ("gl1d", 8) if dim == 1 else ("octant", 2, 2)
+    hh = (h, h, h)
+    return dict(dim=dim, n=tuple(n), h=hh, nb=nb, C=C, v=vv, tau=tt, quad=quad, bc=list(bc), Tw=list(Tw),
+                dt=inputs.cfl_time_step(hh[:dim], vv, beta))
+
+
+def rel_linf(a, b):
+    a = np.asarray(a, float)
+    b = np.asarray(b, float)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))

@@ -1,0 +1,392 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (no GPU).
+
+Each test names the passage of arXiv 2306.14181 it follows.  None of them retypes the
+oracle's formulas: they check closed forms, conservation laws, invariances, limits and an
+independently built Fourier-mode amplification matrix.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import quadrature as oq
+from oracle.oracle import (BC_DIFFUSE, BC_ISOTHERMAL, BC_PERIODIC, BC_SPECULAR, LIM_FIRST_ORDER, LIM_MINMOD,
+                           LIM_VANALBADA)
+from paper_2306_14181_gb300 import inputs
+from tests.support import oracle_problem, oracle_quadrature, rel_linf, small_cfg
+
+ISO, DIF, SPE, PER = BC_ISOTHERMAL, BC_DIFFUSE, BC_SPECULAR, BC_PERIODIC
+FOURPI = 4.0 * math.pi
+
+
+# ---------------------------------------------------------------------------------------
+# P1  quadrature identities (Sec. 3.2, Eq. directiondis)
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("rule", [("gl1d", 16), ("gl1d", 8), ("octant", 4, 4), ("octant", 4, 3),
+                                  ("octant", 2, 4), ("octant", 2, 1), ("octant", 3, 5), ("octant", 8, 8)])
+def test_p1_quadrature_identities(rule):
+    s, w, mirror = oracle_quadrature(rule)
+    assert abs(w.sum() - FOURPI) <= 1e-14 * FOURPI
+    assert np.all(w > 0)
+    if rule[0] == "octant":      # the 1-D rule keeps only the projection mu = s_x
+        assert np.allclose(np.linalg.norm(s, axis=1), 1.0, atol=1e-15, rtol=0)
+    first = (w[:, None] * s).sum(axis=0)
+    assert np.max(np.abs(first)) <= 1e-14
+    second = np.einsum("d,di,dj->ij", w, s, s)
+    expect = np.diag([FOURPI / 3, 0, 0]) if rule[0] == "gl1d" else FOURPI / 3 * np.eye(3)
+    assert np.max(np.abs(second - expect)) <= 1e-14
+    # number of directions: 8 Ntheta Nphi (octant rule)
+    if rule[0] == "octant":
+        assert s.shape[0] == 8 * rule[1] * rule[2]
+    # mirror table: component a negated, everything else kept
+    for a in range(3):
+        t = s.copy()
+        t[:, a] *= -1
+        assert np.array_equal(s[mirror[a]], t)
+        assert np.array_equal(w[mirror[a]], w)
+
+
+def test_p1_paper_theta_rule_is_only_approximate():
+    """The literal reading (GL in theta times sin(theta)) meets the identities only to
+    quadrature error, which shrinks with Ntheta."""
+    errs = []
+    for nt in (2, 4, 8):
+        s, w, _ = oq.octant_rule(nt, 4, paper_theta_rule=True)
+        errs.append(abs(w.sum() - FOURPI) / FOURPI)
+    assert errs[0] > 1e-4 and errs[2] < errs[1] < errs[0]
+
+
+def test_p1_half_range_flux_moment_near_one_quarter():
+    """sum_{s_x>0} w s_x / W -> 1/4 (the hemispherical flux factor behind q = C v dT / 4)."""
+    for rule in [("gl1d", 16), ("octant", 4, 4)]:
+        s, w, _ = oracle_quadrature(rule)
+        f = (w * np.clip(s[:, 0], 0, None)).sum() / w.sum()
+        assert abs(f - 0.25) < 3e-3
+
+
+# ---------------------------------------------------------------------------------------
+# P2  discrete global energy balance (Eq. disretized_transientBTE summed over cells, bands
+#     and directions; the relaxation term conserves energy through Eq. BTE_get_e0)
+# ---------------------------------------------------------------------------------------
+P2_CASES = [
+    (1, (17, 1, 1), [ISO, ISO, PER, PER, PER, PER]),
+    (1, (13, 1, 1), [DIF, SPE, PER, PER, PER, PER]),
+    (1, (11, 1, 1), [PER, PER, PER, PER, PER, PER]),
+    (2, (9, 7, 1), [DIF, SPE, ISO, DIF, PER, PER]),
+    (2, (8, 6, 1), [PER, PER, ISO, ISO, PER, PER]),
+    (2, (6, 5, 1), [SPE, SPE, SPE, SPE, PER, PER]),
+    (3, (6, 5, 4), [PER, PER, SPE, DIF, ISO, DIF]),
+    (3, (5, 4, 6), [DIF, ISO, PER, PER, SPE, ISO]),
+]
+
+
+@pytest.mark.parametrize("limiter", [LIM_FIRST_ORDER, LIM_MINMOD, LIM_VANALBADA])
+@pytest.mark.parametrize("dim,n,bc", P2_CASES)
+def test_p2_energy_balance(dim, n, bc, limiter):
+    cfg = small_cfg(dim, n, bc, Tw=[0.3, -0.2, 0.1, 0.4, -0.3, 0.2])
+    P = oracle_problem(cfg, limiter)
+    e = inputs.random_state(P.shape, 11) * 1e3
+    rng = np.random.default_rng(3)
+    Q = (rng.random((P.nz, P.ny, P.nx)) * 1e17).astype(np.float32)
+    amp = 0.7
+    E0, F0 = P.energy(e)
+    e1 = P.step(e, Q, amp)
+    E1, _ = P.energy(e1)
+    V = P.cell_volume
+    rhs = P.dt * (V * amp * float(Q.astype(np.float64).sum()) - F0.sum())
+    scale = max(abs(E0), abs(E1), P.dt * np.abs(F0).sum())
+    assert abs((E1 - E0) - rhs) <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("bc", [[DIF, SPE, SPE, DIF, SPE, DIF], [PER, PER, DIF, SPE, DIF, SPE]])
+def test_p2_adiabatic_walls_conserve_energy(bc):
+    """With adiabatic (specular/diffuse) or periodic walls and no source, E is constant over
+    many steps and each wall's net heat flow vanishes."""
+    cfg = small_cfg(3, (5, 6, 4), bc)
+    P = oracle_problem(cfg)
+    e = inputs.random_state(P.shape, 5) * 10.0
+    E0, _ = P.energy(e)
+    for _ in range(20):
+        e = P.step(e)
+        E, F = P.energy(e)
+        tol = 1e-12 * np.abs(E0) / P.dt
+        for a in range(3):
+            if bc[2 * a] == PER:          # flow leaving one periodic side re-enters the other
+                assert abs(F[2 * a] + F[2 * a + 1]) <= tol
+            else:
+                assert abs(F[2 * a]) <= tol and abs(F[2 * a + 1]) <= tol
+    assert abs(E - E0) <= 1e-12 * abs(E0)
+
+
+# ---------------------------------------------------------------------------------------
+# P3  a uniform equilibrium state without source stays uniform (Eq. BTE_get_e0: e = e0)
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("dim,n", [(2, (7, 6, 1)), (3, (5, 4, 6))])
+@pytest.mark.parametrize("bc,exact", [([PER] * 6, True), ([SPE] * 6, True), ([SPE, PER, PER, SPE, SPE, PER], False),
+                                      ([ISO] * 6, False), ([DIF] * 6, False)])
+def test_p3_uniform_state_stays_uniform(dim, n, bc, exact):
+    if any(b == PER for b in bc):
+        # periodic must pair up on an axis
+        bc = [bc[0], bc[0], bc[2], bc[2], bc[4], bc[4]]
+    dT = 0.37
+    cfg = small_cfg(dim, n, bc, Tw=[dT] * 6)
+    P = oracle_problem(cfg)
+    e = P.equilibrium(dT)
+    for _ in range(6):
+        e = P.step(e)
+        planes = e.reshape(P.nb * P.nd, -1)
+        spread = planes.max(axis=1) - planes.min(axis=1)
+        if exact:
+            assert np.all(spread == 0.0)
+        else:
+            assert np.all(spread <= 4e-15 * np.abs(planes).max(axis=1))
+    TL = P.lattice_temperature(e)
+    assert np.max(np.abs(TL - dT)) <= 1e-14 * dT
+
+
+# ---------------------------------------------------------------------------------------
+# P4  ballistic limit between black isothermal walls (Eq. thermal, Eq. getTQ):
+#     q = sum_k C_k v_k dT (sum_{s_x>0} w s_x) / W
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("limiter", [LIM_FIRST_ORDER, LIM_VANALBADA])
+def test_p4_ballistic_flux(limiter):
+    cfg = small_cfg(1, (20, 1, 1), [ISO, ISO, PER, PER, PER, PER], Tw=[0.5, -0.5, 0, 0, 0, 0], nb=3,
+                    quad=("gl1d", 16), h=1e-9, tau=1e3)
+    P = oracle_problem(cfg, limiter)
+    s, w = P.s, P.w
+    mu_min = np.min(np.abs(s[:, 0]))
+    cross = P.nx * P.dx / (np.min(P.v) * mu_min) / P.dt
+    e = P.run(P.equilibrium(0.0), int(4 * cross))
+    _, _, q = P.moments(e)
+    half = float((w * np.clip(s[:, 0], 0, None)).sum()) / P.W
+    expect = float(np.sum(P.C * P.v)) * 1.0 * half
+    assert rel_linf(q[0].ravel(), np.full(P.nx, expect)) <= 1e-6
+
+
+# ---------------------------------------------------------------------------------------
+# P5  diffusive limit: local Fourier law with kappa = sum C v^2 tau / 3 (Sec. 3.4, k_bulk)
+# ---------------------------------------------------------------------------------------
+def test_p5_diffusive_limit_fourier_law():
+    C = np.array([1.66e6])
+    cfg = small_cfg(1, (100, 1, 1), [ISO, ISO, PER, PER, PER, PER], Tw=[0.5, -0.5, 0, 0, 0, 0], nb=1,
+                    quad=("gl1d", 16), h=1e-9, tau=1e-12, v=1e3)
+    cfg["C"] = C
+    P = oracle_problem(cfg, LIM_VANALBADA)
+    x = (np.arange(P.nx) + 0.5) / P.nx
+    e = P.run(P.equilibrium((0.5 - x)[None, None, :]), 4000)
+    _, TL, q = P.moments(e)
+    TL = TL.ravel()
+    sl = slice(20, 80)
+    xs = (np.arange(P.nx) + 0.5) * P.dx
+    slope, icpt = np.polyfit(xs[sl], TL[sl], 1)
+    resid = TL[sl] - (slope * xs[sl] + icpt)
+    assert np.max(np.abs(resid)) <= 1e-3 * np.ptp(TL)        # linear interior profile
+    kappa = float(np.sum(P.C * P.v ** 2 * P.tau)) / 3.0
+    ratio = np.mean(q[0].ravel()[sl]) / (-kappa * slope)
+    assert abs(ratio - 1.0) <= 1e-2
+
+
+# ---------------------------------------------------------------------------------------
+# P6  transient thermal grating (Sec. 4.2): with the first-order face value the fully
+#     discrete scheme maps each Fourier mode to itself, e_hat^{n+1} = G(theta) e_hat^n.
+# ---------------------------------------------------------------------------------------
+def _ttg_matrix(P, theta):
+    nb, nd = P.nb, P.nd
+    D = float(np.sum(P.C / P.tau))
+    G = np.zeros((nb * nd, nb * nd), dtype=complex)
+    col = np.zeros(nb * nd)
+    for k in range(nb):
+        for d in range(nd):
+            col[k * nd + d] = P.w[d] / P.tau[k] / D
+    for k in range(nb):
+        for d in range(nd):
+            r = k * nd + d
+            nu = P.dt * P.v[k] * P.s[d, 0] / P.dx
+            sg = 1.0 if nu > 0 else -1.0
+            G[r, r] += 1.0 - abs(nu) * (1.0 - np.exp(-1j * sg * theta)) - P.dt / P.tau[k]
+            G[r, :] += P.dt / P.tau[k] * (P.C[k] / P.W) * col
+    return G, col
+
+
+@pytest.mark.parametrize("nb,quad", [(1, ("gl1d", 8)), (3, ("gl1d", 6))])
+def test_p6_ttg_fourier_mode_exact(nb, quad):
+    cfg = small_cfg(1, (24, 1, 1), [PER] * 6, nb=nb, quad=quad, h=1e-9)
+    P = oracle_problem(cfg, LIM_FIRST_ORDER)
+    theta = 2 * math.pi / P.nx
+    j = np.arange(P.nx)
+    e0 = P.equilibrium(np.cos(theta * (j + 0.5))[None, None, :])
+    nsteps = 150
+    e = P.run(e0, nsteps)
+    G, col = _ttg_matrix(P, theta)
+    a = np.repeat((P.C / P.W)[:, None], P.nd, axis=1).ravel() * np.exp(0.5j * theta)
+    a = np.linalg.matrix_power(G, nsteps) @ a
+    pred_e = np.real(a[:, None] * np.exp(1j * theta * j)[None, :])
+    assert rel_linf(e.reshape(P.nb * P.nd, P.nx), pred_e) <= 1e-12
+    pred_TL = np.real((col @ a) * np.exp(1j * theta * j))
+    assert rel_linf(P.lattice_temperature(e).ravel(), pred_TL) <= 1e-12
+
+
+def test_p6_limited_scheme_order_of_accuracy():
+    """Free streaming of a smooth periodic profile (tau -> infinity).  Forward Euler is first
+    order in time, so dt is scaled with dx^2 to expose the spatial reconstruction: the limited
+    face values then converge at about second order, the first-order face value at first."""
+    def err(N, limiter):
+        beta = 0.02 * (64.0 / N)
+        cfg = small_cfg(1, (N, 1, 1), [PER] * 6, nb=1, quad=("gl1d", 4), h=64e-9 / N, tau=1e3, v=1e3,
+                        beta=beta)
+        P = oracle_problem(cfg, limiter)
+        L = N * P.dx
+        xc = (np.arange(N) + 0.5) * P.dx
+        nsteps = int(round(0.25 * L / (P.v[0] * P.dt)))
+        t = nsteps * P.dt
+        e = P.run(P.equilibrium(np.sin(2 * math.pi * xc / L)[None, None, :]), nsteps)
+        ex = np.array([np.sin(2 * math.pi * (xc - P.v[0] * P.s[d, 0] * t) / L) for d in range(P.nd)])
+        ex = ex * P.C[0] / P.W
+        return np.mean(np.abs(e.reshape(P.nd, N) - ex))
+    for limiter, lo, hi in [(LIM_FIRST_ORDER, 0.8, 1.2), (LIM_MINMOD, 1.4, 2.3), (LIM_VANALBADA, 1.7, 2.3)]:
+        e1, e2 = err(64, limiter), err(128, limiter)
+        order = math.log2(e1 / e2)
+        assert lo <= order <= hi, (limiter, order)
+
+
+# ---------------------------------------------------------------------------------------
+# P7  specular wall (Sec. 2.2 (ii)) == the mirror image of the domain across the wall
+# ---------------------------------------------------------------------------------------
+def test_p7_specular_equals_mirrored_double_domain():
+    nx, ny = 6, 5
+    Tw = [0.0, 0.3, 0.2, 0.0, 0, 0]
+    base = small_cfg(2, (nx, ny, 1), [SPE, ISO, ISO, DIF, PER, PER], Tw=Tw, nb=2)
+    P = oracle_problem(base)
+    dbl = dict(base)
+    dbl["n"] = (2 * nx, ny, 1)
+    dbl["bc"] = [ISO, ISO, ISO, DIF, PER, PER]
+    dbl["Tw"] = [0.3, 0.3, 0.2, 0.0, 0, 0]
+    P2 = oracle_problem(dbl)
+    e = inputs.random_state(P.shape, 21)
+    Q = (np.random.default_rng(2).random((1, ny, nx)) * 1e17).astype(np.float32)
+    mx = P.mirror[0]
+    e2 = np.concatenate([e[:, mx][..., ::-1], e], axis=-1)
+    Q2 = np.concatenate([Q[..., ::-1], Q], axis=-1)
+    one = P.step(e, Q)
+    one2 = P2.step(e2, Q2)
+    assert np.array_equal(one2[..., nx:], one)            # one step: bitwise
+    many = P.run(e, 15, Q)
+    many2 = P2.run(e2, 15, Q2)
+    assert rel_linf(many2[..., nx:], many) <= 1e-13        # later steps: sums over mirrored order
+
+
+# ---------------------------------------------------------------------------------------
+# P8  translation invariance with periodic walls (Eq. periodic)
+# ---------------------------------------------------------------------------------------
+def test_p8_periodic_translation():
+    cfg = small_cfg(2, (8, 6, 1), [PER] * 6, nb=2)
+    P = oracle_problem(cfg)
+    e = inputs.random_state(P.shape, 31)
+    Q = (np.random.default_rng(4).random((1, 6, 8)) * 1e17).astype(np.float32)
+    a = P.run(e, 12, Q)
+    b = P.run(np.roll(e, (2, 3), axis=(3, 4)), 12, np.roll(Q, (2, 3), axis=(1, 2)))
+    assert np.array_equal(np.roll(b, (-2, -3), axis=(3, 4)), a)
+
+
+# ---------------------------------------------------------------------------------------
+# P9  uniform source from equilibrium with adiabatic walls: T = T_L = sum_n a_n dt Q / sum C
+#     (heat split in proportion to C, uniform in angle; Sec. 6.2)
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("bc", [[SPE] * 6, [DIF] * 6, [PER] * 6])
+def test_p9_uniform_source(bc):
+    cfg = small_cfg(3, (4, 5, 3), bc, nb=3)
+    P = oracle_problem(cfg)
+    Qv = 3e17
+    Q = np.full((P.nz, P.ny, P.nx), Qv, dtype=np.float32)
+    amps = np.linspace(0.2, 1.0, 25)
+    e = P.run(P.equilibrium(0.0), 25, Q, amps)
+    T, TL, _ = P.moments(e)
+    expect = float(np.sum(amps)) * P.dt * float(np.float32(Qv)) / float(np.sum(P.C))
+    assert np.max(np.abs(T - expect)) <= 1e-13 * expect
+    assert np.max(np.abs(TL - expect)) <= 1e-13 * expect
+
+
+# ---------------------------------------------------------------------------------------
+# P11 mirror symmetry: a setup symmetric under x -> -x gives a symmetric solution
+# ---------------------------------------------------------------------------------------
+def test_p11_mirror_symmetry():
+    nx, ny = 8, 6
+    cfg = small_cfg(2, (nx, ny, 1), [DIF, DIF, ISO, SPE, PER, PER], Tw=[0, 0, 0.4, 0, 0, 0], nb=2)
+    P = oracle_problem(cfg)
+    Q = inputs.gaussian_spot((nx, ny, 1), cfg["h"], (0.5 * nx * cfg["h"][0], 0.3 * ny * cfg["h"][1]), 4e-9, 1e18)
+    e = P.run(P.equilibrium(0.0), 30, Q)
+    mirrored = e[:, P.mirror[0]][..., ::-1]
+    assert rel_linf(mirrored, e) <= 1e-13
+
+
+def test_source_and_band_generators_are_seeded():
+    a = inputs.bands(1002, 40)
+    b = inputs.bands(1002, 40)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    C, v, tau = a
+    assert abs(C.sum() - 1.66e6) < 1e-6 * 1.66e6
+    assert v.min() >= 1e3 and v.max() <= 8e3 and tau.min() >= 1e-12 and tau.max() <= 1e-8
+
+
+# ---------------------------------------------------------------------------------------
+# Isothermal wall heat flow (Eq. thermal): incoming directions carry the wall emission
+# C_k T_w / W, outgoing directions leave with the wall cell's own value (first-order wall
+# face).  The heat flow is formed here from the state alone and must equal -dE/dt.
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("limiter", [LIM_MINMOD, LIM_VANALBADA])
+@pytest.mark.parametrize("dim,n", [(1, (9, 1, 1)), (2, (7, 5, 1))])
+def test_isothermal_wall_heat_flow(dim, n, limiter):
+    Tw = 0.3
+    bc = [ISO, SPE, SPE, SPE, SPE, SPE]
+    cfg = small_cfg(dim, n, bc, Tw=[Tw, 0, 0, 0, 0, 0])
+    P = oracle_problem(cfg, limiter)
+    e = inputs.random_state(P.shape, 41) + 2.0
+    E0, _ = P.energy(e)
+    E1, _ = P.energy(P.step(e))
+    S = P.cell_volume / P.dx
+    F = 0.0                                   # outward flow through the -x wall
+    for k in range(P.nb):
+        for d in range(P.nd):
+            sn = -P.s[d, 0]
+            if sn > 0:
+                F += S * P.w[d] * P.v[k] * sn * e[k, d, :, :, 0].sum()
+            elif sn < 0:
+                F += S * P.w[d] * P.v[k] * sn * (P.C[k] * Tw / P.W) * (P.ny * P.nz)
+    assert abs((E1 - E0) + P.dt * F) <= 1e-12 * max(abs(E0), P.dt * abs(F))
+
+
+# ---------------------------------------------------------------------------------------
+# Discrete maximum principle: free streaming of a square wave at CFL 0.4 creates no new
+# extrema with the limited (total-variation-diminishing) face values.
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("limiter", [LIM_FIRST_ORDER, LIM_MINMOD, LIM_VANALBADA])
+def test_limited_streaming_has_no_new_extrema(limiter):
+    N = 40
+    cfg = small_cfg(1, (N, 1, 1), [PER] * 6, nb=1, quad=("gl1d", 4), h=1e-9, tau=1e3, v=1e3, beta=0.4)
+    P = oracle_problem(cfg, limiter)
+    x = np.arange(N)
+    e0 = P.equilibrium(((x >= 10) & (x < 22)).astype(float)[None, None, :])
+    lo, hi = e0.min(), e0.max()
+    e = e0
+    for _ in range(12):
+        e = P.run(e, 10)
+        assert e.min() >= lo - 1e-12 * hi and e.max() <= hi * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("limiter", [LIM_MINMOD, LIM_VANALBADA])
+@pytest.mark.parametrize("dim,n,quad", [(2, (20, 20, 1), ("octant", 4, 4)), (3, (12, 12, 12), ("octant", 4, 3))])
+def test_multid_time_step_keeps_maximum_principle(dim, n, quad, limiter):
+    """The time step of the multi-dimensional workloads (beta = 0.5 over sqrt(dim) times the
+    largest speed) keeps the limited unsplit update free of new extrema."""
+    cfg = small_cfg(dim, n, [PER] * 6, nb=2, quad=quad, h=1e-9, tau=1e3)
+    P = oracle_problem(cfg, limiter)
+    z, y, x = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    f = (x >= 3) & (x < 10) & (y >= 4) & (y < 11)
+    if dim == 3:
+        f &= (z >= 2) & (z < 9)
+    e = P.equilibrium(f.astype(float))
+    lo, hi = e.min(), e.max()
+    for _ in range(6):
+        e = P.run(e, 4)
+        assert e.min() >= lo - 1e-12 * hi and e.max() <= hi * (1 + 1e-12)
