@@ -1,0 +1,376 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 explicit DOM transient step of the non-gray phonon BTE.
+
+One "step" is one time step of Eq. (disretized_transientBTE) over the whole workload: the
+fused forward kernel over every (band, direction, cell) plus the T_L finalize pass.  Default
+workload: the 2-D hot spot (256x256 cells, 40 bands, 128 directions, FP32 state), the
+configuration the updates/s figure is quoted on.  Inputs are resident in HBM before the timed
+region; the state (1.34 GB) is larger than L2, so no L2 flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--storage f32|f16|bf16]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload on its own GPU
+(weak scaling, no data-path collective); the time is the max over ranks.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell·dir·band updates/s and % HBM roofline; adjoint/forward step time"
+UNIT = "cell·dir·band updates/s"
+FALLBACK_HBM_GBS = 6800.0
+STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
+KERNEL = {"auto": 0, "generic": 1, "tiled": 2}
+
+
+def workloads():
+    from paper_2306_14181_gb300 import inputs
+    return {
+        "hotspot_2d": inputs.hotspot_2d,
+        "laser_3d": inputs.laser_3d,
+        "film_1d": inputs.film_1d,
+        "film_adjoint_2d": inputs.film_adjoint_2d,
+        "block_adjoint_3d": inputs.block_adjoint_3d,
+    }
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--workload", default="hotspot_2d")
+    p.add_argument("--storage", default="f32", choices=sorted(STORAGE))
+    p.add_argument("--kernel", default="auto", choices=sorted(KERNEL))
+    p.add_argument("--limiter", type=int, default=2)
+    p.add_argument("--e2e-steps", type=int, default=20)
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    a = p.parse_args()
+    if a.warmup < 3:
+        p.error("--warmup must be >= 3")
+    return a
+
+
+# ------------------------------------------------------------------------------------------
+# distributed plumbing: one process per GPU, barrier + max over ranks
+# ------------------------------------------------------------------------------------------
+class Dist:
+    def __init__(self, backend):
+        import torch
+        import torch.distributed as dist
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.dist = dist if self.world > 1 else None
+        if self.dist is not None and not dist.is_initialized():
+            dist.init_process_group(backend=backend)
+        self.torch = torch
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max(self, x):
+        if self.dist is None:
+            return float(x)
+        dev = "cuda" if self.torch.cuda.is_available() and self.dist.get_backend() == "nccl" else "cpu"
+        t = self.torch.tensor([float(x)], dtype=self.torch.float64, device=dev)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------
+REASONS = ["clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+           "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+
+class ClockSampler:
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," + ",".join(REASONS)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        load = [x for x in sm if x > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------
+# roofline helpers
+# ------------------------------------------------------------------------------------------
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2306_14181_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".h")):
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def measured_traffic(workload, storage, kernel_name):
+    """DRAM bytes per launch of the forward kernel from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = kernel_source_hash()
+    for line in open(path):
+        m = re.match(r"^(\S+)\s+(\S+)\s+(\S+)\s+(\S+)\s+([0-9.eE+]+)\s*$", line.strip())
+        if m and m.group(1) == workload and m.group(2) == storage and m.group(3) == kernel_name and m.group(4) == src:
+            return float(m.group(5))
+    return None
+
+
+# ------------------------------------------------------------------------------------------
+# the oracle on the host cores (CPU baseline and the reference arm)
+# ------------------------------------------------------------------------------------------
+def oracle_for(cfg, ny_sample=None, limiter=2):
+    from oracle import Problem
+    from oracle import quadrature as oq
+    c = dict(cfg)
+    if ny_sample is not None and c["dim"] >= 2 and ny_sample < c["n"][c["dim"] - 1]:
+        n = list(c["n"])
+        n[c["dim"] - 1] = ny_sample
+        c["n"] = tuple(n)
+    s, w, mirror = oq.polar_1d(c["quad"][1]) if c["quad"][0] == "gl1d" else oq.octant_rule(c["quad"][1], c["quad"][2])
+    return c, Problem(c["dim"], c["n"], c["h"], c["C"], c["v"], c["tau"], s, w, mirror, c["bc"], c["Tw"], c["dt"],
+                      limiter)
+
+
+def cpu_sample_size(cfg):
+    """Cells along the slowest axis of the host sample: about 40 M updates per oracle step."""
+    if cfg["dim"] == 1:
+        return None
+    per_row = cfg["nb"] * (8 * cfg["quad"][1] * cfg["quad"][2]) * cfg["n"][0] * (cfg["n"][1] if cfg["dim"] == 3 else 1)
+    return max(2, min(cfg["n"][cfg["dim"] - 1], int(40e6 // per_row)))
+
+
+def time_oracle(cfg, seconds, limiter=2):
+    """Oracle steps on a slab of the workload until `seconds` of host time is used."""
+    from paper_2306_14181_gb300 import inputs
+    c, P = oracle_for(cfg, cpu_sample_size(cfg), limiter)
+    Q = None
+    if cfg.get("source") is not None:
+        c2 = dict(c)
+        Q = inputs.source_field(c2)
+    e = P.equilibrium(0.0)
+    nel = P.nb * P.nd * P.ncell
+    t0 = time.perf_counter()
+    e = P.step(e, Q, 1.0)
+    t1 = time.perf_counter()
+    n = 1
+    while t1 - t0 < seconds:
+        e = P.step(e, Q, 1.0)
+        n += 1
+        t1 = time.perf_counter()
+    return nel * n / (t1 - t0), n, c["n"], t1 - t0
+
+
+def omp_threads():
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v else (os.cpu_count() or 1)
+
+
+# ------------------------------------------------------------------------------------------
+def run_reference(args):
+    d = Dist("gloo")
+    if d.rank != 0:
+        d.barrier()
+        d.close()
+        return
+    cfg = workloads()[args.workload]()
+    from oracle import build_oracle
+    build_oracle()
+    c, P = oracle_for(cfg, cpu_sample_size(cfg), args.limiter)
+    from paper_2306_14181_gb300 import inputs
+    Q = inputs.source_field(c) if cfg.get("source") is not None else None
+    e = P.equilibrium(0.0)
+    for _ in range(args.warmup):
+        e = P.step(e, Q, 1.0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e = P.step(e, Q, 1.0)
+    t = time.perf_counter() - t0
+    nel = P.nb * P.nd * P.ncell
+    value = nel * args.steps / t
+    sample = "%d oracle steps on a %s slab of %s (all bands and directions)" % (args.steps, "x".join(map(str, c["n"])),
+                                                                              cfg["name"])
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg["name"], "sample_grid": list(c["n"]), "bands": c["nb"], "dirs": P.nd,
+                       "limiter": args.limiter},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": omp_threads(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    d.barrier()
+    d.close()
+
+
+def run_gb300(args):
+    import numpy as np
+    import torch
+
+    d = Dist("nccl")
+    torch.cuda.set_device(d.local)
+    from paper_2306_14181_gb300 import bte, build, inputs
+    build.build()
+    cfg = workloads()[args.workload]()
+    storage = STORAGE[args.storage]
+    Q = inputs.source_field(cfg)
+    total = args.warmup + args.steps + args.e2e_steps + 8
+    amps = inputs.source_amplitudes(cfg, total)
+    stream = torch.cuda.current_stream()
+    T_scale = 1.0
+    ctx = bte.bte_from_workload(cfg, storage=storage, limiter=args.limiter, kernel=KERNEL[args.kernel],
+                                stream=stream.cuda_stream, T_scale=T_scale)
+    info = ctx.info
+    kernel_name = "tiled" if info.kernel == bte.BTE_KERNEL_TILED else "generic"
+    if Q is not None:
+        bte.bte_set_source(ctx, torch.from_numpy(Q.reshape(-1)).cuda(), amps)
+    bte.bte_step(ctx, args.warmup)
+    torch.cuda.synchronize()
+    d.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    bte.bte_profile(ctx, True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    bte.bte_step(ctx, args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    d.barrier()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    t_ms = ev0.elapsed_time(ev1)
+    fwd_ms, nfwd, fin_ms, nfin = bte.bte_profile_read(ctx)
+    bte.bte_profile(ctx, False)
+    t_max = d.max(t_ms)
+    value = info.nelem * args.steps * d.world / (t_max / 1e3)
+
+    # roofline of the forward kernel: algorithmic bytes = read e + write e per update
+    peak, peak_kind = hbm_peak()
+    bytes_per_launch = info.nelem * 2 * info.elem_bytes
+    fwd_avg_s = fwd_ms / max(nfwd, 1) / 1e3
+    achieved = bytes_per_launch / fwd_avg_s / 1e9
+    traffic = measured_traffic(args.workload, args.storage, kernel_name)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "forward step (%s)" % kernel_name, "peak_source": peak_kind,
+                "bytes_per_launch": bytes_per_launch, "kernel_ms": fwd_avg_s * 1e3,
+                "finalize_ms": fin_ms / max(nfin, 1)}
+
+    # end to end through the C ABI with host buffers: upload the step's source (pinned), step,
+    # read the step's lattice temperature back
+    e2e = None
+    if not args.no_e2e:
+        Qh = torch.from_numpy(np.ascontiguousarray(Q.reshape(-1))).pin_memory() if Q is not None else None
+        TLh = np.empty(info.ncell)
+        torch.cuda.synchronize()
+        d.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            if Qh is not None:
+                bte.bte_set_source(ctx, Qh.numpy(), amps)
+            bte.bte_step(ctx, 1)
+            bte.bte_lattice_temperature(ctx, TLh)
+        torch.cuda.synchronize()
+        te = d.max(time.perf_counter() - t0)
+        e2e = {"value": info.nelem * args.e2e_steps * d.world / te, "unit": UNIT,
+               "h2d_bytes_per_step": int(info.ncell * 4 if Qh is not None else 0),
+               "d2h_bytes_per_step": int(info.ncell * 4)}
+    cpu = None
+    if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:
+        v, n, grid, secs = time_oracle(cfg, args.cpu_seconds, args.limiter)
+        cpu = {"value": v, "unit": UNIT, "cores": omp_threads(), "kind": "oracle",
+               "sample": "%d FP64 oracle steps on a %s slab of the workload (all bands and directions), %.1f s"
+                         % (n, "x".join(map(str, grid)), secs)}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": d.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": cfg["name"], "grid": list(cfg["n"]), "bands": info.nbands, "dirs": info.ndirs,
+                       "storage": args.storage, "limiter": args.limiter, "kernel": kernel_name,
+                       "updates_per_step": info.nelem, "l2": "state %.2f GB > L2, no flush" % (info.state_bytes / 1e9),
+                       "parallelism": "replicas" if d.world > 1 else "single"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(nfwd + nfin),
+            "clocks": ck}
+    if d.rank == 0:
+        print(json.dumps(line), flush=True)
+    d.barrier()
+    d.close()
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gb300(a)

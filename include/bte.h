@@ -1,0 +1,239 @@
+/*
+ * bte.h - C ABI of the GB300 explicit discrete-ordinates (DOM) transient step of the
+ * non-gray phonon Boltzmann transport equation (BTE) in the energy form of
+ * arXiv 2306.14181 (GiftBTE), Sec. 4.
+ *
+ * The library (libbte_gb300.so) advances, on one GPU, the deviational energy density
+ * e[k][d][z][y][x] (band k, direction d, Cartesian cell) with the forward-Euler finite-volume
+ * update of Eq. (disretized_transientBTE):
+ *
+ *   e^{n+1} = e^n - sum_a (dt/dx_a) v_k s_{d,a} (e_{i+1/2} - e_{i-1/2})
+ *                 + dt [ (C_k T_L^n / W - e^n) / tau_k + a(t_n) Q_i C_k / (sum_k C_k W) ]
+ *
+ * with the face value e_ij = e_m + grad(e_m).l taken at the upwind cell m (Sec. 4.1) through
+ * a slope limiter, the lattice temperature T_L of Eq. (BTE_get_e0) formed from the new state
+ * in the same pass, and the four wall types of Sec. 2.2 (thermalizing, diffusely and
+ * specularly reflecting, periodic).  W = sum_d w_d is the discrete total solid angle (4 pi).
+ *
+ * Conventions for every call:
+ *   - Temperatures are offsets from T_ref (K): T_wall, dT0, and the dT / dTL outputs.
+ *   - The caller owns every pointer it passes; input arrays are copied or consumed before
+ *     the call returns, output arrays are written before it returns.
+ *   - Host arrays are plain C arrays; "device" pointers are CUDA device addresses on the
+ *     device that was current when bte_create ran.
+ *   - Work is issued on options.stream (NULL: the CUDA default stream) in call order.  Calls
+ *     that return data to host memory synchronise that stream; the others do not block.
+ *   - Nothing throws or aborts across the ABI.  Every call returns a bte_status; on failure
+ *     bte_last_error() gives a one-line reason and the context is left unchanged where the
+ *     failure was detected before any work was issued.
+ *   - A context is not thread safe: use one context per host thread (or serialise calls).
+ */
+#ifndef BTE_GB300_H
+#define BTE_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BTE_OK = 0,
+    BTE_EINVAL = 1,        /* an argument is out of range or inconsistent */
+    BTE_ENOMEM = 2,        /* device or host allocation failed */
+    BTE_ECUDA = 3,         /* a CUDA runtime call failed (message in bte_last_error) */
+    BTE_ESTATE = 4,        /* call not valid in the context's current state */
+    BTE_ENONFINITE = 5,    /* a non-finite value was found in the state or an output */
+    BTE_ETIMEOUT = 6,      /* reserved: a bounded device wait gave up */
+    BTE_EUNSUPPORTED = 7   /* valid request this build does not implement */
+} bte_status;
+
+/* Directional discretisation (Sec. 3.2, Eq. directiondis). */
+enum {
+    BTE_QUAD_GL1D_POLAR = 0, /* 1-D geometries: Gauss-Legendre in mu = cos(theta) on [-1, 1],
+                                s = (mu, 0, 0), w = 2 pi w_mu; ntheta = number of nodes */
+    BTE_QUAD_OCTANT = 1,     /* ntheta Gauss-Legendre nodes in mu on [0, 1] times nphi nodes in
+                                phi on [0, pi/2], w = w_mu w_phi, mirrored into 8 octants:
+                                ndirs = 8 ntheta nphi.  Order: octant-major, then mu, then phi;
+                                octant bit a set = component a negative */
+    BTE_QUAD_EXPLICIT = 2    /* caller-given s[3*ndirs] and w[ndirs] */
+};
+
+/* Wall types (Sec. 2.2).  Walls are indexed -x, +x, -y, +y, -z, +z. */
+enum {
+    BTE_BC_ISOTHERMAL = 0, /* thermalizing wall, Eq. (thermal): emits C_k T_wall / W */
+    BTE_BC_DIFFUSE = 1,    /* diffusely reflecting wall, Eq. (diff_bound) */
+    BTE_BC_SPECULAR = 2,   /* specularly reflecting wall, Sec. 2.2 (ii) */
+    BTE_BC_PERIODIC = 3    /* periodic pair, Eq. (periodic); both walls of the axis */
+};
+
+/* Storage of e in device memory.  All arithmetic is FP32 in every mode. */
+enum {
+    BTE_STORE_F32 = 0,
+    BTE_STORE_F16 = 1,  /* e = s_k * h, h binary16, s_k = C_k T_scale / W */
+    BTE_STORE_BF16 = 2  /* e = s_k * h, h bfloat16 */
+};
+
+/* Slope limiter L(a, b) of the one-sided differences at the upwind cell; e_face = e_m + L/2.
+ * The paper's least-squares gradient on a uniform grid is the unlimited central slope, which
+ * forward Euler makes unstable for ballistic bands; a limiter keeps the step bounded. */
+enum {
+    BTE_LIM_FIRST_ORDER = 0, /* L = 0 */
+    BTE_LIM_MINMOD = 1,      /* the smaller of a, b in magnitude if ab > 0, else 0 */
+    BTE_LIM_VANALBADA = 2    /* ab(a+b)/(a^2+b^2) if ab > 0, else 0 (default) */
+};
+
+enum { BTE_ROUND_NEAREST = 0, BTE_ROUND_STOCHASTIC = 1 };
+
+/* Which forward kernel to run. */
+enum {
+    BTE_KERNEL_AUTO = 0,    /* the tiled kernel where its shape limits allow, else generic */
+    BTE_KERNEL_GENERIC = 1, /* one thread per (cell, band); any grid shape */
+    BTE_KERNEL_TILED = 2    /* shared-memory tiled kernel; BTE_EUNSUPPORTED if the grid does not fit */
+};
+
+typedef struct bte_ctx bte_ctx;
+
+/* Cartesian finite-volume grid (Sec. 4.1).  dim 1: nx cells (ny = nz = 1); dim 2: nx*ny
+ * (nz = 1); dim 3: nx*ny*nz.  Cell sizes in metres; every active extent must be >= 2.
+ * Axes beyond dim have unit length in volumes and face areas. */
+typedef struct {
+    int dim;
+    int nx, ny, nz;
+    double dx, dy, dz;
+    double Tref; /* reference temperature (K); reported back, not used in the arithmetic */
+} bte_grid;
+
+/* Phonon bands (Sec. 3.1, Eq. banddis): heat capacity C_k (J/m^3/K), group speed |v_k| (m/s),
+ * relaxation time tau_k (s), all > 0.  Host arrays of length nbands, copied. */
+typedef struct {
+    int nbands;
+    const double *C;
+    const double *vabs;
+    const double *tau;
+} bte_bands;
+
+/* Directions (Sec. 3.2).  For BTE_QUAD_EXPLICIT, s (3*ndirs, unit vectors or, in 1-D, their
+ * x projections) and w (ndirs, > 0) are host arrays, copied; ntheta/nphi are ignored.  Walls
+ * of type specular need, for every direction, the one with the normal component negated. */
+typedef struct {
+    int kind;
+    int ntheta;
+    int nphi;
+    int ndirs;
+    const double *s;
+    const double *w;
+} bte_quadrature;
+
+/* Wall types and thermalizing-wall temperatures (offsets from T_ref, K). */
+typedef struct {
+    int type[6];
+    double T_wall[6];
+} bte_boundaries;
+
+typedef struct {
+    double dt;        /* time step (s), > 0 (Sec. 4.1: dt = beta dx_min / v) */
+    int storage;      /* BTE_STORE_* */
+    int limiter;      /* BTE_LIM_* */
+    double T_scale;   /* K; 16-bit storage scale s_k = C_k T_scale / W.  <= 0: 1 K */
+    int rounding;     /* BTE_ROUND_*; only meaningful for 16-bit storage */
+    void *stream;     /* cudaStream_t; NULL = CUDA default stream */
+    uint64_t seed;    /* key of the stochastic-rounding hash */
+    int kernel;       /* BTE_KERNEL_* */
+} bte_options;
+
+/* Sizes and settings of a context. */
+typedef struct {
+    int dim, nx, ny, nz;
+    int nbands, ndirs;
+    long long ncell;        /* nx*ny*nz */
+    long long nelem;        /* nbands * ndirs * ncell, the updates per step */
+    size_t state_bytes;     /* nelem * element size; the size bte_get_state/bte_set_state take */
+    int elem_bytes;         /* 4 (FP32) or 2 (16-bit) */
+    int storage, limiter, kernel; /* kernel actually used: BTE_KERNEL_GENERIC or _TILED */
+    double dt;
+    double W;               /* sum_d w_d */
+    long long step;         /* steps taken since bte_init_temperature / bte_set_state */
+    size_t device_bytes;    /* device memory held by the context */
+} bte_info;
+
+/* Create a context: validate, build the quadrature, band tables and mirror maps on the host,
+ * allocate the device state and set it to equilibrium at dT = 0 (Algorithm 2, "Initial e").
+ * On success *out owns device memory until bte_destroy.  Errors: BTE_EINVAL (bad sizes,
+ * non-positive band data or dt, a periodic wall without its partner, a specular wall on a
+ * quadrature without mirror partners), BTE_EUNSUPPORTED (kernel = TILED on a grid it cannot
+ * tile), BTE_ENOMEM, BTE_ECUDA.  The reason of a failed create is returned by
+ * bte_last_error(NULL) on the same thread. */
+bte_status bte_create(const bte_grid *grid, const bte_bands *bands, const bte_quadrature *quad,
+                      const bte_boundaries *walls, const bte_options *opts, bte_ctx **out);
+
+/* Release every resource of the context (NULL is ignored).  Synchronises its stream first. */
+void bte_destroy(bte_ctx *ctx);
+
+/* One-line reason of the last failure on ctx (NULL: of the last failed bte_create on this
+ * thread).  The string stays valid until the next call on the same context. */
+const char *bte_last_error(const bte_ctx *ctx);
+
+/* Equilibrium start (Algorithm 2; Sec. 4.2): e_{k,d,i} = C_k dT0_i / W for every band and
+ * direction, T_L = dT0.  dT0: host array of ncell doubles (cell order x fastest), or NULL for
+ * dT0 = 0.  Resets the step counter to 0. */
+bte_status bte_init_temperature(bte_ctx *ctx, const double *dT0);
+
+/* Volumetric heat source (Eq. BTE_origin, Q-dot): Q_i in W/m^3 per cell (ncell floats, host
+ * or device per on_device), split over bands in proportion to C_k and uniformly over
+ * directions.  amp[n] (host, n_amp doubles) scales the source at step n (t_n = n dt); steps
+ * n >= n_amp get amplitude 0.  amp = NULL means amplitude 1 at every step.  Q = NULL removes
+ * the source. */
+bte_status bte_set_source(bte_ctx *ctx, const float *Q, int on_device, const double *amp, int n_amp);
+
+/* Advance n >= 0 steps of Eq. (disretized_transientBTE).  Each step is one fused pass of the
+ * forward kernel over all (band, direction, cell) (flux, relaxation, source, walls, moment
+ * partials), then one short pass that finishes T_L and the diffuse-wall values.  Stream
+ * ordered, non-blocking. */
+bte_status bte_step(bte_ctx *ctx, int n);
+
+/* The lattice temperature the last step formed (FP32 on the device), as doubles into dTL
+ * (host, ncell).  Synchronises. */
+bte_status bte_lattice_temperature(bte_ctx *ctx, double *dTL);
+
+/* FP64 moments of the current state (Eq. getTQ and Eq. BTE_get_e0): dT (ncell), dTL (ncell)
+ * and q (3*ncell, component-major: qx for all cells, then qy, then qz; W/m^2).  Host arrays;
+ * any may be NULL.  Synchronises.  BTE_ENONFINITE if the state holds a non-finite value. */
+bte_status bte_moments(bte_ctx *ctx, double *dT, double *dTL, double *q);
+
+/* FP64 global energy-balance reductions of the current state: E_total = V sum_i sum_k sum_d
+ * w_d e (J per unit length/area for dim < 3) and the outward heat flow through each wall,
+ * wall_flux[6] = S_wall sum sum sum w_d v_k (s_d.n) e_face with e_face the wall-face value
+ * the step uses.  One step then obeys E^{n+1} - E^n = dt (V a_n sum_i Q_i - sum wall_flux^n).
+ * Host outputs; synchronises.  BTE_ENONFINITE on a non-finite state. */
+bte_status bte_energy(bte_ctx *ctx, double *E_total, double wall_flux[6]);
+
+/* Copy the stored state out / in, in its storage format (FP32, or the 16-bit code h with
+ * e = s_k h), layout e[k][d][z][y][x].  bytes must equal bte_info.state_bytes.  bte_set_state
+ * recomputes T_L and the diffuse-wall values from the new state and resets the step counter
+ * to 0 unless keep_step is non-zero. */
+bte_status bte_get_state(bte_ctx *ctx, void *dst, size_t bytes, int on_device);
+bte_status bte_set_state(bte_ctx *ctx, const void *src, size_t bytes, int on_device, int keep_step);
+
+/* Sizes and settings; the quadrature the context built (s: 3*ndirs, w: ndirs, host). */
+bte_status bte_get_info(const bte_ctx *ctx, bte_info *info);
+bte_status bte_get_quadrature(const bte_ctx *ctx, double *s, double *w);
+
+/* Wait for all work issued on the context's stream. */
+bte_status bte_synchronize(bte_ctx *ctx);
+
+/* Kernel tracing with CUDA events on the context's stream.  bte_profile(ctx, 1) clears the
+ * counters and starts recording an event pair around every forward-step launch and every
+ * finalize launch of bte_step; bte_profile(ctx, 0) stops.  bte_profile_read synchronises and
+ * returns the summed device time (ms) and the launch counts since the last start.  Any output
+ * pointer may be NULL. */
+bte_status bte_profile(bte_ctx *ctx, int enable);
+bte_status bte_profile_read(bte_ctx *ctx, double *fwd_ms, long long *fwd_launches, double *fin_ms,
+                            long long *fin_launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BTE_GB300_H */

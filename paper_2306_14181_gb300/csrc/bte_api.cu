@@ -1,0 +1,776 @@
+// Host side of the C ABI declared in include/bte.h: validation, the directional and band
+// tables (arXiv 2306.14181, Sec. 3.1-3.2), device buffers, and the step schedule of
+// Algorithm 2 (transient solver).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/bte.h"
+#include "bte_internal.h"
+#include "bte_tiled.h"
+
+using namespace bte;
+
+static thread_local std::string g_create_error;
+
+struct bte_ctx {
+    // problem
+    int dim = 0, n[3] = {1, 1, 1};
+    double h[3] = {1, 1, 1};
+    double Tref = 0;
+    int nb = 0, nd = 0;
+    std::vector<double> C, v, tau, s, w;
+    std::vector<int> mirror;  // [3][nd], -1 = none
+    int bc[6] = {0, 0, 0, 0, 0, 0};
+    double Tw[6] = {0, 0, 0, 0, 0, 0};
+    double dt = 0, T_scale = 1;
+    int storage = 0, limiter = 0, rounding = 0, kernel = 0;
+    uint64_t seed = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    double W = 0, sumC = 0, D = 0;
+    long long ncell = 0, nelem = 0;
+    size_t elem_bytes = 4, state_bytes = 0;
+    // device state
+    void *e[2] = {nullptr, nullptr};
+    int cur = 0;
+    float *TL = nullptr, *Q = nullptr, *P = nullptr;
+    int G = 0;
+    float *ediff[2] = {nullptr, nullptr};
+    int ecur = 0;
+    int wc_max = 1;
+    float inv_den[6] = {0, 0, 0, 0, 0, 0};
+    // device tables
+    float *nu = nullptr, *wmom = nullptr, *wdiff = nullptr, *iso = nullptr;
+    int *mirror_d = nullptr;
+    BandConst *band = nullptr;
+    double *d_w = nullptr, *d_s = nullptr, *d_v = nullptr, *d_invtau = nullptr;
+    // diagnostics scratch (allocated on first use)
+    double *dg = nullptr;
+    int *dflag = nullptr;
+    // tiled-kernel plan
+    TiledPlan plan;
+    bool tiled = false;
+    // source
+    bool has_source = false, has_amp = false;
+    std::vector<double> amp;
+    long long step = 0;
+    size_t device_bytes = 0;
+    std::string err;
+    // tracing: event triples (before forward, after forward, after finalize) per step
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;
+    size_t ev_used = 0;
+};
+
+// ------------------------------------------------------------------------------------------
+// helpers
+// ------------------------------------------------------------------------------------------
+static bte_status fail(bte_ctx *c, bte_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    else g_create_error = buf;
+    return st;
+}
+
+#define CU(ctx, call)                                                                                  \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess)                                                                         \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? BTE_ENOMEM : BTE_ECUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                            \
+    } while (0)
+
+template <class T>
+static bte_status dalloc(bte_ctx *c, T **p, size_t count) {
+    const size_t bytes = count * sizeof(T);
+    cudaError_t e = cudaMalloc((void **)p, bytes ? bytes : sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(c, BTE_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    }
+    c->device_bytes += bytes;
+    return BTE_OK;
+}
+
+template <class T>
+static bte_status upload(bte_ctx *c, T *dst, const T *src, size_t count) {
+    CU(c, cudaMemcpy(dst, src, count * sizeof(T), cudaMemcpyHostToDevice));
+    return BTE_OK;
+}
+
+#define TRY(x)                       \
+    do {                             \
+        bte_status st_ = (x);        \
+        if (st_ != BTE_OK) return st_; \
+    } while (0)
+
+// Gauss-Legendre rule on [lo, hi] by Newton iteration on the Legendre polynomial P_n,
+// evaluated with the three-term recurrence (j+1) P_{j+1} = (2j+1) x P_j - j P_{j-1}; the
+// weights are 2 / ((1 - x^2) P_n'(x)^2).  Roots are found in pairs +-x so the rule is
+// exactly symmetric.
+static void gauss_legendre(int n, double lo, double hi, std::vector<double> &x, std::vector<double> &wt) {
+    x.assign(n, 0.0);
+    wt.assign(n, 0.0);
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double z = std::cos(pi * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int j = 1; j < n; ++j) {
+                const double p2 = ((2.0 * j + 1.0) * z * p1 - j * p0) / (j + 1.0);
+                p0 = p1;
+                p1 = p2;
+            }
+            if (n == 1) { p0 = 1.0; p1 = z; }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) {
+                // derivative at the converged root
+                double q0 = 1.0, q1 = z;
+                for (int j = 1; j < n; ++j) {
+                    const double q2 = ((2.0 * j + 1.0) * z * q1 - j * q0) / (j + 1.0);
+                    q0 = q1;
+                    q1 = q2;
+                }
+                if (n == 1) { q0 = 1.0; q1 = z; }
+                dp = n * (z * q1 - q0) / (z * z - 1.0);
+                break;
+            }
+        }
+        if (2 * i + 1 == n) z = 0.0;
+        const double wi = 2.0 / ((1.0 - z * z) * dp * dp);
+        x[i] = -z;
+        x[n - 1 - i] = z;
+        wt[i] = wi;
+        wt[n - 1 - i] = wi;
+    }
+    const double half = 0.5 * (hi - lo);
+    for (int i = 0; i < n; ++i) {
+        x[i] = lo + half * (x[i] + 1.0);
+        wt[i] *= half;
+    }
+}
+
+static bte_status build_quadrature(const bte_quadrature *q, int dim, bte_ctx *c) {
+    const double pi = 3.14159265358979323846;
+    c->s.clear();
+    c->w.clear();
+    if (q->kind == BTE_QUAD_GL1D_POLAR) {
+        if (q->ntheta < 2 || q->ntheta > 1024) return fail(nullptr, BTE_EINVAL, "GL1D_POLAR needs 2..1024 nodes");
+        std::vector<double> mu, wm;
+        gauss_legendre(q->ntheta, -1.0, 1.0, mu, wm);
+        for (int i = 0; i < q->ntheta; ++i) {
+            c->s.push_back(mu[i]);
+            c->s.push_back(0.0);
+            c->s.push_back(0.0);
+            c->w.push_back(2.0 * pi * wm[i]);
+        }
+    } else if (q->kind == BTE_QUAD_OCTANT) {
+        if (q->ntheta < 1 || q->nphi < 1 || q->ntheta > 64 || q->nphi > 64)
+            return fail(nullptr, BTE_EINVAL, "OCTANT needs 1..64 polar and azimuthal nodes");
+        std::vector<double> mu, wm, ph, wp;
+        gauss_legendre(q->ntheta, 0.0, 1.0, mu, wm);
+        gauss_legendre(q->nphi, 0.0, 0.5 * pi, ph, wp);
+        for (int o = 0; o < 8; ++o)
+            for (int j = 0; j < q->ntheta; ++j)
+                for (int l = 0; l < q->nphi; ++l) {
+                    const double st = std::sqrt(1.0 - mu[j] * mu[j]);
+                    const double sx = (o & 1) ? -1.0 : 1.0, sy = (o & 2) ? -1.0 : 1.0, sz = (o & 4) ? -1.0 : 1.0;
+                    c->s.push_back(sx * st * std::cos(ph[l]));
+                    c->s.push_back(sy * st * std::sin(ph[l]));
+                    c->s.push_back(sz * mu[j]);
+                    c->w.push_back(wm[j] * wp[l]);
+                }
+    } else if (q->kind == BTE_QUAD_EXPLICIT) {
+        if (q->ndirs < 1 || !q->s || !q->w) return fail(nullptr, BTE_EINVAL, "EXPLICIT quadrature needs s, w, ndirs");
+        for (int d = 0; d < q->ndirs; ++d) {
+            for (int a = 0; a < 3; ++a) {
+                if (!std::isfinite(q->s[3 * d + a])) return fail(nullptr, BTE_EINVAL, "non-finite direction");
+                c->s.push_back(q->s[3 * d + a]);
+            }
+            if (!(q->w[d] > 0.0) || !std::isfinite(q->w[d])) return fail(nullptr, BTE_EINVAL, "weights must be > 0");
+            c->w.push_back(q->w[d]);
+        }
+    } else {
+        return fail(nullptr, BTE_EINVAL, "unknown quadrature kind %d", q->kind);
+    }
+    c->nd = (int)c->w.size();
+    (void)dim;
+    // mirror partners: direction with component a negated (same weight)
+    c->mirror.assign(3 * c->nd, -1);
+    for (int a = 0; a < 3; ++a)
+        for (int d = 0; d < c->nd; ++d)
+            for (int m = 0; m < c->nd; ++m) {
+                bool ok = std::fabs(c->w[m] - c->w[d]) <= 1e-12 * c->w[d];
+                for (int b = 0; b < 3 && ok; ++b) {
+                    const double t = (b == a) ? -c->s[3 * d + b] : c->s[3 * d + b];
+                    ok = std::fabs(c->s[3 * m + b] - t) <= 1e-12;
+                }
+                if (ok) {
+                    c->mirror[a * c->nd + d] = m;
+                    break;
+                }
+            }
+    return BTE_OK;
+}
+
+static StepArgs make_args(const bte_ctx *c) {
+    StepArgs a;
+    memset(&a, 0, sizeof a);
+    a.dim = c->dim;
+    for (int i = 0; i < 3; ++i) a.n[i] = c->n[i];
+    a.stride[0] = 1;
+    a.stride[1] = c->n[0];
+    a.stride[2] = (long long)c->n[0] * c->n[1];
+    a.ncell = c->ncell;
+    a.nb = c->nb;
+    a.nd = c->nd;
+    for (int i = 0; i < 6; ++i) {
+        a.bc[i] = c->bc[i];
+        a.inv_den[i] = c->inv_den[i];
+    }
+    a.wc_max = c->wc_max;
+    a.amp = 0.f;
+    a.invD = (float)(1.0 / c->D);
+    a.nu = c->nu;
+    a.wmom = c->wmom;
+    a.wdiff = c->wdiff;
+    a.mirror = c->mirror_d;
+    a.band = c->band;
+    a.iso = c->iso;
+    a.Q = c->has_source ? c->Q : nullptr;
+    a.P = c->P;
+    return a;
+}
+
+static double amplitude_at(const bte_ctx *c, long long n) {
+    if (!c->has_amp) return 1.0;
+    return n < (long long)c->amp.size() ? c->amp[n] : 0.0;
+}
+
+// T_L and the diffuse-wall values of the current state (after a fill or an upload).
+static bte_status refresh_moments(bte_ctx *c) {
+    StepArgs a = make_args(c);
+    a.e_in = c->e[c->cur];
+    a.ediff_out = c->ediff[c->ecur ^ 1];
+    CU(c, launch_moment_only(a, c->storage, c->stream));
+    c->ecur ^= 1;
+    CU(c, launch_finalize(a, c->nb, c->TL, c->stream));
+    return BTE_OK;
+}
+
+static void free_all(bte_ctx *c) {
+    void *ptrs[] = {c->e[0], c->e[1], c->TL, c->Q, c->P, c->ediff[0], c->ediff[1], c->nu, c->wmom, c->wdiff,
+                    c->iso, c->mirror_d, c->band, c->d_w, c->d_s, c->d_v, c->d_invtau, c->dg, c->dflag};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    tiled_free(c->plan);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    c->ev.clear();
+}
+
+static bte_status prof_event(bte_ctx *c, cudaEvent_t *out) {
+    if (c->ev_used == c->ev.size()) {
+        cudaEvent_t e;
+        CU(c, cudaEventCreate(&e));
+        c->ev.push_back(e);
+    }
+    *out = c->ev[c->ev_used++];
+    CU(c, cudaEventRecord(*out, c->stream));
+    return BTE_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// ABI
+// ------------------------------------------------------------------------------------------
+extern "C" bte_status bte_create(const bte_grid *grid, const bte_bands *bands, const bte_quadrature *quad,
+                                 const bte_boundaries *walls, const bte_options *opts, bte_ctx **out) {
+    if (!out) return fail(nullptr, BTE_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!grid || !bands || !quad || !walls || !opts) return fail(nullptr, BTE_EINVAL, "NULL argument");
+    bte_ctx tmp;
+    bte_ctx *c = &tmp;
+    // grid
+    if (grid->dim < 1 || grid->dim > 3) return fail(nullptr, BTE_EINVAL, "dim must be 1, 2 or 3");
+    c->dim = grid->dim;
+    c->n[0] = grid->nx;
+    c->n[1] = grid->ny;
+    c->n[2] = grid->nz;
+    c->h[0] = grid->dx;
+    c->h[1] = grid->dy;
+    c->h[2] = grid->dz;
+    c->Tref = grid->Tref;
+    for (int a = 0; a < 3; ++a) {
+        if (a < c->dim) {
+            if (c->n[a] < 2) return fail(nullptr, BTE_EINVAL, "active extent %d is %d; must be >= 2", a, c->n[a]);
+            if (!(c->h[a] > 0.0) || !std::isfinite(c->h[a])) return fail(nullptr, BTE_EINVAL, "cell size must be > 0");
+        } else if (c->n[a] != 1) {
+            return fail(nullptr, BTE_EINVAL, "extent of inactive axis %d must be 1", a);
+        }
+    }
+    c->ncell = (long long)c->n[0] * c->n[1] * c->n[2];
+    // bands
+    if (bands->nbands < 1 || !bands->C || !bands->vabs || !bands->tau)
+        return fail(nullptr, BTE_EINVAL, "bands need nbands >= 1 and C, vabs, tau");
+    c->nb = bands->nbands;
+    for (int k = 0; k < c->nb; ++k) {
+        const double Ck = bands->C[k], vk = bands->vabs[k], tk = bands->tau[k];
+        if (!(Ck > 0) || !(vk > 0) || !(tk > 0) || !std::isfinite(Ck) || !std::isfinite(vk) || !std::isfinite(tk))
+            return fail(nullptr, BTE_EINVAL, "band %d: C, |v| and tau must be finite and > 0", k);
+        c->C.push_back(Ck);
+        c->v.push_back(vk);
+        c->tau.push_back(tk);
+    }
+    // quadrature
+    TRY(build_quadrature(quad, c->dim, c));
+    if ((long long)c->nb * c->nd > 65535) return fail(nullptr, BTE_EINVAL, "nbands * ndirs must be <= 65535");
+    // walls
+    for (int wl = 0; wl < 6; ++wl) {
+        const int t = walls->type[wl];
+        if (t < BTE_BC_ISOTHERMAL || t > BTE_BC_PERIODIC) return fail(nullptr, BTE_EINVAL, "wall %d: bad type %d", wl, t);
+        if (!std::isfinite(walls->T_wall[wl])) return fail(nullptr, BTE_EINVAL, "wall %d: non-finite T_wall", wl);
+        c->bc[wl] = t;
+        c->Tw[wl] = walls->T_wall[wl];
+    }
+    for (int a = 0; a < 3; ++a) {
+        if (a >= c->dim) {
+            c->bc[2 * a] = c->bc[2 * a + 1] = BTE_BC_PERIODIC;  // unused
+            continue;
+        }
+        if ((c->bc[2 * a] == BTE_BC_PERIODIC) != (c->bc[2 * a + 1] == BTE_BC_PERIODIC))
+            return fail(nullptr, BTE_EINVAL, "axis %d: a periodic wall needs a periodic partner", a);
+        for (int side = 0; side < 2; ++side)
+            if (c->bc[2 * a + side] == BTE_BC_SPECULAR)
+                for (int d = 0; d < c->nd; ++d)
+                    if (c->mirror[a * c->nd + d] < 0)
+                        return fail(nullptr, BTE_EINVAL, "specular wall on axis %d: direction %d has no mirror", a, d);
+    }
+    // options
+    if (!(opts->dt > 0.0) || !std::isfinite(opts->dt)) return fail(nullptr, BTE_EINVAL, "dt must be > 0");
+    if (opts->storage < BTE_STORE_F32 || opts->storage > BTE_STORE_BF16) return fail(nullptr, BTE_EINVAL, "bad storage");
+    if (opts->limiter < BTE_LIM_FIRST_ORDER || opts->limiter > BTE_LIM_VANALBADA)
+        return fail(nullptr, BTE_EINVAL, "bad limiter");
+    if (opts->kernel < BTE_KERNEL_AUTO || opts->kernel > BTE_KERNEL_TILED) return fail(nullptr, BTE_EINVAL, "bad kernel");
+    if (opts->rounding != BTE_ROUND_NEAREST && opts->rounding != BTE_ROUND_STOCHASTIC)
+        return fail(nullptr, BTE_EINVAL, "bad rounding");
+    if (opts->rounding == BTE_ROUND_STOCHASTIC)
+        return fail(nullptr, BTE_EUNSUPPORTED, "stochastic rounding is not implemented in this build");
+    c->dt = opts->dt;
+    c->storage = opts->storage;
+    c->limiter = opts->limiter;
+    c->rounding = opts->rounding;
+    c->kernel = opts->kernel;
+    c->seed = opts->seed;
+    c->T_scale = opts->T_scale > 0 ? opts->T_scale : 1.0;
+    c->stream = (cudaStream_t)opts->stream;
+    c->elem_bytes = c->storage == BTE_STORE_F32 ? 4 : 2;
+    c->nelem = c->ncell * c->nb * c->nd;
+    c->state_bytes = (size_t)c->nelem * c->elem_bytes;
+    // derived sums (sequential order)
+    c->W = 0;
+    for (double x : c->w) c->W += x;
+    c->sumC = 0;
+    c->D = 0;
+    for (int k = 0; k < c->nb; ++k) {
+        c->sumC += c->C[k];
+        c->D += c->C[k] / c->tau[k];
+    }
+
+    // the context proper
+    bte_ctx *ctx = new (std::nothrow) bte_ctx(*c);
+    if (!ctx) return fail(nullptr, BTE_ENOMEM, "host allocation failed");
+    c = ctx;
+    auto bail = [&](bte_status st) {
+        g_create_error = c->err;
+        free_all(c);
+        delete c;
+        return st;
+    };
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        cudaGetLastError();
+        c->err = "no CUDA device";
+        return bail(BTE_ECUDA);
+    }
+    const int nplanes = c->nb * c->nd;
+    // kernel plan
+    c->G = c->nb;
+    if (c->kernel != BTE_KERNEL_GENERIC) {
+        std::string why;
+        c->tiled = tiled_plan(c->dim, c->n, c->nb, c->nd, c->storage, c->bc, c->plan, why);
+        if (!c->tiled && c->kernel == BTE_KERNEL_TILED) {
+            c->err = "tiled kernel unavailable: " + why;
+            return bail(BTE_EUNSUPPORTED);
+        }
+        if (c->tiled) c->G = c->plan.G;
+    }
+    // wall-cell slots
+    c->wc_max = 1;
+    for (int a = 0; a < c->dim; ++a) {
+        long long m = c->ncell / c->n[a];
+        if (m > c->wc_max) c->wc_max = (int)m;
+    }
+    // diffuse normalisers
+    for (int wl = 0; wl < 2 * c->dim; ++wl) {
+        const int a = wl >> 1;
+        const double ns = (wl & 1) ? 1.0 : -1.0;
+        double den = 0;
+        for (int d = 0; d < c->nd; ++d) {
+            const double sn = ns * c->s[3 * d + a];
+            if (sn < 0) den += c->w[d] * (-sn);
+        }
+        c->inv_den[wl] = den > 0 ? (float)(1.0 / den) : 0.f;
+        if (c->bc[wl] == BTE_BC_DIFFUSE && !(den > 0)) {
+            c->err = "diffuse wall without incoming directions";
+            return bail(BTE_EINVAL);
+        }
+    }
+    // host tables
+    std::vector<float> nu(3 * nplanes, 0.f), wmom(nplanes), wdiff(6 * c->nd, 0.f), iso(6 * c->nb, 0.f);
+    std::vector<BandConst> band(c->nb);
+    for (int k = 0; k < c->nb; ++k) {
+        BandConst &b = band[k];
+        b.dtinv = (float)(c->dt / c->tau[k]);
+        b.ck = (float)(c->C[k] / c->W);
+        b.srck = (float)(c->dt * c->C[k] / (c->sumC * c->W));
+        const double sc = c->storage == BTE_STORE_F32 ? 1.0 : c->C[k] * c->T_scale / c->W;
+        b.scale = (float)sc;
+        b.inv_scale = (float)(1.0 / (double)b.scale);
+        b.wtau = (float)(1.0 / c->tau[k]);
+        b.pad0 = b.pad1 = 0.f;
+        for (int d = 0; d < c->nd; ++d) {
+            const int p = k * c->nd + d;
+            for (int a = 0; a < c->dim; ++a) nu[3 * p + a] = (float)(c->dt * c->v[k] * c->s[3 * d + a] / c->h[a]);
+            wmom[p] = (float)(c->w[d] / c->tau[k]);
+        }
+        for (int wl = 0; wl < 2 * c->dim; ++wl)
+            if (c->bc[wl] == BTE_BC_ISOTHERMAL) iso[wl * c->nb + k] = (float)(c->C[k] * c->Tw[wl] / c->W);
+    }
+    for (int wl = 0; wl < 2 * c->dim; ++wl) {
+        const int a = wl >> 1;
+        const double ns = (wl & 1) ? 1.0 : -1.0;
+        for (int d = 0; d < c->nd; ++d) {
+            const double sn = ns * c->s[3 * d + a];
+            if (sn > 0) wdiff[wl * c->nd + d] = (float)(c->w[d] * sn);
+        }
+    }
+    std::vector<double> invtau(c->nb);
+    for (int k = 0; k < c->nb; ++k) invtau[k] = 1.0 / c->tau[k];
+    std::vector<int> mir(c->mirror);
+    for (auto &m : mir)
+        if (m < 0) m = 0;  // never read: specular walls require a partner
+
+    bte_status st;
+    if ((st = dalloc(c, (char **)&c->e[0], c->state_bytes)) != BTE_OK) return bail(st);
+    if ((st = dalloc(c, (char **)&c->e[1], c->state_bytes)) != BTE_OK) return bail(st);
+    if ((st = dalloc(c, &c->TL, c->ncell)) != BTE_OK) return bail(st);
+    if ((st = dalloc(c, &c->Q, c->ncell)) != BTE_OK) return bail(st);
+    if ((st = dalloc(c, &c->P, (size_t)c->G * c->ncell)) != BTE_OK) return bail(st);
+    for (int i = 0; i < 2; ++i)
+        if ((st = dalloc(c, &c->ediff[i], (size_t)6 * c->nb * c->wc_max)) != BTE_OK) return bail(st);
+    if ((st = dalloc(c, &c->nu, nu.size())) != BTE_OK) return bail(st);
+    if ((st = dalloc(c, &c->wmom, wmom.size())) != BTE_OK) return bail(st);
+    if ((st = dalloc(c, &c->wdiff, wdiff.size())) != BTE_OK) return bail(st);
+    if ((st = dalloc(c, &c->iso, iso.size())) != BTE_OK) return bail(st);
+    if ((st = dalloc(c, &c->mirror_d, mir.size())) != BTE_OK) return bail(st);
+    if ((st = dalloc(c, &c->band, band.size())) != BTE_OK) return bail(st);
+    if ((st = dalloc(c, &c->d_w, c->w.size())) != BTE_OK) return bail(st);
+    if ((st = dalloc(c, &c->d_s, c->s.size())) != BTE_OK) return bail(st);
+    if ((st = dalloc(c, &c->d_v, c->v.size())) != BTE_OK) return bail(st);
+    if ((st = dalloc(c, &c->d_invtau, invtau.size())) != BTE_OK) return bail(st);
+    if ((st = upload(c, c->nu, nu.data(), nu.size())) != BTE_OK) return bail(st);
+    if ((st = upload(c, c->wmom, wmom.data(), wmom.size())) != BTE_OK) return bail(st);
+    if ((st = upload(c, c->wdiff, wdiff.data(), wdiff.size())) != BTE_OK) return bail(st);
+    if ((st = upload(c, c->iso, iso.data(), iso.size())) != BTE_OK) return bail(st);
+    if ((st = upload(c, c->mirror_d, mir.data(), mir.size())) != BTE_OK) return bail(st);
+    if ((st = upload(c, c->band, band.data(), band.size())) != BTE_OK) return bail(st);
+    if ((st = upload(c, c->d_w, c->w.data(), c->w.size())) != BTE_OK) return bail(st);
+    if ((st = upload(c, c->d_s, c->s.data(), c->s.size())) != BTE_OK) return bail(st);
+    if ((st = upload(c, c->d_v, c->v.data(), c->v.size())) != BTE_OK) return bail(st);
+    if ((st = upload(c, c->d_invtau, invtau.data(), invtau.size())) != BTE_OK) return bail(st);
+    if (cudaMemset(c->ediff[0], 0, sizeof(float) * 6 * c->nb * c->wc_max) != cudaSuccess ||
+        cudaMemset(c->ediff[1], 0, sizeof(float) * 6 * c->nb * c->wc_max) != cudaSuccess) {
+        c->err = "cudaMemset failed";
+        return bail(BTE_ECUDA);
+    }
+    if (c->tiled) {
+        std::string why;
+        if (!tiled_setup(c->plan, c->e[0], c->e[1], c->elem_bytes, why)) {
+            c->err = "tiled kernel setup failed: " + why;
+            return bail(BTE_ECUDA);
+        }
+    }
+    if ((st = bte_init_temperature(c, nullptr)) != BTE_OK) return bail(st);
+    if ((st = bte_synchronize(c)) != BTE_OK) return bail(st);
+    *out = c;
+    return BTE_OK;
+}
+
+extern "C" void bte_destroy(bte_ctx *ctx) {
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    free_all(ctx);
+    delete ctx;
+}
+
+extern "C" const char *bte_last_error(const bte_ctx *ctx) {
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+extern "C" bte_status bte_init_temperature(bte_ctx *c, const double *dT0) {
+    if (!c) return fail(nullptr, BTE_EINVAL, "ctx is NULL");
+    double *d = nullptr;
+    if (dT0) {
+        for (long long i = 0; i < c->ncell; ++i)
+            if (!std::isfinite(dT0[i])) return fail(c, BTE_EINVAL, "dT0 holds a non-finite value at cell %lld", i);
+        TRY(dalloc(c, &d, c->ncell));
+        c->device_bytes -= c->ncell * sizeof(double);
+        cudaError_t e = cudaMemcpyAsync(d, dT0, c->ncell * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) {
+            cudaFree(d);
+            return fail(c, BTE_ECUDA, "upload of dT0: %s", cudaGetErrorString(e));
+        }
+    }
+    StepArgs a = make_args(c);
+    a.e_out = c->e[c->cur];
+    cudaError_t e = launch_fill(a, c->storage, d, c->stream);
+    if (d) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(d);
+    }
+    if (e != cudaSuccess) return fail(c, BTE_ECUDA, "equilibrium fill: %s", cudaGetErrorString(e));
+    TRY(refresh_moments(c));
+    c->step = 0;
+    return BTE_OK;
+}
+
+extern "C" bte_status bte_set_source(bte_ctx *c, const float *Q, int on_device, const double *amp, int n_amp) {
+    if (!c) return fail(nullptr, BTE_EINVAL, "ctx is NULL");
+    if (n_amp < 0 || (n_amp > 0 && !amp)) return fail(c, BTE_EINVAL, "bad amplitude array");
+    if (amp)
+        for (int i = 0; i < n_amp; ++i)
+            if (!std::isfinite(amp[i])) return fail(c, BTE_EINVAL, "amplitude %d is not finite", i);
+    if (!Q) {
+        c->has_source = false;
+        c->has_amp = false;
+        c->amp.clear();
+        return BTE_OK;
+    }
+    if (!on_device)
+        for (long long i = 0; i < c->ncell; ++i)
+            if (!std::isfinite(Q[i])) return fail(c, BTE_EINVAL, "Q holds a non-finite value at cell %lld", i);
+    CU(c, cudaMemcpyAsync(c->Q, Q, c->ncell * sizeof(float), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                          c->stream));
+    if (!on_device) CU(c, cudaStreamSynchronize(c->stream));  // the caller may free Q on return
+    c->has_source = true;
+    c->has_amp = amp != nullptr;
+    c->amp.assign(amp ? amp : (const double *)nullptr, amp ? amp + n_amp : (const double *)nullptr);
+    return BTE_OK;
+}
+
+extern "C" bte_status bte_step(bte_ctx *c, int nsteps) {
+    if (!c) return fail(nullptr, BTE_EINVAL, "ctx is NULL");
+    if (nsteps < 0) return fail(c, BTE_EINVAL, "n must be >= 0");
+    for (int s = 0; s < nsteps; ++s) {
+        StepArgs a = make_args(c);
+        a.amp = (float)amplitude_at(c, c->step);
+        a.e_in = c->e[c->cur];
+        a.e_out = c->e[c->cur ^ 1];
+        a.TL = c->TL;
+        a.ediff_in = c->ediff[c->ecur];
+        a.ediff_out = c->ediff[c->ecur ^ 1];
+        cudaError_t e;
+        cudaEvent_t ev;
+        if (c->prof) TRY(prof_event(c, &ev));
+        if (c->tiled) e = launch_step_tiled(a, c->plan, c->cur, c->storage, c->limiter, c->stream);
+        else e = launch_step_generic(a, c->storage, c->limiter, c->stream);
+        if (e != cudaSuccess) return fail(c, BTE_ECUDA, "forward step launch: %s", cudaGetErrorString(e));
+        if (c->prof) TRY(prof_event(c, &ev));
+        if (c->tiled) e = launch_finalize_tiled(a, c->plan, c->TL, c->stream);
+        else e = launch_finalize(a, c->G, c->TL, c->stream);
+        if (e != cudaSuccess) return fail(c, BTE_ECUDA, "finalize launch: %s", cudaGetErrorString(e));
+        if (c->prof) TRY(prof_event(c, &ev));
+        c->cur ^= 1;
+        c->ecur ^= 1;
+        ++c->step;
+    }
+    return BTE_OK;
+}
+
+extern "C" bte_status bte_synchronize(bte_ctx *c) {
+    if (!c) return fail(nullptr, BTE_EINVAL, "ctx is NULL");
+    CU(c, cudaStreamSynchronize(c->stream));
+    CU(c, cudaGetLastError());
+    return BTE_OK;
+}
+
+extern "C" bte_status bte_lattice_temperature(bte_ctx *c, double *dTL) {
+    if (!c || !dTL) return fail(c, BTE_EINVAL, "NULL argument");
+    std::vector<float> t(c->ncell);
+    CU(c, cudaMemcpyAsync(t.data(), c->TL, c->ncell * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    CU(c, cudaStreamSynchronize(c->stream));
+    for (long long i = 0; i < c->ncell; ++i) dTL[i] = t[i];
+    return BTE_OK;
+}
+
+static bte_status diag_buffers(bte_ctx *c) {
+    if (!c->dg) {
+        // T, TL, cellE: ncell each; q: 3 ncell; wall partials: 6 nb wc_max; sums: 1024 + 8
+        const size_t n = (size_t)6 * c->ncell + (size_t)6 * c->nb * c->wc_max + 1032;
+        TRY(dalloc(c, &c->dg, n));
+        TRY(dalloc(c, &c->dflag, 1));
+    }
+    return BTE_OK;
+}
+
+static DiagOut diag_layout(bte_ctx *c) {
+    DiagOut o;
+    o.T = c->dg;
+    o.TL = c->dg + c->ncell;
+    o.cellE = c->dg + 2 * c->ncell;
+    o.q = c->dg + 3 * c->ncell;
+    o.wallpart = c->dg + 6 * c->ncell;
+    o.nonfinite = c->dflag;
+    return o;
+}
+
+extern "C" bte_status bte_moments(bte_ctx *c, double *dT, double *dTL, double *q) {
+    if (!c) return fail(nullptr, BTE_EINVAL, "ctx is NULL");
+    TRY(diag_buffers(c));
+    DiagOut o = diag_layout(c);
+    CU(c, cudaMemsetAsync(c->dflag, 0, sizeof(int), c->stream));
+    StepArgs a = make_args(c);
+    a.e_in = c->e[c->cur];
+    CU(c, launch_moments64(a, c->storage, c->d_w, c->d_s, c->d_v, c->d_invtau, c->sumC, c->D, o, c->stream));
+    int flag = 0;
+    CU(c, cudaMemcpyAsync(&flag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    if (dT) CU(c, cudaMemcpyAsync(dT, o.T, c->ncell * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (dTL) CU(c, cudaMemcpyAsync(dTL, o.TL, c->ncell * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (q) CU(c, cudaMemcpyAsync(q, o.q, 3 * c->ncell * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CU(c, cudaStreamSynchronize(c->stream));
+    if (flag) return fail(c, BTE_ENONFINITE, "the state holds a non-finite value");
+    return BTE_OK;
+}
+
+extern "C" bte_status bte_energy(bte_ctx *c, double *E_total, double wall_flux[6]) {
+    if (!c) return fail(nullptr, BTE_EINVAL, "ctx is NULL");
+    TRY(diag_buffers(c));
+    DiagOut o = diag_layout(c);
+    double *sums = c->dg + 6 * c->ncell + (size_t)6 * c->nb * c->wc_max;  // [1024 scratch][8 results]
+    CU(c, cudaMemsetAsync(c->dflag, 0, sizeof(int), c->stream));
+    CU(c, cudaMemsetAsync(o.wallpart, 0, sizeof(double) * 6 * c->nb * c->wc_max, c->stream));
+    StepArgs a = make_args(c);
+    a.e_in = c->e[c->cur];
+    a.ediff_in = c->ediff[c->ecur];
+    DiagOut o2 = o;
+    o2.T = o2.TL = o2.q = nullptr;
+    CU(c, launch_moments64(a, c->storage, c->d_w, c->d_s, c->d_v, c->d_invtau, c->sumC, c->D, o2, c->stream));
+    CU(c, launch_sum64(o.cellE, c->ncell, sums, sums + 1024, c->stream));
+    CU(c, launch_wallflux64(a, c->storage, c->limiter, c->d_w, c->d_s, c->d_v, o, c->stream));
+    for (int wl = 0; wl < 6; ++wl)
+        CU(c, launch_sum64(o.wallpart + (size_t)wl * c->nb * c->wc_max, (long long)c->nb * c->wc_max, sums,
+                           sums + 1025 + wl, c->stream));
+    double res[7];
+    int flag = 0;
+    CU(c, cudaMemcpyAsync(res, sums + 1024, 7 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CU(c, cudaMemcpyAsync(&flag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CU(c, cudaStreamSynchronize(c->stream));
+    double L[3];
+    for (int ax = 0; ax < 3; ++ax) L[ax] = ax < c->dim ? c->h[ax] : 1.0;
+    const double V = L[0] * L[1] * L[2];
+    if (E_total) *E_total = V * res[0];
+    if (wall_flux)
+        for (int wl = 0; wl < 6; ++wl) wall_flux[wl] = (wl < 2 * c->dim) ? (V / L[wl >> 1]) * res[1 + wl] : 0.0;
+    if (flag) return fail(c, BTE_ENONFINITE, "the state holds a non-finite value");
+    return BTE_OK;
+}
+
+extern "C" bte_status bte_get_state(bte_ctx *c, void *dst, size_t bytes, int on_device) {
+    if (!c || !dst) return fail(c, BTE_EINVAL, "NULL argument");
+    if (bytes != c->state_bytes) return fail(c, BTE_EINVAL, "bytes %zu != state_bytes %zu", bytes, c->state_bytes);
+    CU(c, cudaMemcpyAsync(dst, c->e[c->cur], bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          c->stream));
+    if (!on_device) CU(c, cudaStreamSynchronize(c->stream));
+    return BTE_OK;
+}
+
+extern "C" bte_status bte_set_state(bte_ctx *c, const void *src, size_t bytes, int on_device, int keep_step) {
+    if (!c || !src) return fail(c, BTE_EINVAL, "NULL argument");
+    if (bytes != c->state_bytes) return fail(c, BTE_EINVAL, "bytes %zu != state_bytes %zu", bytes, c->state_bytes);
+    CU(c, cudaMemcpyAsync(c->e[c->cur], src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                          c->stream));
+    if (!on_device) CU(c, cudaStreamSynchronize(c->stream));
+    TRY(refresh_moments(c));
+    if (!keep_step) c->step = 0;
+    return BTE_OK;
+}
+
+extern "C" bte_status bte_get_info(const bte_ctx *c, bte_info *info) {
+    if (!c || !info) return fail(nullptr, BTE_EINVAL, "NULL argument");
+    info->dim = c->dim;
+    info->nx = c->n[0];
+    info->ny = c->n[1];
+    info->nz = c->n[2];
+    info->nbands = c->nb;
+    info->ndirs = c->nd;
+    info->ncell = c->ncell;
+    info->nelem = c->nelem;
+    info->state_bytes = c->state_bytes;
+    info->elem_bytes = (int)c->elem_bytes;
+    info->storage = c->storage;
+    info->limiter = c->limiter;
+    info->kernel = c->tiled ? BTE_KERNEL_TILED : BTE_KERNEL_GENERIC;
+    info->dt = c->dt;
+    info->W = c->W;
+    info->step = c->step;
+    info->device_bytes = c->device_bytes;
+    return BTE_OK;
+}
+
+extern "C" bte_status bte_get_quadrature(const bte_ctx *c, double *s, double *w) {
+    if (!c) return fail(nullptr, BTE_EINVAL, "ctx is NULL");
+    if (s) memcpy(s, c->s.data(), c->s.size() * sizeof(double));
+    if (w) memcpy(w, c->w.data(), c->w.size() * sizeof(double));
+    return BTE_OK;
+}
+
+extern "C" bte_status bte_profile(bte_ctx *c, int enable) {
+    if (!c) return fail(nullptr, BTE_EINVAL, "ctx is NULL");
+    if (enable) {
+        CU(c, cudaStreamSynchronize(c->stream));
+        c->ev_used = 0;
+    }
+    c->prof = enable != 0;
+    return BTE_OK;
+}
+
+extern "C" bte_status bte_profile_read(bte_ctx *c, double *fwd_ms, long long *fwd_launches, double *fin_ms,
+                                       long long *fin_launches) {
+    if (!c) return fail(nullptr, BTE_EINVAL, "ctx is NULL");
+    CU(c, cudaStreamSynchronize(c->stream));
+    double f = 0, g = 0;
+    const size_t n = c->ev_used / 3;
+    for (size_t i = 0; i < n; ++i) {
+        float a = 0, b = 0;
+        CU(c, cudaEventElapsedTime(&a, c->ev[3 * i], c->ev[3 * i + 1]));
+        CU(c, cudaEventElapsedTime(&b, c->ev[3 * i + 1], c->ev[3 * i + 2]));
+        f += a;
+        g += b;
+    }
+    if (fwd_ms) *fwd_ms = f;
+    if (fin_ms) *fin_ms = g;
+    if (fwd_launches) *fwd_launches = (long long)n;
+    if (fin_launches) *fin_launches = (long long)n;
+    return BTE_OK;
+}

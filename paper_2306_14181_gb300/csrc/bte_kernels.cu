@@ -1,0 +1,448 @@
+// Generic kernels of the GB300 explicit DOM transient step (arXiv 2306.14181, Sec. 4):
+// equilibrium fill, the per-(cell, band) forward step for any grid shape, the moment-only
+// pass, the T_L finalisation and the FP64 diagnostics.  The shared-memory tiled forward
+// kernel lives in bte_tiled.cu.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "bte_internal.h"
+
+namespace bte {
+
+// ------------------------------------------------------------------------------------------
+// Storage codecs: e = s_k * h for 16-bit storage, all arithmetic in FP32.
+// st() stores the rounded code and returns the value it represents, so that the moment and
+// the diffuse-wall sums use the stored state.
+// ------------------------------------------------------------------------------------------
+template <int S> struct Codec;
+template <> struct Codec<kStoreF32> {
+    using T = float;
+    static __device__ __forceinline__ float ld(const T *p, long long i, const BandConst &) { return p[i]; }
+    static __device__ __forceinline__ double ld64(const T *p, long long i, const BandConst &) { return (double)p[i]; }
+    static __device__ __forceinline__ float st(T *p, long long i, float v, const BandConst &) { p[i] = v; return v; }
+};
+template <> struct Codec<kStoreF16> {
+    using T = __half;
+    static __device__ __forceinline__ float ld(const T *p, long long i, const BandConst &b) {
+        return b.scale * __half2float(p[i]);
+    }
+    static __device__ __forceinline__ double ld64(const T *p, long long i, const BandConst &b) {
+        return (double)b.scale * (double)__half2float(p[i]);
+    }
+    static __device__ __forceinline__ float st(T *p, long long i, float v, const BandConst &b) {
+        const __half h = __float2half_rn(v * b.inv_scale);
+        p[i] = h;
+        return b.scale * __half2float(h);
+    }
+};
+template <> struct Codec<kStoreBF16> {
+    using T = __nv_bfloat16;
+    static __device__ __forceinline__ float ld(const T *p, long long i, const BandConst &b) {
+        return b.scale * __bfloat162float(p[i]);
+    }
+    static __device__ __forceinline__ double ld64(const T *p, long long i, const BandConst &b) {
+        return (double)b.scale * (double)__bfloat162float(p[i]);
+    }
+    static __device__ __forceinline__ float st(T *p, long long i, float v, const BandConst &b) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(v * b.inv_scale);
+        p[i] = h;
+        return b.scale * __bfloat162float(h);
+    }
+};
+
+// Slope limiter of the one-sided differences a (upwind) and b (downwind); e_face = e_m + L/2.
+template <int LIM> __device__ __forceinline__ float limit(float a, float b);
+template <> __device__ __forceinline__ float limit<kLimFirst>(float, float) { return 0.f; }
+template <> __device__ __forceinline__ float limit<kLimMinmod>(float a, float b) {
+    return (a * b > 0.f) ? (fabsf(a) < fabsf(b) ? a : b) : 0.f;
+}
+template <> __device__ __forceinline__ float limit<kLimVanAlbada>(float a, float b) {
+    const float ab = a * b;
+    return ab > 0.f ? ab * (a + b) / (a * a + b * b) : 0.f;
+}
+
+__device__ __forceinline__ double limit64(int lim, double a, double b) {
+    if (lim == kLimFirst || a * b <= 0.0) return 0.0;
+    if (lim == kLimMinmod) return fabs(a) < fabs(b) ? a : b;
+    return a * b * (a + b) / (a * a + b * b);
+}
+
+// Index of a wall-adjacent cell within its wall (the two coordinates along the wall).
+__device__ __forceinline__ int wall_cell(const StepArgs &a, int ax, const int c[3]) {
+    return ax == 0 ? c[2] * a.n[1] + c[1] : (ax == 1 ? c[2] * a.n[0] + c[0] : c[1] * a.n[0] + c[0]);
+}
+
+__device__ __forceinline__ void cell_coords(const StepArgs &a, long long i, int c[3]) {
+    c[0] = (int)(i % a.n[0]);
+    c[1] = (int)((i / a.n[0]) % a.n[1]);
+    c[2] = (int)(i / ((long long)a.n[0] * a.n[1]));
+}
+
+// Value of plane (k,d) at position pos along axis ax through cell i (coords c), where pos may
+// be a ghost (-2, -1, n, n+1).  Ghosts follow Sec. 2.2: periodic wrap; thermalizing wall
+// emission C_k T_w / W for incoming directions; diffuse wall value e_diff for incoming
+// directions; the wall cell itself for directions leaving through a thermalizing or diffuse
+// wall; the mirrored direction at the mirrored cell for a specular wall.
+template <class Cd>
+__device__ __forceinline__ float ext_value(const StepArgs &a, const typename Cd::T *e, const BandConst &b, int k,
+                                           int d, long long base, long long i, const int c[3], int ax, int pos,
+                                           float nu) {
+    const int n = a.n[ax];
+    const long long st = a.stride[ax];
+    if (pos >= 0 && pos < n) return Cd::ld(e, base + i + (long long)(pos - c[ax]) * st, b);
+    const int side = pos < 0 ? 0 : 1;
+    const int wall = 2 * ax + side;
+    const int bc = a.bc[wall];
+    if (bc == kBcPeriodic) {
+        const int p2 = side ? pos - n : pos + n;
+        return Cd::ld(e, base + i + (long long)(p2 - c[ax]) * st, b);
+    }
+    if (bc == kBcSpecular) {
+        const int layer = side ? pos - n + 1 : -pos;
+        const int mpos = side ? n - layer : layer - 1;
+        const long long mbase = ((long long)k * a.nd + a.mirror[ax * a.nd + d]) * a.ncell;
+        return Cd::ld(e, mbase + i + (long long)(mpos - c[ax]) * st, b);
+    }
+    const bool incoming = side == 0 ? (nu > 0.f) : (nu < 0.f);
+    if (!incoming) {
+        const int wpos = side ? n - 1 : 0;
+        return Cd::ld(e, base + i + (long long)(wpos - c[ax]) * st, b);
+    }
+    if (bc == kBcIsothermal) return a.iso[wall * a.nb + k];
+    return a.ediff_in[((long long)wall * a.nb + k) * a.wc_max + wall_cell(a, ax, c)];
+}
+
+// Diffuse walls touched by cell c: their indices into wl[], count returned.
+__device__ __forceinline__ int diffuse_walls_of(const StepArgs &a, const int c[3], int wl[6]) {
+    int nw = 0;
+    for (int w = 0; w < 2 * a.dim; ++w) {
+        const int ax = w >> 1;
+        if (a.bc[w] == kBcDiffuse && c[ax] == ((w & 1) ? a.n[ax] - 1 : 0)) wl[nw++] = w;
+    }
+    return nw;
+}
+
+// ------------------------------------------------------------------------------------------
+// Generic forward step: one thread per (cell, band), looping over the band's directions.
+// Eq. (disretized_transientBTE) with the limited upwind face value of Sec. 4.1, in upwind
+// orientation: with sg = sign(nu_a) and u_j = e(i + j sg),
+//   e_out = u_0 + L(u_0 - u_-1, u_1 - u_0)/2,  e_in = u_-1 + L(u_-1 - u_-2, u_0 - u_-1)/2,
+//   e^{n+1} = e - sum_a |nu_a| (e_out - e_in) + dt/tau (C T_L / W - e) + a Q dt C/(sum C W).
+// The same pass accumulates the T_L moment sum_d w_d e^{n+1}/tau_k (Eq. BTE_get_e0) into
+// P[k][i] and, at diffuse walls, the outgoing sums of Eq. (diff_bound) for the next step.
+// ------------------------------------------------------------------------------------------
+template <int S, int LIM>
+__global__ void __launch_bounds__(256) k_step_generic(const StepArgs a) {
+    using Cd = Codec<S>;
+    using T = typename Cd::T;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.ncell) return;
+    const int k = blockIdx.y;
+    int c[3];
+    cell_coords(a, i, c);
+    const BandConst b = a.band[k];
+    const T *ein = static_cast<const T *>(a.e_in);
+    T *eout = static_cast<T *>(a.e_out);
+    const float eq = b.ck * a.TL[i];
+    const float src = a.Q ? b.srck * (a.amp * a.Q[i]) : 0.f;
+    int wl[6];
+    const int nw = diffuse_walls_of(a, c, wl);
+    float wacc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float acc = 0.f;
+    for (int d = 0; d < a.nd; ++d) {
+        const int plane = k * a.nd + d;
+        const long long base = (long long)plane * a.ncell;
+        const float e0 = Cd::ld(ein, base + i, b);
+        float div = 0.f;
+        for (int ax = 0; ax < a.dim; ++ax) {
+            const float nu = a.nu[plane * 3 + ax];
+            if (nu == 0.f) continue;
+            const int sg = nu > 0.f ? 1 : -1;
+            const float um2 = ext_value<Cd>(a, ein, b, k, d, base, i, c, ax, c[ax] - 2 * sg, nu);
+            const float um1 = ext_value<Cd>(a, ein, b, k, d, base, i, c, ax, c[ax] - sg, nu);
+            const float up1 = ext_value<Cd>(a, ein, b, k, d, base, i, c, ax, c[ax] + sg, nu);
+            const float fo = e0 + 0.5f * limit<LIM>(e0 - um1, up1 - e0);
+            const float fi = um1 + 0.5f * limit<LIM>(um1 - um2, e0 - um1);
+            div += fabsf(nu) * (fo - fi);
+        }
+        const float en = e0 - div + b.dtinv * (eq - e0) + src;
+        const float es = Cd::st(eout, base + i, en, b);
+        acc += a.wmom[plane] * es;
+        for (int j = 0; j < nw; ++j) wacc[j] += a.wdiff[wl[j] * a.nd + d] * es;
+    }
+    a.P[(long long)k * a.ncell + i] = acc;
+    for (int j = 0; j < nw; ++j) {
+        const int w = wl[j];
+        a.ediff_out[((long long)w * a.nb + k) * a.wc_max + wall_cell(a, w >> 1, c)] = wacc[j] * a.inv_den[w];
+    }
+}
+
+// Moment partials and diffuse-wall values of the current state without stepping (after an
+// equilibrium fill or a state upload).  Writes P[k][i] and ediff_out.
+template <int S>
+__global__ void __launch_bounds__(256) k_moment_only(const StepArgs a) {
+    using Cd = Codec<S>;
+    using T = typename Cd::T;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.ncell) return;
+    const int k = blockIdx.y;
+    int c[3];
+    cell_coords(a, i, c);
+    const BandConst b = a.band[k];
+    const T *e = static_cast<const T *>(a.e_in);
+    int wl[6];
+    const int nw = diffuse_walls_of(a, c, wl);
+    float wacc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float acc = 0.f;
+    for (int d = 0; d < a.nd; ++d) {
+        const int plane = k * a.nd + d;
+        const float es = Cd::ld(e, (long long)plane * a.ncell + i, b);
+        acc += a.wmom[plane] * es;
+        for (int j = 0; j < nw; ++j) wacc[j] += a.wdiff[wl[j] * a.nd + d] * es;
+    }
+    a.P[(long long)k * a.ncell + i] = acc;
+    for (int j = 0; j < nw; ++j) {
+        const int w = wl[j];
+        a.ediff_out[((long long)w * a.nb + k) * a.wc_max + wall_cell(a, w >> 1, c)] = wacc[j] * a.inv_den[w];
+    }
+}
+
+// T_L_i = (sum_g P[g][i]) / sum_k C_k/tau_k, Eq. (BTE_get_e0), summed in fixed g order.
+__global__ void __launch_bounds__(256) k_finalize(const float *__restrict__ P, int G, long long ncell, float invD,
+                                                  float *__restrict__ TL) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ncell) return;
+    float s = 0.f;
+    for (int g = 0; g < G; ++g) s += P[(long long)g * ncell + i];
+    TL[i] = s * invD;
+}
+
+// Equilibrium fill e_{k,d,i} = C_k dT0_i / W (Algorithm 2, initial state).
+template <int S>
+__global__ void __launch_bounds__(256) k_fill(const StepArgs a, const double *dT0) {
+    using Cd = Codec<S>;
+    using T = typename Cd::T;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.ncell) return;
+    const int plane = blockIdx.y;
+    const int k = plane / a.nd;
+    const BandConst b = a.band[k];
+    const float t = dT0 ? (float)dT0[i] : 0.f;
+    Cd::st(static_cast<T *>(a.e_out), (long long)plane * a.ncell + i, b.ck * t, b);
+}
+
+static dim3 cell_grid(long long ncell, int y) { return dim3((unsigned)((ncell + 255) / 256), (unsigned)y); }
+
+template <int S>
+static void fill_s(const StepArgs &a, const double *dT0, cudaStream_t s) {
+    k_fill<S><<<cell_grid(a.ncell, a.nb * a.nd), 256, 0, s>>>(a, dT0);
+}
+
+cudaError_t launch_fill(const StepArgs &a, int storage, const double *dT0, cudaStream_t s) {
+    if (storage == kStoreF32) fill_s<kStoreF32>(a, dT0, s);
+    else if (storage == kStoreF16) fill_s<kStoreF16>(a, dT0, s);
+    else fill_s<kStoreBF16>(a, dT0, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moment_only(const StepArgs &a, int storage, cudaStream_t s) {
+    const dim3 g = cell_grid(a.ncell, a.nb);
+    if (storage == kStoreF32) k_moment_only<kStoreF32><<<g, 256, 0, s>>>(a);
+    else if (storage == kStoreF16) k_moment_only<kStoreF16><<<g, 256, 0, s>>>(a);
+    else k_moment_only<kStoreBF16><<<g, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int S>
+static void step_generic_s(const StepArgs &a, int limiter, cudaStream_t s) {
+    const dim3 g = cell_grid(a.ncell, a.nb);
+    if (limiter == kLimFirst) k_step_generic<S, kLimFirst><<<g, 256, 0, s>>>(a);
+    else if (limiter == kLimMinmod) k_step_generic<S, kLimMinmod><<<g, 256, 0, s>>>(a);
+    else k_step_generic<S, kLimVanAlbada><<<g, 256, 0, s>>>(a);
+}
+
+cudaError_t launch_step_generic(const StepArgs &a, int storage, int limiter, cudaStream_t s) {
+    if (storage == kStoreF32) step_generic_s<kStoreF32>(a, limiter, s);
+    else if (storage == kStoreF16) step_generic_s<kStoreF16>(a, limiter, s);
+    else step_generic_s<kStoreBF16>(a, limiter, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const StepArgs &a, int G, float *TL_out, cudaStream_t s) {
+    k_finalize<<<cell_grid(a.ncell, 1), 256, 0, s>>>(a.P, G, a.ncell, a.invD, TL_out);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// FP64 diagnostics (off the timed path).
+// ------------------------------------------------------------------------------------------
+
+// Per-cell moments of Eq. (getTQ) and Eq. (BTE_get_e0), FP64 accumulation.
+template <int S>
+__global__ void __launch_bounds__(256) k_moments64(const StepArgs a, const double *w, const double *sv,
+                                                   const double *v, const double *invtau, double sumC, double D,
+                                                   DiagOut o) {
+    using Cd = Codec<S>;
+    using T = typename Cd::T;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.ncell) return;
+    const T *e = static_cast<const T *>(a.e_in);
+    double et = 0.0, tl = 0.0, qx = 0.0, qy = 0.0, qz = 0.0;
+    bool bad = false;
+    for (int k = 0; k < a.nb; ++k) {
+        const BandConst b = a.band[k];
+        double sk = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+        for (int d = 0; d < a.nd; ++d) {
+            const double ed = Cd::ld64(e, ((long long)k * a.nd + d) * a.ncell + i, b);
+            bad |= !isfinite(ed);
+            const double we = w[d] * ed;
+            sk += we;
+            sx += we * sv[3 * d];
+            sy += we * sv[3 * d + 1];
+            sz += we * sv[3 * d + 2];
+        }
+        et += sk;
+        tl += invtau[k] * sk;
+        qx += v[k] * sx;
+        qy += v[k] * sy;
+        qz += v[k] * sz;
+    }
+    if (bad) atomicOr(o.nonfinite, 1);
+    if (o.T) o.T[i] = et / sumC;
+    if (o.TL) o.TL[i] = tl / D;
+    if (o.q) {
+        o.q[i] = qx;
+        o.q[a.ncell + i] = qy;
+        o.q[2 * a.ncell + i] = qz;
+    }
+    if (o.cellE) o.cellE[i] = et;
+}
+
+template <class Cd>
+__device__ double ext64(const StepArgs &a, const typename Cd::T *e, const BandConst &b, int k, int d, long long i,
+                        const int c[3], int ax, int pos, double sa) {
+    const int n = a.n[ax];
+    const long long st = a.stride[ax];
+    const long long base = ((long long)k * a.nd + d) * a.ncell;
+    if (pos >= 0 && pos < n) return Cd::ld64(e, base + i + (long long)(pos - c[ax]) * st, b);
+    const int side = pos < 0 ? 0 : 1;
+    const int wall = 2 * ax + side;
+    const int bc = a.bc[wall];
+    if (bc == kBcPeriodic) return Cd::ld64(e, base + i + (long long)((side ? pos - n : pos + n) - c[ax]) * st, b);
+    if (bc == kBcSpecular) {
+        const int layer = side ? pos - n + 1 : -pos;
+        const int mpos = side ? n - layer : layer - 1;
+        const long long mbase = ((long long)k * a.nd + a.mirror[ax * a.nd + d]) * a.ncell;
+        return Cd::ld64(e, mbase + i + (long long)(mpos - c[ax]) * st, b);
+    }
+    const bool incoming = side == 0 ? (sa > 0.0) : (sa < 0.0);
+    if (!incoming) return Cd::ld64(e, base + i + (long long)((side ? n - 1 : 0) - c[ax]) * st, b);
+    if (bc == kBcIsothermal) return (double)a.iso[wall * a.nb + k];
+    return (double)a.ediff_in[((long long)wall * a.nb + k) * a.wc_max + wall_cell(a, ax, c)];
+}
+
+// Outward heat flow through one wall, per (wall cell j, band k): sum_d w v (s.n) e_face, with
+// e_face the wall-face value of the step (upwind side chosen by the sign of s_a).
+template <int S>
+__global__ void __launch_bounds__(256) k_wallflux64(const StepArgs a, int wall, int lim, const double *w,
+                                                    const double *sv, const double *v, DiagOut o) {
+    using Cd = Codec<S>;
+    using T = typename Cd::T;
+    const int ax = wall >> 1, side = wall & 1;
+    const int n0 = ax == 0 ? a.n[1] : a.n[0];
+    const int n1 = ax == 2 ? a.n[1] : a.n[2];
+    const long long nwc = (long long)n0 * n1;
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
+    if (j >= nwc) return;
+    int c[3];
+    const int ja = (int)(j % n0), jb = (int)(j / n0);
+    c[ax] = side ? a.n[ax] - 1 : 0;
+    if (ax == 0) { c[1] = ja; c[2] = jb; }
+    else if (ax == 1) { c[0] = ja; c[2] = jb; }
+    else { c[0] = ja; c[1] = jb; }
+    const long long i = c[0] + a.stride[1] * c[1] + a.stride[2] * c[2];
+    const T *e = static_cast<const T *>(a.e_in);
+    const BandConst b = a.band[k];
+    const int n = a.n[ax];
+    const double nsign = side ? 1.0 : -1.0;
+    double F = 0.0;
+    for (int d = 0; d < a.nd; ++d) {
+        const double sa = sv[3 * d + ax];
+        if (sa == 0.0) continue;
+        const int sg = sa > 0.0 ? 1 : -1;
+        // the wall face lies between p and p + sg along the flow, p = upwind cell
+        const int pin = side ? n - 1 : 0;          // wall cell
+        const int pg = side ? n : -1;              // first ghost
+        const int pu = (sa * nsign > 0.0) ? pin : pg;  // upwind position: wall cell if leaving
+        const double um = ext64<Cd>(a, e, b, k, d, i, c, ax, pu, sa);
+        const double ul = ext64<Cd>(a, e, b, k, d, i, c, ax, pu - sg, sa);
+        const double ur = ext64<Cd>(a, e, b, k, d, i, c, ax, pu + sg, sa);
+        const double ef = um + 0.5 * limit64(lim, um - ul, ur - um);
+        F += w[d] * v[k] * (nsign * sa) * ef;
+    }
+    o.wallpart[((long long)wall * a.nb + k) * a.wc_max + j] = F;
+}
+
+cudaError_t launch_moments64(const StepArgs &a, int storage, const double *w, const double *sv, const double *v,
+                             const double *invtau, double sumC, double D, DiagOut o, cudaStream_t s) {
+    const dim3 g = cell_grid(a.ncell, 1);
+    if (storage == kStoreF32) k_moments64<kStoreF32><<<g, 256, 0, s>>>(a, w, sv, v, invtau, sumC, D, o);
+    else if (storage == kStoreF16) k_moments64<kStoreF16><<<g, 256, 0, s>>>(a, w, sv, v, invtau, sumC, D, o);
+    else k_moments64<kStoreBF16><<<g, 256, 0, s>>>(a, w, sv, v, invtau, sumC, D, o);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wallflux64(const StepArgs &a, int storage, int limiter, const double *w, const double *sv,
+                              const double *v, DiagOut o, cudaStream_t s) {
+    for (int wall = 0; wall < 2 * a.dim; ++wall) {
+        const int ax = wall >> 1;
+        const long long nwc = ax == 0 ? (long long)a.n[1] * a.n[2]
+                                      : (ax == 1 ? (long long)a.n[0] * a.n[2] : (long long)a.n[0] * a.n[1]);
+        const dim3 g((unsigned)((nwc + 255) / 256), (unsigned)a.nb);
+        if (storage == kStoreF32) k_wallflux64<kStoreF32><<<g, 256, 0, s>>>(a, wall, limiter, w, sv, v, o);
+        else if (storage == kStoreF16) k_wallflux64<kStoreF16><<<g, 256, 0, s>>>(a, wall, limiter, w, sv, v, o);
+        else k_wallflux64<kStoreBF16><<<g, 256, 0, s>>>(a, wall, limiter, w, sv, v, o);
+    }
+    return cudaGetLastError();
+}
+
+// Deterministic FP64 sum: fixed per-thread chunks, fixed tree order, then one block.
+__global__ void __launch_bounds__(256) k_sum64_a(const double *x, long long n, double *part) {
+    __shared__ double sm[256];
+    const long long nb = gridDim.x;
+    const long long chunk = (n + nb - 1) / nb;
+    const long long lo = blockIdx.x * chunk;
+    const long long hi = lo + chunk < n ? lo + chunk : n;
+    double s = 0.0;
+    for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) s += x[t];
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) sm[threadIdx.x] += sm[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+
+__global__ void __launch_bounds__(256) k_sum64_b(const double *part, int np, double *out) {
+    __shared__ double sm[256];
+    double s = 0.0;
+    for (int t = threadIdx.x; t < np; t += blockDim.x) s += part[t];
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) sm[threadIdx.x] += sm[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sm[0];
+}
+
+cudaError_t launch_sum64(const double *x, long long n, double *scratch, double *out, cudaStream_t s) {
+    const int np = 1024;
+    k_sum64_a<<<np, 256, 0, s>>>(x, n, scratch);
+    k_sum64_b<<<1, 256, 0, s>>>(scratch, np, out);
+    return cudaGetLastError();
+}
+
+}  // namespace bte

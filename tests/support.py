@@ -39,3 +39,33 @@ def rel_linf(a, b):
     a = np.asarray(a, float)
     b = np.asarray(b, float)
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def gpu_ctx(cfg, **opts):
+    """A GPU context for a workload/small-config dict (imports the binding lazily)."""
+    from paper_2306_14181_gb300 import bte
+    return bte.bte_create(cfg["dim"], cfg["n"], cfg["h"], cfg["C"], cfg["v"], cfg["tau"], cfg["quad"], cfg["bc"],
+                          cfg["Tw"], opts.pop("dt", cfg["dt"]), **opts)
+
+
+def run_both(cfg, e0, nsteps, Q=None, amps=None, limiter=2, storage=0, kernel=0, T_scale=1.0):
+    """Run the same start state on the GPU and on the oracle.  e0 is taken as float32 (the GPU
+    state); the oracle starts from exactly those values.  Returns (gpu_e, gpu_TL, orc_e, orc_TL)."""
+    from paper_2306_14181_gb300 import bte
+    P = oracle_problem(cfg, limiter)
+    ctx = gpu_ctx(cfg, limiter=limiter, storage=storage, kernel=kernel, T_scale=T_scale)
+    e32 = np.ascontiguousarray(e0, dtype=np.float32)
+    if storage == 0:
+        bte.bte_set_state(ctx, e32)
+        start = e32.astype(np.float64)
+    else:
+        bte.bte_init_temperature(ctx, None)
+        start = P.equilibrium(0.0)
+        assert not np.any(e0), "16-bit runs start from the zero state"
+    if Q is not None:
+        bte.bte_set_source(ctx, np.ascontiguousarray(Q, dtype=np.float32), amps)
+    bte.bte_step(ctx, nsteps)
+    g = bte.bte_get_state(ctx)
+    _, gTL, _ = bte.bte_moments(ctx)
+    eo = P.run(start, nsteps, Q, amps)
+    return ctx, g, gTL, eo, P.lattice_temperature(eo)

@@ -1,0 +1,76 @@
+"""The C-ABI library builds, loads and exports every entry point include/bte.h declares; its
+host-side validation rejects bad inputs before any CUDA call (runs without a GPU)."""
+import ctypes as ct
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2306_14181_gb300 import bte, build, inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return bte.load()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "bte.h")).read()
+    return sorted(set(re.findall(r"^(?:bte_status|void|const char \*)\s*\**\s*(bte_\w+)\s*\(", text, re.M)))
+
+
+def test_header_declares_the_binding_exports():
+    assert declared_symbols() == sorted(bte.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+    out = os.popen("nm -D --defined-only %s" % bte.LIB_PATH).read()
+    for name in declared_symbols():
+        assert re.search(r"\bT %s\b" % name, out), name
+
+
+def _create(**over):
+    cfg = inputs.hotspot_2d(nx=8, ny=6, nb=2, ntheta=1, nphi=1)
+    args = dict(dim=cfg["dim"], n=cfg["n"], h=cfg["h"], C=cfg["C"], vabs=cfg["v"], tau=cfg["tau"], quad=cfg["quad"],
+                bc=cfg["bc"], T_wall=cfg["Tw"], dt=cfg["dt"], stream=0)
+    args.update(over)
+    return bte.bte_create(**args)
+
+
+@pytest.mark.parametrize("over,frag", [
+    (dict(dim=4), "dim"),
+    (dict(n=(1, 6, 1)), "extent"),
+    (dict(n=(8, 6, 3)), "inactive"),
+    (dict(dt=0.0), "dt"),
+    (dict(dt=float("nan")), "dt"),
+    (dict(tau=np.array([1e-12, -1.0])), "band 1"),
+    (dict(C=np.array([1.0, 0.0])), "band 1"),
+    (dict(bc=[3, 1, 0, 1, 3, 3]), "periodic"),
+    (dict(bc=[9, 1, 0, 1, 3, 3]), "bad type"),
+    (dict(quad=("octant", 0, 2)), "OCTANT"),
+    (dict(quad=("gl1d", 1)), "GL1D"),
+    (dict(storage=7), "storage"),
+    (dict(limiter=5), "limiter"),
+    (dict(quad=("explicit", np.array([[1.0, 0, 0], [0.0, 1, 0]]), np.array([1.0, 1.0])), bc=[2, 2, 0, 0, 3, 3]),
+     "mirror"),
+])
+def test_host_validation_rejects_bad_input(lib, over, frag):
+    with pytest.raises(bte.BteError) as ei:
+        _create(**over)
+    assert ei.value.status == bte.BTE_EINVAL
+    assert frag in str(ei.value)
+
+
+def test_null_arguments_are_rejected(lib):
+    out = ct.c_void_p()
+    assert lib.bte_create(None, None, None, None, None, ct.byref(out)) == bte.BTE_EINVAL
+    assert lib.bte_create(None, None, None, None, None, None) == bte.BTE_EINVAL
+    assert lib.bte_step(None, 1) == bte.BTE_EINVAL
+    lib.bte_destroy(None)   # ignored
+    assert b"NULL" in lib.bte_last_error(None)
