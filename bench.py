@@ -60,6 +60,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--nb", type=int, default=None, help="override the workload's band count (profiling runs)")
     a = p.parse_args()
     if a.warmup < 3:
         p.error("--warmup must be >= 3")
@@ -169,7 +170,7 @@ def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2306_14181_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".h")):
+        if name.endswith((".cu", ".cuh", ".h")):
             h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()[:12]
 
@@ -245,7 +246,7 @@ def run_reference(args):
         d.barrier()
         d.close()
         return
-    cfg = workloads()[args.workload]()
+    cfg = make_workload(args)
     from oracle import build_oracle
     build_oracle()
     c, P = oracle_for(cfg, cpu_sample_size(cfg), args.limiter)
@@ -274,6 +275,11 @@ def run_reference(args):
     d.close()
 
 
+def make_workload(args):
+    kw = {} if args.nb is None else {"nb": args.nb}
+    return workloads()[args.workload](**kw)
+
+
 def run_gb300(args):
     import numpy as np
     import torch
@@ -282,7 +288,7 @@ def run_gb300(args):
     torch.cuda.set_device(d.local)
     from paper_2306_14181_gb300 import bte, build, inputs
     build.build()
-    cfg = workloads()[args.workload]()
+    cfg = make_workload(args)
     storage = STORAGE[args.storage]
     Q = inputs.source_field(cfg)
     total = args.warmup + args.steps + args.e2e_steps + 8

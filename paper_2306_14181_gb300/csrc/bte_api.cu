@@ -1,9 +1,13 @@
 // Host side of the C ABI declared in include/bte.h: validation, the directional and band
 // tables (arXiv 2306.14181, Sec. 3.1-3.2), device buffers, and the step schedule of
 // Algorithm 2 (transient solver).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -39,7 +43,7 @@ struct bte_ctx {
     int cur = 0;
     float *TL = nullptr, *Q = nullptr, *P = nullptr;
     int G = 0;
-    float *ediff[2] = {nullptr, nullptr};
+    void *ediff[2] = {nullptr, nullptr};
     int ecur = 0;
     int wc_max = 1;
     float inv_den[6] = {0, 0, 0, 0, 0, 0};
@@ -407,19 +411,19 @@ extern "C" bte_status bte_create(const bte_grid *grid, const bte_bands *bands, c
     c->G = c->nb;
     if (c->kernel != BTE_KERNEL_GENERIC) {
         std::string why;
-        c->tiled = tiled_plan(c->dim, c->n, c->nb, c->nd, c->storage, c->bc, c->plan, why);
+        c->tiled = tiled_plan(c->dim, c->n, c->nb, c->nd, c->storage, c->limiter, c->bc, c->plan, why);
         if (!c->tiled && c->kernel == BTE_KERNEL_TILED) {
             c->err = "tiled kernel unavailable: " + why;
             return bail(BTE_EUNSUPPORTED);
         }
-        if (c->tiled) c->G = c->plan.G;
     }
-    // wall-cell slots
+    // wall-cell slots (a multiple of 8 elements keeps every e_diff row 16-byte aligned)
     c->wc_max = 1;
     for (int a = 0; a < c->dim; ++a) {
         long long m = c->ncell / c->n[a];
         if (m > c->wc_max) c->wc_max = (int)m;
     }
+    c->wc_max = (c->wc_max + 7) / 8 * 8;
     // diffuse normalisers
     for (int wl = 0; wl < 2 * c->dim; ++wl) {
         const int a = wl >> 1;
@@ -454,7 +458,13 @@ extern "C" bte_status bte_create(const bte_grid *grid, const bte_bands *bands, c
             wmom[p] = (float)(c->w[d] / c->tau[k]);
         }
         for (int wl = 0; wl < 2 * c->dim; ++wl)
-            if (c->bc[wl] == BTE_BC_ISOTHERMAL) iso[wl * c->nb + k] = (float)(c->C[k] * c->Tw[wl] / c->W);
+            if (c->bc[wl] == BTE_BC_ISOTHERMAL) {
+                // the wall emission as a value the storage format represents exactly
+                float v = (float)(c->C[k] * c->Tw[wl] / c->W);
+                if (c->storage == BTE_STORE_F16) v = b.scale * __half2float(__float2half_rn(v * b.inv_scale));
+                if (c->storage == BTE_STORE_BF16) v = b.scale * __bfloat162float(__float2bfloat16_rn(v * b.inv_scale));
+                iso[wl * c->nb + k] = v;
+            }
     }
     for (int wl = 0; wl < 2 * c->dim; ++wl) {
         const int a = wl >> 1;
@@ -475,9 +485,15 @@ extern "C" bte_status bte_create(const bte_grid *grid, const bte_bands *bands, c
     if ((st = dalloc(c, (char **)&c->e[1], c->state_bytes)) != BTE_OK) return bail(st);
     if ((st = dalloc(c, &c->TL, c->ncell)) != BTE_OK) return bail(st);
     if ((st = dalloc(c, &c->Q, c->ncell)) != BTE_OK) return bail(st);
-    if ((st = dalloc(c, &c->P, (size_t)c->G * c->ncell)) != BTE_OK) return bail(st);
+    {
+        // moment partials: band-major rows for the generic passes, segment rows for the tiled one
+        size_t np = (size_t)c->nb * c->ncell;
+        if (c->tiled) np = std::max(np, (size_t)c->plan.G * c->plan.tcells);
+        if ((st = dalloc(c, &c->P, np)) != BTE_OK) return bail(st);
+    }
     for (int i = 0; i < 2; ++i)
-        if ((st = dalloc(c, &c->ediff[i], (size_t)6 * c->nb * c->wc_max)) != BTE_OK) return bail(st);
+        if ((st = dalloc(c, (char **)&c->ediff[i], (size_t)6 * c->nb * c->wc_max * c->elem_bytes)) != BTE_OK)
+            return bail(st);
     if ((st = dalloc(c, &c->nu, nu.size())) != BTE_OK) return bail(st);
     if ((st = dalloc(c, &c->wmom, wmom.size())) != BTE_OK) return bail(st);
     if ((st = dalloc(c, &c->wdiff, wdiff.size())) != BTE_OK) return bail(st);
@@ -498,14 +514,14 @@ extern "C" bte_status bte_create(const bte_grid *grid, const bte_bands *bands, c
     if ((st = upload(c, c->d_s, c->s.data(), c->s.size())) != BTE_OK) return bail(st);
     if ((st = upload(c, c->d_v, c->v.data(), c->v.size())) != BTE_OK) return bail(st);
     if ((st = upload(c, c->d_invtau, invtau.data(), invtau.size())) != BTE_OK) return bail(st);
-    if (cudaMemset(c->ediff[0], 0, sizeof(float) * 6 * c->nb * c->wc_max) != cudaSuccess ||
-        cudaMemset(c->ediff[1], 0, sizeof(float) * 6 * c->nb * c->wc_max) != cudaSuccess) {
+    if (cudaMemset(c->ediff[0], 0, c->elem_bytes * 6 * c->nb * c->wc_max) != cudaSuccess ||
+        cudaMemset(c->ediff[1], 0, c->elem_bytes * 6 * c->nb * c->wc_max) != cudaSuccess) {
         c->err = "cudaMemset failed";
         return bail(BTE_ECUDA);
     }
     if (c->tiled) {
         std::string why;
-        if (!tiled_setup(c->plan, c->e[0], c->e[1], c->elem_bytes, why)) {
+        if (!tiled_setup(c->plan, why)) {
             c->err = "tiled kernel setup failed: " + why;
             return bail(BTE_ECUDA);
         }
@@ -593,11 +609,11 @@ extern "C" bte_status bte_step(bte_ctx *c, int nsteps) {
         cudaError_t e;
         cudaEvent_t ev;
         if (c->prof) TRY(prof_event(c, &ev));
-        if (c->tiled) e = launch_step_tiled(a, c->plan, c->cur, c->storage, c->limiter, c->stream);
+        if (c->tiled) e = launch_step_tiled(a, c->plan, c->stream);
         else e = launch_step_generic(a, c->storage, c->limiter, c->stream);
         if (e != cudaSuccess) return fail(c, BTE_ECUDA, "forward step launch: %s", cudaGetErrorString(e));
         if (c->prof) TRY(prof_event(c, &ev));
-        if (c->tiled) e = launch_finalize_tiled(a, c->plan, c->TL, c->stream);
+        if (c->tiled) e = launch_finalize_tiled(a, c->plan, c->storage, c->TL, c->stream);
         else e = launch_finalize(a, c->G, c->TL, c->stream);
         if (e != cudaSuccess) return fail(c, BTE_ECUDA, "finalize launch: %s", cudaGetErrorString(e));
         if (c->prof) TRY(prof_event(c, &ev));
@@ -608,11 +624,25 @@ extern "C" bte_status bte_step(bte_ctx *c, int nsteps) {
     return BTE_OK;
 }
 
+// Bounded device waits of the tiled kernel report through a flag; a set flag means a step
+// gave up (its output is invalid) and is returned as BTE_ETIMEOUT once.
+static bte_status check_device_flags(bte_ctx *c) {
+    if (!c->tiled || !c->plan.err) return BTE_OK;
+    int flag = 0;
+    CU(c, cudaMemcpyAsync(&flag, c->plan.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CU(c, cudaStreamSynchronize(c->stream));
+    if (flag) {
+        CU(c, cudaMemsetAsync(c->plan.err, 0, sizeof(int), c->stream));
+        return fail(c, BTE_ETIMEOUT, "a bounded wait in the tiled forward kernel gave up (flag %d)", flag);
+    }
+    return BTE_OK;
+}
+
 extern "C" bte_status bte_synchronize(bte_ctx *c) {
     if (!c) return fail(nullptr, BTE_EINVAL, "ctx is NULL");
     CU(c, cudaStreamSynchronize(c->stream));
     CU(c, cudaGetLastError());
-    return BTE_OK;
+    return check_device_flags(c);
 }
 
 extern "C" bte_status bte_lattice_temperature(bte_ctx *c, double *dTL) {

@@ -40,14 +40,14 @@ struct StepArgs {
     const float *wdiff;    // [6][nd]     w_d (s_d.n) for directions leaving through the wall, else 0
     const int *mirror;     // [3][nd]
     const BandConst *band; // [nb]
-    const float *iso;      // [6][nb]     C_k T_wall / W
+    const float *iso;      // [6][nb]     C_k T_wall / W, rounded to a value the storage format holds
     // fields
     const void *e_in;
     void *e_out;
     const float *TL;       // [ncell] T_L^n
     const float *Q;        // [ncell] or null
-    const float *ediff_in; // [6][nb][wc_max]  diffuse-wall incoming values from e^n
-    float *ediff_out;      // [6][nb][wc_max]  from e^{n+1}
+    const void *ediff_in;  // [6][nb][wc_max] diffuse-wall incoming values from e^n (storage format)
+    void *ediff_out;       // [6][nb][wc_max] from e^{n+1} (storage format)
     float *P;              // moment partials [G][ncell]
 };
 

@@ -109,7 +109,8 @@ __device__ __forceinline__ float ext_value(const StepArgs &a, const typename Cd:
         return Cd::ld(e, base + i + (long long)(wpos - c[ax]) * st, b);
     }
     if (bc == kBcIsothermal) return a.iso[wall * a.nb + k];
-    return a.ediff_in[((long long)wall * a.nb + k) * a.wc_max + wall_cell(a, ax, c)];
+    return Cd::ld(static_cast<const typename Cd::T *>(a.ediff_in),
+                  ((long long)wall * a.nb + k) * a.wc_max + wall_cell(a, ax, c), b);
 }
 
 // Diffuse walls touched by cell c: their indices into wl[], count returned.
@@ -173,7 +174,8 @@ __global__ void __launch_bounds__(256) k_step_generic(const StepArgs a) {
     a.P[(long long)k * a.ncell + i] = acc;
     for (int j = 0; j < nw; ++j) {
         const int w = wl[j];
-        a.ediff_out[((long long)w * a.nb + k) * a.wc_max + wall_cell(a, w >> 1, c)] = wacc[j] * a.inv_den[w];
+        Cd::st(static_cast<T *>(a.ediff_out), ((long long)w * a.nb + k) * a.wc_max + wall_cell(a, w >> 1, c),
+               wacc[j] * a.inv_den[w], b);
     }
 }
 
@@ -203,7 +205,8 @@ __global__ void __launch_bounds__(256) k_moment_only(const StepArgs a) {
     a.P[(long long)k * a.ncell + i] = acc;
     for (int j = 0; j < nw; ++j) {
         const int w = wl[j];
-        a.ediff_out[((long long)w * a.nb + k) * a.wc_max + wall_cell(a, w >> 1, c)] = wacc[j] * a.inv_den[w];
+        Cd::st(static_cast<T *>(a.ediff_out), ((long long)w * a.nb + k) * a.wc_max + wall_cell(a, w >> 1, c),
+               wacc[j] * a.inv_den[w], b);
     }
 }
 
@@ -338,7 +341,8 @@ __device__ double ext64(const StepArgs &a, const typename Cd::T *e, const BandCo
     const bool incoming = side == 0 ? (sa > 0.0) : (sa < 0.0);
     if (!incoming) return Cd::ld64(e, base + i + (long long)((side ? n - 1 : 0) - c[ax]) * st, b);
     if (bc == kBcIsothermal) return (double)a.iso[wall * a.nb + k];
-    return (double)a.ediff_in[((long long)wall * a.nb + k) * a.wc_max + wall_cell(a, ax, c)];
+    return Cd::ld64(static_cast<const typename Cd::T *>(a.ediff_in),
+                    ((long long)wall * a.nb + k) * a.wc_max + wall_cell(a, ax, c), b);
 }
 
 // Outward heat flow through one wall, per (wall cell j, band k): sum_d w v (s.n) e_face, with

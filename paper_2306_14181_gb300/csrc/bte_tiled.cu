@@ -1,23 +1,292 @@
-// Shared-memory tiled forward kernel of the explicit DOM step (arXiv 2306.14181, Sec. 4).
-#include "bte_tiled.h"
+// Shared-memory tiled forward kernel of the explicit DOM transient step (arXiv 2306.14181,
+// Sec. 4, Eq. disretized_transientBTE), written for sm_103a.
+//
+// Work unit: a plane-tile = one (band k, direction d) plane restricted to a spatial tile of full
+// x-rows (nx = 32 * VX cells) by TY rows (by TZ slices in 3-D).  Persistent CTAs take equal,
+// contiguous ranges of the tile-major list of plane-tiles.  In each CTA one producer warp moves
+// every box row the stencil needs into a ring of shared-memory stages with TMA bulk copies
+// (cp.async.bulk, completion counted on an mbarrier): the tile with its upwind-oriented halo
+// (two rows upwind, one downwind per axis) and, for rows outside the domain, the ghost rows of
+// Sec. 2.2 - the wrapped row (periodic), the mirrored direction's row (specular), the wall row
+// itself (outgoing directions), the diffuse-wall value row, or a constant (thermalizing wall).
+// Eight consumer warps own whole x-rows (VX cells per lane), take the x-stencil from warp
+// shuffles, stream y in registers and read z from shared memory, store e^{n+1} straight to
+// global memory and keep the T_L moment partials and the per-cell source terms in registers
+// for a whole segment (one tile and one band).  A segment's partials go to one row of P (and of
+// PW for diffuse walls); the finalize passes sum a tile's segments in a fixed order, so the
+// reduction is deterministic without atomics.  Every mbarrier wait is bounded.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "bte_tiled_kernel.cuh"
 
 namespace bte {
 
-bool tiled_plan(int, const int *, int, int, int, const int *, TiledPlan &plan, std::string &why) {
+namespace tiled {
+
+// ---- finalize passes ---------------------------------------------------------------------
+// T_L_i = (sum over the segments of i's tile, in order) / sum_k C_k / tau_k
+__global__ void __launch_bounds__(256) k_finalize_tiled(const StepArgs a, const TiledArgs p, float *TL) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.ncell) return;
+    const int nx = a.n[0], ny = a.n[1];
+    const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long long)nx * ny));
+    const int ty = y / p.ty, tz = z / p.tz;
+    const int tile = tz * p.nty + ty;
+    const int li = ((z - tz * p.tz) * p.ty + (y - ty * p.ty)) * nx + x;
+    float s = 0.f;
+    for (int g = p.tile_seg0[tile]; g < p.tile_seg0[tile + 1]; ++g) s += a.P[(size_t)g * p.tcells + li];
+    TL[i] = s * a.invD;
+}
+
+// e_diff[w][k][wall cell] = (sum over the band-k segments of the cell's tile) / sum_in w|s.n|
+template <int S>
+__global__ void __launch_bounds__(256) k_ediff_tiled(const StepArgs a, const TiledArgs p, int wall) {
+    using T = typename St<S>::T;
+    const int ax = wall >> 1, side = wall & 1;
+    const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
+    const int n0 = ax == 0 ? ny : nx;            // fastest wall-cell coordinate extent
+    const int n1 = ax == 2 ? ny : nz;
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
+    if (j >= (long long)n0 * n1) return;
+    const int ja = (int)(j % n0), jb = (int)(j / n0);
+    int x, y, z;
+    if (ax == 0) { x = side ? nx - 1 : 0; y = ja; z = jb; }
+    else if (ax == 1) { x = ja; y = side ? ny - 1 : 0; z = jb; }
+    else { x = ja; y = jb; z = side ? nz - 1 : 0; }
+    const int ty = y / p.ty, tz = z / p.tz;
+    const int tile = tz * p.nty + ty;
+    const int yl = y - ty * p.ty, zl = z - tz * p.tz;
+    const int slot = ax == 0 ? zl * p.ty + yl : (ax == 1 ? zl * nx + x : yl * nx + x);
+    float s = 0.f;
+    for (int g = p.tbs[tile * a.nb + k]; g < p.tbs[tile * a.nb + k + 1]; ++g)
+        s += p.PW[((size_t)g * p.nwd + p.wslot[wall]) * p.tw + slot];
+    const BandConst b = a.band[k];
+    static_cast<T *>(a.ediff_out)[((long long)wall * a.nb + k) * a.wc_max + j] = St<S>::enc(s * a.inv_den[wall],
+                                                                                            b.inv_scale);
+}
+
+// ---- dispatch -------------------------------------------------------------------------------
+StepKernel pick(int storage, int lim, int nx, int dim) {
+    if (storage == kStoreF32) return dim == 2 ? pick_f32_2d(lim, nx) : pick_f32_3d(lim, nx);
+    if (storage == kStoreF16) return dim == 2 ? pick_f16_2d(lim, nx) : pick_f16_3d(lim, nx);
+    return dim == 2 ? pick_bf16_2d(lim, nx) : pick_bf16_3d(lim, nx);
+}
+
+template <class V>
+bool upload_vec(V **dst, const std::vector<V> &v, std::string &why) {
+    if (cudaMalloc((void **)dst, std::max<size_t>(1, v.size()) * sizeof(V)) != cudaSuccess) {
+        cudaGetLastError();
+        why = "cudaMalloc failed";
+        return false;
+    }
+    if (!v.empty() && cudaMemcpy(*dst, v.data(), v.size() * sizeof(V), cudaMemcpyHostToDevice) != cudaSuccess) {
+        why = "cudaMemcpy failed";
+        return false;
+    }
+    return true;
+}
+
+}  // namespace tiled
+
+using namespace tiled;
+
+// ------------------------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------------------------
+bool tiled_plan(int dim, const int n[3], int nb, int nd, int storage, int limiter, const int bc[6], TiledPlan &plan,
+                std::string &why) {
     plan = TiledPlan();
-    why = "not built yet";
-    return false;
+    if (dim != 2 && dim != 3) {
+        why = "the tiled kernel covers 2-D and 3-D grids";
+        return false;
+    }
+    const int nx = n[0];
+    if (!(nx == 96 || nx == 128 || (nx == 256 && dim == 2))) {
+        why = "the tiled kernel needs nx = 96, 128 or 256 (2-D) or nx = 96 or 128 (3-D)";
+        return false;
+    }
+    const int esz = storage == kStoreF32 ? 4 : 2;
+    const int wpr = nx == 256 ? 2 : 1;
+    const int ncw = dim == 2 ? Geo<2, 1>::NCW : Geo<3, 1>::NCW;
+    const int TZ = dim == 2 ? Geo<2, 1>::TZ : Geo<3, 1>::TZ;
+    const int TY = ncw / (TZ * wpr) * kR;
+    plan.vx = nx / 32;
+    plan.dim = dim;
+    plan.ty = TY;
+    plan.tz = TZ;
+    plan.threads = (ncw + 1) * 32;
+    plan.nty = (n[1] + TY - 1) / TY;
+    plan.ntz = dim == 3 ? (n[2] + TZ - 1) / TZ : 1;
+    plan.ntiles = plan.nty * plan.ntz;
+    plan.tcells = nx * TY * TZ;
+    plan.tw = std::max(std::max(TY * TZ, nx * TZ), dim == 3 ? nx * TY : 0);
+    const size_t box = (size_t)(TY + 3) * (dim == 3 ? TZ + 3 : 1) * nx * esz;
+    plan.side_off = (int)((box + 127) / 128 * 128);
+    plan.hdr_off = plan.side_off + (int)((size_t)TY * TZ * 4 * sizeof(float));
+    plan.stage_bytes = (int)((plan.hdr_off + kHdrFloats * sizeof(float) + 127) / 128 * 128);
+    plan.stage0 = 128;
+    const size_t budget = 227 * 1024;
+    for (int w = 0; w < 2 * dim; ++w)
+        if (bc[w] == kBcDiffuse) plan.wslot[w] = plan.nwd++;
+    const size_t wall_bytes = (size_t)std::max(1, plan.nwd) * plan.tw * sizeof(float);
+    const size_t bt_bytes = (size_t)plan.tcells * sizeof(float);
+    plan.ns = 0;
+    for (int ns = 4; ns >= 2; --ns)
+        if (plan.stage0 + (size_t)ns * plan.stage_bytes + wall_bytes + bt_bytes <= budget) {
+            plan.ns = ns;
+            break;
+        }
+    if (plan.ns == 0) {
+        why = "tile does not fit in shared memory";
+        return false;
+    }
+    plan.wall_off = (int)(plan.stage0 + (size_t)plan.ns * plan.stage_bytes);
+    plan.bt_off = plan.wall_off + (int)((wall_bytes + 127) / 128 * 128);
+    plan.smem = plan.bt_off + (int)bt_bytes;
+    plan.kernel = (void *)pick(storage, limiter, nx, dim);
+    if (!plan.kernel) {
+        why = "no kernel instance";
+        return false;
+    }
+    // persistent grid: SMs x resident CTAs
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        why = "no CUDA device";
+        return false;
+    }
+    StepKernel kf = (StepKernel)plan.kernel;
+    if (cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, plan.threads, plan.smem) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        why = "kernel does not fit on an SM";
+        return false;
+    }
+    plan.nctas = sms * per_sm;
+    // static balanced schedule and its segments
+    const long long npl = (long long)nb * nd;
+    const long long T = plan.ntiles * npl;
+    if (T > 0x7fffffffLL) {
+        why = "too many plane-tiles";
+        return false;
+    }
+    if (plan.nctas > T) plan.nctas = (int)T;
+    std::vector<int> begin(plan.nctas + 1), seg_first(plan.nctas), seg_tile, seg_band;
+    for (int b = 0; b <= plan.nctas; ++b) begin[b] = (int)(T * b / plan.nctas);
+    for (int b = 0; b < plan.nctas; ++b) {
+        seg_first[b] = (int)seg_tile.size();
+        int ct = -1, ck = -1;
+        for (int t = begin[b]; t < begin[b + 1]; ++t) {
+            const int tile = (int)(t / npl), k = (int)((t % npl) / nd);
+            if (tile != ct || k != ck) {
+                seg_tile.push_back(tile);
+                seg_band.push_back(k);
+                ct = tile;
+                ck = k;
+            }
+        }
+    }
+    plan.G = (int)seg_tile.size();
+    std::vector<int> tile_seg0(plan.ntiles + 1, plan.G), tbs((size_t)plan.ntiles * nb + 1, plan.G);
+    for (int g = plan.G - 1; g >= 0; --g) {
+        tile_seg0[seg_tile[g]] = g;
+        tbs[(size_t)seg_tile[g] * nb + seg_band[g]] = g;
+    }
+    // tiles or (tile, band) pairs without segments cannot occur (every plane-tile is covered),
+    // so the "next start" of each entry is its successor's start
+    plan.h_begin = begin;
+    plan.h_seg_first = seg_first;
+    plan.h_tile_seg0 = tile_seg0;
+    plan.h_tbs = tbs;
+    plan.valid = 1;
+    return true;
 }
-bool tiled_setup(TiledPlan &, void *, void *, size_t, std::string &why) {
-    why = "not built yet";
-    return false;
+
+bool tiled_setup(TiledPlan &plan, std::string &why) {
+    if (!upload_vec(&plan.cta_begin, plan.h_begin, why) || !upload_vec(&plan.seg_first, plan.h_seg_first, why) ||
+        !upload_vec(&plan.tile_seg0, plan.h_tile_seg0, why) || !upload_vec(&plan.tbs, plan.h_tbs, why))
+        return false;
+    const size_t npw = std::max<size_t>(1, (size_t)plan.G * plan.nwd * plan.tw);
+    if (cudaMalloc((void **)&plan.PW, npw * sizeof(float)) != cudaSuccess ||
+        cudaMemset(plan.PW, 0, npw * sizeof(float)) != cudaSuccess ||
+        cudaMalloc((void **)&plan.err, sizeof(int)) != cudaSuccess || cudaMemset(plan.err, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        why = "cudaMalloc failed";
+        return false;
+    }
+    return true;
 }
-void tiled_free(TiledPlan &) {}
-cudaError_t launch_step_tiled(const StepArgs &, const TiledPlan &, int, int, int, cudaStream_t) {
-    return cudaErrorNotSupported;
+
+void tiled_free(TiledPlan &plan) {
+    void *ptrs[] = {plan.cta_begin, plan.seg_first, plan.tile_seg0, plan.tbs, plan.PW, plan.err};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    plan.cta_begin = plan.seg_first = plan.tile_seg0 = plan.tbs = nullptr;
+    plan.PW = nullptr;
+    plan.err = nullptr;
 }
-cudaError_t launch_finalize_tiled(const StepArgs &, const TiledPlan &, float *, cudaStream_t) {
-    return cudaErrorNotSupported;
+
+static TiledArgs device_args(const TiledPlan &plan) {
+    TiledArgs t;
+    memset(&t, 0, sizeof t);
+    t.cta_begin = plan.cta_begin;
+    t.seg_first = plan.seg_first;
+    t.tile_seg0 = plan.tile_seg0;
+    t.tbs = plan.tbs;
+    t.PW = plan.PW;
+    t.err = plan.err;
+    t.tw = plan.tw;
+    t.nwd = plan.nwd;
+    for (int w = 0; w < 6; ++w) t.wslot[w] = plan.wslot[w];
+    t.bt_off = plan.bt_off;
+    t.nty = plan.nty;
+    t.ntz = plan.ntz;
+    t.ns = plan.ns;
+    t.stage0 = plan.stage0;
+    t.stage_bytes = plan.stage_bytes;
+    t.side_off = plan.side_off;
+    t.hdr_off = plan.hdr_off;
+    t.ty = plan.ty;
+    t.tz = plan.tz;
+    t.wall_off = plan.wall_off;
+    t.tcells = plan.tcells;
+    return t;
+}
+
+cudaError_t launch_step_tiled(const StepArgs &a, const TiledPlan &plan, cudaStream_t s) {
+    StepKernel kf = (StepKernel)plan.kernel;
+    kf<<<plan.nctas, plan.threads, plan.smem, s>>>(a, device_args(plan));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_tiled(const StepArgs &a, const TiledPlan &plan, int storage, float *TL_out,
+                                  cudaStream_t s) {
+    const TiledArgs t = device_args(plan);
+    const unsigned nblk = (unsigned)((a.ncell + 255) / 256);
+    k_finalize_tiled<<<nblk, 256, 0, s>>>(a, t, TL_out);
+    for (int w = 0; w < 2 * plan.dim; ++w) {
+        if (a.bc[w] != kBcDiffuse) continue;
+        const int ax = w >> 1;
+        const long long nwc = ax == 0 ? (long long)a.n[1] * a.n[2]
+                                      : (ax == 1 ? (long long)a.n[0] * a.n[2] : (long long)a.n[0] * a.n[1]);
+        const dim3 g((unsigned)((nwc + 255) / 256), (unsigned)a.nb);
+        if (storage == kStoreF32) k_ediff_tiled<kStoreF32><<<g, 256, 0, s>>>(a, t, w);
+        else if (storage == kStoreF16) k_ediff_tiled<kStoreF16><<<g, 256, 0, s>>>(a, t, w);
+        else k_ediff_tiled<kStoreBF16><<<g, 256, 0, s>>>(a, t, w);
+    }
+    return cudaGetLastError();
+}
+
+int tiled_finalize_launches(const TiledPlan &plan, const int bc[6]) {
+    int n = 1;
+    for (int w = 0; w < 2 * plan.dim; ++w) n += bc[w] == kBcDiffuse;
+    return n;
 }
 
 }  // namespace bte

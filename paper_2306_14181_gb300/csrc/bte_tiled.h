@@ -2,36 +2,58 @@
 #pragma once
 
 #include <string>
+#include <vector>
 
 #include "bte_internal.h"
 
 namespace bte {
 
-// Static, balanced schedule of the tiled forward kernel.  Work is the ordered list of
-// (spatial tile, band, direction) plane-tiles, tile-major; CTA b processes the contiguous
-// range [begin[b], begin[b+1]).  A "segment" is a run of one CTA's range with one tile and one
-// band; each segment writes one moment partial row P[seg][tile cells] and, for diffuse walls,
-// one wall partial row.  The finalize pass sums, per tile, its segments in order.
-struct TiledPlan {
-    int valid = 0;
-    int G = 0;                  // number of segments (rows of P)
-    int nctas = 0;
-    int tx = 0, ty = 0, tz = 0; // tile extents (cells)
-    int ntiles = 0;
-    // device arrays
-    int *cta_begin = nullptr;   // [nctas + 1] first plane-tile of each CTA
-    int *tile_seg0 = nullptr;   // [ntiles + 1] first segment of each tile
-    int *seg_band = nullptr;    // [G] band of each segment
-    float *PW = nullptr;        // diffuse-wall partials [G][wall slots of the tile]
-    void *maps = nullptr;       // TMA descriptors (two state buffers)
+// Device-side view of the plan, passed by value to the kernels.
+struct TiledArgs {
+    const int *cta_begin;  // [nctas + 1] first plane-tile of each CTA
+    const int *seg_first;  // [nctas]     first segment of each CTA
+    const int *tile_seg0;  // [ntiles + 1] segments of tile t are [tile_seg0[t], tile_seg0[t+1])
+    const int *tbs;        // [ntiles*nb + 1] segments of (tile t, band k) start at tbs[t*nb + k]
+    float *PW;             // diffuse-wall partials [G][nwd][tw]
+    int *err;              // bounded-wait failure flags (1: consumer, 2: producer)
+    int tw;                // wall slots per wall per segment
+    int nwd;               // number of diffuse walls
+    int wslot[6];          // compact index of each diffuse wall, -1 for the others
+    int nty, ntz;          // tiles along y and z
+    int ns;                // shared-memory stages
+    int stage0, stage_bytes, side_off, hdr_off, wall_off, bt_off;  // shared-memory layout (bytes)
+    int ty, tz;            // tile extents (rows, slices)
+    int tcells;            // cells of a full tile (row length of P)
 };
 
-bool tiled_plan(int dim, const int n[3], int nb, int nd, int storage, const int bc[6], TiledPlan &plan,
+// Static, balanced schedule of the tiled forward kernel.  Work is the tile-major list of
+// (spatial tile, band, direction) plane-tiles; CTA b processes [begin[b], begin[b+1]).  A
+// segment is a run of one CTA's range with one tile and one band; each writes one row of
+// moment partials P[seg][tile cells] and one row of diffuse-wall partials PW[seg].
+struct TiledPlan {
+    int valid = 0;
+    int dim = 0, vx = 0;
+    int G = 0, nctas = 0;
+    int nty = 0, ntz = 0, ntiles = 0, tcells = 0, tw = 0;
+    int ns = 0, stage0 = 0, stage_bytes = 0, side_off = 0, hdr_off = 0, wall_off = 0, bt_off = 0, smem = 0;
+    int ty = 0, tz = 0, threads = 0;
+    int nwd = 0, wslot[6] = {-1, -1, -1, -1, -1, -1};
+    void *kernel = nullptr;
+    std::vector<int> h_begin, h_seg_first, h_tile_seg0, h_tbs;
+    int *cta_begin = nullptr, *seg_first = nullptr, *tile_seg0 = nullptr, *tbs = nullptr;
+    float *PW = nullptr;
+    int *err = nullptr;
+};
+
+// Shape check, tile geometry and the schedule (queries the current device for its SM count
+// and the kernel's occupancy).  false + reason if the grid cannot be tiled.
+bool tiled_plan(int dim, const int n[3], int nb, int nd, int storage, int limiter, const int bc[6], TiledPlan &plan,
                 std::string &why);
-bool tiled_setup(TiledPlan &plan, void *e0, void *e1, size_t elem_bytes, std::string &why);
+// Device copies of the schedule tables, the wall partials and the error flag.
+bool tiled_setup(TiledPlan &plan, std::string &why);
 void tiled_free(TiledPlan &plan);
-cudaError_t launch_step_tiled(const StepArgs &a, const TiledPlan &plan, int cur, int storage, int limiter,
-                              cudaStream_t s);
-cudaError_t launch_finalize_tiled(const StepArgs &a, const TiledPlan &plan, float *TL_out, cudaStream_t s);
+cudaError_t launch_step_tiled(const StepArgs &a, const TiledPlan &plan, cudaStream_t s);
+cudaError_t launch_finalize_tiled(const StepArgs &a, const TiledPlan &plan, int storage, float *TL_out,
+                                  cudaStream_t s);
 
 }  // namespace bte

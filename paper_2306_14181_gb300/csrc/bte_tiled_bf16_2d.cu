@@ -1,0 +1,8 @@
+// Instances of the tiled forward kernel: BF16 storage, 2-D grids.
+#include "bte_tiled_kernel.cuh"
+
+namespace bte {
+namespace tiled {
+StepKernel pick_bf16_2d(int lim, int nx) { return pick_instance<kStoreBF16, 2>(lim, nx); }
+}  // namespace tiled
+}  // namespace bte

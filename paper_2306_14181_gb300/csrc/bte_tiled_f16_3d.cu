@@ -1,0 +1,8 @@
+// Instances of the tiled forward kernel: F16 storage, 3-D grids.
+#include "bte_tiled_kernel.cuh"
+
+namespace bte {
+namespace tiled {
+StepKernel pick_f16_3d(int lim, int nx) { return pick_instance<kStoreF16, 3>(lim, nx); }
+}  // namespace tiled
+}  // namespace bte
