@@ -492,7 +492,8 @@ extern "C" bte_status bte_create(const bte_grid *grid, const bte_bands *bands, c
         if ((st = dalloc(c, &c->P, np)) != BTE_OK) return bail(st);
     }
     for (int i = 0; i < 2; ++i)
-        if ((st = dalloc(c, (char **)&c->ediff[i], (size_t)6 * c->nb * c->wc_max * c->elem_bytes)) != BTE_OK)
+        // + 16 elements: the tiled kernel copies 16-byte aligned spans that may reach past the last slot
+        if ((st = dalloc(c, (char **)&c->ediff[i], ((size_t)6 * c->nb * c->wc_max + 16) * c->elem_bytes)) != BTE_OK)
             return bail(st);
     if ((st = dalloc(c, &c->nu, nu.size())) != BTE_OK) return bail(st);
     if ((st = dalloc(c, &c->wmom, wmom.size())) != BTE_OK) return bail(st);
@@ -514,14 +515,14 @@ extern "C" bte_status bte_create(const bte_grid *grid, const bte_bands *bands, c
     if ((st = upload(c, c->d_s, c->s.data(), c->s.size())) != BTE_OK) return bail(st);
     if ((st = upload(c, c->d_v, c->v.data(), c->v.size())) != BTE_OK) return bail(st);
     if ((st = upload(c, c->d_invtau, invtau.data(), invtau.size())) != BTE_OK) return bail(st);
-    if (cudaMemset(c->ediff[0], 0, c->elem_bytes * 6 * c->nb * c->wc_max) != cudaSuccess ||
-        cudaMemset(c->ediff[1], 0, c->elem_bytes * 6 * c->nb * c->wc_max) != cudaSuccess) {
+    if (cudaMemset(c->ediff[0], 0, c->elem_bytes * (6 * c->nb * c->wc_max + 16)) != cudaSuccess ||
+        cudaMemset(c->ediff[1], 0, c->elem_bytes * (6 * c->nb * c->wc_max + 16)) != cudaSuccess) {
         c->err = "cudaMemset failed";
         return bail(BTE_ECUDA);
     }
     if (c->tiled) {
         std::string why;
-        if (!tiled_setup(c->plan, why)) {
+        if (!tiled_setup(c->plan, make_args(c), why)) {
             c->err = "tiled kernel setup failed: " + why;
             return bail(BTE_ECUDA);
         }

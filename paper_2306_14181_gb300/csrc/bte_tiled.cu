@@ -71,6 +71,27 @@ __global__ void __launch_bounds__(256) k_ediff_tiled(const StepArgs a, const Til
                                                                                             b.inv_scale);
 }
 
+// Per-plane constants the producer copies into each stage:
+// [nu_x, nu_y, nu_z, w/tau, dt/tau, s_k, 1/s_k, iso(-x), iso(+x), wdiff(w=0..5), 0]
+__global__ void k_build_headers(const StepArgs a, float *hdr) {
+    const int pl = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pl >= a.nb * a.nd) return;
+    const int k = pl / a.nd, d = pl % a.nd;
+    const BandConst b = a.band[k];
+    float *h = hdr + (size_t)pl * kHdrFloats;
+    h[0] = a.nu[3 * pl];
+    h[1] = a.nu[3 * pl + 1];
+    h[2] = a.nu[3 * pl + 2];
+    h[3] = a.wmom[pl];
+    h[4] = b.dtinv;
+    h[5] = b.scale;
+    h[6] = b.inv_scale;
+    h[7] = a.iso[0 * a.nb + k];
+    h[8] = a.iso[1 * a.nb + k];
+    for (int w = 0; w < 6; ++w) h[9 + w] = (w < 2 * a.dim && a.bc[w] == kBcDiffuse) ? a.wdiff[w * a.nd + d] : 0.f;
+    h[15] = 0.f;
+}
+
 // ---- dispatch -------------------------------------------------------------------------------
 StepKernel pick(int storage, int lim, int nx, int dim) {
     if (storage == kStoreF32) return dim == 2 ? pick_f32_2d(lim, nx) : pick_f32_3d(lim, nx);
@@ -127,8 +148,10 @@ bool tiled_plan(int dim, const int n[3], int nb, int nd, int storage, int limite
     plan.tcells = nx * TY * TZ;
     plan.tw = std::max(std::max(TY * TZ, nx * TZ), dim == 3 ? nx * TY : 0);
     const size_t box = (size_t)(TY + 3) * (dim == 3 ? TZ + 3 : 1) * nx * esz;
+    const int V = 16 / esz;  // elements in 16 bytes
+    const size_t side_bytes = ((size_t)2 * TZ * TY * V + (size_t)2 * TZ * (TY + V)) * esz;
     plan.side_off = (int)((box + 127) / 128 * 128);
-    plan.hdr_off = plan.side_off + (int)((size_t)TY * TZ * 4 * sizeof(float));
+    plan.hdr_off = plan.side_off + (int)((side_bytes + 15) / 16 * 16);
     plan.stage_bytes = (int)((plan.hdr_off + kHdrFloats * sizeof(float) + 127) / 128 * 128);
     plan.stage0 = 128;
     const size_t budget = 227 * 1024;
@@ -138,7 +161,7 @@ bool tiled_plan(int dim, const int n[3], int nb, int nd, int storage, int limite
     const size_t bt_bytes = (size_t)plan.tcells * sizeof(float);
     plan.ns = 0;
     for (int ns = 4; ns >= 2; --ns)
-        if (plan.stage0 + (size_t)ns * plan.stage_bytes + wall_bytes + bt_bytes <= budget) {
+        if (plan.stage0 + (size_t)ns * plan.stage_bytes + wall_bytes + 2 * bt_bytes + 128 <= budget) {
             plan.ns = ns;
             break;
         }
@@ -148,7 +171,8 @@ bool tiled_plan(int dim, const int n[3], int nb, int nd, int storage, int limite
     }
     plan.wall_off = (int)(plan.stage0 + (size_t)plan.ns * plan.stage_bytes);
     plan.bt_off = plan.wall_off + (int)((wall_bytes + 127) / 128 * 128);
-    plan.smem = plan.bt_off + (int)bt_bytes;
+    plan.acc_off = plan.bt_off + (int)((bt_bytes + 127) / 128 * 128);
+    plan.smem = plan.acc_off + (int)bt_bytes;
     plan.kernel = (void *)pick(storage, limiter, nx, dim);
     if (!plan.kernel) {
         why = "no kernel instance";
@@ -208,28 +232,35 @@ bool tiled_plan(int dim, const int n[3], int nb, int nd, int storage, int limite
     return true;
 }
 
-bool tiled_setup(TiledPlan &plan, std::string &why) {
+bool tiled_setup(TiledPlan &plan, const StepArgs &a, std::string &why) {
     if (!upload_vec(&plan.cta_begin, plan.h_begin, why) || !upload_vec(&plan.seg_first, plan.h_seg_first, why) ||
         !upload_vec(&plan.tile_seg0, plan.h_tile_seg0, why) || !upload_vec(&plan.tbs, plan.h_tbs, why))
         return false;
     const size_t npw = std::max<size_t>(1, (size_t)plan.G * plan.nwd * plan.tw);
     if (cudaMalloc((void **)&plan.PW, npw * sizeof(float)) != cudaSuccess ||
         cudaMemset(plan.PW, 0, npw * sizeof(float)) != cudaSuccess ||
-        cudaMalloc((void **)&plan.err, sizeof(int)) != cudaSuccess || cudaMemset(plan.err, 0, sizeof(int)) != cudaSuccess) {
+        cudaMalloc((void **)&plan.err, sizeof(int)) != cudaSuccess || cudaMemset(plan.err, 0, sizeof(int)) != cudaSuccess ||
+        cudaMalloc((void **)&plan.hdr, (size_t)a.nb * a.nd * kHdrFloats * sizeof(float)) != cudaSuccess) {
         cudaGetLastError();
         why = "cudaMalloc failed";
+        return false;
+    }
+    k_build_headers<<<(a.nb * a.nd + 127) / 128, 128>>>(a, plan.hdr);
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+        why = "header build failed";
         return false;
     }
     return true;
 }
 
 void tiled_free(TiledPlan &plan) {
-    void *ptrs[] = {plan.cta_begin, plan.seg_first, plan.tile_seg0, plan.tbs, plan.PW, plan.err};
+    void *ptrs[] = {plan.cta_begin, plan.seg_first, plan.tile_seg0, plan.tbs, plan.PW, plan.err, plan.hdr};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     plan.cta_begin = plan.seg_first = plan.tile_seg0 = plan.tbs = nullptr;
     plan.PW = nullptr;
     plan.err = nullptr;
+    plan.hdr = nullptr;
 }
 
 static TiledArgs device_args(const TiledPlan &plan) {
@@ -240,11 +271,13 @@ static TiledArgs device_args(const TiledPlan &plan) {
     t.tile_seg0 = plan.tile_seg0;
     t.tbs = plan.tbs;
     t.PW = plan.PW;
+    t.hdr = plan.hdr;
     t.err = plan.err;
     t.tw = plan.tw;
     t.nwd = plan.nwd;
     for (int w = 0; w < 6; ++w) t.wslot[w] = plan.wslot[w];
     t.bt_off = plan.bt_off;
+    t.acc_off = plan.acc_off;
     t.nty = plan.nty;
     t.ntz = plan.ntz;
     t.ns = plan.ns;

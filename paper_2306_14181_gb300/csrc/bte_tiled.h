@@ -15,13 +15,14 @@ struct TiledArgs {
     const int *tile_seg0;  // [ntiles + 1] segments of tile t are [tile_seg0[t], tile_seg0[t+1])
     const int *tbs;        // [ntiles*nb + 1] segments of (tile t, band k) start at tbs[t*nb + k]
     float *PW;             // diffuse-wall partials [G][nwd][tw]
+    const float *hdr;      // per-plane constants [nb*nd][16] (see tiled_build_headers)
     int *err;              // bounded-wait failure flags (1: consumer, 2: producer)
     int tw;                // wall slots per wall per segment
     int nwd;               // number of diffuse walls
     int wslot[6];          // compact index of each diffuse wall, -1 for the others
     int nty, ntz;          // tiles along y and z
     int ns;                // shared-memory stages
-    int stage0, stage_bytes, side_off, hdr_off, wall_off, bt_off;  // shared-memory layout (bytes)
+    int stage0, stage_bytes, side_off, hdr_off, wall_off, bt_off, acc_off;  // shared-memory layout (bytes)
     int ty, tz;            // tile extents (rows, slices)
     int tcells;            // cells of a full tile (row length of P)
 };
@@ -35,13 +36,14 @@ struct TiledPlan {
     int dim = 0, vx = 0;
     int G = 0, nctas = 0;
     int nty = 0, ntz = 0, ntiles = 0, tcells = 0, tw = 0;
-    int ns = 0, stage0 = 0, stage_bytes = 0, side_off = 0, hdr_off = 0, wall_off = 0, bt_off = 0, smem = 0;
+    int ns = 0, stage0 = 0, stage_bytes = 0, side_off = 0, hdr_off = 0, wall_off = 0, bt_off = 0, acc_off = 0, smem = 0;
     int ty = 0, tz = 0, threads = 0;
     int nwd = 0, wslot[6] = {-1, -1, -1, -1, -1, -1};
     void *kernel = nullptr;
     std::vector<int> h_begin, h_seg_first, h_tile_seg0, h_tbs;
     int *cta_begin = nullptr, *seg_first = nullptr, *tile_seg0 = nullptr, *tbs = nullptr;
     float *PW = nullptr;
+    float *hdr = nullptr;
     int *err = nullptr;
 };
 
@@ -49,8 +51,9 @@ struct TiledPlan {
 // and the kernel's occupancy).  false + reason if the grid cannot be tiled.
 bool tiled_plan(int dim, const int n[3], int nb, int nd, int storage, int limiter, const int bc[6], TiledPlan &plan,
                 std::string &why);
-// Device copies of the schedule tables, the wall partials and the error flag.
-bool tiled_setup(TiledPlan &plan, std::string &why);
+// Device copies of the schedule tables, the wall partials and the error flag, and the per-plane
+// constant records the producer copies into each stage (built from the step tables in a).
+bool tiled_setup(TiledPlan &plan, const StepArgs &a, std::string &why);
 void tiled_free(TiledPlan &plan);
 cudaError_t launch_step_tiled(const StepArgs &a, const TiledPlan &plan, cudaStream_t s);
 cudaError_t launch_finalize_tiled(const StepArgs &a, const TiledPlan &plan, int storage, float *TL_out,

@@ -43,20 +43,64 @@ template <> struct St<kStoreBF16> {
     static __device__ __forceinline__ T enc(float v, float inv) { return __float2bfloat16_rn(v * inv); }
 };
 
-// Limiter with an approximate division; pairs with ab below 1e-30 get a zero slope, which
-// keeps the denominator a normal number.
+// PTX approximate reciprocal (one MUFU operation, no special-case branches).
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Limiter; the van Albada ratio uses the approximate reciprocal and a select (pairs with
+// ab <= 1e-30 get a zero slope, so a selected denominator is always a normal number).
 template <int LIM> __device__ __forceinline__ float lim(float a, float b);
 template <> __device__ __forceinline__ float lim<kLimFirst>(float, float) { return 0.f; }
 template <> __device__ __forceinline__ float lim<kLimMinmod>(float a, float b) {
-    return (a * b > 0.f) ? (fabsf(a) < fabsf(b) ? a : b) : 0.f;
+    const float m = fabsf(a) < fabsf(b) ? a : b;
+    return a * b > 0.f ? m : 0.f;
 }
 template <> __device__ __forceinline__ float lim<kLimVanAlbada>(float a, float b) {
     const float ab = a * b;
-    return ab > 1e-30f ? __fdividef(ab * (a + b), fmaf(a, a, b * b)) : 0.f;
+    const float r = ab * (a + b) * rcp_approx(fmaf(a, a, b * b));
+    return ab > 1e-30f ? r : 0.f;
 }
 // face value e_m + L(e_m - e_l, e_r - e_m) / 2 at the upwind cell m
 template <int LIM> __device__ __forceinline__ float face(float ul, float um, float ur) {
     return fmaf(0.5f, lim<LIM>(um - ul, ur - um), um);
+}
+
+// The same for two independent faces with the packed FP32x2 instructions of sm_100+ (each
+// lane-pair operation rounds exactly like the scalar one).
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+
+template <int LIM> __device__ __forceinline__ float2 face2(float2 ul, float2 um, float2 ur);
+template <> __device__ __forceinline__ float2 face2<kLimFirst>(float2, float2 um, float2) { return um; }
+template <> __device__ __forceinline__ float2 face2<kLimMinmod>(float2 ul, float2 um, float2 ur) {
+    const float2 a = sub2(um, ul), b = sub2(ur, um);
+    const float2 L = make_float2(lim<kLimMinmod>(a.x, b.x), lim<kLimMinmod>(a.y, b.y));
+    return __ffma2_rn(make_float2(0.5f, 0.5f), L, um);
+}
+template <> __device__ __forceinline__ float2 face2<kLimVanAlbada>(float2 ul, float2 um, float2 ur) {
+    const float2 a = sub2(um, ul), b = sub2(ur, um);
+    const float2 ab = __fmul2_rn(a, b);
+    const float2 num = __fmul2_rn(ab, __fadd2_rn(a, b));
+    const float2 den = __ffma2_rn(a, a, __fmul2_rn(b, b));
+    float2 L = __fmul2_rn(num, make_float2(rcp_approx(den.x), rcp_approx(den.y)));
+    L.x = ab.x > 1e-30f ? L.x : 0.f;
+    L.y = ab.y > 1e-30f ? L.y : 0.f;
+    return __ffma2_rn(make_float2(0.5f, 0.5f), L, um);
+}
+
+// out[i] = face(ul[i], um[i], ur[i]) for i < N, two at a time
+template <int LIM, int N>
+__device__ __forceinline__ void faces(const float *ul, const float *um, const float *ur, float *out) {
+    #pragma unroll
+    for (int i = 0; i + 1 < N; i += 2) {
+        const float2 f = face2<LIM>(make_float2(ul[i], ul[i + 1]), make_float2(um[i], um[i + 1]),
+                                    make_float2(ur[i], ur[i + 1]));
+        out[i] = f.x;
+        out[i + 1] = f.y;
+    }
+    if constexpr (N & 1) out[N - 1] = face<LIM>(ul[N - 1], um[N - 1], ur[N - 1]);
 }
 
 // ---- PTX wrappers: mbarrier, bulk copy, timers ---------------------------------------------
@@ -102,6 +146,9 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                      su32(dst)),
                  "l"(src), "r"(bytes), "r"(su32(bar))
                  : "memory");
+}
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 template <int NCW>
@@ -218,16 +265,43 @@ __device__ __forceinline__ int classify_row(const StepArgs &a, const PT &q, int 
     return kCopy;
 }
 
+// Shared-memory side arrays of a stage for the x-wall ghosts (storage format, bulk-copied):
+//   spec[wall][TZ][TY][V]   16 bytes of the mirrored direction's row at the wall (specular)
+//   dcol[wall][TZ][TY + V]  the diffuse-wall values of the tile's rows (from a 16-byte aligned start)
+// with V = 16 / sizeof(T) elements.
+template <int S, int WPR, int DIM> struct Side {
+    using T = typename St<S>::T;
+    static constexpr int V = 16 / (int)sizeof(T);
+    static constexpr int TY = Geo<DIM, WPR>::TY, TZ = Geo<DIM, WPR>::TZ, TYP = TY + V;
+    static constexpr int spec_elems = 2 * TZ * TY * V;
+    static constexpr int bytes = (spec_elems + 2 * TZ * TYP) * (int)sizeof(T);
+    static __device__ __forceinline__ T *spec(char *side, int sd, int zl, int yl) {
+        return reinterpret_cast<T *>(side) + ((sd * TZ + zl) * TY + yl) * V;
+    }
+    static __device__ __forceinline__ T *dcol(char *side, int sd, int zl) {
+        return reinterpret_cast<T *>(side) + spec_elems + (sd * TZ + zl) * TYP;
+    }
+};
+
+// element index of the first diffuse value of the tile's rows at slice z, and its offset from
+// the 16-byte aligned start the copy uses
+__device__ __forceinline__ long long dcol_src(const StepArgs &a, int sd, int k, int z, int y0) {
+    return ((long long)sd * a.nb + k) * a.wc_max + (long long)z * a.n[1] + y0;
+}
+
 template <int S, int VL, int WPR, int DIM>
 __device__ void producer(const StepArgs &a, const TiledArgs &p, char *smem, uint64_t *full, uint64_t *empty, int t0,
                          int t1) {
     using T = typename St<S>::T;
+    using SD = Side<S, WPR, DIM>;
     constexpr int NX = 32 * VL * WPR, TY = Geo<DIM, WPR>::TY;
     constexpr uint32_t rowb = NX * sizeof(T);
+    constexpr int V = SD::V;
     const int lane = threadIdx.x & 31;
-    const int ny = a.n[1];
+    const int ny = a.n[1], nz = a.n[2];
     const T *e = static_cast<const T *>(a.e_in);
     const T *ed = static_cast<const T *>(a.ediff_in);
+    const int bx[2] = {a.bc[0], a.bc[1]};
     int i = 0;
     for (int t = t0; t < t1; ++t, ++i) {
         const int s = i % p.ns;
@@ -240,98 +314,99 @@ __device__ void producer(const StepArgs &a, const TiledArgs &p, char *smem, uint
         const float nuz = DIM == 3 ? a.nu[3 * q.plane + 2] : 0.f;
         const int ybox0 = q.y0 - (nuy > 0.f ? 2 : 1);
         const int zbox0 = DIM == 3 ? q.z0 - (nuz > 0.f ? 2 : 1) : 0;
-        const int nrow = (q.nyt + 3) * (DIM == 3 ? q.nzt + 3 : 1);
+        const int nry = q.nyt + 3;
+        const int nrow = nry * (DIM == 3 ? q.nzt + 3 : 1);
         char *stage = smem + p.stage0 + (size_t)s * p.stage_bytes;
-        const BandConst b = a.band[q.k];
+        char *side = stage + p.side_off;
+        const int ncore = q.nyt * q.nzt;
+        const bool spec[2] = {bx[0] == kBcSpecular, bx[1] == kBcSpecular};
+        const bool dif[2] = {bx[0] == kBcDiffuse && nux > 0.f, bx[1] == kBcDiffuse && nux < 0.f};
         // bytes the bulk copies of this stage deliver
         uint32_t bytes = 0;
         for (int r = lane; r < nrow; r += 32) {
             const T *src;
             float cv;
-            if (classify_row<S, NX, DIM>(a, q, ybox0 + r % (q.nyt + 3), zbox0 + r / (q.nyt + 3), nuy, nuz, src, cv) ==
-                kCopy)
-                bytes += rowb;
+            if (classify_row<S, NX, DIM>(a, q, ybox0 + r % nry, zbox0 + r / nry, nuy, nuz, src, cv) == kCopy) bytes += rowb;
+        }
+        for (int sd = 0; sd < 2; ++sd) {
+            if (spec[sd])
+                for (int j = lane; j < ncore; j += 32) bytes += 16;
+            if (dif[sd])
+                for (int zl = lane; zl < q.nzt; zl += 32) {
+                    const long long s0 = dcol_src(a, sd, q.k, q.z0 + zl, q.y0);
+                    const int off = (int)(s0 & (V - 1));
+                    bytes += (uint32_t)(((off + q.nyt + V - 1) / V) * 16);
+                }
         }
         bytes = __reduce_add_sync(0xffffffffu, bytes);
-        if (lane == 0) mbar_expect_tx(&full[s], bytes);
+        if (lane == 0) mbar_expect_tx(&full[s], bytes + 64);
         __syncwarp();
+        // per-plane constants (64 bytes, prepared on the host side)
+        if (lane == 0) bulk_g2s(stage + p.hdr_off, p.hdr + (size_t)q.plane * kHdrFloats, 64, &full[s]);
         for (int base = 0; base < nrow; base += 32) {
             const int r = base + lane;
             const T *src = nullptr;
             float cv = 0.f;
-            const int kind = r < nrow ? classify_row<S, NX, DIM>(a, q, ybox0 + r % (q.nyt + 3),
-                                                                   zbox0 + r / (q.nyt + 3), nuy, nuz, src, cv)
+            const int kind = r < nrow ? classify_row<S, NX, DIM>(a, q, ybox0 + r % nry, zbox0 + r / nry, nuy, nuz, src, cv)
                                       : kSkip;
             // box rows are stored with the full-tile stride: row (ry, rz) at (rz (TY + 3) + ry) NX
             if (kind == kCopy)
-                bulk_g2s(reinterpret_cast<T *>(stage) + ((size_t)(r / (q.nyt + 3)) * (TY + 3) + r % (q.nyt + 3)) * NX,
-                         src, rowb, &full[s]);
+                bulk_g2s(reinterpret_cast<T *>(stage) + ((size_t)(r / nry) * (TY + 3) + r % nry) * NX, src, rowb, &full[s]);
             // thermalizing-wall rows: the whole warp writes each one, 16 bytes per lane and store
             unsigned m = __ballot_sync(0xffffffffu, kind == kConst);
             while (m) {
                 const int j = __ffs(m) - 1;
                 m &= m - 1;
                 const float v = __shfl_sync(0xffffffffu, cv, j);
-                const T h = St<S>::enc(v, b.inv_scale);
-                T pack[16 / sizeof(T)];
+                const T h = St<S>::enc(v, a.band[q.k].inv_scale);
+                T pack[V];
                 #pragma unroll
-                for (int c = 0; c < (int)(16 / sizeof(T)); ++c) pack[c] = h;
+                for (int c = 0; c < V; ++c) pack[c] = h;
                 const int rj = base + j;
-                uint4 *row = reinterpret_cast<uint4 *>(reinterpret_cast<T *>(stage) +
-                                                       ((size_t)(rj / (q.nyt + 3)) * (TY + 3) + rj % (q.nyt + 3)) * NX);
+                uint4 *row = reinterpret_cast<uint4 *>(reinterpret_cast<T *>(stage) + ((size_t)(rj / nry) * (TY + 3) + rj % nry) * NX);
                 for (int c = lane; c < (int)(rowb / 16); c += 32) row[c] = *reinterpret_cast<const uint4 *>(pack);
             }
         }
-        // x-wall ghosts that are not in the tile: specular (mirror plane at x = 0, 1 / nx-1, nx-2)
-        // and diffuse incoming values; four floats per core row
-        const int bx0 = a.bc[0], bx1 = a.bc[1];
-        if (bx0 == kBcSpecular || bx0 == kBcDiffuse || bx1 == kBcSpecular || bx1 == kBcDiffuse) {
-            float *side = reinterpret_cast<float *>(stage + p.side_off);
-            for (int j = lane; j < q.nyt * q.nzt; j += 32) {
-                const int yl = j % q.nyt, zl = j / q.nyt;
-                const int y = q.y0 + yl, z = q.z0 + zl;
-                const long long rowoff = ((long long)z * ny + y) * NX;
-                float g[4] = {0.f, 0.f, 0.f, 0.f};
-                #pragma unroll
-                for (int sd = 0; sd < 2; ++sd) {
-                    const int bc = sd ? bx1 : bx0;
-                    if (bc == kBcSpecular) {
-                        const long long mb = ((long long)q.k * a.nd + a.mirror[q.d]) * a.ncell + rowoff;
-                        g[2 * sd] = St<S>::dec(e[mb + (sd ? NX - 1 : 0)], b.scale);
-                        g[2 * sd + 1] = St<S>::dec(e[mb + (sd ? NX - 2 : 1)], b.scale);
-                    } else if (bc == kBcDiffuse && (sd ? nux < 0.f : nux > 0.f)) {
-                        const float v = St<S>::dec(ed[((long long)sd * a.nb + q.k) * a.wc_max + (long long)z * ny + y], b.scale);
-                        g[2 * sd] = g[2 * sd + 1] = v;
-                    }
+        // x-wall ghosts outside the tile: 16 bytes of the mirrored direction's row (specular), or
+        // the diffuse values of the tile's rows (incoming directions only)
+        for (int sd = 0; sd < 2; ++sd) {
+            if (spec[sd]) {
+                const long long mb = ((long long)q.k * a.nd + a.mirror[q.d]) * a.ncell + (sd ? NX - V : 0);
+                for (int j = lane; j < ncore; j += 32) {
+                    const int yl = j % q.nyt, zl = j / q.nyt;
+                    bulk_g2s(SD::spec(side, sd, zl, yl), e + mb + ((long long)(q.z0 + zl) * ny + q.y0 + yl) * NX, 16, &full[s]);
                 }
-                *reinterpret_cast<float4 *>(side + ((size_t)zl * TY + yl) * 4) = make_float4(g[0], g[1], g[2], g[3]);
             }
-        }
-        // per-plane constants for the consumers
-        if (lane == 0) {
-            float *hd = reinterpret_cast<float *>(stage + p.hdr_off);
-            hd[0] = nux;
-            hd[1] = nuy;
-            hd[2] = nuz;
-            hd[3] = a.wmom[q.plane];
-            hd[4] = b.dtinv;
-            hd[5] = b.scale;
-            hd[6] = b.inv_scale;
-            hd[7] = a.iso[0 * a.nb + q.k];
-            hd[8] = a.iso[1 * a.nb + q.k];
-            #pragma unroll
-            for (int w = 0; w < 6; ++w) hd[9 + w] = (w < 2 * DIM && a.bc[w] == kBcDiffuse) ? a.wdiff[w * a.nd + q.d] : 0.f;
-            hd[15] = 0.f;
+            if (dif[sd])
+                for (int zl = lane; zl < q.nzt; zl += 32) {
+                    const long long s0 = dcol_src(a, sd, q.k, q.z0 + zl, q.y0);
+                    const int off = (int)(s0 & (V - 1));
+                    bulk_g2s(SD::dcol(side, sd, zl), ed + (s0 - off), (uint32_t)(((off + q.nyt + V - 1) / V) * 16), &full[s]);
+                }
         }
         mbar_arrive(&full[s]);
+        // pull the rows of a later plane-tile towards L2 (no shared memory involved)
+        const int tp = t + p.ns;
+        if (tp < t1) {
+            const PT qp = decode<DIM, WPR>(a, p, tp);
+            const float pnuy = a.nu[3 * qp.plane + 1];
+            const float pnuz = DIM == 3 ? a.nu[3 * qp.plane + 2] : 0.f;
+            const int ylo = max(qp.y0 - (pnuy > 0.f ? 2 : 1), 0), yhi = min(qp.y0 + qp.nyt + (pnuy > 0.f ? 1 : 2), ny);
+            const int zlo = DIM == 3 ? max(qp.z0 - (pnuz > 0.f ? 2 : 1), 0) : 0;
+            const int zhi = DIM == 3 ? min(qp.z0 + qp.nzt + (pnuz > 0.f ? 1 : 2), nz) : 1;
+            for (int z = zlo + lane; z < zhi; z += 32)
+                bulk_prefetch_l2(e + (long long)qp.plane * a.ncell + ((long long)z * ny + ylo) * NX, (uint32_t)(yhi - ylo) * rowb);
+        }
     }
 }
 
 // ---- consumer warps -----------------------------------------------------------------------
-template <int S, int LIM, int VL, int WPR, int DIM, int SY>
+// Where an end lane of a warp takes its two x-neighbours from (besides the plain shuffle).
+enum { kGhShfl = 0, kGhSmem = 1, kGhSpec = 2, kGhDiff = 3, kGhConst = 4, kGhOwn = 5 };
+
+template <int S, int LIM, int VL, int WPR, int DIM>
 __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs &p, const PT &q, const char *stage,
-                                             int zl, int rb, int half, float (&acc)[kR][VL], const float *btsm,
-                                             float *wsm) {
+                                             int zl, int rb, int half, float *accsm, const float *btsm, float *wsm) {
     using T = typename St<S>::T;
     constexpr int NX = 32 * VL * WPR, TY = Geo<DIM, WPR>::TY;
     const int lane = threadIdx.x & 31, x0 = (half * 32 + lane) * VL;
@@ -341,46 +416,82 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
     const float nux = h0.x, nuy = h0.y, nuz = h0.z, wm = h0.w;
     const float dtinv = hd[4], sc = hd[5], isc = hd[6];
     const float any = fabsf(nuy), anz = fabsf(nuz);
-    const int sz = nuz > 0.f ? 1 : -1;
-    const int ybox0 = q.y0 - (SY > 0 ? 2 : 1);
-    const int zbox0 = DIM == 3 ? q.z0 - (nuz > 0.f ? 2 : 1) : 0;
+    const int sy = nuy > 0.f ? 1 : -1, sz = nuz > 0.f ? 1 : -1;
+    const int nrows = min(kR, q.nyt - rb);
+    const int yl0 = sy > 0 ? rb : rb + nrows - 1;  // first row in streaming (upwind-to-downwind) order
+    const int ybox0 = q.y0 - (sy > 0 ? 2 : 1);
+    const int zbox0 = DIM == 3 ? q.z0 - (sz > 0 ? 2 : 1) : 0;
     const int z = q.z0 + zl;
-    const int rz = z - zbox0;
     const T *box = reinterpret_cast<const T *>(stage);
-    const float *side = reinterpret_cast<const float *>(stage + p.side_off);
-    auto rowbase = [&](int y, int zr) { return box + ((size_t)zr * (TY + 3) + (y - ybox0)) * NX; };
-    const int bx0 = a.bc[0], bx1 = a.bc[1];
-    const bool left_edge = lane == 0, right_edge = lane == 31;
-    const bool xlo = left_edge && half == 0, xhi = right_edge && half == WPR - 1;
-    T *eo = static_cast<T *>(a.e_out) + (long long)q.plane * a.ncell;
+    const int dy = sy * NX;                    // next row in streaming order (elements)
+    const int dz = sz * (TY + 3) * NX;         // next slice downwind (elements)
+    int o = ((z - zbox0) * (TY + 3) + (q.y0 + yl0 - ybox0)) * NX;  // row start in the box
+    int c = (zl * TY + yl0) * NX + x0;         // this lane's cells in the tile arrays
+    T *eo = static_cast<T *>(a.e_out) + (long long)q.plane * a.ncell + ((long long)z * ny + q.y0 + yl0) * NX + x0;
+    using SD = Side<S, WPR, DIM>;
+    char *side = const_cast<char *>(stage) + p.side_off;
+    // x ghosts of the two end lanes, decided once per plane-tile
+    const bool xlo = lane == 0 && half == 0, xhi = lane == 31 && half == WPR - 1;
+    // Ghost sources of the two end lanes, decided once per plane-tile.  Every lane then reads two
+    // values g0 (next to its end) and g1 (second ghost) per row from gptr + j * gstep at gi0 / gi1
+    // (other lanes read their own cells), and the mode picks between them, a constant and the
+    // lane's own end cell -- no divergent code in the row loop.
+    int gmode = kGhShfl;
+    const T *gptr = box + o + x0;
+    int gstep = dy, gi0 = 0, gi1 = 0;
+    float gc = 0.f;
+    if (lane == 0 || lane == 31) {
+        const int sd = lane == 0 ? 0 : 1;
+        const int bc = a.bc[sd];
+        const bool wall_lane = sd == 0 ? xlo : xhi;
+        const bool leaving = sd == 0 ? nux <= 0.f : nux >= 0.f;
+        gmode = kGhSmem;
+        if (!wall_lane || bc == kBcPeriodic) {
+            const int gi = !wall_lane ? (sd == 0 ? x0 - 2 : x0 + VL) : (sd == 0 ? NX - 2 : 0);
+            gptr = box + o + gi;
+            gi0 = sd == 0 ? 1 : 0;
+            gi1 = sd == 0 ? 0 : 1;
+        } else if (bc == kBcSpecular) {
+            gptr = SD::spec(side, sd, zl, yl0);
+            gstep = sy * SD::V;
+            gi0 = sd == 0 ? 0 : SD::V - 1;
+            gi1 = sd == 0 ? 1 : SD::V - 2;
+        } else if (leaving) {
+            gmode = kGhOwn;
+        } else if (bc == kBcIsothermal) {
+            gmode = kGhConst;
+            gc = hd[7 + sd];
+        } else {
+            gptr = SD::dcol(side, sd, zl) + (int)(dcol_src(a, sd, q.k, z, q.y0) & (SD::V - 1)) + yl0;
+            gstep = sy;
+        }
+    }
+    // diffuse-wall sums of Eq. (diff_bound) for the next step: cells next to a diffuse wall add
+    // w_d (s_d.n) e for the directions leaving through it (weight 0 otherwise)
+    const float wx = xlo ? hd[9] : (xhi ? hd[10] : 0.f);
+    float *wxp = wsm + (xlo ? max(p.wslot[0], 0) : max(p.wslot[1], 0)) * p.tw + zl * TY + yl0;
+    const float wz = DIM == 3 ? (z == 0 ? hd[13] : (z == nz - 1 ? hd[14] : 0.f)) : 0.f;
+    float *wzp = wsm + (z == 0 ? max(p.wslot[4], 0) : max(p.wslot[5], 0)) * p.tw + yl0 * NX + x0;
+    const float wy0 = hd[11], wy1 = hd[12];
+    float *wy0p = wsm + max(p.wslot[2], 0) * p.tw + zl * NX + x0;
+    float *wy1p = wsm + max(p.wslot[3], 0) * p.tw + zl * NX + x0;
 
     float wm2[VL], wm1[VL], w0[VL], wp1[VL], fin[VL];
-    bool started = false;
+    ld_row<S, VL>(wm2, box + o - 2 * dy + x0, sc);
+    ld_row<S, VL>(wm1, box + o - dy + x0, sc);
+    ld_row<S, VL>(w0, box + o + x0, sc);
+    faces<LIM, VL>(wm2, wm1, w0, fin);
     #pragma unroll
-    for (int jj = 0; jj < kR; ++jj) {
-        const int r = SY > 0 ? jj : kR - 1 - jj;  // row of the warp, compile-time after unrolling
-        const int yl = rb + r;
-        if (yl >= q.nyt) continue;  // ragged tile (uniform across the warp)
-        const int y = q.y0 + yl;
-        const T *rb0 = rowbase(y, rz);
-        if (!started) {
-            ld_row<S, VL>(wm2, rowbase(y - 2 * SY, rz) + x0, sc);
-            ld_row<S, VL>(wm1, rowbase(y - SY, rz) + x0, sc);
-            ld_row<S, VL>(w0, rb0 + x0, sc);
-            #pragma unroll
-            for (int v = 0; v < VL; ++v) fin[v] = face<LIM>(wm2[v], wm1[v], w0[v]);
-            started = true;
-        }
-        ld_row<S, VL>(wp1, rowbase(y + SY, rz) + x0, sc);
+    for (int j = 0; j < kR; ++j) {
+        if (j >= nrows) break;
+        const int y = q.y0 + yl0 + j * sy;
+        ld_row<S, VL>(wp1, box + o + dy + x0, sc);
         float div[VL], fout[VL];
-        // y: out face between y and y + SY (upwind y); the in face is the previous row's out face
+        // y: out face between y and y + sy (upwind y); the in face is the previous row's out face
+        faces<LIM, VL>(wm1, w0, wp1, fout);
         #pragma unroll
-        for (int v = 0; v < VL; ++v) {
-            fout[v] = face<LIM>(wm1[v], w0[v], wp1[v]);
-            div[v] = any * (fout[v] - fin[v]);
-        }
-        // x: neighbours from the adjacent lanes; at a warp's two ends from shared memory (the
-        // neighbouring warp's cells, or the periodic wrap), at the domain walls the ghosts
+        for (int v = 0; v < VL; ++v) div[v] = any * (fout[v] - fin[v]);
+        // x: neighbours from the adjacent lanes, the end lanes as decided above
         float ex[VL + 4];
         #pragma unroll
         for (int v = 0; v < VL; ++v) ex[v + 2] = w0[v];
@@ -388,69 +499,45 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
         ex[1] = __shfl_sync(0xffffffffu, w0[VL - 1], (lane + 31) & 31);
         ex[VL + 2] = __shfl_sync(0xffffffffu, w0[0], (lane + 1) & 31);
         ex[VL + 3] = __shfl_sync(0xffffffffu, w0[1], (lane + 1) & 31);
-        if (left_edge) {
-            if (!xlo) {
-                ex[0] = St<S>::dec(rb0[x0 - 2], sc);
-                ex[1] = St<S>::dec(rb0[x0 - 1], sc);
-            } else if (bx0 == kBcPeriodic) {
-                ex[0] = St<S>::dec(rb0[NX - 2], sc);
-                ex[1] = St<S>::dec(rb0[NX - 1], sc);
-            } else {
-                const float *g = side + ((size_t)zl * TY + yl) * 4;
-                if (bx0 == kBcSpecular) { ex[1] = g[0]; ex[0] = g[1]; }
-                else if (nux <= 0.f) { ex[1] = ex[0] = w0[0]; }
-                else if (bx0 == kBcIsothermal) { ex[1] = ex[0] = hd[7]; }
-                else { ex[1] = ex[0] = g[0]; }
-            }
-        }
-        if (right_edge) {
-            if (!xhi) {
-                ex[VL + 2] = St<S>::dec(rb0[x0 + VL], sc);
-                ex[VL + 3] = St<S>::dec(rb0[x0 + VL + 1], sc);
-            } else if (bx1 == kBcPeriodic) {
-                ex[VL + 2] = St<S>::dec(rb0[0], sc);
-                ex[VL + 3] = St<S>::dec(rb0[1], sc);
-            } else {
-                const float *g = side + ((size_t)zl * TY + yl) * 4;
-                if (bx1 == kBcSpecular) { ex[VL + 2] = g[2]; ex[VL + 3] = g[3]; }
-                else if (nux >= 0.f) { ex[VL + 2] = ex[VL + 3] = w0[VL - 1]; }
-                else if (bx1 == kBcIsothermal) { ex[VL + 2] = ex[VL + 3] = hd[8]; }
-                else { ex[VL + 2] = ex[VL + 3] = g[2]; }
-            }
+        {
+            const T *gp = gptr + j * gstep;
+            float g0 = St<S>::dec(gp[gi0], sc), g1 = St<S>::dec(gp[gi1], sc);
+            const float own = lane == 0 ? w0[0] : w0[VL - 1];
+            g0 = gmode == kGhConst ? gc : (gmode == kGhOwn ? own : g0);
+            g1 = gmode == kGhConst ? gc : (gmode == kGhOwn ? own : g1);
+            const bool l0 = gmode != kGhShfl && lane == 0, l31 = gmode != kGhShfl && lane == 31;
+            ex[1] = l0 ? g0 : ex[1];
+            ex[0] = l0 ? g1 : ex[0];
+            ex[VL + 2] = l31 ? g0 : ex[VL + 2];
+            ex[VL + 3] = l31 ? g1 : ex[VL + 3];
         }
         // faces F_j between x0+j and x0+j+1, j = -1..VL-1 (index j+1); flux in signed form
         float F[VL + 1];
-        if (nux > 0.f) {
-            #pragma unroll
-            for (int j = -1; j < VL; ++j) F[j + 1] = face<LIM>(ex[j + 1], ex[j + 2], ex[j + 3]);
-        } else {
-            #pragma unroll
-            for (int j = -1; j < VL; ++j) F[j + 1] = face<LIM>(ex[j + 4], ex[j + 3], ex[j + 2]);
-        }
+        if (nux > 0.f) faces<LIM, VL + 1>(ex, ex + 1, ex + 2, F);       // upwind cell x0+j
+        else faces<LIM, VL + 1>(ex + 3, ex + 2, ex + 1, F);             // upwind cell x0+j+1
         #pragma unroll
         for (int v = 0; v < VL; ++v) div[v] = fmaf(nux, F[v + 1] - F[v], div[v]);
         if constexpr (DIM == 3) {
             float zm1[VL], zm2[VL], zp1[VL];
-            ld_row<S, VL>(zm1, rowbase(y, rz - sz) + x0, sc);
-            ld_row<S, VL>(zm2, rowbase(y, rz - 2 * sz) + x0, sc);
-            ld_row<S, VL>(zp1, rowbase(y, rz + sz) + x0, sc);
+            ld_row<S, VL>(zm1, box + o - dz + x0, sc);
+            ld_row<S, VL>(zm2, box + o - 2 * dz + x0, sc);
+            ld_row<S, VL>(zp1, box + o + dz + x0, sc);
+            float zo[VL], zi[VL];
+            faces<LIM, VL>(zm1, w0, zp1, zo);
+            faces<LIM, VL>(zm2, zm1, w0, zi);
             #pragma unroll
-            for (int v = 0; v < VL; ++v) div[v] = fmaf(anz, face<LIM>(zm1[v], w0[v], zp1[v]) - face<LIM>(zm2[v], zm1[v], w0[v]), div[v]);
+            for (int v = 0; v < VL; ++v) div[v] = fmaf(anz, zo[v] - zi[v], div[v]);
         }
         // update, store, moment and diffuse-wall partials
-        float bt[VL];
-        {
-            const float *bp = btsm + ((size_t)zl * TY + yl) * NX + x0;
-            if constexpr (VL == 4) {
-                const float4 f = *reinterpret_cast<const float4 *>(bp);
-                bt[0] = f.x;
-                bt[1] = f.y;
-                bt[2] = f.z;
-                bt[3] = f.w;
-            } else {
-                #pragma unroll
-                for (int v = 0; v < VL; ++v) bt[v] = bp[v];
-            }
+        float bt[VL], ac[VL];
+        if constexpr (VL == 4) {
+            const float4 f = *reinterpret_cast<const float4 *>(btsm + c);
+            const float4 g = *reinterpret_cast<const float4 *>(accsm + c);
+            bt[0] = f.x; bt[1] = f.y; bt[2] = f.z; bt[3] = f.w;
+            ac[0] = g.x; ac[1] = g.y; ac[2] = g.z; ac[3] = g.w;
+        } else {
+            #pragma unroll
+            for (int v = 0; v < VL; ++v) { bt[v] = btsm[c + v]; ac[v] = accsm[c + v]; }
         }
         T h[VL];
         float es[VL];
@@ -459,32 +546,25 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
             const float en = fmaf(-dtinv, w0[v], w0[v] - div[v]) + bt[v];
             h[v] = St<S>::enc(en, isc);
             es[v] = St<S>::dec(h[v], sc);
-            acc[r][v] = fmaf(wm, es[v], acc[r][v]);
+            ac[v] = fmaf(wm, es[v], ac[v]);
         }
-        st_row<S, VL>(eo + ((long long)z * ny + y) * NX + x0, h);
-        // diffuse-wall sums of Eq. (diff_bound) for the next step: cells next to a diffuse wall
-        // add w_d (s_d.n) e for directions leaving through it (weight 0 otherwise)
-        if (xlo && hd[9] != 0.f) wsm[p.wslot[0] * p.tw + zl * TY + yl] += hd[9] * es[0];
-        if (xhi && hd[10] != 0.f) wsm[p.wslot[1] * p.tw + zl * TY + yl] += hd[10] * es[VL - 1];
-        if (y == 0 && hd[11] != 0.f) {
-            float *w = wsm + p.wslot[2] * p.tw + zl * NX + x0;
+        if constexpr (VL == 4) *reinterpret_cast<float4 *>(accsm + c) = make_float4(ac[0], ac[1], ac[2], ac[3]);
+        else {
             #pragma unroll
-            for (int v = 0; v < VL; ++v) w[v] += hd[11] * es[v];
+            for (int v = 0; v < VL; ++v) accsm[c + v] = ac[v];
         }
-        if (y == ny - 1 && hd[12] != 0.f) {
-            float *w = wsm + p.wslot[3] * p.tw + zl * NX + x0;
+        st_row<S, VL>(eo, h);
+        // x walls: only the two end lanes have a non-zero weight (a predicated update)
+        if (wx != 0.f) wxp[j * sy] += wx * (lane == 0 ? es[0] : es[VL - 1]);
+        const float wy = y == 0 ? wy0 : (y == ny - 1 ? wy1 : 0.f);  // uniform across the warp
+        if (wy != 0.f) {
+            float *w = y == 0 ? wy0p : wy1p;
             #pragma unroll
-            for (int v = 0; v < VL; ++v) w[v] += hd[12] * es[v];
+            for (int v = 0; v < VL; ++v) w[v] += wy * es[v];
         }
-        if (DIM == 3 && z == 0 && hd[13] != 0.f) {
-            float *w = wsm + p.wslot[4] * p.tw + yl * NX + x0;
+        if (DIM == 3 && wz != 0.f) {
             #pragma unroll
-            for (int v = 0; v < VL; ++v) w[v] += hd[13] * es[v];
-        }
-        if (DIM == 3 && z == nz - 1 && hd[14] != 0.f) {
-            float *w = wsm + p.wslot[5] * p.tw + yl * NX + x0;
-            #pragma unroll
-            for (int v = 0; v < VL; ++v) w[v] += hd[14] * es[v];
+            for (int v = 0; v < VL; ++v) wzp[j * sy * NX + v] += wz * es[v];
         }
         #pragma unroll
         for (int v = 0; v < VL; ++v) {
@@ -493,6 +573,9 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
             w0[v] = wp1[v];
             fin[v] = fout[v];
         }
+        o += dy;
+        c += dy;
+        eo += dy;
     }
 }
 
@@ -505,10 +588,12 @@ __device__ __forceinline__ void warp_place(int &zl, int &rb, int &half) {
     rb = (u / Geo<DIM, WPR>::TZ) * kR;
 }
 
+// End of a segment: this thread's moment partials to P[seg], the diffuse-wall partials of
+// the tile to PW[seg]; both shared arrays are cleared for the next segment.
 template <int VL, int WPR, int DIM>
 __device__ __forceinline__ void flush_segment(const StepArgs &a, const TiledArgs &p, int seg, const PT &q,
-                                              float (&acc)[kR][VL], float *wsm) {
-    constexpr int NX = 32 * VL * WPR, TY = Geo<DIM, WPR>::TY;
+                                              float *accsm, float *wsm) {
+    constexpr int NX = 32 * VL * WPR, TY = Geo<DIM, WPR>::TY, NCW = Geo<DIM, WPR>::NCW;
     int zl, rb, half;
     warp_place<VL, WPR, DIM>(zl, rb, half);
     const int x0 = (half * 32 + (threadIdx.x & 31)) * VL;
@@ -516,14 +601,14 @@ __device__ __forceinline__ void flush_segment(const StepArgs &a, const TiledArgs
     #pragma unroll
     for (int r = 0; r < kR; ++r) {
         const int yl = rb + r;
+        const int c = (zl * TY + yl) * NX + x0;
         if (yl < q.nyt && zl < q.nzt) {
             #pragma unroll
-            for (int v = 0; v < VL; ++v) P[((size_t)zl * TY + yl) * NX + x0 + v] = acc[r][v];
+            for (int v = 0; v < VL; ++v) P[c + v] = accsm[c + v];
         }
         #pragma unroll
-        for (int v = 0; v < VL; ++v) acc[r][v] = 0.f;
+        for (int v = 0; v < VL; ++v) accsm[c + v] = 0.f;
     }
-    constexpr int NCW = Geo<DIM, WPR>::NCW;
     consumer_sync<NCW>();
     for (int idx = threadIdx.x; idx < p.nwd * p.tw; idx += NCW * 32) {
         p.PW[(size_t)seg * p.nwd * p.tw + idx] = wsm[idx];
@@ -541,20 +626,16 @@ __device__ void consumer(const StepArgs &a, const TiledArgs &p, char *smem, uint
     warp_place<VL, WPR, DIM>(zl, rb, half);
     const int x0 = (half * 32 + lane) * VL;
     const int ny = a.n[1];
-    float acc[kR][VL];
-    #pragma unroll
-    for (int r = 0; r < kR; ++r)
-        #pragma unroll
-        for (int v = 0; v < VL; ++v) acc[r][v] = 0.f;
     float *wsm = reinterpret_cast<float *>(smem + p.wall_off);
     float *btsm = reinterpret_cast<float *>(smem + p.bt_off);
+    float *accsm = reinterpret_cast<float *>(smem + p.acc_off);
     int seg = seg0 - 1, cur_tile = -1, cur_band = -1;
     PT cur{};
     int i = 0;
     for (int t = t0; t < t1; ++t, ++i) {
         const PT q = decode<DIM, WPR>(a, p, t);
         if (q.tile != cur_tile || q.k != cur_band) {
-            if (seg >= seg0) flush_segment<VL, WPR, DIM>(a, p, seg, cur, acc, wsm);
+            if (seg >= seg0) flush_segment<VL, WPR, DIM>(a, p, seg, cur, accsm, wsm);
             ++seg;
             cur_tile = q.tile;
             cur_band = q.k;
@@ -566,7 +647,7 @@ __device__ void consumer(const StepArgs &a, const TiledArgs &p, char *smem, uint
                 const int yl = rb + r;
                 if (yl < q.nyt && zl < q.nzt) {
                     const long long i0 = ((long long)(q.z0 + zl) * ny + (q.y0 + yl)) * NX + x0;
-                    float *bp = btsm + ((size_t)zl * TY + yl) * NX + x0;
+                    float *bp = btsm + (zl * TY + yl) * NX + x0;
                     #pragma unroll
                     for (int v = 0; v < VL; ++v) {
                         const float src = a.Q ? b.srck * (a.amp * a.Q[i0 + v]) : 0.f;
@@ -579,16 +660,12 @@ __device__ void consumer(const StepArgs &a, const TiledArgs &p, char *smem, uint
         const uint32_t ph = (uint32_t)(i / p.ns) & 1u;
         if (!mbar_wait(&full[s], ph, p.err, 1)) return;
         const char *stage = smem + p.stage0 + (size_t)s * p.stage_bytes;
-        if (zl < q.nzt && rb < q.nyt) {
-            if (a.nu[3 * q.plane + 1] > 0.f)
-                rows_of_warp<S, LIM, VL, WPR, DIM, 1>(a, p, q, stage, zl, rb, half, acc, btsm, wsm);
-            else
-                rows_of_warp<S, LIM, VL, WPR, DIM, -1>(a, p, q, stage, zl, rb, half, acc, btsm, wsm);
-        }
+        if (zl < q.nzt && rb < q.nyt)
+            rows_of_warp<S, LIM, VL, WPR, DIM>(a, p, q, stage, zl, rb, half, accsm, btsm, wsm);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
     }
-    if (seg >= seg0) flush_segment<VL, WPR, DIM>(a, p, seg, cur, acc, wsm);
+    if (seg >= seg0) flush_segment<VL, WPR, DIM>(a, p, seg, cur, accsm, wsm);
 }
 
 template <int S, int LIM, int VL, int WPR, int DIM>
@@ -606,6 +683,8 @@ __global__ void __launch_bounds__((Geo<DIM, WPR>::NCW + 1) * 32, 1) k_step_tiled
     }
     float *wsm = reinterpret_cast<float *>(smem + p.wall_off);
     for (int j = threadIdx.x; j < p.nwd * p.tw; j += blockDim.x) wsm[j] = 0.f;
+    float *accsm = reinterpret_cast<float *>(smem + p.acc_off);
+    for (int j = threadIdx.x; j < p.tcells; j += blockDim.x) accsm[j] = 0.f;
     __syncthreads();
     if ((int)(threadIdx.x >> 5) == Geo<DIM, WPR>::NCW)
         producer<S, VL, WPR, DIM>(a, p, smem, full, empty, t0, t1);
