@@ -19,6 +19,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -39,7 +40,13 @@ __global__ void __launch_bounds__(256) k_finalize_tiled(const StepArgs a, const 
     const int tile = tz * p.nty + ty;
     const int li = ((z - tz * p.tz) * p.ty + (y - ty * p.ty)) * nx + x;
     float s = 0.f;
-    for (int g = p.tile_seg0[tile]; g < p.tile_seg0[tile + 1]; ++g) s += a.P[(size_t)g * p.tcells + li];
+    for (int j = 0; j < p.J; ++j) {  // the tile's units in part order, each unit's bands in order
+        const int u = j * p.ntiles + tile;
+        const int p0 = part_begin(p, j), p1 = part_begin(p, j + 1);
+        if (p0 >= p1) continue;
+        const int g0 = p.unit_seg0[u], g1 = p.unit_seg0[u + 1];
+        for (int g = g0; g < g1; ++g) s += a.P[(size_t)g * p.tcells + li];
+    }
     TL[i] = s * a.invD;
 }
 
@@ -64,8 +71,14 @@ __global__ void __launch_bounds__(256) k_ediff_tiled(const StepArgs a, const Til
     const int yl = y - ty * p.ty, zl = z - tz * p.tz;
     const int slot = ax == 0 ? zl * p.ty + yl : (ax == 1 ? zl * nx + x : yl * nx + x);
     float s = 0.f;
-    for (int g = p.tbs[tile * a.nb + k]; g < p.tbs[tile * a.nb + k + 1]; ++g)
-        s += p.PW[((size_t)g * p.nwd + p.wslot[wall]) * p.tw + slot];
+    for (int j = 0; j < p.J; ++j) {
+        const int u = j * p.ntiles + tile;
+        const int p0 = part_begin(p, j), p1 = part_begin(p, j + 1);
+        if (p0 >= p1) continue;
+        const int b0 = p0 / a.nd, b1 = (p1 - 1) / a.nd;
+        if (k < b0 || k > b1) continue;
+        s += p.PW[((size_t)(p.unit_seg0[u] + k - b0) * p.nwd + p.wslot[wall]) * p.tw + slot];
+    }
     const BandConst b = a.band[k];
     static_cast<T *>(a.ediff_out)[((long long)wall * a.nb + k) * a.wc_max + j] = St<S>::enc(s * a.inv_den[wall],
                                                                                             b.inv_scale);
@@ -90,6 +103,16 @@ __global__ void k_build_headers(const StepArgs a, float *hdr) {
     h[8] = a.iso[1 * a.nb + k];
     for (int w = 0; w < 6; ++w) h[9 + w] = (w < 2 * a.dim && a.bc[w] == kBcDiffuse) ? a.wdiff[w * a.nd + d] : 0.f;
     h[15] = 0.f;
+}
+
+// Rows of the thermalizing-wall emission C_k T_w / W (already representable) in the storage format.
+template <int S>
+__global__ void k_fill_isorows(const StepArgs a, int nx, void *rows) {
+    using T = typename St<S>::T;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;  // over 6 * nb * nx
+    if (i >= 6 * a.nb * nx) return;
+    const int wk = i / nx, k = wk % a.nb;
+    static_cast<T *>(rows)[i] = St<S>::enc(a.iso[wk], a.band[k].inv_scale);
 }
 
 // ---- dispatch -------------------------------------------------------------------------------
@@ -139,6 +162,14 @@ bool tiled_plan(int dim, const int n[3], int nb, int nd, int storage, int limite
     const int TY = ncw / (TZ * wpr) * kR;
     plan.vx = nx / 32;
     plan.dim = dim;
+    plan.storage = storage;
+    plan.nx = nx;
+    // rows per bulk copy of a box slice (BTE_TILED_CHUNK overrides, for tuning runs)
+    plan.chunk = 16;
+    if (const char *env = std::getenv("BTE_TILED_CHUNK")) {
+        const int c = std::atoi(env);
+        if (c >= 1 && c <= 1024) plan.chunk = c;
+    }
     plan.ty = TY;
     plan.tz = TZ;
     plan.threads = (ncw + 1) * 32;
@@ -193,49 +224,32 @@ bool tiled_plan(int dim, const int n[3], int nb, int nd, int storage, int limite
         return false;
     }
     plan.nctas = sms * per_sm;
-    // static balanced schedule and its segments
+    // plane-synchronous schedule: J parts per tile, units dealt round-robin to the CTAs
     const long long npl = (long long)nb * nd;
-    const long long T = plan.ntiles * npl;
-    if (T > 0x7fffffffLL) {
+    if (npl * plan.ntiles > 0x7fffffffLL) {
         why = "too many plane-tiles";
         return false;
     }
-    if (plan.nctas > T) plan.nctas = (int)T;
-    std::vector<int> begin(plan.nctas + 1), seg_first(plan.nctas), seg_tile, seg_band;
-    for (int b = 0; b <= plan.nctas; ++b) begin[b] = (int)(T * b / plan.nctas);
-    for (int b = 0; b < plan.nctas; ++b) {
-        seg_first[b] = (int)seg_tile.size();
-        int ct = -1, ck = -1;
-        for (int t = begin[b]; t < begin[b + 1]; ++t) {
-            const int tile = (int)(t / npl), k = (int)((t % npl) / nd);
-            if (tile != ct || k != ck) {
-                seg_tile.push_back(tile);
-                seg_band.push_back(k);
-                ct = tile;
-                ck = k;
-            }
-        }
+    int g = plan.ntiles, hcf = plan.nctas;
+    while (g) { const int r = hcf % g; hcf = g; g = r; }
+    plan.np = (int)npl;
+    plan.J = std::min(plan.nctas / hcf, plan.np);
+    plan.U = plan.ntiles * plan.J;
+    if (plan.nctas > plan.U) plan.nctas = plan.U;
+    plan.h_unit_seg0.assign(plan.U + 1, 0);
+    for (int u = 0; u < plan.U; ++u) {
+        const int j = u / plan.ntiles;
+        const long long p0 = (long long)j * plan.np / plan.J, p1 = (long long)(j + 1) * plan.np / plan.J;
+        const int nseg = p1 > p0 ? (int)((p1 - 1) / nd - p0 / nd + 1) : 0;
+        plan.h_unit_seg0[u + 1] = plan.h_unit_seg0[u] + nseg;
     }
-    plan.G = (int)seg_tile.size();
-    std::vector<int> tile_seg0(plan.ntiles + 1, plan.G), tbs((size_t)plan.ntiles * nb + 1, plan.G);
-    for (int g = plan.G - 1; g >= 0; --g) {
-        tile_seg0[seg_tile[g]] = g;
-        tbs[(size_t)seg_tile[g] * nb + seg_band[g]] = g;
-    }
-    // tiles or (tile, band) pairs without segments cannot occur (every plane-tile is covered),
-    // so the "next start" of each entry is its successor's start
-    plan.h_begin = begin;
-    plan.h_seg_first = seg_first;
-    plan.h_tile_seg0 = tile_seg0;
-    plan.h_tbs = tbs;
+    plan.G = plan.h_unit_seg0[plan.U];
     plan.valid = 1;
     return true;
 }
 
 bool tiled_setup(TiledPlan &plan, const StepArgs &a, std::string &why) {
-    if (!upload_vec(&plan.cta_begin, plan.h_begin, why) || !upload_vec(&plan.seg_first, plan.h_seg_first, why) ||
-        !upload_vec(&plan.tile_seg0, plan.h_tile_seg0, why) || !upload_vec(&plan.tbs, plan.h_tbs, why))
-        return false;
+    if (!upload_vec(&plan.unit_seg0, plan.h_unit_seg0, why)) return false;
     const size_t npw = std::max<size_t>(1, (size_t)plan.G * plan.nwd * plan.tw);
     if (cudaMalloc((void **)&plan.PW, npw * sizeof(float)) != cudaSuccess ||
         cudaMemset(plan.PW, 0, npw * sizeof(float)) != cudaSuccess ||
@@ -246,6 +260,16 @@ bool tiled_setup(TiledPlan &plan, const StepArgs &a, std::string &why) {
         return false;
     }
     k_build_headers<<<(a.nb * a.nd + 127) / 128, 128>>>(a, plan.hdr);
+    const int esz = plan.storage == kStoreF32 ? 4 : 2;
+    const int nrow = 6 * a.nb * plan.nx;
+    if (cudaMalloc(&plan.isorow, (size_t)nrow * esz) != cudaSuccess) {
+        cudaGetLastError();
+        why = "cudaMalloc failed";
+        return false;
+    }
+    if (plan.storage == kStoreF32) k_fill_isorows<kStoreF32><<<(nrow + 255) / 256, 256>>>(a, plan.nx, plan.isorow);
+    else if (plan.storage == kStoreF16) k_fill_isorows<kStoreF16><<<(nrow + 255) / 256, 256>>>(a, plan.nx, plan.isorow);
+    else k_fill_isorows<kStoreBF16><<<(nrow + 255) / 256, 256>>>(a, plan.nx, plan.isorow);
     if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
         why = "header build failed";
         return false;
@@ -254,10 +278,11 @@ bool tiled_setup(TiledPlan &plan, const StepArgs &a, std::string &why) {
 }
 
 void tiled_free(TiledPlan &plan) {
-    void *ptrs[] = {plan.cta_begin, plan.seg_first, plan.tile_seg0, plan.tbs, plan.PW, plan.err, plan.hdr};
+    void *ptrs[] = {plan.unit_seg0, plan.PW, plan.err, plan.hdr, plan.isorow};
     for (void *q : ptrs)
         if (q) cudaFree(q);
-    plan.cta_begin = plan.seg_first = plan.tile_seg0 = plan.tbs = nullptr;
+    plan.unit_seg0 = nullptr;
+    plan.isorow = nullptr;
     plan.PW = nullptr;
     plan.err = nullptr;
     plan.hdr = nullptr;
@@ -266,12 +291,14 @@ void tiled_free(TiledPlan &plan) {
 static TiledArgs device_args(const TiledPlan &plan) {
     TiledArgs t;
     memset(&t, 0, sizeof t);
-    t.cta_begin = plan.cta_begin;
-    t.seg_first = plan.seg_first;
-    t.tile_seg0 = plan.tile_seg0;
-    t.tbs = plan.tbs;
+    t.unit_seg0 = plan.unit_seg0;
+    t.U = plan.U;
+    t.J = plan.J;
+    t.np = plan.np;
+    t.ntiles = plan.ntiles;
     t.PW = plan.PW;
     t.hdr = plan.hdr;
+    t.isorow = plan.isorow;
     t.err = plan.err;
     t.tw = plan.tw;
     t.nwd = plan.nwd;
@@ -289,6 +316,7 @@ static TiledArgs device_args(const TiledPlan &plan) {
     t.tz = plan.tz;
     t.wall_off = plan.wall_off;
     t.tcells = plan.tcells;
+    t.chunk = plan.chunk;
     return t;
 }
 

@@ -10,12 +10,11 @@ namespace bte {
 
 // Device-side view of the plan, passed by value to the kernels.
 struct TiledArgs {
-    const int *cta_begin;  // [nctas + 1] first plane-tile of each CTA
-    const int *seg_first;  // [nctas]     first segment of each CTA
-    const int *tile_seg0;  // [ntiles + 1] segments of tile t are [tile_seg0[t], tile_seg0[t+1])
-    const int *tbs;        // [ntiles*nb + 1] segments of (tile t, band k) start at tbs[t*nb + k]
+    const int *unit_seg0;  // [U + 1] first segment (row of P / PW) of each unit
+    int U, J, np, ntiles;  // units, parts per tile, planes (nb*nd), tiles
     float *PW;             // diffuse-wall partials [G][nwd][tw]
     const float *hdr;      // per-plane constants [nb*nd][16] (see tiled_build_headers)
+    const void *isorow;    // thermalizing-wall emission rows [6][nb][nx] in the storage format
     int *err;              // bounded-wait failure flags (1: consumer, 2: producer)
     int tw;                // wall slots per wall per segment
     int nwd;               // number of diffuse walls
@@ -25,12 +24,16 @@ struct TiledArgs {
     int stage0, stage_bytes, side_off, hdr_off, wall_off, bt_off, acc_off;  // shared-memory layout (bytes)
     int ty, tz;            // tile extents (rows, slices)
     int tcells;            // cells of a full tile (row length of P)
+    int chunk;             // rows per bulk copy of a box slice
 };
 
-// Static, balanced schedule of the tiled forward kernel.  Work is the tile-major list of
-// (spatial tile, band, direction) plane-tiles; CTA b processes [begin[b], begin[b+1]).  A
-// segment is a run of one CTA's range with one tile and one band; each writes one row of
-// moment partials P[seg][tile cells] and one row of diffuse-wall partials PW[seg].
+// Plane-synchronous schedule of the tiled forward kernel.  The plane list (k*nd + d) of every
+// spatial tile is cut into J parts; unit u covers part u / ntiles of tile u % ntiles.  CTA c
+// processes units c, c + nctas, c + 2 nctas, ... so in each round neighbouring tiles are
+// worked on by neighbouring CTAs over the same planes, and the halo rows one CTA loads are
+// still in L2 when its neighbour needs them.  J = nctas / gcd(ntiles, nctas) makes the unit
+// count a multiple of the CTA count.  A segment is the run of one unit within one band; it
+// writes one row of moment partials P[seg][tile cells] and one row of diffuse-wall partials.
 struct TiledPlan {
     int valid = 0;
     int dim = 0, vx = 0;
@@ -40,10 +43,13 @@ struct TiledPlan {
     int ty = 0, tz = 0, threads = 0;
     int nwd = 0, wslot[6] = {-1, -1, -1, -1, -1, -1};
     void *kernel = nullptr;
-    std::vector<int> h_begin, h_seg_first, h_tile_seg0, h_tbs;
-    int *cta_begin = nullptr, *seg_first = nullptr, *tile_seg0 = nullptr, *tbs = nullptr;
+    int U = 0, J = 0, np = 0;
+    std::vector<int> h_unit_seg0;
+    int *unit_seg0 = nullptr;
     float *PW = nullptr;
     float *hdr = nullptr;
+    void *isorow = nullptr;
+    int storage = 0, nx = 0, chunk = 4;
     int *err = nullptr;
 };
 

@@ -194,14 +194,13 @@ struct PT {
 };
 
 template <int DIM, int WPR>
-__device__ __forceinline__ PT decode(const StepArgs &a, const TiledArgs &p, int t) {
+__device__ __forceinline__ PT decode(const StepArgs &a, const TiledArgs &p, int tile, int plane) {
     PT r;
-    const int npl = a.nb * a.nd;
-    r.tile = t / npl;
-    r.plane = t - r.tile * npl;
-    r.k = r.plane / a.nd;
-    r.d = r.plane - r.k * a.nd;
-    const int ty = r.tile % p.nty, tz = r.tile / p.nty;
+    r.tile = tile;
+    r.plane = plane;
+    r.k = plane / a.nd;
+    r.d = plane - r.k * a.nd;
+    const int ty = tile % p.nty, tz = tile / p.nty;
     r.y0 = ty * Geo<DIM, WPR>::TY;
     r.z0 = tz * Geo<DIM, WPR>::TZ;
     r.nyt = min(Geo<DIM, WPR>::TY, a.n[1] - r.y0);
@@ -209,60 +208,75 @@ __device__ __forceinline__ PT decode(const StepArgs &a, const TiledArgs &p, int 
     return r;
 }
 
+// first plane of part j of a tile's plane list
+__device__ __forceinline__ int part_begin(const TiledArgs &p, int j) { return (int)((long long)j * p.np / p.J); }
+
+// Walks this CTA's plane-tiles: units blockIdx.x, blockIdx.x + gridDim.x, ...; within a unit its
+// planes in order.  q is kept current without divisions inside a unit.
+template <int DIM, int WPR>
+struct Cursor {
+    int u, p0, p1;
+    PT q;
+    __device__ __forceinline__ bool enter(const StepArgs &a, const TiledArgs &p) {
+        for (; u < p.U; u += gridDim.x) {
+            const int j = u / p.ntiles;
+            p0 = part_begin(p, j);
+            p1 = part_begin(p, j + 1);
+            if (p0 < p1) {
+                q = decode<DIM, WPR>(a, p, u - j * p.ntiles, p0);
+                return true;
+            }
+        }
+        return false;
+    }
+    __device__ __forceinline__ bool start(const StepArgs &a, const TiledArgs &p) {
+        u = blockIdx.x;
+        return enter(a, p);
+    }
+    __device__ __forceinline__ bool next(const StepArgs &a, const TiledArgs &p) {
+        if (++q.plane < p1) {
+            if (++q.d == a.nd) {
+                q.d = 0;
+                ++q.k;
+            }
+            return true;
+        }
+        u += gridDim.x;
+        return enter(a, p);
+    }
+};
+
 // ---- producer warp ----------------------------------------------------------------------------
 enum { kSkip = 0, kCopy = 1, kConst = 2 };
 
-// What fills box row (y, z): a bulk copy from src, a constant, or nothing (box corner).
-template <int S, int NX, int DIM>
-__device__ __forceinline__ int classify_row(const StepArgs &a, const PT &q, int y, int z, float nuy, float nuz,
-                                            const typename St<S>::T *&src, float &cval) {
+// Source row of a ghost row of the box: position pos (< 0 or >= n) along axis ax (1: y, 2: z)
+// at the other coordinate `other` (z for a y-ghost, y for a z-ghost).  Sec. 2.2: the wrapped
+// row (periodic), the mirrored direction's row (specular), the wall row itself for directions
+// leaving through the wall, the diffuse-wall value row, or the thermalizing wall's emission row.
+template <int S, int NX>
+__device__ __forceinline__ const typename St<S>::T *ghost_row_src(const StepArgs &a, const TiledArgs &p, const PT &q,
+                                                                  int ax, int pos, int other, float nu) {
     using T = typename St<S>::T;
-    const int ny = a.n[1], nz = a.n[2];
-    const bool inY = y >= 0 && y < ny;
-    const bool inZ = DIM == 2 || (z >= 0 && z < nz);
-    const bool coreY = y >= q.y0 && y < q.y0 + q.nyt;
-    const bool coreZ = DIM == 2 || (z >= q.z0 && z < q.z0 + q.nzt);
-    if (!coreY && !coreZ) return kSkip;  // box corner: no stencil reads it
-    const T *e = static_cast<const T *>(a.e_in);
-    const long long pbase = (long long)q.plane * a.ncell;
-    if (inY && inZ) {
-        src = e + pbase + ((long long)z * ny + y) * NX;
-        return kCopy;
-    }
-    const int ax = inY ? 2 : 1;
-    const int pos = ax == 1 ? y : z;
-    const int n = ax == 1 ? ny : nz;
+    const int ny = a.n[1];
+    const int n = a.n[ax];
     const int side = pos < 0 ? 0 : 1;
     const int wall = 2 * ax + side;
     const int bc = a.bc[wall];
-    const float nu = ax == 1 ? nuy : nuz;
-    auto row_at = [&](long long base, int yy, int zz) { return e + base + ((long long)zz * ny + yy) * NX; };
-    if (bc == kBcPeriodic) {
-        const int p2 = side ? pos - n : pos + n;
-        src = ax == 1 ? row_at(pbase, p2, z) : row_at(pbase, y, p2);
-        return kCopy;
-    }
+    const T *e = static_cast<const T *>(a.e_in);
+    auto row_at = [&](int plane, int along) {
+        const int yy = ax == 1 ? along : other, zz = ax == 1 ? other : along;
+        return e + (long long)plane * a.ncell + ((long long)zz * ny + yy) * NX;
+    };
+    if (bc == kBcPeriodic) return row_at(q.plane, side ? pos - n : pos + n);
     if (bc == kBcSpecular) {
         const int layer = side ? pos - n + 1 : -pos;
-        const int mpos = side ? n - layer : layer - 1;
-        const long long mbase = ((long long)q.k * a.nd + a.mirror[ax * a.nd + q.d]) * a.ncell;
-        src = ax == 1 ? row_at(mbase, mpos, z) : row_at(mbase, y, mpos);
-        return kCopy;
+        return row_at(q.k * a.nd + a.mirror[ax * a.nd + q.d], side ? n - layer : layer - 1);
     }
     const bool incoming = side == 0 ? (nu > 0.f) : (nu < 0.f);
-    if (!incoming) {
-        const int wpos = side ? n - 1 : 0;
-        src = ax == 1 ? row_at(pbase, wpos, z) : row_at(pbase, y, wpos);
-        return kCopy;
-    }
-    if (bc == kBcIsothermal) {
-        cval = a.iso[wall * a.nb + q.k];
-        return kConst;
-    }
-    // diffuse wall: the row of incoming values (wall cells of a y-wall are indexed z*nx + x,
-    // those of a z-wall y*nx + x)
-    src = static_cast<const T *>(a.ediff_in) + ((long long)wall * a.nb + q.k) * a.wc_max + (long long)(ax == 1 ? z : y) * NX;
-    return kCopy;
+    if (!incoming) return row_at(q.plane, side ? n - 1 : 0);
+    if (bc == kBcIsothermal) return static_cast<const T *>(p.isorow) + ((long long)wall * a.nb + q.k) * NX;
+    // diffuse wall: wall cells of a y-wall are indexed z*nx + x, those of a z-wall y*nx + x
+    return static_cast<const T *>(a.ediff_in) + ((long long)wall * a.nb + q.k) * a.wc_max + (long long)other * NX;
 }
 
 // Shared-memory side arrays of a stage for the x-wall ghosts (storage format, bulk-copied):
@@ -290,8 +304,7 @@ __device__ __forceinline__ long long dcol_src(const StepArgs &a, int sd, int k, 
 }
 
 template <int S, int VL, int WPR, int DIM>
-__device__ void producer(const StepArgs &a, const TiledArgs &p, char *smem, uint64_t *full, uint64_t *empty, int t0,
-                         int t1) {
+__device__ void producer(const StepArgs &a, const TiledArgs &p, char *smem, uint64_t *full, uint64_t *empty) {
     using T = typename St<S>::T;
     using SD = Side<S, WPR, DIM>;
     constexpr int NX = 32 * VL * WPR, TY = Geo<DIM, WPR>::TY;
@@ -302,69 +315,70 @@ __device__ void producer(const StepArgs &a, const TiledArgs &p, char *smem, uint
     const T *e = static_cast<const T *>(a.e_in);
     const T *ed = static_cast<const T *>(a.ediff_in);
     const int bx[2] = {a.bc[0], a.bc[1]};
-    int i = 0;
-    for (int t = t0; t < t1; ++t, ++i) {
+    Cursor<DIM, WPR> cur, ahead;
+    bool more = cur.start(a, p);
+    bool ahead_ok = ahead.start(a, p);
+    for (int j = 0; j < p.ns && ahead_ok; ++j) ahead_ok = ahead.next(a, p);  // the plane-tile ns later
+    for (int i = 0; more; ++i, more = cur.next(a, p)) {
         const int s = i % p.ns;
         const uint32_t ph = (uint32_t)(i / p.ns) & 1u;
         if (i >= p.ns && !mbar_wait(&empty[s], ph ^ 1u, p.err, 2)) return;
         fence_proxy_async();
         __syncwarp();
-        const PT q = decode<DIM, WPR>(a, p, t);
+        const PT &q = cur.q;
         const float nux = a.nu[3 * q.plane], nuy = a.nu[3 * q.plane + 1];
         const float nuz = DIM == 3 ? a.nu[3 * q.plane + 2] : 0.f;
         const int ybox0 = q.y0 - (nuy > 0.f ? 2 : 1);
         const int zbox0 = DIM == 3 ? q.z0 - (nuz > 0.f ? 2 : 1) : 0;
-        const int nry = q.nyt + 3;
-        const int nrow = nry * (DIM == 3 ? q.nzt + 3 : 1);
+        const int nry = q.nyt + 3, nrz = DIM == 3 ? q.nzt + 3 : 1;
         char *stage = smem + p.stage0 + (size_t)s * p.stage_bytes;
         char *side = stage + p.side_off;
+        const long long pbase = (long long)q.plane * a.ncell;
         const int ncore = q.nyt * q.nzt;
         const bool spec[2] = {bx[0] == kBcSpecular, bx[1] == kBcSpecular};
         const bool dif[2] = {bx[0] == kBcDiffuse && nux > 0.f, bx[1] == kBcDiffuse && nux < 0.f};
-        // bytes the bulk copies of this stage deliver
-        uint32_t bytes = 0;
-        for (int r = lane; r < nrow; r += 32) {
-            const T *src;
-            float cv;
-            if (classify_row<S, NX, DIM>(a, q, ybox0 + r % nry, zbox0 + r / nry, nuy, nuz, src, cv) == kCopy) bytes += rowb;
+        // Every box row the stencil reads is filled by exactly one bulk copy, so the byte count is
+        // closed-form: core slices need all nry rows, the z-halo slices the nyt core rows.  x-wall
+        // side copies have fixed sizes.
+        const int nneed = DIM == 3 ? q.nzt * nry + (nrz - q.nzt) * q.nyt : nry;
+        const int ndcol = (q.nyt + V - 1) / V + 1;  // 16-byte units of a diffuse column copy
+        if (lane == 0) {
+            const uint32_t bytes = (uint32_t)nneed * rowb + (spec[0] + spec[1]) * (uint32_t)ncore * 16u +
+                                   (dif[0] + dif[1]) * (uint32_t)q.nzt * ndcol * 16u + 64u;
+            mbar_expect_tx(&full[s], bytes);
+            // per-plane constants (64 bytes, prepared once on the device)
+            bulk_g2s(stage + p.hdr_off, p.hdr + (size_t)q.plane * kHdrFloats, 64, &full[s]);
         }
-        for (int sd = 0; sd < 2; ++sd) {
-            if (spec[sd])
-                for (int j = lane; j < ncore; j += 32) bytes += 16;
-            if (dif[sd])
-                for (int zl = lane; zl < q.nzt; zl += 32) {
-                    const long long s0 = dcol_src(a, sd, q.k, q.z0 + zl, q.y0);
-                    const int off = (int)(s0 & (V - 1));
-                    bytes += (uint32_t)(((off + q.nyt + V - 1) / V) * 16);
-                }
-        }
-        bytes = __reduce_add_sync(0xffffffffu, bytes);
-        if (lane == 0) mbar_expect_tx(&full[s], bytes + 64);
         __syncwarp();
-        // per-plane constants (64 bytes, prepared on the host side)
-        if (lane == 0) bulk_g2s(stage + p.hdr_off, p.hdr + (size_t)q.plane * kHdrFloats, 64, &full[s]);
-        for (int base = 0; base < nrow; base += 32) {
-            const int r = base + lane;
-            const T *src = nullptr;
-            float cv = 0.f;
-            const int kind = r < nrow ? classify_row<S, NX, DIM>(a, q, ybox0 + r % nry, zbox0 + r / nry, nuy, nuz, src, cv)
-                                      : kSkip;
-            // box rows are stored with the full-tile stride: row (ry, rz) at (rz (TY + 3) + ry) NX
-            if (kind == kCopy)
-                bulk_g2s(reinterpret_cast<T *>(stage) + ((size_t)(r / nry) * (TY + 3) + r % nry) * NX, src, rowb, &full[s]);
-            // thermalizing-wall rows: the whole warp writes each one, 16 bytes per lane and store
-            unsigned m = __ballot_sync(0xffffffffu, kind == kConst);
-            while (m) {
-                const int j = __ffs(m) - 1;
-                m &= m - 1;
-                const float v = __shfl_sync(0xffffffffu, cv, j);
-                const T h = St<S>::enc(v, a.band[q.k].inv_scale);
-                T pack[V];
-                #pragma unroll
-                for (int c = 0; c < V; ++c) pack[c] = h;
-                const int rj = base + j;
-                uint4 *row = reinterpret_cast<uint4 *>(reinterpret_cast<T *>(stage) + ((size_t)(rj / nry) * (TY + 3) + rj % nry) * NX);
-                for (int c = lane; c < (int)(rowb / 16); c += 32) row[c] = *reinterpret_cast<const uint4 *>(pack);
+        // Work items: per box slice, nch chunks of its in-domain rows (one contiguous run in global
+        // and in shared memory) and 4 ghost-row slots (two below, two above the domain in y); a
+        // slice outside the domain (a z-wall) uses its first nyt items for the core rows' ghosts.
+        const int nch = (nry + p.chunk - 1) / p.chunk;
+        const int per = max(nch + 4, DIM == 3 ? q.nyt : 0);
+        for (int w = lane; w < nrz * per; w += 32) {
+            const int rz = w / per, it = w - rz * per;
+            const int z = zbox0 + rz;
+            T *slice = reinterpret_cast<T *>(stage) + (size_t)rz * (TY + 3) * NX;
+            if (DIM == 3 && (z < 0 || z >= nz)) {
+                if (it < q.nyt) {
+                    const int y = q.y0 + it;
+                    bulk_g2s(slice + (size_t)(y - ybox0) * NX, ghost_row_src<S, NX>(a, p, q, 2, z, y, nuz), rowb, &full[s]);
+                }
+                continue;
+            }
+            const bool coreZ = DIM == 2 || (z >= q.z0 && z < q.z0 + q.nzt);
+            const int ylo = coreZ ? ybox0 : q.y0, yhi = coreZ ? ybox0 + nry : q.y0 + q.nyt;
+            const int ya = max(ylo, 0), yb = min(yhi, ny);
+            if (it < nch) {
+                const int y = ya + it * p.chunk;
+                if (y < yb)
+                    bulk_g2s(slice + (size_t)(y - ybox0) * NX, e + pbase + ((long long)z * ny + y) * NX,
+                             (uint32_t)min(p.chunk, yb - y) * rowb, &full[s]);
+            } else if (it < nch + 4) {
+                const int g = it - nch;  // 0, 1: below the domain; 2, 3: above it
+                const int y = g < 2 ? ylo + g : yb + (g - 2);
+                if (g < 2 ? y < ya : y < yhi)
+                    bulk_g2s(slice + (size_t)(y - ybox0) * NX, ghost_row_src<S, NX>(a, p, q, 1, y, z, nuy), rowb, &full[s]);
             }
         }
         // x-wall ghosts outside the tile: 16 bytes of the mirrored direction's row (specular), or
@@ -380,15 +394,13 @@ __device__ void producer(const StepArgs &a, const TiledArgs &p, char *smem, uint
             if (dif[sd])
                 for (int zl = lane; zl < q.nzt; zl += 32) {
                     const long long s0 = dcol_src(a, sd, q.k, q.z0 + zl, q.y0);
-                    const int off = (int)(s0 & (V - 1));
-                    bulk_g2s(SD::dcol(side, sd, zl), ed + (s0 - off), (uint32_t)(((off + q.nyt + V - 1) / V) * 16), &full[s]);
+                    bulk_g2s(SD::dcol(side, sd, zl), ed + (s0 - (s0 & (V - 1))), (uint32_t)ndcol * 16u, &full[s]);
                 }
         }
         mbar_arrive(&full[s]);
         // pull the rows of a later plane-tile towards L2 (no shared memory involved)
-        const int tp = t + p.ns;
-        if (tp < t1) {
-            const PT qp = decode<DIM, WPR>(a, p, tp);
+        if (ahead_ok) {
+            const PT &qp = ahead.q;
             const float pnuy = a.nu[3 * qp.plane + 1];
             const float pnuz = DIM == 3 ? a.nu[3 * qp.plane + 2] : 0.f;
             const int ylo = max(qp.y0 - (pnuy > 0.f ? 2 : 1), 0), yhi = min(qp.y0 + qp.nyt + (pnuy > 0.f ? 1 : 2), ny);
@@ -396,6 +408,7 @@ __device__ void producer(const StepArgs &a, const TiledArgs &p, char *smem, uint
             const int zhi = DIM == 3 ? min(qp.z0 + qp.nzt + (pnuz > 0.f ? 1 : 2), nz) : 1;
             for (int z = zlo + lane; z < zhi; z += 32)
                 bulk_prefetch_l2(e + (long long)qp.plane * a.ncell + ((long long)z * ny + ylo) * NX, (uint32_t)(yhi - ylo) * rowb);
+            ahead_ok = ahead.next(a, p);
         }
     }
 }
@@ -618,8 +631,7 @@ __device__ __forceinline__ void flush_segment(const StepArgs &a, const TiledArgs
 }
 
 template <int S, int LIM, int VL, int WPR, int DIM>
-__device__ void consumer(const StepArgs &a, const TiledArgs &p, char *smem, uint64_t *full, uint64_t *empty, int t0,
-                         int t1, int seg0) {
+__device__ void consumer(const StepArgs &a, const TiledArgs &p, char *smem, uint64_t *full, uint64_t *empty) {
     constexpr int NX = 32 * VL * WPR, TY = Geo<DIM, WPR>::TY;
     const int lane = threadIdx.x & 31;
     int zl, rb, half;
@@ -629,15 +641,16 @@ __device__ void consumer(const StepArgs &a, const TiledArgs &p, char *smem, uint
     float *wsm = reinterpret_cast<float *>(smem + p.wall_off);
     float *btsm = reinterpret_cast<float *>(smem + p.bt_off);
     float *accsm = reinterpret_cast<float *>(smem + p.acc_off);
-    int seg = seg0 - 1, cur_tile = -1, cur_band = -1;
+    int seg = -1, cur_unit = -1, cur_band = -1;
     PT cur{};
-    int i = 0;
-    for (int t = t0; t < t1; ++t, ++i) {
-        const PT q = decode<DIM, WPR>(a, p, t);
-        if (q.tile != cur_tile || q.k != cur_band) {
-            if (seg >= seg0) flush_segment<VL, WPR, DIM>(a, p, seg, cur, accsm, wsm);
-            ++seg;
-            cur_tile = q.tile;
+    Cursor<DIM, WPR> c;
+    bool more = c.start(a, p);
+    for (int i = 0; more; ++i, more = c.next(a, p)) {
+        const PT q = c.q;
+        if (c.u != cur_unit || q.k != cur_band) {
+            if (seg >= 0) flush_segment<VL, WPR, DIM>(a, p, seg, cur, accsm, wsm);
+            seg = p.unit_seg0[c.u] + q.k - c.p0 / a.nd;
+            cur_unit = c.u;
             cur_band = q.k;
             cur = q;
             // per-cell relaxation target and source of this band: dt/tau C T_L / W + a dt C Q/(sum C W)
@@ -665,7 +678,7 @@ __device__ void consumer(const StepArgs &a, const TiledArgs &p, char *smem, uint
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
     }
-    if (seg >= seg0) flush_segment<VL, WPR, DIM>(a, p, seg, cur, accsm, wsm);
+    if (seg >= 0) flush_segment<VL, WPR, DIM>(a, p, seg, cur, accsm, wsm);
 }
 
 template <int S, int LIM, int VL, int WPR, int DIM>
@@ -673,7 +686,6 @@ __global__ void __launch_bounds__((Geo<DIM, WPR>::NCW + 1) * 32, 1) k_step_tiled
     extern __shared__ __align__(128) char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint64_t *empty = full + p.ns;
-    const int t0 = p.cta_begin[blockIdx.x], t1 = p.cta_begin[blockIdx.x + 1];
     if (threadIdx.x == 0) {
         for (int s = 0; s < p.ns; ++s) {
             mbar_init(&full[s], 32);
@@ -687,9 +699,9 @@ __global__ void __launch_bounds__((Geo<DIM, WPR>::NCW + 1) * 32, 1) k_step_tiled
     for (int j = threadIdx.x; j < p.tcells; j += blockDim.x) accsm[j] = 0.f;
     __syncthreads();
     if ((int)(threadIdx.x >> 5) == Geo<DIM, WPR>::NCW)
-        producer<S, VL, WPR, DIM>(a, p, smem, full, empty, t0, t1);
+        producer<S, VL, WPR, DIM>(a, p, smem, full, empty);
     else
-        consumer<S, LIM, VL, WPR, DIM>(a, p, smem, full, empty, t0, t1, p.seg_first[blockIdx.x]);
+        consumer<S, LIM, VL, WPR, DIM>(a, p, smem, full, empty);
 }
 
 typedef void (*StepKernel)(const StepArgs, const TiledArgs);
