@@ -209,6 +209,26 @@ bte_status bte_moments(bte_ctx *ctx, double *dT, double *dTL, double *q);
  * Host outputs; synchronises.  BTE_ENONFINITE on a non-finite state. */
 bte_status bte_energy(bte_ctx *ctx, double *E_total, double wall_flux[6]);
 
+/* The reductions of bte_energy without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that must not allocate device memory after set-up, for
+ * example a host application that hands all device memory to its own pool, or code that runs
+ * where a cudaMalloc would block or is not permitted.  bte_energy allocates its diagnostic
+ * buffers on first use; this variant instead keeps its block partials, its seven results and a
+ * non-finite flag in one fixed array of the library (2048 partial slots per reduction, about
+ * 112 KB of device memory, held by every device that loads the library until the process
+ * exits).  It calls no cudaMalloc, cudaFree or allocating library routine.
+ *   - Inputs and outputs as for bte_energy (the context's current state; host E_total and
+ *     wall_flux[6], either may be NULL).  Results equal bte_energy's up to FP64 rounding order.
+ *   - Limit: each reduction - the cells, and each wall's (wall cells x bands) - may have at most
+ *     2048 * 4096 = 8,388,608 items; larger grids return BTE_EINVAL and nothing is launched.
+ *   - The first call made on a device looks up the array's device address (once per device,
+ *     with that device current); make that first call before any stream capture.
+ *   - Every call overwrites what it reads and clears the flag first, so nothing carries over
+ *     between calls.  All calls in the process share the one array: calls that overlap on the
+ *     GPU (other streams, contexts or host threads) race and must be serialised by the caller.
+ * Synchronises the context's stream.  BTE_ENONFINITE on a non-finite state. */
+bte_status bte_energy_noalloc(bte_ctx *ctx, double *E_total, double wall_flux[6]);
+
 /* Copy the stored state out / in, in its storage format (FP32, or the 16-bit code h with
  * e = s_k h), layout e[k][d][z][y][x].  bytes must equal bte_info.state_bytes.  bte_set_state
  * recomputes T_L and the diffuse-wall values from the new state and resets the step counter

@@ -26,7 +26,7 @@ BTE_KERNEL_AUTO, BTE_KERNEL_GENERIC, BTE_KERNEL_TILED = 0, 1, 2
 # every entry point include/bte.h declares
 EXPORTS = ["bte_create", "bte_destroy", "bte_last_error", "bte_init_temperature", "bte_set_source", "bte_step",
            "bte_lattice_temperature", "bte_moments", "bte_energy", "bte_get_state", "bte_set_state",
-           "bte_get_info", "bte_get_quadrature", "bte_synchronize", "bte_profile", "bte_profile_read"]
+           "bte_get_info", "bte_get_quadrature", "bte_synchronize", "bte_profile", "bte_profile_read", "bte_energy_noalloc"]
 
 _STATUS = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESTATE", 5: "ENONFINITE", 6: "ETIMEOUT", 7: "EUNSUPPORTED"}
 
@@ -94,6 +94,7 @@ def load():
     lib.bte_lattice_temperature.argtypes = [P, dp]
     lib.bte_moments.argtypes = [P, dp, dp, dp]
     lib.bte_energy.argtypes = [P, dp, dp]
+    lib.bte_energy_noalloc.argtypes = [P, dp, dp]
     lib.bte_get_state.argtypes = [P, P, ct.c_size_t, ct.c_int]
     lib.bte_set_state.argtypes = [P, P, ct.c_size_t, ct.c_int, ct.c_int]
     lib.bte_get_info.argtypes = [P, ct.POINTER(bte_info)]
@@ -248,6 +249,15 @@ def bte_energy(ctx):
     E = np.zeros(1)
     F = np.zeros(6)
     _check(load().bte_energy(ctx.handle, _dp(E), _dp(F)), ctx.handle)
+    return float(E[0]), F
+
+
+def bte_energy_noalloc(ctx):
+    """bte_energy's reductions without device allocation (for callers that may not allocate
+    device memory after set-up); see include/bte.h for its size limit and concurrency rules."""
+    E = np.zeros(1)
+    F = np.zeros(6)
+    _check(load().bte_energy_noalloc(ctx.handle, _dp(E), _dp(F)), ctx.handle)
     return float(E[0]), F
 
 

@@ -805,3 +805,28 @@ extern "C" bte_status bte_profile_read(bte_ctx *c, double *fwd_ms, long long *fw
     if (fin_launches) *fin_launches = (long long)n;
     return BTE_OK;
 }
+
+extern "C" bte_status bte_energy_noalloc(bte_ctx *c, double *E_total, double wall_flux[6]) {
+    if (!c) return fail(nullptr, BTE_EINVAL, "ctx is NULL");
+    StepArgs a = make_args(c);
+    a.e_in = c->e[c->cur];
+    a.ediff_in = c->ediff[c->ecur];
+    double res[7];
+    int nonfinite = 0;
+    cudaError_t e = cudaSuccess;
+    const int rc = launch_energy_noalloc(a, c->storage, c->limiter, c->d_w, c->d_s, c->d_v, res, &nonfinite, c->stream, &e);
+    if (rc == 1)
+        return fail(c, BTE_EINVAL,
+                    "grid too large for the allocation-free reduction: every reduction (cells, or wall cells x bands) "
+                    "must have at most %lld items",
+                    energy_noalloc_max_items());
+    if (rc != 0) return fail(c, BTE_ECUDA, "allocation-free energy reduction: %s", cudaGetErrorString(e));
+    double L[3];
+    for (int ax = 0; ax < 3; ++ax) L[ax] = ax < c->dim ? c->h[ax] : 1.0;
+    const double V = L[0] * L[1] * L[2];
+    if (E_total) *E_total = V * res[0];
+    if (wall_flux)
+        for (int wl = 0; wl < 6; ++wl) wall_flux[wl] = (wl < 2 * c->dim) ? (V / L[wl >> 1]) * res[1 + wl] : 0.0;
+    if (nonfinite) return fail(c, BTE_ENONFINITE, "the state holds a non-finite value");
+    return BTE_OK;
+}

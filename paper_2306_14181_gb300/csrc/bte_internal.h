@@ -70,5 +70,10 @@ cudaError_t launch_wallflux64(const StepArgs &a, int storage, int limiter, const
                               const double *v, DiagOut o, cudaStream_t s);
 // Deterministic FP64 sum of n values into *out (device); scratch holds >= 1024 doubles.
 cudaError_t launch_sum64(const double *x, long long n, double *scratch, double *out, cudaStream_t s);
+// Energy and wall flows into host7[7] with no device allocation (file-scope device scratch).
+// Returns 0, 1 (grid larger than the scratch covers) or 2 (CUDA error in *err).
+int launch_energy_noalloc(const StepArgs &a, int storage, int limiter, const double *w, const double *sv,
+                          const double *v, double *host7, int *nonfinite, cudaStream_t s, cudaError_t *err);
+long long energy_noalloc_max_items();
 
 }  // namespace bte

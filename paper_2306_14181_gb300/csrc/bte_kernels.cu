@@ -5,6 +5,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <mutex>
+
 #include "bte_internal.h"
 
 namespace bte {
@@ -447,6 +449,187 @@ cudaError_t launch_sum64(const double *x, long long n, double *scratch, double *
     k_sum64_a<<<np, 256, 0, s>>>(x, n, scratch);
     k_sum64_b<<<1, 256, 0, s>>>(scratch, np, out);
     return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// Allocation-free variant of the FP64 energy-balance reduction.
+//
+// bte_energy stages per-cell sums and block partials in device buffers it allocates on first
+// use.  This variant fuses the per-cell work into per-block FP64 partials and keeps them, the
+// seven results and a non-finite flag in one file-scope device array, so a caller that may not
+// allocate device memory can still take the reductions.  Each reduction (total energy and the
+// six wall flows) has kNaSlots partial slots and a block covers kNaPerBlock items, which bounds
+// the grids it accepts.  Every call overwrites the slots it reads and clears the flag, so no
+// state carries over between calls; calls that overlap on the GPU share the array and race.
+// ------------------------------------------------------------------------------------------
+constexpr int kNaThreads = 256;
+constexpr int kNaSlots = 2048;                      // block partials per reduction
+constexpr long long kNaPerBlock = kNaThreads * 16;  // items a block covers
+constexpr int kNaReductions = 7;                    // E_total, wall flows -x..+z
+constexpr int kNaResults = kNaReductions * kNaSlots;   // 7 results follow the partials
+constexpr int kNaFlag = kNaResults + kNaReductions;    // then the non-finite flag (as a double slot)
+static __device__ __align__(256) double g_na_scratch[kNaFlag + 1];
+
+long long energy_noalloc_max_items() { return (long long)kNaSlots * kNaPerBlock; }
+
+// fixed-order block sum of one double per thread
+__device__ __forceinline__ double na_block_sum(double v) {
+    __shared__ double sm[kNaThreads];
+    sm[threadIdx.x] = v;
+    __syncthreads();
+    for (int h = kNaThreads / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) sm[threadIdx.x] += sm[threadIdx.x + h];
+        __syncthreads();
+    }
+    return sm[0];
+}
+
+// partial[b] = sum over the cells b covers of sum_k sum_d w_d e (Eq. getTQ numerator)
+template <int S>
+__global__ void __launch_bounds__(kNaThreads) k_na_energy(const StepArgs a, const double *w, double *scratch) {
+    using Cd = Codec<S>;
+    using T = typename Cd::T;
+    const T *e = static_cast<const T *>(a.e_in);
+    const long long lo = (long long)blockIdx.x * kNaPerBlock;
+    const long long hi = lo + kNaPerBlock < a.ncell ? lo + kNaPerBlock : a.ncell;
+    double acc = 0.0;
+    bool bad = false;
+    for (long long i = lo + threadIdx.x; i < hi; i += kNaThreads) {
+        double et = 0.0;
+        for (int k = 0; k < a.nb; ++k) {
+            const BandConst b = a.band[k];
+            double sk = 0.0;
+            for (int d = 0; d < a.nd; ++d) {
+                const double ed = Cd::ld64(e, ((long long)k * a.nd + d) * a.ncell + i, b);
+                bad |= !isfinite(ed);
+                sk += w[d] * ed;
+            }
+            et += sk;
+        }
+        acc += et;
+    }
+    const double tot = na_block_sum(acc);
+    if (bad) scratch[kNaFlag] = 1.0;
+    if (threadIdx.x == 0) scratch[blockIdx.x] = tot;
+}
+
+// partial[b] of wall `wall` = sum over the (wall cell, band) items b covers of
+// sum_d w_d v_k (s_d.n) e_face, e_face the wall-face value of the step
+template <int S>
+__global__ void __launch_bounds__(kNaThreads) k_na_wallflux(const StepArgs a, int wall, int lim, const double *w,
+                                                            const double *sv, const double *v, double *scratch) {
+    using Cd = Codec<S>;
+    using T = typename Cd::T;
+    const int ax = wall >> 1, side = wall & 1;
+    const int n0 = ax == 0 ? a.n[1] : a.n[0];
+    const int n1 = ax == 2 ? a.n[1] : a.n[2];
+    const long long nwc = (long long)n0 * n1, nitem = nwc * a.nb;
+    const long long lo = (long long)blockIdx.x * kNaPerBlock;
+    const long long hi = lo + kNaPerBlock < nitem ? lo + kNaPerBlock : nitem;
+    const T *e = static_cast<const T *>(a.e_in);
+    const int n = a.n[ax];
+    const double nsign = side ? 1.0 : -1.0;
+    double acc = 0.0;
+    for (long long it = lo + threadIdx.x; it < hi; it += kNaThreads) {
+        const int k = (int)(it / nwc);
+        const long long j = it - (long long)k * nwc;
+        int c[3];
+        const int ja = (int)(j % n0), jb = (int)(j / n0);
+        c[ax] = side ? n - 1 : 0;
+        if (ax == 0) { c[1] = ja; c[2] = jb; }
+        else if (ax == 1) { c[0] = ja; c[2] = jb; }
+        else { c[0] = ja; c[1] = jb; }
+        const long long i = c[0] + a.stride[1] * c[1] + a.stride[2] * c[2];
+        const BandConst b = a.band[k];
+        double F = 0.0;
+        for (int d = 0; d < a.nd; ++d) {
+            const double sa = sv[3 * d + ax];
+            if (sa == 0.0) continue;
+            const int sg = sa > 0.0 ? 1 : -1;
+            const int pu = (sa * nsign > 0.0) ? (side ? n - 1 : 0) : (side ? n : -1);  // upwind position
+            const double um = ext64<Cd>(a, e, b, k, d, i, c, ax, pu, sa);
+            const double ul = ext64<Cd>(a, e, b, k, d, i, c, ax, pu - sg, sa);
+            const double ur = ext64<Cd>(a, e, b, k, d, i, c, ax, pu + sg, sa);
+            F += w[d] * v[k] * (nsign * sa) * (um + 0.5 * limit64(lim, um - ul, ur - um));
+        }
+        acc += F;
+    }
+    const double tot = na_block_sum(acc);
+    if (threadIdx.x == 0) scratch[(1 + wall) * kNaSlots + blockIdx.x] = tot;
+}
+
+// result[r] = sum of the nblk[r] partials of reduction r, in slot order (one block per r)
+struct NaCounts {
+    int nblk[kNaReductions];
+};
+__global__ void __launch_bounds__(kNaThreads) k_na_finish(NaCounts cnt, double *scratch) {
+    const int r = blockIdx.x;
+    double acc = 0.0;
+    for (int t = threadIdx.x; t < cnt.nblk[r]; t += kNaThreads) acc += scratch[r * kNaSlots + t];
+    const double tot = na_block_sum(acc);
+    if (threadIdx.x == 0) scratch[kNaResults + r] = tot;
+}
+
+// Device address of g_na_scratch, looked up once per device on the first call made with that
+// device current (that first call must come before any stream capture).
+static double *na_scratch_address(cudaError_t *err) {
+    static std::mutex mu;
+    static double *addr[64] = {};
+    int dev = 0;
+    if ((*err = cudaGetDevice(&dev)) != cudaSuccess) return nullptr;
+    if (dev < 0 || dev >= 64) {
+        *err = cudaErrorInvalidDevice;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        if ((*err = cudaGetSymbolAddress(&p, g_na_scratch)) != cudaSuccess) return nullptr;
+        addr[dev] = static_cast<double *>(p);
+    }
+    *err = cudaSuccess;
+    return addr[dev];
+}
+
+int launch_energy_noalloc(const StepArgs &a, int storage, int limiter, const double *w, const double *sv,
+                          const double *v, double *host7, int *nonfinite, cudaStream_t s, cudaError_t *err) {
+    // item counts of the seven reductions, checked against the fixed partial slots
+    NaCounts cnt;
+    long long items[kNaReductions];
+    items[0] = a.ncell;
+    for (int wl = 0; wl < 6; ++wl) {
+        const int ax = wl >> 1;
+        const long long nwc = ax == 0 ? (long long)a.n[1] * a.n[2] : (ax == 1 ? (long long)a.n[0] * a.n[2] : (long long)a.n[0] * a.n[1]);
+        items[1 + wl] = wl < 2 * a.dim ? nwc * a.nb : 0;
+    }
+    for (int r = 0; r < kNaReductions; ++r) {
+        if (items[r] > energy_noalloc_max_items()) return 1;  // too large for the fixed slots
+        cnt.nblk[r] = (int)((items[r] + kNaPerBlock - 1) / kNaPerBlock);
+    }
+    double *scratch = na_scratch_address(err);
+    if (!scratch) return 2;
+    // the flag must start at zero; partials and results are overwritten before they are read
+    if ((*err = cudaMemsetAsync(scratch + kNaFlag, 0, sizeof(double), s)) != cudaSuccess) return 2;
+    if (cnt.nblk[0] > 0) {
+        if (storage == kStoreF32) k_na_energy<kStoreF32><<<cnt.nblk[0], kNaThreads, 0, s>>>(a, w, scratch);
+        else if (storage == kStoreF16) k_na_energy<kStoreF16><<<cnt.nblk[0], kNaThreads, 0, s>>>(a, w, scratch);
+        else k_na_energy<kStoreBF16><<<cnt.nblk[0], kNaThreads, 0, s>>>(a, w, scratch);
+    }
+    for (int wl = 0; wl < 2 * a.dim; ++wl) {
+        if (cnt.nblk[1 + wl] == 0) continue;
+        if (storage == kStoreF32) k_na_wallflux<kStoreF32><<<cnt.nblk[1 + wl], kNaThreads, 0, s>>>(a, wl, limiter, w, sv, v, scratch);
+        else if (storage == kStoreF16) k_na_wallflux<kStoreF16><<<cnt.nblk[1 + wl], kNaThreads, 0, s>>>(a, wl, limiter, w, sv, v, scratch);
+        else k_na_wallflux<kStoreBF16><<<cnt.nblk[1 + wl], kNaThreads, 0, s>>>(a, wl, limiter, w, sv, v, scratch);
+    }
+    k_na_finish<<<kNaReductions, kNaThreads, 0, s>>>(cnt, scratch);
+    if ((*err = cudaGetLastError()) != cudaSuccess) return 2;
+    double flag = 0.0;
+    if ((*err = cudaMemcpyAsync(host7, scratch + kNaResults, kNaReductions * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (*err = cudaMemcpyAsync(&flag, scratch + kNaFlag, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (*err = cudaStreamSynchronize(s)) != cudaSuccess)
+        return 2;
+    *nonfinite = flag != 0.0;
+    return 0;
 }
 
 }  // namespace bte
