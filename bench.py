@@ -55,6 +55,9 @@ def parse():
     p.add_argument("--workload", default="hotspot_2d")
     p.add_argument("--storage", default="f32", choices=sorted(STORAGE))
     p.add_argument("--kernel", default="auto", choices=sorted(KERNEL))
+    p.add_argument("--rounding", default="nearest", choices=["nearest", "stochastic"],
+                   help="rounding of 16-bit codes")
+    p.add_argument("--t-scale", type=float, default=1.0, help="16-bit code scale T_scale (K)")
     p.add_argument("--limiter", type=int, default=2)
     p.add_argument("--e2e-steps", type=int, default=20)
     p.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -294,9 +297,9 @@ def run_gb300(args):
     total = args.warmup + args.steps + args.e2e_steps + 8
     amps = inputs.source_amplitudes(cfg, total)
     stream = torch.cuda.current_stream()
-    T_scale = 1.0
     ctx = bte.bte_from_workload(cfg, storage=storage, limiter=args.limiter, kernel=KERNEL[args.kernel],
-                                stream=stream.cuda_stream, T_scale=T_scale)
+                                stream=stream.cuda_stream, T_scale=args.t_scale,
+                                rounding=1 if args.rounding == "stochastic" else 0, seed=1)
     info = ctx.info
     kernel_name = "tiled" if info.kernel == bte.BTE_KERNEL_TILED else "generic"
     if Q is not None:
@@ -364,6 +367,7 @@ def run_gb300(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": cfg["name"], "grid": list(cfg["n"]), "bands": info.nbands, "dirs": info.ndirs,
                        "storage": args.storage, "limiter": args.limiter, "kernel": kernel_name,
+                       **({"rounding": args.rounding, "T_scale": args.t_scale} if args.storage != "f32" else {}),
                        "updates_per_step": info.nelem, "l2": "state %.2f GB > L2, no flush" % (info.state_bytes / 1e9),
                        "parallelism": "replicas" if d.world > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(nfwd + nfin),

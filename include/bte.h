@@ -71,8 +71,8 @@ enum {
 /* Storage of e in device memory.  All arithmetic is FP32 in every mode. */
 enum {
     BTE_STORE_F32 = 0,
-    BTE_STORE_F16 = 1,  /* e = s_k * h, h binary16, s_k = C_k T_scale / W */
-    BTE_STORE_BF16 = 2  /* e = s_k * h, h bfloat16 */
+    BTE_STORE_F16 = 1,  /* e = s_k (h + R / T_scale), h binary16, s_k = C_k T_scale / W (see bte_get_state) */
+    BTE_STORE_BF16 = 2  /* the same with h bfloat16 */
 };
 
 /* Slope limiter L(a, b) of the one-sided differences at the upwind cell; e_face = e_m + L/2.
@@ -84,6 +84,11 @@ enum {
     BTE_LIM_VANALBADA = 2    /* ab(a+b)/(a^2+b^2) if ab > 0, else 0 (default) */
 };
 
+/* Rounding of the 16-bit codes the forward step writes.  Round to nearest loses every
+ * per-step change below half a code step, so a slowly drifting state stalls; stochastic
+ * rounding rounds up with probability equal to the fraction of a code step, unbiased, with
+ * the random bits a counter-based hash of (seed, step index, plane k*ndirs+d, cell): the same
+ * seed and inputs give bitwise the same run. */
 enum { BTE_ROUND_NEAREST = 0, BTE_ROUND_STOCHASTIC = 1 };
 
 /* Which forward kernel to run. */
@@ -136,10 +141,12 @@ typedef struct {
     double dt;        /* time step (s), > 0 (Sec. 4.1: dt = beta dx_min / v) */
     int storage;      /* BTE_STORE_* */
     int limiter;      /* BTE_LIM_* */
-    double T_scale;   /* K; 16-bit storage scale s_k = C_k T_scale / W.  <= 0: 1 K */
+    double T_scale;   /* K; 16-bit storage scale s_k = C_k T_scale / W.  <= 0: 1 K.  The codes hold
+                         departures from local equilibrium in units of T_scale: for binary16 pick
+                         T_scale near the expected temperature rise (subnormals below 6e-5) */
     int rounding;     /* BTE_ROUND_*; only meaningful for 16-bit storage */
     void *stream;     /* cudaStream_t; NULL = CUDA default stream */
-    uint64_t seed;    /* key of the stochastic-rounding hash */
+    uint64_t seed;    /* key of the stochastic-rounding hash (BTE_ROUND_STOCHASTIC) */
     int kernel;       /* BTE_KERNEL_* */
 } bte_options;
 
@@ -229,12 +236,23 @@ bte_status bte_energy(bte_ctx *ctx, double *E_total, double wall_flux[6]);
  * Synchronises the context's stream.  BTE_ENONFINITE on a non-finite state. */
 bte_status bte_energy_noalloc(bte_ctx *ctx, double *E_total, double wall_flux[6]);
 
-/* Copy the stored state out / in, in its storage format (FP32, or the 16-bit code h with
- * e = s_k h), layout e[k][d][z][y][x].  bytes must equal bte_info.state_bytes.  bte_set_state
- * recomputes T_L and the diffuse-wall values from the new state and resets the step counter
- * to 0 unless keep_step is non-zero. */
-bte_status bte_get_state(bte_ctx *ctx, void *dst, size_t bytes, int on_device);
-bte_status bte_set_state(bte_ctx *ctx, const void *src, size_t bytes, int on_device, int keep_step);
+/* Copy the stored state out / in, in its storage format, layout e[k][d][z][y][x].  FP32
+ * storage holds e.  16-bit storage holds codes h with
+ *     e_{k,d,i} = s_k (h_{k,d,i} + R_i / T_scale),   s_k = C_k T_scale / W,
+ * against a per-cell reference temperature R (the T_L the step that wrote the state relaxed
+ * towards, Eq. BTE_get_e0), so h is the departure from the band's local equilibrium.
+ * ref (ncell floats, K; same memory space as the state; may be NULL) receives R from
+ * bte_get_state and supplies it to bte_set_state (NULL there: R = 0, i.e. e = s_k h).  FP32
+ * storage ignores ref on input and returns zeros.  bytes must equal bte_info.state_bytes.
+ * bte_set_state recomputes T_L and the wall ghost values from the new state and resets the
+ * step counter to 0 unless keep_step is non-zero; BTE_EINVAL on a non-finite host ref. */
+bte_status bte_get_state(bte_ctx *ctx, void *dst, size_t bytes, float *ref, int on_device);
+bte_status bte_set_state(bte_ctx *ctx, const void *src, size_t bytes, const float *ref, int on_device, int keep_step);
+
+/* The decoded state e (FP32, nbands*ndirs*ncell values, layout as above) into dst (host, or
+ * device memory of the context's device when on_device is non-zero).  A host dst uses a
+ * temporary device buffer of the same size; the context's stream is synchronised. */
+bte_status bte_get_values(bte_ctx *ctx, float *dst, int on_device);
 
 /* Sizes and settings; the quadrature the context built (s: 3*ndirs, w: ndirs, host). */
 bte_status bte_get_info(const bte_ctx *ctx, bte_info *info);

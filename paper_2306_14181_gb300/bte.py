@@ -26,6 +26,7 @@ BTE_KERNEL_AUTO, BTE_KERNEL_GENERIC, BTE_KERNEL_TILED = 0, 1, 2
 # every entry point include/bte.h declares
 EXPORTS = ["bte_create", "bte_destroy", "bte_last_error", "bte_init_temperature", "bte_set_source", "bte_step",
            "bte_lattice_temperature", "bte_moments", "bte_energy", "bte_get_state", "bte_set_state",
+           "bte_get_values",
            "bte_get_info", "bte_get_quadrature", "bte_synchronize", "bte_profile", "bte_profile_read", "bte_energy_noalloc"]
 
 _STATUS = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESTATE", 5: "ENONFINITE", 6: "ETIMEOUT", 7: "EUNSUPPORTED"}
@@ -95,8 +96,9 @@ def load():
     lib.bte_moments.argtypes = [P, dp, dp, dp]
     lib.bte_energy.argtypes = [P, dp, dp]
     lib.bte_energy_noalloc.argtypes = [P, dp, dp]
-    lib.bte_get_state.argtypes = [P, P, ct.c_size_t, ct.c_int]
-    lib.bte_set_state.argtypes = [P, P, ct.c_size_t, ct.c_int, ct.c_int]
+    lib.bte_get_state.argtypes = [P, P, ct.c_size_t, P, ct.c_int]
+    lib.bte_set_state.argtypes = [P, P, ct.c_size_t, P, ct.c_int, ct.c_int]
+    lib.bte_get_values.argtypes = [P, P, ct.c_int]
     lib.bte_get_info.argtypes = [P, ct.POINTER(bte_info)]
     lib.bte_get_quadrature.argtypes = [P, dp, dp]
     lib.bte_synchronize.argtypes = [P]
@@ -264,23 +266,40 @@ def bte_energy_noalloc(ctx):
 _NP_STORE = {BTE_STORE_F32: np.float32, BTE_STORE_F16: np.float16, BTE_STORE_BF16: np.uint16}
 
 
-def bte_get_state(ctx, out=None):
+def bte_get_state(ctx, out=None, ref=None):
     """The stored state: numpy (float32, float16, or uint16 holding bfloat16 bits) by default,
-    or into ``out`` (numpy or CUDA tensor) of state_bytes bytes."""
+    or into ``out`` (numpy or CUDA tensor) of state_bytes bytes.  With 16-bit storage the codes
+    are departures from the reference field R: e = s_k (h + R / T_scale); ``ref`` (float32,
+    ncell values, same memory space as ``out``) receives R when given."""
     i = ctx.info
     if out is None:
         out = np.empty(ctx.shape, dtype=_NP_STORE[i.storage])
     p, dev = _ptr(out)
-    _check(load().bte_get_state(ctx.handle, p, i.state_bytes, dev), ctx.handle)
+    rp = _ptr(ref)[0] if ref is not None else None
+    _check(load().bte_get_state(ctx.handle, p, i.state_bytes, rp, dev), ctx.handle)
     return out
 
 
-def bte_set_state(ctx, src, keep_step=False):
+def bte_set_state(ctx, src, ref=None, keep_step=False):
+    """Load a state in the storage format; ``ref`` is the code reference R of 16-bit codes
+    (None: R = 0, so a 16-bit state is e = s_k h)."""
     i = ctx.info
     if not hasattr(src, "data_ptr"):
         src = np.ascontiguousarray(src, dtype=_NP_STORE[i.storage])
     p, dev = _ptr(src)
-    _check(load().bte_set_state(ctx.handle, p, i.state_bytes, dev, int(bool(keep_step))), ctx.handle)
+    if ref is not None and not hasattr(ref, "data_ptr"):
+        ref = np.ascontiguousarray(ref, dtype=np.float32)
+    rp = _ptr(ref)[0] if ref is not None else None
+    _check(load().bte_set_state(ctx.handle, p, i.state_bytes, rp, dev, int(bool(keep_step))), ctx.handle)
+
+
+def bte_get_values(ctx, out=None):
+    """The decoded state e as float32 (numpy of the state's shape, or into a CUDA tensor)."""
+    if out is None:
+        out = np.empty(ctx.shape, dtype=np.float32)
+    p, dev = _ptr(out)
+    _check(load().bte_get_values(ctx.handle, p, dev), ctx.handle)
+    return out
 
 
 def bte_get_info(ctx):

@@ -42,6 +42,7 @@ struct bte_ctx {
     void *e[2] = {nullptr, nullptr};
     int cur = 0;
     float *TL = nullptr, *Q = nullptr, *P = nullptr;
+    float *R = nullptr;  // code reference of the current state (16-bit storage): T_L of the step that wrote it
     int G = 0;
     void *ediff[2] = {nullptr, nullptr};
     int ecur = 0;
@@ -253,6 +254,11 @@ static StepArgs make_args(const bte_ctx *c) {
     a.mirror = c->mirror_d;
     a.band = c->band;
     a.iso = c->iso;
+    a.TL = c->TL;
+    a.R = c->R;
+    a.invTs = (float)(1.0 / c->T_scale);
+    a.sr = 0;
+    a.srkey = 0;
     a.Q = c->has_source ? c->Q : nullptr;
     a.P = c->P;
     return a;
@@ -275,7 +281,7 @@ static bte_status refresh_moments(bte_ctx *c) {
 }
 
 static void free_all(bte_ctx *c) {
-    void *ptrs[] = {c->e[0], c->e[1], c->TL, c->Q, c->P, c->ediff[0], c->ediff[1], c->nu, c->wmom, c->wdiff,
+    void *ptrs[] = {c->e[0], c->e[1], c->TL, c->R, c->Q, c->P, c->ediff[0], c->ediff[1], c->nu, c->wmom, c->wdiff,
                     c->iso, c->mirror_d, c->band, c->d_w, c->d_s, c->d_v, c->d_invtau, c->dg, c->dflag};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -368,8 +374,6 @@ extern "C" bte_status bte_create(const bte_grid *grid, const bte_bands *bands, c
     if (opts->kernel < BTE_KERNEL_AUTO || opts->kernel > BTE_KERNEL_TILED) return fail(nullptr, BTE_EINVAL, "bad kernel");
     if (opts->rounding != BTE_ROUND_NEAREST && opts->rounding != BTE_ROUND_STOCHASTIC)
         return fail(nullptr, BTE_EINVAL, "bad rounding");
-    if (opts->rounding == BTE_ROUND_STOCHASTIC)
-        return fail(nullptr, BTE_EUNSUPPORTED, "stochastic rounding is not implemented in this build");
     c->dt = opts->dt;
     c->storage = opts->storage;
     c->limiter = opts->limiter;
@@ -458,13 +462,7 @@ extern "C" bte_status bte_create(const bte_grid *grid, const bte_bands *bands, c
             wmom[p] = (float)(c->w[d] / c->tau[k]);
         }
         for (int wl = 0; wl < 2 * c->dim; ++wl)
-            if (c->bc[wl] == BTE_BC_ISOTHERMAL) {
-                // the wall emission as a value the storage format represents exactly
-                float v = (float)(c->C[k] * c->Tw[wl] / c->W);
-                if (c->storage == BTE_STORE_F16) v = b.scale * __half2float(__float2half_rn(v * b.inv_scale));
-                if (c->storage == BTE_STORE_BF16) v = b.scale * __bfloat162float(__float2bfloat16_rn(v * b.inv_scale));
-                iso[wl * c->nb + k] = v;
-            }
+            if (c->bc[wl] == BTE_BC_ISOTHERMAL) iso[wl * c->nb + k] = (float)(c->C[k] * c->Tw[wl] / c->W);
     }
     for (int wl = 0; wl < 2 * c->dim; ++wl) {
         const int a = wl >> 1;
@@ -484,6 +482,7 @@ extern "C" bte_status bte_create(const bte_grid *grid, const bte_bands *bands, c
     if ((st = dalloc(c, (char **)&c->e[0], c->state_bytes)) != BTE_OK) return bail(st);
     if ((st = dalloc(c, (char **)&c->e[1], c->state_bytes)) != BTE_OK) return bail(st);
     if ((st = dalloc(c, &c->TL, c->ncell)) != BTE_OK) return bail(st);
+    if ((st = dalloc(c, &c->R, c->ncell)) != BTE_OK) return bail(st);
     if ((st = dalloc(c, &c->Q, c->ncell)) != BTE_OK) return bail(st);
     {
         // moment partials: band-major rows for the generic passes, segment rows for the tiled one
@@ -561,7 +560,7 @@ extern "C" bte_status bte_init_temperature(bte_ctx *c, const double *dT0) {
     }
     StepArgs a = make_args(c);
     a.e_out = c->e[c->cur];
-    cudaError_t e = launch_fill(a, c->storage, d, c->stream);
+    cudaError_t e = launch_fill(a, c->storage, d, c->R, c->stream);
     if (d) {
         cudaStreamSynchronize(c->stream);
         cudaFree(d);
@@ -602,9 +601,13 @@ extern "C" bte_status bte_step(bte_ctx *c, int nsteps) {
     for (int s = 0; s < nsteps; ++s) {
         StepArgs a = make_args(c);
         a.amp = (float)amplitude_at(c, c->step);
+        if (c->rounding == BTE_ROUND_STOCHASTIC && c->storage != BTE_STORE_F32) {
+            // the step's rounding key: the seed's two halves and the step index, hashed
+            a.sr = 1;
+            a.srkey = mix32((uint32_t)c->seed ^ mix32((uint32_t)(c->seed >> 32) ^ mix32((uint32_t)c->step)));
+        }
         a.e_in = c->e[c->cur];
         a.e_out = c->e[c->cur ^ 1];
-        a.TL = c->TL;
         a.ediff_in = c->ediff[c->ecur];
         a.ediff_out = c->ediff[c->ecur ^ 1];
         cudaError_t e;
@@ -614,10 +617,15 @@ extern "C" bte_status bte_step(bte_ctx *c, int nsteps) {
         else e = launch_step_generic(a, c->storage, c->limiter, c->stream);
         if (e != cudaSuccess) return fail(c, BTE_ECUDA, "forward step launch: %s", cudaGetErrorString(e));
         if (c->prof) TRY(prof_event(c, &ev));
-        if (c->tiled) e = launch_finalize_tiled(a, c->plan, c->storage, c->TL, c->stream);
-        else e = launch_finalize(a, c->G, c->TL, c->stream);
+        // T_L^{n+1} goes to the buffer of the old code reference; T_L^n becomes the reference of
+        // the new state
+        float *TL_next = c->R;
+        if (c->tiled) e = launch_finalize_tiled(a, c->plan, c->storage, TL_next, c->stream);
+        else e = launch_finalize(a, c->G, TL_next, c->stream);
         if (e != cudaSuccess) return fail(c, BTE_ECUDA, "finalize launch: %s", cudaGetErrorString(e));
         if (c->prof) TRY(prof_event(c, &ev));
+        c->R = c->TL;
+        c->TL = TL_next;
         c->cur ^= 1;
         c->ecur ^= 1;
         ++c->step;
@@ -727,23 +735,50 @@ extern "C" bte_status bte_energy(bte_ctx *c, double *E_total, double wall_flux[6
     return BTE_OK;
 }
 
-extern "C" bte_status bte_get_state(bte_ctx *c, void *dst, size_t bytes, int on_device) {
+extern "C" bte_status bte_get_state(bte_ctx *c, void *dst, size_t bytes, float *ref, int on_device) {
     if (!c || !dst) return fail(c, BTE_EINVAL, "NULL argument");
     if (bytes != c->state_bytes) return fail(c, BTE_EINVAL, "bytes %zu != state_bytes %zu", bytes, c->state_bytes);
-    CU(c, cudaMemcpyAsync(dst, c->e[c->cur], bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                          c->stream));
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CU(c, cudaMemcpyAsync(dst, c->e[c->cur], bytes, kind, c->stream));
+    if (ref && c->storage != BTE_STORE_F32) CU(c, cudaMemcpyAsync(ref, c->R, c->ncell * sizeof(float), kind, c->stream));
+    else if (ref && on_device) CU(c, cudaMemsetAsync(ref, 0, c->ncell * sizeof(float), c->stream));
+    else if (ref) memset(ref, 0, c->ncell * sizeof(float));
     if (!on_device) CU(c, cudaStreamSynchronize(c->stream));
     return BTE_OK;
 }
 
-extern "C" bte_status bte_set_state(bte_ctx *c, const void *src, size_t bytes, int on_device, int keep_step) {
+extern "C" bte_status bte_set_state(bte_ctx *c, const void *src, size_t bytes, const float *ref, int on_device,
+                                    int keep_step) {
     if (!c || !src) return fail(c, BTE_EINVAL, "NULL argument");
     if (bytes != c->state_bytes) return fail(c, BTE_EINVAL, "bytes %zu != state_bytes %zu", bytes, c->state_bytes);
-    CU(c, cudaMemcpyAsync(c->e[c->cur], src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                          c->stream));
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (ref && !on_device)
+        for (long long i = 0; i < c->ncell; ++i)
+            if (!std::isfinite(ref[i])) return fail(c, BTE_EINVAL, "ref holds a non-finite value at cell %lld", i);
+    CU(c, cudaMemcpyAsync(c->e[c->cur], src, bytes, kind, c->stream));
+    if (ref) CU(c, cudaMemcpyAsync(c->R, ref, c->ncell * sizeof(float), kind, c->stream));
+    else CU(c, cudaMemsetAsync(c->R, 0, c->ncell * sizeof(float), c->stream));
     if (!on_device) CU(c, cudaStreamSynchronize(c->stream));
     TRY(refresh_moments(c));
     if (!keep_step) c->step = 0;
+    return BTE_OK;
+}
+
+extern "C" bte_status bte_get_values(bte_ctx *c, float *dst, int on_device) {
+    if (!c || !dst) return fail(c, BTE_EINVAL, "NULL argument");
+    StepArgs a = make_args(c);
+    a.e_in = c->e[c->cur];
+    float *out = dst;
+    const size_t bytes = (size_t)c->nelem * sizeof(float);
+    if (!on_device) CU(c, cudaMalloc((void **)&out, bytes));
+    cudaError_t e = launch_decode(a, c->storage, out, c->stream);
+    if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(dst, out, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (!on_device) {
+        const cudaError_t e2 = cudaStreamSynchronize(c->stream);
+        if (e == cudaSuccess) e = e2;
+        cudaFree(out);
+    }
+    if (e != cudaSuccess) return fail(c, BTE_ECUDA, "state decode: %s", cudaGetErrorString(e));
     return BTE_OK;
 }
 

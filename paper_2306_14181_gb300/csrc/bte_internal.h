@@ -11,6 +11,21 @@ constexpr int kBcIsothermal = 0, kBcDiffuse = 1, kBcSpecular = 2, kBcPeriodic = 
 constexpr int kStoreF32 = 0, kStoreF16 = 1, kStoreBF16 = 2;
 constexpr int kLimFirst = 0, kLimMinmod = 1, kLimVanAlbada = 2;
 
+// Random bits of the stochastic rounding of element (plane, cell): the 32-bit integer hash
+// lowbias32 (C. Wellons, "hash-prospector") applied to the cell index xor a per-plane key,
+// itself the hash of the step key plus the plane index times the golden-ratio constant.
+__host__ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+__host__ __device__ __forceinline__ uint32_t plane_key(uint32_t srkey, int plane) {
+    return mix32(srkey + (uint32_t)plane * 0x9e3779b9u);
+}
+
 // Per-band FP32 constants of the update (index k).
 struct BandConst {
     float dtinv;   // dt / tau_k
@@ -44,18 +59,26 @@ struct StepArgs {
     // fields
     const void *e_in;
     void *e_out;
-    const float *TL;       // [ncell] T_L^n
+    const float *TL;       // [ncell] T_L^n; also the code reference of e_out (16-bit storage)
+    const float *R;        // [ncell] code reference of e_in (16-bit storage: T_L of the step that wrote it)
+    float invTs;           // 1 / T_scale
+    int sr;                // 16-bit codes of e_out: 0 round to nearest, 1 stochastic rounding
+    unsigned srkey;        // key of this step's rounding bits (from the seed and the step index)
     const float *Q;        // [ncell] or null
-    const void *ediff_in;  // [6][nb][wc_max] diffuse-wall incoming values from e^n (storage format)
-    void *ediff_out;       // [6][nb][wc_max] from e^{n+1} (storage format)
+    const void *ediff_in;  // [6][nb][wc_max] wall ghost values of e^n: diffuse-wall values, and for
+                           // 16-bit storage the thermalizing-wall emission (storage format, coded
+                           // against the reference of the wall cell like the state)
+    void *ediff_out;       // [6][nb][wc_max] the same for e^{n+1}
     float *P;              // moment partials [G][ncell]
 };
 
 // Launchers (bte_kernels.cu).  All return the launch error (cudaGetLastError()).
-cudaError_t launch_fill(const StepArgs &a, int storage, const double *dT0, cudaStream_t s);
+cudaError_t launch_fill(const StepArgs &a, int storage, const double *dT0, float *R_out, cudaStream_t s);
 cudaError_t launch_moment_only(const StepArgs &a, int storage, cudaStream_t s);
 cudaError_t launch_step_generic(const StepArgs &a, int storage, int limiter, cudaStream_t s);
 cudaError_t launch_finalize(const StepArgs &a, int G, float *TL_out, cudaStream_t s);
+// Decoded state values e (FP32, [nb*nd][ncell]) of e_in into out (device).
+cudaError_t launch_decode(const StepArgs &a, int storage, float *out, cudaStream_t s);
 
 // FP64 diagnostics (bte_kernels.cu).
 struct DiagOut {

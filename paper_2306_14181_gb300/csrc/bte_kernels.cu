@@ -12,45 +12,86 @@
 namespace bte {
 
 // ------------------------------------------------------------------------------------------
-// Storage codecs: e = s_k * h for 16-bit storage, all arithmetic in FP32.
+// Storage codecs.  FP32 storage keeps e itself.  16-bit storage keeps, per (k, d, cell i),
+//   h = round(e / s_k - rho_i),   s_k = C_k T_scale / W,   rho_i = R_i / T_scale,
+// where R is the reference temperature field of the state (the T_L the step that wrote it
+// relaxed towards).  s_k rho_i = C_k R_i / W is band k's equilibrium at R_i, so h holds only
+// the departure from the local equilibrium and the 16-bit rounding error scales with that
+// departure instead of with e: e = s_k (h + rho_i).  All arithmetic is FP32.
 // st() stores the rounded code and returns the value it represents, so that the moment and
 // the diffuse-wall sums use the stored state.
 // ------------------------------------------------------------------------------------------
 template <int S> struct Codec;
 template <> struct Codec<kStoreF32> {
     using T = float;
-    static __device__ __forceinline__ float ld(const T *p, long long i, const BandConst &) { return p[i]; }
-    static __device__ __forceinline__ double ld64(const T *p, long long i, const BandConst &) { return (double)p[i]; }
-    static __device__ __forceinline__ float st(T *p, long long i, float v, const BandConst &) { p[i] = v; return v; }
+    static constexpr bool kRef = false;
+    static __device__ __forceinline__ float ld(const T *p, long long i, const BandConst &, float) { return p[i]; }
+    static __device__ __forceinline__ double ld64(const T *p, long long i, const BandConst &, float) {
+        return (double)p[i];
+    }
+    static __device__ __forceinline__ float st(T *p, long long i, float v, const BandConst &, float) {
+        p[i] = v;
+        return v;
+    }
+    static __device__ __forceinline__ float st_sr(T *p, long long i, float v, const BandConst &, float, uint32_t) {
+        p[i] = v;
+        return v;
+    }
 };
 template <> struct Codec<kStoreF16> {
     using T = __half;
-    static __device__ __forceinline__ float ld(const T *p, long long i, const BandConst &b) {
-        return b.scale * __half2float(p[i]);
+    static constexpr bool kRef = true;
+    static __device__ __forceinline__ float ld(const T *p, long long i, const BandConst &b, float rho) {
+        return b.scale * (__half2float(p[i]) + rho);
     }
-    static __device__ __forceinline__ double ld64(const T *p, long long i, const BandConst &b) {
-        return (double)b.scale * (double)__half2float(p[i]);
+    static __device__ __forceinline__ double ld64(const T *p, long long i, const BandConst &b, float rho) {
+        return (double)b.scale * ((double)__half2float(p[i]) + (double)rho);
     }
-    static __device__ __forceinline__ float st(T *p, long long i, float v, const BandConst &b) {
-        const __half h = __float2half_rn(v * b.inv_scale);
+    static __device__ __forceinline__ float st(T *p, long long i, float v, const BandConst &b, float rho) {
+        const __half h = __float2half_rn(fmaf(v, b.inv_scale, -rho));
         p[i] = h;
-        return b.scale * __half2float(h);
+        return b.scale * (__half2float(h) + rho);
+    }
+    // stochastic rounding: 13 random bits added below binary16's 10 fraction bits, then
+    // truncated (exact for normal binary16 values; round to nearest in the subnormal range)
+    static __device__ __forceinline__ float st_sr(T *p, long long i, float v, const BandConst &b, float rho,
+                                                  uint32_t bits) {
+        const uint32_t u = __float_as_uint(fmaf(v, b.inv_scale, -rho)) + (bits >> 19);
+        const __half h = __float2half_rn(__uint_as_float(u & 0xffffe000u));
+        p[i] = h;
+        return b.scale * (__half2float(h) + rho);
     }
 };
 template <> struct Codec<kStoreBF16> {
     using T = __nv_bfloat16;
-    static __device__ __forceinline__ float ld(const T *p, long long i, const BandConst &b) {
-        return b.scale * __bfloat162float(p[i]);
+    static constexpr bool kRef = true;
+    static __device__ __forceinline__ float ld(const T *p, long long i, const BandConst &b, float rho) {
+        return b.scale * (__bfloat162float(p[i]) + rho);
     }
-    static __device__ __forceinline__ double ld64(const T *p, long long i, const BandConst &b) {
-        return (double)b.scale * (double)__bfloat162float(p[i]);
+    static __device__ __forceinline__ double ld64(const T *p, long long i, const BandConst &b, float rho) {
+        return (double)b.scale * ((double)__bfloat162float(p[i]) + (double)rho);
     }
-    static __device__ __forceinline__ float st(T *p, long long i, float v, const BandConst &b) {
-        const __nv_bfloat16 h = __float2bfloat16_rn(v * b.inv_scale);
+    static __device__ __forceinline__ float st(T *p, long long i, float v, const BandConst &b, float rho) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(fmaf(v, b.inv_scale, -rho));
         p[i] = h;
-        return b.scale * __bfloat162float(h);
+        return b.scale * (__bfloat162float(h) + rho);
+    }
+    // stochastic rounding: 16 random bits added below bfloat16's 7 fraction bits, then truncated
+    static __device__ __forceinline__ float st_sr(T *p, long long i, float v, const BandConst &b, float rho,
+                                                  uint32_t bits) {
+        const uint32_t u = __float_as_uint(fmaf(v, b.inv_scale, -rho)) + (bits >> 16);
+        const __nv_bfloat16 h = __ushort_as_bfloat16((unsigned short)(u >> 16));
+        p[i] = h;
+        return b.scale * (__bfloat162float(h) + rho);
     }
 };
+
+// Scaled code reference rho_j = R_j / T_scale of cell j (0 for FP32 storage, R untouched).
+template <class Cd>
+__device__ __forceinline__ float rho_at(const float *R, float invTs, long long j) {
+    if constexpr (Cd::kRef) return R[j] * invTs;
+    else return 0.f;
+}
 
 // Slope limiter of the one-sided differences a (upwind) and b (downwind); e_face = e_m + L/2.
 template <int LIM> __device__ __forceinline__ float limit(float a, float b);
@@ -91,28 +132,29 @@ __device__ __forceinline__ float ext_value(const StepArgs &a, const typename Cd:
                                            float nu) {
     const int n = a.n[ax];
     const long long st = a.stride[ax];
-    if (pos >= 0 && pos < n) return Cd::ld(e, base + i + (long long)(pos - c[ax]) * st, b);
+    if (pos >= 0 && pos < n) {
+        const long long j = i + (long long)(pos - c[ax]) * st;
+        return Cd::ld(e, base + j, b, rho_at<Cd>(a.R, a.invTs, j));
+    }
     const int side = pos < 0 ? 0 : 1;
     const int wall = 2 * ax + side;
     const int bc = a.bc[wall];
     if (bc == kBcPeriodic) {
-        const int p2 = side ? pos - n : pos + n;
-        return Cd::ld(e, base + i + (long long)(p2 - c[ax]) * st, b);
+        const long long j = i + (long long)((side ? pos - n : pos + n) - c[ax]) * st;
+        return Cd::ld(e, base + j, b, rho_at<Cd>(a.R, a.invTs, j));
     }
     if (bc == kBcSpecular) {
         const int layer = side ? pos - n + 1 : -pos;
-        const int mpos = side ? n - layer : layer - 1;
+        const long long j = i + (long long)((side ? n - layer : layer - 1) - c[ax]) * st;
         const long long mbase = ((long long)k * a.nd + a.mirror[ax * a.nd + d]) * a.ncell;
-        return Cd::ld(e, mbase + i + (long long)(mpos - c[ax]) * st, b);
+        return Cd::ld(e, mbase + j, b, rho_at<Cd>(a.R, a.invTs, j));
     }
     const bool incoming = side == 0 ? (nu > 0.f) : (nu < 0.f);
-    if (!incoming) {
-        const int wpos = side ? n - 1 : 0;
-        return Cd::ld(e, base + i + (long long)(wpos - c[ax]) * st, b);
-    }
+    const long long jw = i + (long long)((side ? n - 1 : 0) - c[ax]) * st;  // the wall cell
+    if (!incoming) return Cd::ld(e, base + jw, b, rho_at<Cd>(a.R, a.invTs, jw));
     if (bc == kBcIsothermal) return a.iso[wall * a.nb + k];
     return Cd::ld(static_cast<const typename Cd::T *>(a.ediff_in),
-                  ((long long)wall * a.nb + k) * a.wc_max + wall_cell(a, ax, c), b);
+                  ((long long)wall * a.nb + k) * a.wc_max + wall_cell(a, ax, c), b, rho_at<Cd>(a.R, a.invTs, jw));
 }
 
 // Diffuse walls touched by cell c: their indices into wl[], count returned.
@@ -147,6 +189,7 @@ __global__ void __launch_bounds__(256) k_step_generic(const StepArgs a) {
     const T *ein = static_cast<const T *>(a.e_in);
     T *eout = static_cast<T *>(a.e_out);
     const float eq = b.ck * a.TL[i];
+    const float rho_i = rho_at<Cd>(a.R, a.invTs, i), rho_new = rho_at<Cd>(a.TL, a.invTs, i);
     const float src = a.Q ? b.srck * (a.amp * a.Q[i]) : 0.f;
     int wl[6];
     const int nw = diffuse_walls_of(a, c, wl);
@@ -155,7 +198,7 @@ __global__ void __launch_bounds__(256) k_step_generic(const StepArgs a) {
     for (int d = 0; d < a.nd; ++d) {
         const int plane = k * a.nd + d;
         const long long base = (long long)plane * a.ncell;
-        const float e0 = Cd::ld(ein, base + i, b);
+        const float e0 = Cd::ld(ein, base + i, b, rho_i);
         float div = 0.f;
         for (int ax = 0; ax < a.dim; ++ax) {
             const float nu = a.nu[plane * 3 + ax];
@@ -169,7 +212,8 @@ __global__ void __launch_bounds__(256) k_step_generic(const StepArgs a) {
             div += fabsf(nu) * (fo - fi);
         }
         const float en = e0 - div + b.dtinv * (eq - e0) + src;
-        const float es = Cd::st(eout, base + i, en, b);
+        const float es = a.sr ? Cd::st_sr(eout, base + i, en, b, rho_new, mix32(plane_key(a.srkey, plane) ^ (uint32_t)i))
+                              : Cd::st(eout, base + i, en, b, rho_new);
         acc += a.wmom[plane] * es;
         for (int j = 0; j < nw; ++j) wacc[j] += a.wdiff[wl[j] * a.nd + d] * es;
     }
@@ -177,11 +221,26 @@ __global__ void __launch_bounds__(256) k_step_generic(const StepArgs a) {
     for (int j = 0; j < nw; ++j) {
         const int w = wl[j];
         Cd::st(static_cast<T *>(a.ediff_out), ((long long)w * a.nb + k) * a.wc_max + wall_cell(a, w >> 1, c),
-               wacc[j] * a.inv_den[w], b);
+               wacc[j] * a.inv_den[w], b, rho_new);
     }
 }
 
-// Moment partials and diffuse-wall values of the current state without stepping (after an
+// Thermalizing-wall emission C_k T_w / W of band k as a ghost code against the reference rho of
+// wall cell i (16-bit storage; the tiled kernel copies these rows like diffuse-wall rows).
+template <class Cd>
+__device__ __forceinline__ void store_iso_codes(const StepArgs &a, int k, long long i, const int c[3], float rho,
+                                                const BandConst &b) {
+    if constexpr (Cd::kRef) {
+        for (int w = 0; w < 2 * a.dim; ++w) {
+            const int ax = w >> 1;
+            if (a.bc[w] != kBcIsothermal || c[ax] != ((w & 1) ? a.n[ax] - 1 : 0)) continue;
+            Cd::st(static_cast<typename Cd::T *>(a.ediff_out), ((long long)w * a.nb + k) * a.wc_max + wall_cell(a, ax, c),
+                   a.iso[w * a.nb + k], b, rho);
+        }
+    }
+}
+
+// Moment partials and wall ghost values of the current state without stepping (after an
 // equilibrium fill or a state upload).  Writes P[k][i] and ediff_out.
 template <int S>
 __global__ void __launch_bounds__(256) k_moment_only(const StepArgs a) {
@@ -194,13 +253,14 @@ __global__ void __launch_bounds__(256) k_moment_only(const StepArgs a) {
     cell_coords(a, i, c);
     const BandConst b = a.band[k];
     const T *e = static_cast<const T *>(a.e_in);
+    const float rho_i = rho_at<Cd>(a.R, a.invTs, i);
     int wl[6];
     const int nw = diffuse_walls_of(a, c, wl);
     float wacc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float acc = 0.f;
     for (int d = 0; d < a.nd; ++d) {
         const int plane = k * a.nd + d;
-        const float es = Cd::ld(e, (long long)plane * a.ncell + i, b);
+        const float es = Cd::ld(e, (long long)plane * a.ncell + i, b, rho_i);
         acc += a.wmom[plane] * es;
         for (int j = 0; j < nw; ++j) wacc[j] += a.wdiff[wl[j] * a.nd + d] * es;
     }
@@ -208,8 +268,9 @@ __global__ void __launch_bounds__(256) k_moment_only(const StepArgs a) {
     for (int j = 0; j < nw; ++j) {
         const int w = wl[j];
         Cd::st(static_cast<T *>(a.ediff_out), ((long long)w * a.nb + k) * a.wc_max + wall_cell(a, w >> 1, c),
-               wacc[j] * a.inv_den[w], b);
+               wacc[j] * a.inv_den[w], b, rho_i);
     }
+    store_iso_codes<Cd>(a, k, i, c, rho_i, b);
 }
 
 // T_L_i = (sum_g P[g][i]) / sum_k C_k/tau_k, Eq. (BTE_get_e0), summed in fixed g order.
@@ -222,9 +283,10 @@ __global__ void __launch_bounds__(256) k_finalize(const float *__restrict__ P, i
     TL[i] = s * invD;
 }
 
-// Equilibrium fill e_{k,d,i} = C_k dT0_i / W (Algorithm 2, initial state).
+// Equilibrium fill e_{k,d,i} = C_k dT0_i / W (Algorithm 2, initial state); the code reference
+// of the filled state is dT0 itself (written to R_out by the plane-0 threads).
 template <int S>
-__global__ void __launch_bounds__(256) k_fill(const StepArgs a, const double *dT0) {
+__global__ void __launch_bounds__(256) k_fill(const StepArgs a, const double *dT0, float *R_out) {
     using Cd = Codec<S>;
     using T = typename Cd::T;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -233,20 +295,42 @@ __global__ void __launch_bounds__(256) k_fill(const StepArgs a, const double *dT
     const int k = plane / a.nd;
     const BandConst b = a.band[k];
     const float t = dT0 ? (float)dT0[i] : 0.f;
-    Cd::st(static_cast<T *>(a.e_out), (long long)plane * a.ncell + i, b.ck * t, b);
+    if (plane == 0 && R_out) R_out[i] = t;
+    Cd::st(static_cast<T *>(a.e_out), (long long)plane * a.ncell + i, b.ck * t, b, t * a.invTs);
+}
+
+// Decoded values e = s_k (h + rho_i) (or e itself for FP32) of the state e_in.
+template <int S>
+__global__ void __launch_bounds__(256) k_decode(const StepArgs a, float *out) {
+    using Cd = Codec<S>;
+    using T = typename Cd::T;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.ncell) return;
+    const int plane = blockIdx.y;
+    const BandConst b = a.band[plane / a.nd];
+    const long long j = (long long)plane * a.ncell + i;
+    out[j] = Cd::ld(static_cast<const T *>(a.e_in), j, b, rho_at<Cd>(a.R, a.invTs, i));
 }
 
 static dim3 cell_grid(long long ncell, int y) { return dim3((unsigned)((ncell + 255) / 256), (unsigned)y); }
 
 template <int S>
-static void fill_s(const StepArgs &a, const double *dT0, cudaStream_t s) {
-    k_fill<S><<<cell_grid(a.ncell, a.nb * a.nd), 256, 0, s>>>(a, dT0);
+static void fill_s(const StepArgs &a, const double *dT0, float *R_out, cudaStream_t s) {
+    k_fill<S><<<cell_grid(a.ncell, a.nb * a.nd), 256, 0, s>>>(a, dT0, R_out);
 }
 
-cudaError_t launch_fill(const StepArgs &a, int storage, const double *dT0, cudaStream_t s) {
-    if (storage == kStoreF32) fill_s<kStoreF32>(a, dT0, s);
-    else if (storage == kStoreF16) fill_s<kStoreF16>(a, dT0, s);
-    else fill_s<kStoreBF16>(a, dT0, s);
+cudaError_t launch_fill(const StepArgs &a, int storage, const double *dT0, float *R_out, cudaStream_t s) {
+    if (storage == kStoreF32) fill_s<kStoreF32>(a, dT0, R_out, s);
+    else if (storage == kStoreF16) fill_s<kStoreF16>(a, dT0, R_out, s);
+    else fill_s<kStoreBF16>(a, dT0, R_out, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decode(const StepArgs &a, int storage, float *out, cudaStream_t s) {
+    const dim3 g = cell_grid(a.ncell, a.nb * a.nd);
+    if (storage == kStoreF32) k_decode<kStoreF32><<<g, 256, 0, s>>>(a, out);
+    else if (storage == kStoreF16) k_decode<kStoreF16><<<g, 256, 0, s>>>(a, out);
+    else k_decode<kStoreBF16><<<g, 256, 0, s>>>(a, out);
     return cudaGetLastError();
 }
 
@@ -292,13 +376,14 @@ __global__ void __launch_bounds__(256) k_moments64(const StepArgs a, const doubl
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.ncell) return;
     const T *e = static_cast<const T *>(a.e_in);
+    const float rho_i = rho_at<Cd>(a.R, a.invTs, i);
     double et = 0.0, tl = 0.0, qx = 0.0, qy = 0.0, qz = 0.0;
     bool bad = false;
     for (int k = 0; k < a.nb; ++k) {
         const BandConst b = a.band[k];
         double sk = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
         for (int d = 0; d < a.nd; ++d) {
-            const double ed = Cd::ld64(e, ((long long)k * a.nd + d) * a.ncell + i, b);
+            const double ed = Cd::ld64(e, ((long long)k * a.nd + d) * a.ncell + i, b, rho_i);
             bad |= !isfinite(ed);
             const double we = w[d] * ed;
             sk += we;
@@ -329,22 +414,29 @@ __device__ double ext64(const StepArgs &a, const typename Cd::T *e, const BandCo
     const int n = a.n[ax];
     const long long st = a.stride[ax];
     const long long base = ((long long)k * a.nd + d) * a.ncell;
-    if (pos >= 0 && pos < n) return Cd::ld64(e, base + i + (long long)(pos - c[ax]) * st, b);
+    if (pos >= 0 && pos < n) {
+        const long long j = i + (long long)(pos - c[ax]) * st;
+        return Cd::ld64(e, base + j, b, rho_at<Cd>(a.R, a.invTs, j));
+    }
     const int side = pos < 0 ? 0 : 1;
     const int wall = 2 * ax + side;
     const int bc = a.bc[wall];
-    if (bc == kBcPeriodic) return Cd::ld64(e, base + i + (long long)((side ? pos - n : pos + n) - c[ax]) * st, b);
+    if (bc == kBcPeriodic) {
+        const long long j = i + (long long)((side ? pos - n : pos + n) - c[ax]) * st;
+        return Cd::ld64(e, base + j, b, rho_at<Cd>(a.R, a.invTs, j));
+    }
     if (bc == kBcSpecular) {
         const int layer = side ? pos - n + 1 : -pos;
-        const int mpos = side ? n - layer : layer - 1;
+        const long long j = i + (long long)((side ? n - layer : layer - 1) - c[ax]) * st;
         const long long mbase = ((long long)k * a.nd + a.mirror[ax * a.nd + d]) * a.ncell;
-        return Cd::ld64(e, mbase + i + (long long)(mpos - c[ax]) * st, b);
+        return Cd::ld64(e, mbase + j, b, rho_at<Cd>(a.R, a.invTs, j));
     }
     const bool incoming = side == 0 ? (sa > 0.0) : (sa < 0.0);
-    if (!incoming) return Cd::ld64(e, base + i + (long long)((side ? n - 1 : 0) - c[ax]) * st, b);
+    const long long jw = i + (long long)((side ? n - 1 : 0) - c[ax]) * st;
+    if (!incoming) return Cd::ld64(e, base + jw, b, rho_at<Cd>(a.R, a.invTs, jw));
     if (bc == kBcIsothermal) return (double)a.iso[wall * a.nb + k];
     return Cd::ld64(static_cast<const typename Cd::T *>(a.ediff_in),
-                    ((long long)wall * a.nb + k) * a.wc_max + wall_cell(a, ax, c), b);
+                    ((long long)wall * a.nb + k) * a.wc_max + wall_cell(a, ax, c), b, rho_at<Cd>(a.R, a.invTs, jw));
 }
 
 // Outward heat flow through one wall, per (wall cell j, band k): sum_d w v (s.n) e_face, with
@@ -495,12 +587,13 @@ __global__ void __launch_bounds__(kNaThreads) k_na_energy(const StepArgs a, cons
     double acc = 0.0;
     bool bad = false;
     for (long long i = lo + threadIdx.x; i < hi; i += kNaThreads) {
+        const float rho_i = rho_at<Cd>(a.R, a.invTs, i);
         double et = 0.0;
         for (int k = 0; k < a.nb; ++k) {
             const BandConst b = a.band[k];
             double sk = 0.0;
             for (int d = 0; d < a.nd; ++d) {
-                const double ed = Cd::ld64(e, ((long long)k * a.nd + d) * a.ncell + i, b);
+                const double ed = Cd::ld64(e, ((long long)k * a.nd + d) * a.ncell + i, b, rho_i);
                 bad |= !isfinite(ed);
                 sk += w[d] * ed;
             }

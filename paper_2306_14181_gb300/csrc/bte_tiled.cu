@@ -50,7 +50,10 @@ __global__ void __launch_bounds__(256) k_finalize_tiled(const StepArgs a, const 
     TL[i] = s * a.invD;
 }
 
-// e_diff[w][k][wall cell] = (sum over the band-k segments of the cell's tile) / sum_in w|s.n|
+// Wall ghost values of e^{n+1} for the next step.  Diffuse wall: e_diff[w][k][wall cell] =
+// (sum over the band-k segments of the cell's tile) / sum_in w|s.n|.  With 16-bit storage the
+// value is coded against the wall cell's new reference rho = T_L^n / T_scale, and thermalizing
+// y/z walls get their emission C_k T_w / W coded the same way.
 template <int S>
 __global__ void __launch_bounds__(256) k_ediff_tiled(const StepArgs a, const TiledArgs p, int wall) {
     using T = typename St<S>::T;
@@ -66,27 +69,35 @@ __global__ void __launch_bounds__(256) k_ediff_tiled(const StepArgs a, const Til
     if (ax == 0) { x = side ? nx - 1 : 0; y = ja; z = jb; }
     else if (ax == 1) { x = ja; y = side ? ny - 1 : 0; z = jb; }
     else { x = ja; y = jb; z = side ? nz - 1 : 0; }
-    const int ty = y / p.ty, tz = z / p.tz;
-    const int tile = tz * p.nty + ty;
-    const int yl = y - ty * p.ty, zl = z - tz * p.tz;
-    const int slot = ax == 0 ? zl * p.ty + yl : (ax == 1 ? zl * nx + x : yl * nx + x);
-    float s = 0.f;
-    for (int j = 0; j < p.J; ++j) {
-        const int u = j * p.ntiles + tile;
-        const int p0 = part_begin(p, j), p1 = part_begin(p, j + 1);
-        if (p0 >= p1) continue;
-        const int b0 = p0 / a.nd, b1 = (p1 - 1) / a.nd;
-        if (k < b0 || k > b1) continue;
-        s += p.PW[((size_t)(p.unit_seg0[u] + k - b0) * p.nwd + p.wslot[wall]) * p.tw + slot];
-    }
     const BandConst b = a.band[k];
-    static_cast<T *>(a.ediff_out)[((long long)wall * a.nb + k) * a.wc_max + j] = St<S>::enc(s * a.inv_den[wall],
-                                                                                            b.inv_scale);
+    float v;
+    if (a.bc[wall] == kBcIsothermal) {
+        v = a.iso[wall * a.nb + k];
+    } else {
+        const int ty = y / p.ty, tz = z / p.tz;
+        const int tile = tz * p.nty + ty;
+        const int yl = y - ty * p.ty, zl = z - tz * p.tz;
+        const int slot = ax == 0 ? zl * p.ty + yl : (ax == 1 ? zl * nx + x : yl * nx + x);
+        float s = 0.f;
+        for (int jj = 0; jj < p.J; ++jj) {
+            const int u = jj * p.ntiles + tile;
+            const int p0 = part_begin(p, jj), p1 = part_begin(p, jj + 1);
+            if (p0 >= p1) continue;
+            const int b0 = p0 / a.nd, b1 = (p1 - 1) / a.nd;
+            if (k < b0 || k > b1) continue;
+            s += p.PW[((size_t)(p.unit_seg0[u] + k - b0) * p.nwd + p.wslot[wall]) * p.tw + slot];
+        }
+        v = s * a.inv_den[wall];
+    }
+    T *out = static_cast<T *>(a.ediff_out) + ((long long)wall * a.nb + k) * a.wc_max + j;
+    if constexpr (St<S>::kRef) *out = St<S>::enc(fmaf(v, b.inv_scale, -a.TL[((long long)z * ny + y) * nx + x] * a.invTs));
+    else *out = St<S>::enc(v);
 }
 
 // Per-plane constants the producer copies into each stage:
 // [nu_x, nu_y, nu_z, w/tau, dt/tau, s_k, 1/s_k, iso(-x), iso(+x), wdiff(w=0..5), 0]
-__global__ void k_build_headers(const StepArgs a, float *hdr) {
+// (with 16-bit storage the two x-wall emissions in units of s_k, as the kernel computes in them)
+__global__ void k_build_headers(const StepArgs a, float *hdr, int scaled) {
     const int pl = blockIdx.x * blockDim.x + threadIdx.x;
     if (pl >= a.nb * a.nd) return;
     const int k = pl / a.nd, d = pl % a.nd;
@@ -99,20 +110,17 @@ __global__ void k_build_headers(const StepArgs a, float *hdr) {
     h[4] = b.dtinv;
     h[5] = b.scale;
     h[6] = b.inv_scale;
-    h[7] = a.iso[0 * a.nb + k];
-    h[8] = a.iso[1 * a.nb + k];
+    h[7] = scaled ? a.iso[0 * a.nb + k] * b.inv_scale : a.iso[0 * a.nb + k];
+    h[8] = scaled ? a.iso[1 * a.nb + k] * b.inv_scale : a.iso[1 * a.nb + k];
     for (int w = 0; w < 6; ++w) h[9 + w] = (w < 2 * a.dim && a.bc[w] == kBcDiffuse) ? a.wdiff[w * a.nd + d] : 0.f;
     h[15] = 0.f;
 }
 
-// Rows of the thermalizing-wall emission C_k T_w / W (already representable) in the storage format.
-template <int S>
-__global__ void k_fill_isorows(const StepArgs a, int nx, void *rows) {
-    using T = typename St<S>::T;
+// Rows of the thermalizing-wall emission C_k T_w / W (FP32 storage).
+__global__ void k_fill_isorows(const StepArgs a, int nx, float *rows) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;  // over 6 * nb * nx
     if (i >= 6 * a.nb * nx) return;
-    const int wk = i / nx, k = wk % a.nb;
-    static_cast<T *>(rows)[i] = St<S>::enc(a.iso[wk], a.band[k].inv_scale);
+    rows[i] = a.iso[i / nx];
 }
 
 // ---- dispatch -------------------------------------------------------------------------------
@@ -190,9 +198,11 @@ bool tiled_plan(int dim, const int n[3], int nb, int nd, int storage, int limite
         if (bc[w] == kBcDiffuse) plan.wslot[w] = plan.nwd++;
     const size_t wall_bytes = (size_t)std::max(1, plan.nwd) * plan.tw * sizeof(float);
     const size_t bt_bytes = (size_t)plan.tcells * sizeof(float);
+    // 16-bit storage: the code references of the tile and its two-cell halo, one float per cell
+    const size_t rho_bytes = storage == kStoreF32 ? 0 : (size_t)(TY + 4) * (dim == 3 ? TZ + 4 : 1) * nx * sizeof(float);
     plan.ns = 0;
     for (int ns = 4; ns >= 2; --ns)
-        if (plan.stage0 + (size_t)ns * plan.stage_bytes + wall_bytes + 2 * bt_bytes + 128 <= budget) {
+        if (plan.stage0 + (size_t)ns * plan.stage_bytes + wall_bytes + 2 * bt_bytes + rho_bytes + 128 <= budget) {
             plan.ns = ns;
             break;
         }
@@ -203,7 +213,8 @@ bool tiled_plan(int dim, const int n[3], int nb, int nd, int storage, int limite
     plan.wall_off = (int)(plan.stage0 + (size_t)plan.ns * plan.stage_bytes);
     plan.bt_off = plan.wall_off + (int)((wall_bytes + 127) / 128 * 128);
     plan.acc_off = plan.bt_off + (int)((bt_bytes + 127) / 128 * 128);
-    plan.smem = plan.acc_off + (int)bt_bytes;
+    plan.rho_off = plan.acc_off + (int)((bt_bytes + 127) / 128 * 128);
+    plan.smem = plan.rho_off + (int)rho_bytes;
     plan.kernel = (void *)pick(storage, limiter, nx, dim);
     if (!plan.kernel) {
         why = "no kernel instance";
@@ -259,17 +270,16 @@ bool tiled_setup(TiledPlan &plan, const StepArgs &a, std::string &why) {
         why = "cudaMalloc failed";
         return false;
     }
-    k_build_headers<<<(a.nb * a.nd + 127) / 128, 128>>>(a, plan.hdr);
-    const int esz = plan.storage == kStoreF32 ? 4 : 2;
-    const int nrow = 6 * a.nb * plan.nx;
-    if (cudaMalloc(&plan.isorow, (size_t)nrow * esz) != cudaSuccess) {
-        cudaGetLastError();
-        why = "cudaMalloc failed";
-        return false;
+    k_build_headers<<<(a.nb * a.nd + 127) / 128, 128>>>(a, plan.hdr, plan.storage != kStoreF32);
+    if (plan.storage == kStoreF32) {
+        const int nrow = 6 * a.nb * plan.nx;
+        if (cudaMalloc(&plan.isorow, (size_t)nrow * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            why = "cudaMalloc failed";
+            return false;
+        }
+        k_fill_isorows<<<(nrow + 255) / 256, 256>>>(a, plan.nx, static_cast<float *>(plan.isorow));
     }
-    if (plan.storage == kStoreF32) k_fill_isorows<kStoreF32><<<(nrow + 255) / 256, 256>>>(a, plan.nx, plan.isorow);
-    else if (plan.storage == kStoreF16) k_fill_isorows<kStoreF16><<<(nrow + 255) / 256, 256>>>(a, plan.nx, plan.isorow);
-    else k_fill_isorows<kStoreBF16><<<(nrow + 255) / 256, 256>>>(a, plan.nx, plan.isorow);
     if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
         why = "header build failed";
         return false;
@@ -305,6 +315,7 @@ static TiledArgs device_args(const TiledPlan &plan) {
     for (int w = 0; w < 6; ++w) t.wslot[w] = plan.wslot[w];
     t.bt_off = plan.bt_off;
     t.acc_off = plan.acc_off;
+    t.rho_off = plan.rho_off;
     t.nty = plan.nty;
     t.ntz = plan.ntz;
     t.ns = plan.ns;
@@ -326,13 +337,19 @@ cudaError_t launch_step_tiled(const StepArgs &a, const TiledPlan &plan, cudaStre
     return cudaGetLastError();
 }
 
+// Walls whose ghost values the finalize pass writes: diffuse walls, and with 16-bit storage the
+// thermalizing y/z walls (x walls use a per-plane constant).
+static bool tiled_wall_pass(const TiledPlan &plan, const int bc[6], int w) {
+    return bc[w] == kBcDiffuse || (plan.storage != kStoreF32 && bc[w] == kBcIsothermal && (w >> 1) > 0);
+}
+
 cudaError_t launch_finalize_tiled(const StepArgs &a, const TiledPlan &plan, int storage, float *TL_out,
                                   cudaStream_t s) {
     const TiledArgs t = device_args(plan);
     const unsigned nblk = (unsigned)((a.ncell + 255) / 256);
     k_finalize_tiled<<<nblk, 256, 0, s>>>(a, t, TL_out);
     for (int w = 0; w < 2 * plan.dim; ++w) {
-        if (a.bc[w] != kBcDiffuse) continue;
+        if (!tiled_wall_pass(plan, a.bc, w)) continue;
         const int ax = w >> 1;
         const long long nwc = ax == 0 ? (long long)a.n[1] * a.n[2]
                                       : (ax == 1 ? (long long)a.n[0] * a.n[2] : (long long)a.n[0] * a.n[1]);
@@ -346,7 +363,7 @@ cudaError_t launch_finalize_tiled(const StepArgs &a, const TiledPlan &plan, int 
 
 int tiled_finalize_launches(const TiledPlan &plan, const int bc[6]) {
     int n = 1;
-    for (int w = 0; w < 2 * plan.dim; ++w) n += bc[w] == kBcDiffuse;
+    for (int w = 0; w < 2 * plan.dim; ++w) n += tiled_wall_pass(plan, bc, w);
     return n;
 }
 

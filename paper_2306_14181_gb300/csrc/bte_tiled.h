@@ -14,14 +14,14 @@ struct TiledArgs {
     int U, J, np, ntiles;  // units, parts per tile, planes (nb*nd), tiles
     float *PW;             // diffuse-wall partials [G][nwd][tw]
     const float *hdr;      // per-plane constants [nb*nd][16] (see tiled_build_headers)
-    const void *isorow;    // thermalizing-wall emission rows [6][nb][nx] in the storage format
+    const void *isorow;    // thermalizing-wall emission rows [6][nb][nx] (FP32 storage)
     int *err;              // bounded-wait failure flags (1: consumer, 2: producer)
     int tw;                // wall slots per wall per segment
     int nwd;               // number of diffuse walls
     int wslot[6];          // compact index of each diffuse wall, -1 for the others
     int nty, ntz;          // tiles along y and z
     int ns;                // shared-memory stages
-    int stage0, stage_bytes, side_off, hdr_off, wall_off, bt_off, acc_off;  // shared-memory layout (bytes)
+    int stage0, stage_bytes, side_off, hdr_off, wall_off, bt_off, acc_off, rho_off;  // shared-memory layout (bytes)
     int ty, tz;            // tile extents (rows, slices)
     int tcells;            // cells of a full tile (row length of P)
     int chunk;             // rows per bulk copy of a box slice
@@ -39,7 +39,8 @@ struct TiledPlan {
     int dim = 0, vx = 0;
     int G = 0, nctas = 0;
     int nty = 0, ntz = 0, ntiles = 0, tcells = 0, tw = 0;
-    int ns = 0, stage0 = 0, stage_bytes = 0, side_off = 0, hdr_off = 0, wall_off = 0, bt_off = 0, acc_off = 0, smem = 0;
+    int ns = 0, stage0 = 0, stage_bytes = 0, side_off = 0, hdr_off = 0, wall_off = 0, bt_off = 0, acc_off = 0;
+    int rho_off = 0, smem = 0;
     int ty = 0, tz = 0, threads = 0;
     int nwd = 0, wslot[6] = {-1, -1, -1, -1, -1, -1};
     void *kernel = nullptr;

@@ -26,21 +26,40 @@ template <> struct Geo<3, 1> {
     static constexpr int NCW = 12, TZ = 6, TY = NCW / TZ * kR;
 };
 
+// Storage codecs.  FP32 storage keeps e.  16-bit storage keeps h = round(e / s_k - rho_i) with
+// rho_i = R_i / T_scale the cell's code reference (the departure from band k's equilibrium at
+// the reference temperature R_i, in units of s_k = C_k T_scale / W).  The 16-bit instances work
+// in these scaled units throughout a plane: decoding is e / s_k = h + rho_i, and the updated
+// value leaves the arithmetic already as the departure from the new reference, so encoding is
+// the rounding alone.
 template <int S> struct St;
 template <> struct St<kStoreF32> {
     using T = float;
+    static constexpr bool kRef = false;
     static __device__ __forceinline__ float dec(T h, float) { return h; }
-    static __device__ __forceinline__ T enc(float v, float) { return v; }
+    static __device__ __forceinline__ T enc(float v) { return v; }
+    static __device__ __forceinline__ T enc_sr(float v, uint32_t) { return v; }
 };
 template <> struct St<kStoreF16> {
     using T = __half;
-    static __device__ __forceinline__ float dec(T h, float sc) { return sc * __half2float(h); }
-    static __device__ __forceinline__ T enc(float v, float inv) { return __float2half_rn(v * inv); }
+    static constexpr bool kRef = true;
+    static __device__ __forceinline__ float dec(T h, float rho) { return __half2float(h) + rho; }
+    static __device__ __forceinline__ T enc(float v) { return __float2half_rn(v); }
+    // stochastic rounding: 13 random bits below binary16's 10 fraction bits, then truncation
+    // (exact for normal binary16 values; round to nearest in the subnormal range)
+    static __device__ __forceinline__ T enc_sr(float v, uint32_t bits) {
+        return __float2half_rn(__uint_as_float((__float_as_uint(v) + (bits >> 19)) & 0xffffe000u));
+    }
 };
 template <> struct St<kStoreBF16> {
     using T = __nv_bfloat16;
-    static __device__ __forceinline__ float dec(T h, float sc) { return sc * __bfloat162float(h); }
-    static __device__ __forceinline__ T enc(float v, float inv) { return __float2bfloat16_rn(v * inv); }
+    static constexpr bool kRef = true;
+    static __device__ __forceinline__ float dec(T h, float rho) { return __bfloat162float(h) + rho; }
+    static __device__ __forceinline__ T enc(float v) { return __float2bfloat16_rn(v); }
+    // stochastic rounding: 16 random bits below bfloat16's 7 fraction bits, then truncation
+    static __device__ __forceinline__ T enc_sr(float v, uint32_t bits) {
+        return __ushort_as_bfloat16((unsigned short)((__float_as_uint(v) + (bits >> 16)) >> 16));
+    }
 };
 
 // PTX approximate reciprocal (one MUFU operation, no special-case branches).
@@ -155,24 +174,36 @@ template <int NCW>
 __device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(NCW * 32) : "memory"); }
 
 // ---- VL-wide loads and stores ---------------------------------------------------------------
+// VL decoded values of a box row: p points at the codes, r at the same cells' references in the
+// shared reference box (read by the 16-bit instances only).
 template <int S, int VL>
-__device__ __forceinline__ void ld_row(float (&v)[VL], const typename St<S>::T *p, float sc) {
+__device__ __forceinline__ void ld_row(float (&v)[VL], const typename St<S>::T *p, const float *r) {
     using T = typename St<S>::T;
     constexpr int B = VL * (int)sizeof(T);
+    alignas(16) T h[VL];
     if constexpr (B == 16) {
-        const uint4 q = *reinterpret_cast<const uint4 *>(p);
-        const T *h = reinterpret_cast<const T *>(&q);
-        #pragma unroll
-        for (int j = 0; j < VL; ++j) v[j] = St<S>::dec(h[j], sc);
+        *reinterpret_cast<uint4 *>(h) = *reinterpret_cast<const uint4 *>(p);
     } else if constexpr (B == 8) {
-        const uint2 q = *reinterpret_cast<const uint2 *>(p);
-        const T *h = reinterpret_cast<const T *>(&q);
-        #pragma unroll
-        for (int j = 0; j < VL; ++j) v[j] = St<S>::dec(h[j], sc);
+        *reinterpret_cast<uint2 *>(h) = *reinterpret_cast<const uint2 *>(p);
     } else {
         #pragma unroll
-        for (int j = 0; j < VL; ++j) v[j] = St<S>::dec(p[j], sc);
+        for (int j = 0; j < VL; ++j) h[j] = p[j];
     }
+    float rr[VL];
+    if constexpr (St<S>::kRef) {
+        if constexpr (VL == 4) {
+            const float4 f = *reinterpret_cast<const float4 *>(r);
+            rr[0] = f.x; rr[1] = f.y; rr[2] = f.z; rr[3] = f.w;
+        } else {
+            #pragma unroll
+            for (int j = 0; j < VL; ++j) rr[j] = r[j];
+        }
+    } else {
+        #pragma unroll
+        for (int j = 0; j < VL; ++j) rr[j] = 0.f;
+    }
+    #pragma unroll
+    for (int j = 0; j < VL; ++j) v[j] = St<S>::dec(h[j], rr[j]);
 }
 
 template <int S, int VL>
@@ -274,8 +305,12 @@ __device__ __forceinline__ const typename St<S>::T *ghost_row_src(const StepArgs
     }
     const bool incoming = side == 0 ? (nu > 0.f) : (nu < 0.f);
     if (!incoming) return row_at(q.plane, side ? n - 1 : 0);
-    if (bc == kBcIsothermal) return static_cast<const T *>(p.isorow) + ((long long)wall * a.nb + q.k) * NX;
-    // diffuse wall: wall cells of a y-wall are indexed z*nx + x, those of a z-wall y*nx + x
+    if constexpr (!St<S>::kRef) {
+        if (bc == kBcIsothermal) return static_cast<const T *>(p.isorow) + ((long long)wall * a.nb + q.k) * NX;
+    }
+    // diffuse wall (and with 16-bit storage the thermalizing wall, whose emission is coded
+    // against each wall cell's reference): wall cells of a y-wall are indexed z*nx + x, those
+    // of a z-wall y*nx + x
     return static_cast<const T *>(a.ediff_in) + ((long long)wall * a.nb + q.k) * a.wc_max + (long long)other * NX;
 }
 
@@ -419,15 +454,17 @@ enum { kGhShfl = 0, kGhSmem = 1, kGhSpec = 2, kGhDiff = 3, kGhConst = 4, kGhOwn 
 
 template <int S, int LIM, int VL, int WPR, int DIM>
 __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs &p, const PT &q, const char *stage,
-                                             int zl, int rb, int half, float *accsm, const float *btsm, float *wsm) {
+                                             int zl, int rb, int half, float *accsm, const float *btsm, float *wsm,
+                                             const float *rbox) {
     using T = typename St<S>::T;
-    constexpr int NX = 32 * VL * WPR, TY = Geo<DIM, WPR>::TY;
+    constexpr bool REF = St<S>::kRef;
+    constexpr int NX = 32 * VL * WPR, TY = Geo<DIM, WPR>::TY, RY = TY + 4;
     const int lane = threadIdx.x & 31, x0 = (half * 32 + lane) * VL;
     const int ny = a.n[1], nz = a.n[2];
     const float *hd = reinterpret_cast<const float *>(stage + p.hdr_off);  // per-plane constants
     const float4 h0 = reinterpret_cast<const float4 *>(hd)[0];
     const float nux = h0.x, nuy = h0.y, nuz = h0.z, wm = h0.w;
-    const float dtinv = hd[4], sc = hd[5], isc = hd[6];
+    const float dtinv = hd[4], sc = hd[5];
     const float any = fabsf(nuy), anz = fabsf(nuz);
     const int sy = nuy > 0.f ? 1 : -1, sz = nuz > 0.f ? 1 : -1;
     const int nrows = min(kR, q.nyt - rb);
@@ -440,6 +477,28 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
     const int dz = sz * (TY + 3) * NX;         // next slice downwind (elements)
     int o = ((z - zbox0) * (TY + 3) + (q.y0 + yl0 - ybox0)) * NX;  // row start in the box
     int c = (zl * TY + yl0) * NX + x0;         // this lane's cells in the tile arrays
+    // the same row in the reference box (rows y0-2.., slices z0-2..), and its upwind steps; a
+    // second ghost layer of a thermalizing or diffuse wall holds the wall value coded against
+    // the wall cell's reference, as the first layer does
+    const int dyR = sy * NX, dzR = sz * RY * NX;
+    const bool sr = REF && a.sr;
+    const uint32_t pkey = sr ? plane_key(a.srkey, q.plane) : 0u;
+    int ro = ((DIM == 3 ? zl + 2 : 0) * RY + yl0 + 2) * NX;
+    int ry2 = 2 * dyR, rz2 = 2 * dzR;
+    if constexpr (REF) {
+        const int yg = q.y0 + yl0 - 2 * sy;
+        if (yg < 0 || yg >= ny) {
+            const int bcy = a.bc[yg < 0 ? 2 : 3];
+            if (bcy == kBcIsothermal || bcy == kBcDiffuse) ry2 = dyR;
+        }
+        if constexpr (DIM == 3) {
+            const int zg = z - 2 * sz;
+            if (zg < 0 || zg >= nz) {
+                const int bcz = a.bc[zg < 0 ? 4 : 5];
+                if (bcz == kBcIsothermal || bcz == kBcDiffuse) rz2 = dzR;
+            }
+        }
+    }
     T *eo = static_cast<T *>(a.e_out) + (long long)q.plane * a.ncell + ((long long)z * ny + q.y0 + yl0) * NX + x0;
     using SD = Side<S, WPR, DIM>;
     char *side = const_cast<char *>(stage) + p.side_off;
@@ -452,6 +511,7 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
     int gmode = kGhShfl;
     const T *gptr = box + o + x0;
     int gstep = dy, gi0 = 0, gi1 = 0;
+    int rx0 = x0, rx1 = x0;  // the two ghosts' cells in the reference box row
     float gc = 0.f;
     if (lane == 0 || lane == 31) {
         const int sd = lane == 0 ? 0 : 1;
@@ -464,11 +524,15 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
             gptr = box + o + gi;
             gi0 = sd == 0 ? 1 : 0;
             gi1 = sd == 0 ? 0 : 1;
+            rx0 = gi + gi0;
+            rx1 = gi + gi1;
         } else if (bc == kBcSpecular) {
             gptr = SD::spec(side, sd, zl, yl0);
             gstep = sy * SD::V;
             gi0 = sd == 0 ? 0 : SD::V - 1;
             gi1 = sd == 0 ? 1 : SD::V - 2;
+            rx0 = (sd == 0 ? 0 : NX - SD::V) + gi0;
+            rx1 = (sd == 0 ? 0 : NX - SD::V) + gi1;
         } else if (leaving) {
             gmode = kGhOwn;
         } else if (bc == kBcIsothermal) {
@@ -477,6 +541,7 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
         } else {
             gptr = SD::dcol(side, sd, zl) + (int)(dcol_src(a, sd, q.k, z, q.y0) & (SD::V - 1)) + yl0;
             gstep = sy;
+            rx0 = rx1 = sd == 0 ? 0 : NX - 1;
         }
     }
     // diffuse-wall sums of Eq. (diff_bound) for the next step: cells next to a diffuse wall add
@@ -490,15 +555,15 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
     float *wy1p = wsm + max(p.wslot[3], 0) * p.tw + zl * NX + x0;
 
     float wm2[VL], wm1[VL], w0[VL], wp1[VL], fin[VL];
-    ld_row<S, VL>(wm2, box + o - 2 * dy + x0, sc);
-    ld_row<S, VL>(wm1, box + o - dy + x0, sc);
-    ld_row<S, VL>(w0, box + o + x0, sc);
+    ld_row<S, VL>(wm2, box + o - 2 * dy + x0, rbox + ro - ry2 + x0);
+    ld_row<S, VL>(wm1, box + o - dy + x0, rbox + ro - dyR + x0);
+    ld_row<S, VL>(w0, box + o + x0, rbox + ro + x0);
     faces<LIM, VL>(wm2, wm1, w0, fin);
     #pragma unroll
     for (int j = 0; j < kR; ++j) {
         if (j >= nrows) break;
         const int y = q.y0 + yl0 + j * sy;
-        ld_row<S, VL>(wp1, box + o + dy + x0, sc);
+        ld_row<S, VL>(wp1, box + o + dy + x0, rbox + ro + dyR + x0);
         float div[VL], fout[VL];
         // y: out face between y and y + sy (upwind y); the in face is the previous row's out face
         faces<LIM, VL>(wm1, w0, wp1, fout);
@@ -514,7 +579,12 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
         ex[VL + 3] = __shfl_sync(0xffffffffu, w0[1], (lane + 1) & 31);
         {
             const T *gp = gptr + j * gstep;
-            float g0 = St<S>::dec(gp[gi0], sc), g1 = St<S>::dec(gp[gi1], sc);
+            float r0 = 0.f, r1 = 0.f;
+            if constexpr (REF) {
+                r0 = rbox[ro + rx0];
+                r1 = rbox[ro + rx1];
+            }
+            float g0 = St<S>::dec(gp[gi0], r0), g1 = St<S>::dec(gp[gi1], r1);
             const float own = lane == 0 ? w0[0] : w0[VL - 1];
             g0 = gmode == kGhConst ? gc : (gmode == kGhOwn ? own : g0);
             g1 = gmode == kGhConst ? gc : (gmode == kGhOwn ? own : g1);
@@ -532,9 +602,9 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
         for (int v = 0; v < VL; ++v) div[v] = fmaf(nux, F[v + 1] - F[v], div[v]);
         if constexpr (DIM == 3) {
             float zm1[VL], zm2[VL], zp1[VL];
-            ld_row<S, VL>(zm1, box + o - dz + x0, sc);
-            ld_row<S, VL>(zm2, box + o - 2 * dz + x0, sc);
-            ld_row<S, VL>(zp1, box + o + dz + x0, sc);
+            ld_row<S, VL>(zm1, box + o - dz + x0, rbox + ro - dzR + x0);
+            ld_row<S, VL>(zm2, box + o - 2 * dz + x0, rbox + ro - rz2 + x0);
+            ld_row<S, VL>(zp1, box + o + dz + x0, rbox + ro + dzR + x0);
             float zo[VL], zi[VL];
             faces<LIM, VL>(zm1, w0, zp1, zo);
             faces<LIM, VL>(zm2, zm1, w0, zi);
@@ -554,11 +624,14 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
         }
         T h[VL];
         float es[VL];
+        const long long grow = ((long long)z * ny + y) * NX;  // global index of the row's first cell
         #pragma unroll
         for (int v = 0; v < VL; ++v) {
+            // FP32: e^{n+1}.  16-bit: bt carries -rho_new, so en is already the new code's value
             const float en = fmaf(-dtinv, w0[v], w0[v] - div[v]) + bt[v];
-            h[v] = St<S>::enc(en, isc);
-            es[v] = St<S>::dec(h[v], sc);
+            if constexpr (REF) h[v] = sr ? St<S>::enc_sr(en, mix32(pkey ^ (uint32_t)(grow + x0 + v))) : St<S>::enc(en);
+            else h[v] = St<S>::enc(en);
+            es[v] = St<S>::dec(h[v], 0.f);
             ac[v] = fmaf(wm, es[v], ac[v]);
         }
         if constexpr (VL == 4) *reinterpret_cast<float4 *>(accsm + c) = make_float4(ac[0], ac[1], ac[2], ac[3]);
@@ -567,17 +640,32 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
             for (int v = 0; v < VL; ++v) accsm[c + v] = ac[v];
         }
         st_row<S, VL>(eo, h);
+        // the stored values at the walls: 16-bit codes are decoded against the new reference
+        // (T_L^n of the cell, read from global memory for wall cells only)
         // x walls: only the two end lanes have a non-zero weight (a predicated update)
-        if (wx != 0.f) wxp[j * sy] += wx * (lane == 0 ? es[0] : es[VL - 1]);
+        if (wx != 0.f) {
+            const int xe = lane == 0 ? 0 : VL - 1;
+            float ev = es[xe];
+            if constexpr (REF) ev = sc * (ev + a.TL[grow + x0 + xe] * a.invTs);
+            wxp[j * sy] += wx * ev;
+        }
         const float wy = y == 0 ? wy0 : (y == ny - 1 ? wy1 : 0.f);  // uniform across the warp
         if (wy != 0.f) {
             float *w = y == 0 ? wy0p : wy1p;
             #pragma unroll
-            for (int v = 0; v < VL; ++v) w[v] += wy * es[v];
+            for (int v = 0; v < VL; ++v) {
+                float ev = es[v];
+                if constexpr (REF) ev = sc * (ev + a.TL[grow + x0 + v] * a.invTs);
+                w[v] += wy * ev;
+            }
         }
         if (DIM == 3 && wz != 0.f) {
             #pragma unroll
-            for (int v = 0; v < VL; ++v) wzp[j * sy * NX + v] += wz * es[v];
+            for (int v = 0; v < VL; ++v) {
+                float ev = es[v];
+                if constexpr (REF) ev = sc * (ev + a.TL[grow + x0 + v] * a.invTs);
+                wzp[j * sy * NX + v] += wz * ev;
+            }
         }
         #pragma unroll
         for (int v = 0; v < VL; ++v) {
@@ -589,6 +677,7 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
         o += dy;
         c += dy;
         eo += dy;
+        ro += dyR;
     }
 }
 
@@ -602,22 +691,34 @@ __device__ __forceinline__ void warp_place(int &zl, int &rb, int &half) {
 }
 
 // End of a segment: this thread's moment partials to P[seg], the diffuse-wall partials of
-// the tile to PW[seg]; both shared arrays are cleared for the next segment.
-template <int VL, int WPR, int DIM>
+// the tile to PW[seg]; both shared arrays are cleared for the next segment.  With 16-bit
+// storage the accumulated sum is sum_d w_d/tau h_d over the segment's planes; the stored
+// values are s_k (h_d + rho_new), so P = s_k * sum + (sum_d w_d/tau) C_k T_L^n / W.
+template <bool REF, int VL, int WPR, int DIM>
 __device__ __forceinline__ void flush_segment(const StepArgs &a, const TiledArgs &p, int seg, const PT &q,
-                                              float *accsm, float *wsm) {
+                                              float *accsm, float *wsm, float wsum) {
     constexpr int NX = 32 * VL * WPR, TY = Geo<DIM, WPR>::TY, NCW = Geo<DIM, WPR>::NCW;
     int zl, rb, half;
     warp_place<VL, WPR, DIM>(zl, rb, half);
     const int x0 = (half * 32 + (threadIdx.x & 31)) * VL;
     float *P = a.P + (size_t)seg * p.tcells;
+    float sc = 1.f, wck = 0.f;
+    if constexpr (REF) {
+        const BandConst b = a.band[q.k];
+        sc = b.scale;
+        wck = wsum * b.ck;
+    }
     #pragma unroll
     for (int r = 0; r < kR; ++r) {
         const int yl = rb + r;
         const int c = (zl * TY + yl) * NX + x0;
         if (yl < q.nyt && zl < q.nzt) {
+            const long long g = ((long long)(q.z0 + zl) * a.n[1] + q.y0 + yl) * NX + x0;
             #pragma unroll
-            for (int v = 0; v < VL; ++v) P[c + v] = accsm[c + v];
+            for (int v = 0; v < VL; ++v) {
+                if constexpr (REF) P[c + v] = fmaf(sc, accsm[c + v], wck * a.TL[g + v]);
+                else P[c + v] = accsm[c + v];
+            }
         }
         #pragma unroll
         for (int v = 0; v < VL; ++v) accsm[c + v] = 0.f;
@@ -630,9 +731,35 @@ __device__ __forceinline__ void flush_segment(const StepArgs &a, const TiledArgs
     consumer_sync<NCW>();
 }
 
+// Row of the reference box for position pos along an axis of n cells: the cell itself inside,
+// the wrapped cell at a periodic wall, else the mirror image (ghost layer L -> cell L-1 from
+// the wall), which is the cell a specular or outgoing ghost is copied from; clamped for rows
+// the stencil never reads.
+__device__ __forceinline__ int ref_row(int pos, int n, int bclo, int bchi) {
+    if (pos < 0) pos = bclo == kBcPeriodic ? pos + n : -pos - 1;
+    else if (pos >= n) pos = bchi == kBcPeriodic ? pos - n : 2 * n - pos - 1;
+    return min(max(pos, 0), n - 1);
+}
+
+// Reference box of a unit's tile: rho = R / T_scale at rows y0-2 .. y0+TY+1 (and slices
+// z0-2 .. z0+TZ+1 in 3-D) of every x, ghost rows mapped by ref_row.
+template <int VL, int WPR, int DIM>
+__device__ __forceinline__ void fill_ref_box(const StepArgs &a, const PT &q, float *rbox) {
+    constexpr int NX = 32 * VL * WPR, TY = Geo<DIM, WPR>::TY, TZ = Geo<DIM, WPR>::TZ, NCW = Geo<DIM, WPR>::NCW;
+    constexpr int RY = TY + 4, RZ = DIM == 3 ? TZ + 4 : 1;
+    const int ny = a.n[1], nz = a.n[2];
+    for (int idx = threadIdx.x; idx < RZ * RY * NX; idx += NCW * 32) {
+        const int x = idx % NX, ry = (idx / NX) % RY, rz = idx / (NX * RY);
+        const int y = ref_row(q.y0 - 2 + ry, ny, a.bc[2], a.bc[3]);
+        const int z = DIM == 3 ? ref_row(q.z0 - 2 + rz, nz, a.bc[4], a.bc[5]) : 0;
+        rbox[idx] = a.R[((long long)z * ny + y) * NX + x] * a.invTs;
+    }
+}
+
 template <int S, int LIM, int VL, int WPR, int DIM>
 __device__ void consumer(const StepArgs &a, const TiledArgs &p, char *smem, uint64_t *full, uint64_t *empty) {
-    constexpr int NX = 32 * VL * WPR, TY = Geo<DIM, WPR>::TY;
+    constexpr bool REF = St<S>::kRef;
+    constexpr int NX = 32 * VL * WPR, TY = Geo<DIM, WPR>::TY, NCW = Geo<DIM, WPR>::NCW;
     const int lane = threadIdx.x & 31;
     int zl, rb, half;
     warp_place<VL, WPR, DIM>(zl, rb, half);
@@ -641,19 +768,30 @@ __device__ void consumer(const StepArgs &a, const TiledArgs &p, char *smem, uint
     float *wsm = reinterpret_cast<float *>(smem + p.wall_off);
     float *btsm = reinterpret_cast<float *>(smem + p.bt_off);
     float *accsm = reinterpret_cast<float *>(smem + p.acc_off);
+    float *rbox = reinterpret_cast<float *>(smem + p.rho_off);
     int seg = -1, cur_unit = -1, cur_band = -1;
+    float wsum = 0.f;  // sum of w_d / tau_k over the segment's planes (16-bit storage)
     PT cur{};
     Cursor<DIM, WPR> c;
     bool more = c.start(a, p);
     for (int i = 0; more; ++i, more = c.next(a, p)) {
         const PT q = c.q;
         if (c.u != cur_unit || q.k != cur_band) {
-            if (seg >= 0) flush_segment<VL, WPR, DIM>(a, p, seg, cur, accsm, wsm);
+            if (seg >= 0) flush_segment<REF, VL, WPR, DIM>(a, p, seg, cur, accsm, wsm, wsum);
+            if constexpr (REF) {
+                // after the flush's barriers no warp reads the previous unit's references
+                if (c.u != cur_unit) {
+                    fill_ref_box<VL, WPR, DIM>(a, q, rbox);
+                    consumer_sync<NCW>();
+                }
+            }
             seg = p.unit_seg0[c.u] + q.k - c.p0 / a.nd;
             cur_unit = c.u;
             cur_band = q.k;
             cur = q;
+            wsum = 0.f;
             // per-cell relaxation target and source of this band: dt/tau C T_L / W + a dt C Q/(sum C W)
+            // (16-bit: in units of s_k, less the new code reference rho_new = T_L^n / T_scale)
             const BandConst b = a.band[q.k];
             #pragma unroll
             for (int r = 0; r < kR; ++r) {
@@ -664,7 +802,10 @@ __device__ void consumer(const StepArgs &a, const TiledArgs &p, char *smem, uint
                     #pragma unroll
                     for (int v = 0; v < VL; ++v) {
                         const float src = a.Q ? b.srck * (a.amp * a.Q[i0 + v]) : 0.f;
-                        bp[v] = fmaf(b.dtinv, b.ck * a.TL[i0 + v], src);
+                        if constexpr (REF)
+                            bp[v] = fmaf(b.dtinv - 1.f, a.TL[i0 + v] * a.invTs, src * b.inv_scale);
+                        else
+                            bp[v] = fmaf(b.dtinv, b.ck * a.TL[i0 + v], src);
                     }
                 }
             }
@@ -673,12 +814,13 @@ __device__ void consumer(const StepArgs &a, const TiledArgs &p, char *smem, uint
         const uint32_t ph = (uint32_t)(i / p.ns) & 1u;
         if (!mbar_wait(&full[s], ph, p.err, 1)) return;
         const char *stage = smem + p.stage0 + (size_t)s * p.stage_bytes;
+        if constexpr (REF) wsum += reinterpret_cast<const float *>(stage + p.hdr_off)[3];
         if (zl < q.nzt && rb < q.nyt)
-            rows_of_warp<S, LIM, VL, WPR, DIM>(a, p, q, stage, zl, rb, half, accsm, btsm, wsm);
+            rows_of_warp<S, LIM, VL, WPR, DIM>(a, p, q, stage, zl, rb, half, accsm, btsm, wsm, rbox);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
     }
-    if (seg >= 0) flush_segment<VL, WPR, DIM>(a, p, seg, cur, accsm, wsm);
+    if (seg >= 0) flush_segment<REF, VL, WPR, DIM>(a, p, seg, cur, accsm, wsm, wsum);
 }
 
 template <int S, int LIM, int VL, int WPR, int DIM>

@@ -48,12 +48,12 @@ def gpu_ctx(cfg, **opts):
                           cfg["Tw"], opts.pop("dt", cfg["dt"]), **opts)
 
 
-def run_both(cfg, e0, nsteps, Q=None, amps=None, limiter=2, storage=0, kernel=0, T_scale=1.0):
+def run_both(cfg, e0, nsteps, Q=None, amps=None, limiter=2, storage=0, kernel=0, T_scale=1.0, **opts):
     """Run the same start state on the GPU and on the oracle.  e0 is taken as float32 (the GPU
     state); the oracle starts from exactly those values.  Returns (gpu_e, gpu_TL, orc_e, orc_TL)."""
     from paper_2306_14181_gb300 import bte
     P = oracle_problem(cfg, limiter)
-    ctx = gpu_ctx(cfg, limiter=limiter, storage=storage, kernel=kernel, T_scale=T_scale)
+    ctx = gpu_ctx(cfg, limiter=limiter, storage=storage, kernel=kernel, T_scale=T_scale, **opts)
     e32 = np.ascontiguousarray(e0, dtype=np.float32)
     if storage == 0:
         bte.bte_set_state(ctx, e32)
