@@ -371,3 +371,301 @@ void orc_energy(const orc_problem *P, const double *e, double *E_total, double *
     }
     free(ediff);
 }
+
+/* ========================================================================= */
+/* Discrete adjoint of the step (not in the paper; the exact transpose of    */
+/* the forward step above, derived by hand).                                  */
+/*                                                                           */
+/* One step is e^{n+1} = F(e^n, T_L(e^n)) with T_L linear in e.  Its          */
+/* Jacobian J = dF/de + dF/dT_L dT_L/de.  For a functional                    */
+/*   J_obj = sum_i p_i T_L,i(e^N)                                             */
+/* the adjoint lambda^N = dT_L/de^T p, lambda^n = J(e^n)^T lambda^{n+1}, and  */
+/*   dJ/dQ_i      = sum_n dt a_n sum_{k,d} lambda^{n+1}_{k,d,i} C_k/(sum C W)  */
+/*   dJ/dlog tau_k = sum_n [ sum_{d,i} lambda^{n+1} (-dt/tau_k)(C_k T_L/W - e) */
+/*                  + sum_i mu_i dT_L,i/dlog tau_k ] + sum_i p_i dT_L^N/dlog tau_k */
+/* with mu_i = sum_{k,d} lambda^{n+1}_{k,d,i} dt C_k/(W tau_k) and            */
+/*   dT_L,i/dlog tau_k = (C_k T_L,i - sum_d w_d e_{k,d,i}) / (tau_k D).       */
+/* Two independent codings of J are given: a forward (tangent) one and a      */
+/* reverse (transpose) one, so that <lambda, J de> = <J^T lambda, de> checks  */
+/* both.                                                                      */
+/* ========================================================================= */
+
+/* Partial derivatives La = dL/da, Lb = dL/db of the slope limiter (0 where ab <= 0). */
+static void limiter_grad(int kind, double a, double b, double *La, double *Lb) {
+    *La = *Lb = 0.0;
+    if (kind == ORC_LIM_FIRST_ORDER || a * b <= 0.0) return;
+    if (kind == ORC_LIM_MINMOD) {
+        if (fabs(a) < fabs(b)) *La = 1.0;
+        else *Lb = 1.0;
+        return;
+    }
+    /* L = ab(a+b)/(a^2+b^2): dL/da = b^2 (2ab + b^2 - a^2)/(a^2+b^2)^2, symmetric in b */
+    const double q = a * a + b * b;
+    *La = b * b * (2.0 * a * b + b * b - a * a) / (q * q);
+    *Lb = a * a * (2.0 * a * b + a * a - b * b) / (q * q);
+}
+
+/* Positions (along axis a) of the upwind-left, upwind and downwind-right values a face
+ * reads, for the face between p and p+1 (same orientation as face_value). */
+static void face_positions(const orc_problem *P, int d, int a, int p, int pos[3]) {
+    if (P->s[3 * d + a] > 0.0) { pos[0] = p - 1; pos[1] = p; pos[2] = p + 1; }
+    else { pos[0] = p + 2; pos[1] = p + 1; pos[2] = p; }
+}
+
+/* d(face)/d(u_l), d(face)/d(u_m), d(face)/d(u_r) of e_face = u_m + L(u_m-u_l, u_r-u_m)/2. */
+static void face_grad(const orc_problem *P, const double *e, const double *ediff, int k, int d, int a,
+                      const int c[3], int p, double g[3]) {
+    int pos[3];
+    face_positions(P, d, a, p, pos);
+    const double ul = ext_value(P, e, ediff, k, d, a, c, pos[0]);
+    const double um = ext_value(P, e, ediff, k, d, a, c, pos[1]);
+    const double ur = ext_value(P, e, ediff, k, d, a, c, pos[2]);
+    double La, Lb;
+    limiter_grad(P->limiter, um - ul, ur - um, &La, &Lb);
+    g[0] = -0.5 * La;
+    g[1] = 1.0 + 0.5 * (La - Lb);
+    g[2] = 0.5 * Lb;
+}
+
+/* The elements an extended value (ext_value) depends on, with their coefficients:
+ * ext = sum_j coef[j] e[idx[j]] + (constant of a thermalizing wall).  Returns the count
+ * (at most nd). */
+static int ext_deps(const orc_problem *P, int k, int d, int a, const int c[3], int p, long *idx, double *coef) {
+    const int n = extent(P, a);
+    int cc[3] = {c[0], c[1], c[2]};
+    if (p >= 0 && p < n) {
+        cc[a] = p;
+        idx[0] = EIDX(P, k, d, cidx(P, cc));
+        coef[0] = 1.0;
+        return 1;
+    }
+    const int side = p < 0 ? 0 : 1;
+    const int layer = p < 0 ? -p : p - n + 1;
+    const int wall = 2 * a + side;
+    const double sa = P->s[3 * d + a];
+    const int incoming = side == 0 ? (sa > 0.0) : (sa < 0.0);
+    const int wallpos = side == 0 ? 0 : n - 1;
+    switch (P->bc[wall]) {
+    case ORC_BC_PERIODIC:
+        cc[a] = ((p % n) + n) % n;
+        idx[0] = EIDX(P, k, d, cidx(P, cc));
+        coef[0] = 1.0;
+        return 1;
+    case ORC_BC_ISOTHERMAL:
+        if (incoming) return 0;
+        cc[a] = wallpos;
+        idx[0] = EIDX(P, k, d, cidx(P, cc));
+        coef[0] = 1.0;
+        return 1;
+    case ORC_BC_DIFFUSE: {
+        cc[a] = wallpos;
+        const long i = cidx(P, cc);
+        if (!incoming) {
+            idx[0] = EIDX(P, k, d, i);
+            coef[0] = 1.0;
+            return 1;
+        }
+        /* e_diff = sum_{s.n>0} w (s.n) e / sum_{s.n<0} w |s.n| at the wall cell */
+        const double nsign = side == 0 ? -1.0 : 1.0;
+        double den = 0.0;
+        for (int dd = 0; dd < P->nd; ++dd) {
+            const double sn = nsign * P->s[3 * dd + a];
+            if (sn < 0.0) den += P->w[dd] * (-sn);
+        }
+        int m = 0;
+        for (int dd = 0; dd < P->nd; ++dd) {
+            const double sn = nsign * P->s[3 * dd + a];
+            if (sn > 0.0) {
+                idx[m] = EIDX(P, k, dd, i);
+                coef[m] = P->w[dd] * sn / den;
+                ++m;
+            }
+        }
+        return m;
+    }
+    case ORC_BC_SPECULAR:
+    default:
+        cc[a] = side == 0 ? layer - 1 : n - layer;
+        idx[0] = EIDX(P, k, P->mirror[a * P->nd + d], cidx(P, cc));
+        coef[0] = 1.0;
+        return 1;
+    }
+}
+
+/* Homogeneous part of an extended value of a perturbation de (thermalizing-wall
+ * emission is a constant, so its perturbation is 0). */
+static double ext_value_lin(const orc_problem *P, const double *de, const double *dediff, int k, int d, int a,
+                            const int c[3], int p) {
+    const int n = extent(P, a);
+    if (p < 0 || p >= n) {
+        const int side = p < 0 ? 0 : 1;
+        const int wall = 2 * a + side;
+        const double sa = P->s[3 * d + a];
+        const int incoming = side == 0 ? (sa > 0.0) : (sa < 0.0);
+        if (P->bc[wall] == ORC_BC_ISOTHERMAL && incoming) return 0.0;
+    }
+    return ext_value(P, de, dediff, k, d, a, c, p);
+}
+
+/* Tangent (forward-mode) step: dout = J(e) de, T_L coupling included. */
+void orc_step_tangent(const orc_problem *P, const double *e, const double *de, double *dout) {
+    const long nc = ncell_of(P);
+    const double W = total_weight(P);
+    double *dTL = (double *)malloc(sizeof(double) * nc);
+    double *ediff = (double *)calloc((size_t)6 * P->nb * nc, sizeof(double));
+    double *dediff = (double *)calloc((size_t)6 * P->nb * nc, sizeof(double));
+    orc_lattice_temperature(P, de, dTL);
+    diffuse_wall_values(P, e, ediff);
+    diffuse_wall_values(P, de, dediff);
+    for (int k = 0; k < P->nb; ++k)
+        for (int d = 0; d < P->nd; ++d)
+            for (int z = 0; z < P->nz; ++z)
+                for (int y = 0; y < P->ny; ++y)
+                    for (int x = 0; x < P->nx; ++x) {
+                        const int c[3] = {x, y, z};
+                        const long i = cidx(P, c);
+                        double ddiv = 0.0;
+                        for (int a = 0; a < P->dim; ++a) {
+                            const double sa = P->s[3 * d + a];
+                            if (sa == 0.0) continue;
+                            const double nu = P->dt * P->v[k] * sa / spacing(P, a);
+                            double dface[2];
+                            for (int f = 0; f < 2; ++f) { /* face i+1/2 (p = c[a]) and i-1/2 (p = c[a]-1) */
+                                const int p = c[a] - f;
+                                int pos[3];
+                                double g[3];
+                                face_positions(P, d, a, p, pos);
+                                face_grad(P, e, ediff, k, d, a, c, p, g);
+                                dface[f] = 0.0;
+                                for (int r = 0; r < 3; ++r)
+                                    dface[f] += g[r] * ext_value_lin(P, de, dediff, k, d, a, c, pos[r]);
+                            }
+                            ddiv += nu * (dface[0] - dface[1]);
+                        }
+                        const double den = de[EIDX(P, k, d, i)];
+                        dout[EIDX(P, k, d, i)] = den - ddiv + P->dt * (P->C[k] * dTL[i] / W - den) / P->tau[k];
+                    }
+    free(dTL);
+    free(ediff);
+    free(dediff);
+}
+
+/* Transposed (reverse-mode) step: lam_out = J(e)^T lam_in.  Every forward element scatters
+ * its adjoint into the elements it read, through the ghost rules. */
+void orc_adjoint_step(const orc_problem *P, const double *e, const double *lam_in, double *lam_out) {
+    const long nc = ncell_of(P);
+    const long total = (long)P->nb * P->nd * nc;
+    const double W = total_weight(P), D = sum_C_over_tau(P);
+    double *ediff = (double *)calloc((size_t)6 * P->nb * nc, sizeof(double));
+    double *mu = (double *)calloc((size_t)nc, sizeof(double));
+    long *idx = (long *)malloc(sizeof(long) * (P->nd + 1));
+    double *coef = (double *)malloc(sizeof(double) * (P->nd + 1));
+    diffuse_wall_values(P, e, ediff);
+    memset(lam_out, 0, sizeof(double) * total);
+    /* T_L coupling: d e^{n+1}_{k,d,i}/d T_L,i = dt C_k/(W tau_k) */
+    for (int k = 0; k < P->nb; ++k)
+        for (int d = 0; d < P->nd; ++d)
+            for (long i = 0; i < nc; ++i) mu[i] += lam_in[EIDX(P, k, d, i)] * P->dt * P->C[k] / (W * P->tau[k]);
+    for (int k = 0; k < P->nb; ++k)
+        for (int d = 0; d < P->nd; ++d)
+            for (int z = 0; z < P->nz; ++z)
+                for (int y = 0; y < P->ny; ++y)
+                    for (int x = 0; x < P->nx; ++x) {
+                        const int c[3] = {x, y, z};
+                        const long i = cidx(P, c);
+                        const double lam = lam_in[EIDX(P, k, d, i)];
+                        /* e^n and the relaxation -dt/tau e^n */
+                        lam_out[EIDX(P, k, d, i)] += lam * (1.0 - P->dt / P->tau[k]);
+                        /* T_L,i = sum w e / tau / D */
+                        lam_out[EIDX(P, k, d, i)] += mu[i] * P->w[d] / (P->tau[k] * D);
+                        /* flux: - nu (face(i+1/2) - face(i-1/2)) */
+                        for (int a = 0; a < P->dim; ++a) {
+                            const double sa = P->s[3 * d + a];
+                            if (sa == 0.0) continue;
+                            const double nu = P->dt * P->v[k] * sa / spacing(P, a);
+                            for (int f = 0; f < 2; ++f) {
+                                const int p = c[a] - f;
+                                const double sgn = f == 0 ? -nu : nu;
+                                int pos[3];
+                                double g[3];
+                                face_positions(P, d, a, p, pos);
+                                face_grad(P, e, ediff, k, d, a, c, p, g);
+                                for (int r = 0; r < 3; ++r) {
+                                    const int m = ext_deps(P, k, d, a, c, pos[r], idx, coef);
+                                    for (int j = 0; j < m; ++j) lam_out[idx[j]] += sgn * lam * g[r] * coef[j];
+                                }
+                            }
+                        }
+                    }
+    free(ediff);
+    free(mu);
+    free(idx);
+    free(coef);
+}
+
+/* Adjoint of a whole run: J = sum_i p_i T_L,i after nsteps steps from e0 (steps n0 ..
+ * n0+nsteps-1, source amplitude amp[n], 1 when amp is NULL, 0 past namp).  Stores every
+ * state.  Outputs J, dJ/dQ (ncell) and dJ/dlog tau (nb).  Returns 0, or 1 when out of memory. */
+int orc_adjoint(const orc_problem *P, const double *e0, const float *Q, const double *amp, int namp, long n0,
+                int nsteps, const double *probe, double *J, double *gQ, double *gtau) {
+    const long nc = ncell_of(P);
+    const long total = (long)P->nb * P->nd * nc;
+    const double W = total_weight(P), SC = sum_C(P), D = sum_C_over_tau(P);
+    double *traj = (double *)malloc(sizeof(double) * total * (size_t)(nsteps + 1));
+    double *lam = (double *)malloc(sizeof(double) * total);
+    double *lam2 = (double *)malloc(sizeof(double) * total);
+    double *TL = (double *)malloc(sizeof(double) * nc);
+    double *mu = (double *)malloc(sizeof(double) * nc);
+    if (!traj || !lam || !lam2 || !TL || !mu) {
+        free(traj); free(lam); free(lam2); free(TL); free(mu);
+        return 1;
+    }
+    memcpy(traj, e0, sizeof(double) * total);
+    for (int s = 0; s < nsteps; ++s) {
+        const long n = n0 + s;
+        const double a = amp ? (n < namp ? amp[n] : 0.0) : 1.0;
+        orc_step(P, traj + (size_t)s * total, traj + (size_t)(s + 1) * total, Q, a);
+    }
+    for (long i = 0; i < nc; ++i) gQ[i] = 0.0;
+    for (int k = 0; k < P->nb; ++k) gtau[k] = 0.0;
+    /* J and lambda^N = dT_L/de^T p; the final T_L's own tau dependence */
+    const double *eN = traj + (size_t)nsteps * total;
+    orc_lattice_temperature(P, eN, TL);
+    double Jv = 0.0;
+    for (long i = 0; i < nc; ++i) Jv += probe[i] * TL[i];
+    *J = Jv;
+    for (int k = 0; k < P->nb; ++k)
+        for (int d = 0; d < P->nd; ++d)
+            for (long i = 0; i < nc; ++i) lam[EIDX(P, k, d, i)] = probe[i] * P->w[d] / (P->tau[k] * D);
+    for (int k = 0; k < P->nb; ++k)
+        for (long i = 0; i < nc; ++i) {
+            double S = 0.0;
+            for (int d = 0; d < P->nd; ++d) S += P->w[d] * eN[EIDX(P, k, d, i)];
+            gtau[k] += probe[i] * (P->C[k] * TL[i] - S) / (P->tau[k] * D);
+        }
+    for (int s = nsteps - 1; s >= 0; --s) {
+        const long n = n0 + s;
+        const double a = amp ? (n < namp ? amp[n] : 0.0) : 1.0;
+        const double *en = traj + (size_t)s * total;
+        orc_lattice_temperature(P, en, TL);
+        for (long i = 0; i < nc; ++i) mu[i] = 0.0;
+        for (int k = 0; k < P->nb; ++k)
+            for (int d = 0; d < P->nd; ++d)
+                for (long i = 0; i < nc; ++i) {
+                    const double l = lam[EIDX(P, k, d, i)];
+                    gQ[i] += P->dt * a * l * P->C[k] / (SC * W);
+                    mu[i] += l * P->dt * P->C[k] / (W * P->tau[k]);
+                    gtau[k] += l * (-P->dt / P->tau[k]) * (P->C[k] * TL[i] / W - en[EIDX(P, k, d, i)]);
+                }
+        for (int k = 0; k < P->nb; ++k)
+            for (long i = 0; i < nc; ++i) {
+                double S = 0.0;
+                for (int d = 0; d < P->nd; ++d) S += P->w[d] * en[EIDX(P, k, d, i)];
+                gtau[k] += mu[i] * (P->C[k] * TL[i] - S) / (P->tau[k] * D);
+            }
+        orc_adjoint_step(P, en, lam, lam2);
+        memcpy(lam, lam2, sizeof(double) * total);
+    }
+    free(traj); free(lam); free(lam2); free(TL); free(mu);
+    return 0;
+}

@@ -65,10 +65,10 @@ def load_oracle():
             _lib.orc_lattice_temperature.argtypes = [pp, dp, dp]
             _lib.orc_energy.argtypes = [pp, dp, dp, dp]
             _lib.orc_step_points.argtypes = [pp, dp, fp, ct.c_double, ct.c_long, ct.POINTER(ct.c_long), dp]
-            if hasattr(_lib, "orc_adjoint"):
-                _lib.orc_adjoint.argtypes = [pp, dp, fp, dp, ct.c_int, ct.c_int, dp, dp, dp, ct.c_int]
-                _lib.orc_adjoint_step.argtypes = [pp, dp, dp, dp, dp]
-                _lib.orc_adjoint.restype = ct.c_int
+            _lib.orc_step_tangent.argtypes = [pp, dp, dp, dp]
+            _lib.orc_adjoint_step.argtypes = [pp, dp, dp, dp]
+            _lib.orc_adjoint.argtypes = [pp, dp, fp, dp, ct.c_int, ct.c_long, ct.c_int, dp, dp, dp, dp]
+            _lib.orc_adjoint.restype = ct.c_int
         return _lib
 
 
@@ -187,6 +187,44 @@ class Problem:
         self._lib.orc_step_points(ct.byref(self._p), _dp(e), _fp(Qc), float(amp), pts.shape[0],
                                   pts.ctypes.data_as(ct.POINTER(ct.c_long)), _dp(out))
         return out
+
+    # -- discrete adjoint (exact transpose of the step; not in the paper) ----------------
+    def step_tangent(self, e, de):
+        """J(e) de: the step's derivative along de (forward mode, T_L coupling included)."""
+        e = np.ascontiguousarray(e, dtype=np.float64)
+        de = np.ascontiguousarray(de, dtype=np.float64)
+        out = np.empty_like(e)
+        self._lib.orc_step_tangent(ct.byref(self._p), _dp(e), _dp(de), _dp(out))
+        return out
+
+    def adjoint_step(self, e, lam):
+        """J(e)^T lam (reverse mode)."""
+        e = np.ascontiguousarray(e, dtype=np.float64)
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        out = np.empty_like(e)
+        self._lib.orc_adjoint_step(ct.byref(self._p), _dp(e), _dp(lam), _dp(out))
+        return out
+
+    def adjoint(self, e0, nsteps, probe, Q=None, amps=None, n0=0):
+        """J = sum_i probe_i T_L,i after nsteps steps from e0, with dJ/dQ (per cell; Q taken
+        as 0 when None) and dJ/dlog tau_k.  Returns (J, dJ_dQ, dJ_dlogtau)."""
+        e0 = np.ascontiguousarray(e0, dtype=np.float64)
+        probe = np.ascontiguousarray(probe, dtype=np.float64).reshape(-1)
+        assert probe.size == self.ncell
+        Qc = self._src(Q)
+        if amps is None:
+            ap, na = None, 0
+        else:
+            amps = np.ascontiguousarray(amps, dtype=np.float64)
+            ap, na = _dp(amps), amps.size
+        J = np.zeros(1)
+        gQ = np.zeros(self.ncell)
+        gt = np.zeros(self.nb)
+        rc = self._lib.orc_adjoint(ct.byref(self._p), _dp(e0), _fp(Qc), ap, na, int(n0), int(nsteps), _dp(probe),
+                                   _dp(J), _dp(gQ), _dp(gt))
+        if rc != 0:
+            raise MemoryError("oracle adjoint: trajectory does not fit in memory")
+        return float(J[0]), gQ.reshape(self.nz, self.ny, self.nx), gt
 
     @property
     def cell_volume(self):
