@@ -58,6 +58,9 @@ def parse():
     p.add_argument("--rounding", default="nearest", choices=["nearest", "stochastic"],
                    help="rounding of 16-bit codes")
     p.add_argument("--t-scale", type=float, default=1.0, help="16-bit code scale T_scale (K)")
+    p.add_argument("--adj-steps", type=int, default=None,
+                   help="adjoint workloads: steps of the timed bte_adjoint call (default: the workload's)")
+    p.add_argument("--ckpt", type=int, default=None, help="adjoint checkpoint spacing (default: the workload's)")
     p.add_argument("--limiter", type=int, default=2)
     p.add_argument("--e2e-steps", type=int, default=20)
     p.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -356,6 +359,32 @@ def run_gb300(args):
         e2e = {"value": info.nelem * args.e2e_steps * d.world / te, "unit": UNIT,
                "h2d_bytes_per_step": int(info.ncell * 4 if Qh is not None else 0),
                "d2h_bytes_per_step": int(info.ncell * 4)}
+    # adjoint workloads: one bte_adjoint call (forward sweep + checkpointed reverse sweep) of
+    # J = mean T_L over the probe, traced: adjoint-step and forward-step device times
+    adjoint = None
+    if "probe" in cfg:
+        nadj = args.adj_steps if args.adj_steps is not None else cfg["steps"]
+        kck = args.ckpt if args.ckpt is not None else cfg.get("ckpt", 0)
+        probe = inputs.probe_weights(cfg)
+        bte.bte_init_temperature(ctx, None)
+        if Q is not None:
+            bte.bte_set_source(ctx, torch.from_numpy(Q.reshape(-1)).cuda(), amps)
+        torch.cuda.synchronize()
+        bte.bte_profile(ctx, True)
+        t0 = time.perf_counter()
+        J, gQ, gt = bte.bte_adjoint(ctx, nadj, probe, kck)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        adj_ms, nadj_k, rec_ms, nrec = bte.bte_adjoint_profile_read(ctx)
+        bte.bte_profile(ctx, False)
+        adj_step = adj_ms / max(nadj_k, 1)
+        fwd_step = fwd_avg_s * 1e3 + fin_ms / max(nfin, 1)
+        adj_bytes = info.nelem * (8 + info.elem_bytes)
+        adjoint = {"steps": nadj, "ckpt": kck, "J": J, "adj_step_ms": adj_step, "fwd_step_ms": fwd_step,
+                   "ratio": adj_step / fwd_step, "recompute_steps": nrec, "recompute_ms": rec_ms, "wall_s": wall,
+                   "bytes_per_adj_step": adj_bytes, "achieved_gbs": adj_bytes / (adj_step / 1e3) / 1e9,
+                   "frac": adj_bytes / (adj_step / 1e3) / 1e9 / peak,
+                   "grad_finite": bool(np.all(np.isfinite(gQ)) and np.all(np.isfinite(gt)))}
     cpu = None
     if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:
         v, n, grid, secs = time_oracle(cfg, args.cpu_seconds, args.limiter)
@@ -372,6 +401,8 @@ def run_gb300(args):
                        "parallelism": "replicas" if d.world > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(nfwd + nfin),
             "clocks": ck}
+    if adjoint is not None:
+        line["adjoint"] = adjoint
     if d.rank == 0:
         print(json.dumps(line), flush=True)
     d.barrier()

@@ -254,6 +254,28 @@ bte_status bte_set_state(bte_ctx *ctx, const void *src, size_t bytes, const floa
  * temporary device buffer of the same size; the context's stream is synchronised. */
 bte_status bte_get_values(bte_ctx *ctx, float *dst, int on_device);
 
+/* Discrete adjoint (the exact transpose of the step; the paper has no adjoint) of
+ *     J = sum_i probe_i T_L,i   after nsteps steps from the context's current state,
+ * T_L of Eq. (BTE_get_e0).  Runs the nsteps forward steps (the context ends in the state
+ * bte_step(ctx, nsteps) leaves), then the adjoint steps backward in time:
+ *     lambda^N = dT_L/de^T probe,  lambda^n = J_n^T lambda^{n+1}
+ * with J_n the step's Jacobian at e^n (limited upwind flux with the limiter's Jacobian,
+ * transposed wall ghosts, relaxation and the T_L coupling).  States are recomputed from
+ * checkpoints taken every ckpt_every steps (0: about sqrt(nsteps)); within a segment every
+ * state is kept when it fits in half the free device memory, else every ceil(sqrt)-th and
+ * the rest recomputed again.  Outputs (host, each may be NULL): J; dJ_dQ[ncell] =
+ * dJ/dQ_i (K m^3/W per cell of the source field Q of bte_set_source, Q taken as 0 when none
+ * is set); dJ_dlogtau[nbands] = dJ/d(log tau_k).  Temporary device memory is allocated and
+ * freed inside the call; BTE_ENOMEM when it does not fit.  probe: host, ncell values. */
+bte_status bte_adjoint(bte_ctx *ctx, int nsteps, int ckpt_every, const double *probe, double *J, double *dJ_dQ,
+                       double *dJ_dlogtau);
+
+/* With tracing on (bte_profile), the last bte_adjoint's device time of its adjoint steps
+ * (transposed step plus its reductions, adj_steps of them) and of its forward steps
+ * (the first sweep and the recomputations, fwd_steps of them).  Any pointer may be NULL. */
+bte_status bte_adjoint_profile_read(bte_ctx *ctx, double *adj_ms, long long *adj_steps, double *fwd_ms,
+                                    long long *fwd_steps);
+
 /* Sizes and settings; the quadrature the context built (s: 3*ndirs, w: ndirs, host). */
 bte_status bte_get_info(const bte_ctx *ctx, bte_info *info);
 bte_status bte_get_quadrature(const bte_ctx *ctx, double *s, double *w);

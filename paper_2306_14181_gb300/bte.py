@@ -26,7 +26,7 @@ BTE_KERNEL_AUTO, BTE_KERNEL_GENERIC, BTE_KERNEL_TILED = 0, 1, 2
 # every entry point include/bte.h declares
 EXPORTS = ["bte_create", "bte_destroy", "bte_last_error", "bte_init_temperature", "bte_set_source", "bte_step",
            "bte_lattice_temperature", "bte_moments", "bte_energy", "bte_get_state", "bte_set_state",
-           "bte_get_values",
+           "bte_get_values", "bte_adjoint", "bte_adjoint_profile_read",
            "bte_get_info", "bte_get_quadrature", "bte_synchronize", "bte_profile", "bte_profile_read", "bte_energy_noalloc"]
 
 _STATUS = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESTATE", 5: "ENONFINITE", 6: "ETIMEOUT", 7: "EUNSUPPORTED"}
@@ -99,6 +99,8 @@ def load():
     lib.bte_get_state.argtypes = [P, P, ct.c_size_t, P, ct.c_int]
     lib.bte_set_state.argtypes = [P, P, ct.c_size_t, P, ct.c_int, ct.c_int]
     lib.bte_get_values.argtypes = [P, P, ct.c_int]
+    lib.bte_adjoint.argtypes = [P, ct.c_int, ct.c_int, P, P, P, P]
+    lib.bte_adjoint_profile_read.argtypes = [P, P, P, P, P]
     lib.bte_get_info.argtypes = [P, ct.POINTER(bte_info)]
     lib.bte_get_quadrature.argtypes = [P, dp, dp]
     lib.bte_synchronize.argtypes = [P]
@@ -300,6 +302,30 @@ def bte_get_values(ctx, out=None):
     p, dev = _ptr(out)
     _check(load().bte_get_values(ctx.handle, p, dev), ctx.handle)
     return out
+
+
+def bte_adjoint(ctx, nsteps, probe, ckpt_every=0):
+    """J = sum_i probe_i T_L,i after nsteps steps from the current state and its gradients:
+    returns (J, dJ/dQ shaped (nz, ny, nx), dJ/dlog tau_k).  The context advances nsteps."""
+    i = ctx.info
+    probe = np.ascontiguousarray(probe, dtype=np.float64).reshape(-1)
+    assert probe.size == i.ncell
+    J = np.zeros(1)
+    gQ = np.zeros(i.ncell)
+    gt = np.zeros(i.nbands)
+    _check(load().bte_adjoint(ctx.handle, int(nsteps), int(ckpt_every), _dp(probe), _dp(J), _dp(gQ), _dp(gt)),
+           ctx.handle)
+    return float(J[0]), gQ.reshape(i.nz, i.ny, i.nx), gt
+
+
+def bte_adjoint_profile_read(ctx):
+    """(adjoint-step ms, adjoint steps, forward ms, forward steps) of the last traced bte_adjoint."""
+    a = np.zeros(1)
+    f = np.zeros(1)
+    na = ct.c_longlong()
+    nf = ct.c_longlong()
+    _check(load().bte_adjoint_profile_read(ctx.handle, _dp(a), ct.byref(na), _dp(f), ct.byref(nf)), ctx.handle)
+    return float(a[0]), na.value, float(f[0]), nf.value
 
 
 def bte_get_info(ctx):

@@ -23,7 +23,7 @@ def sources():
 
 
 def _newest_input():
-    files = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    files = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     files.append(os.path.join(ROOT, "include", "bte.h"))
     return max(os.path.getmtime(f) for f in files)
 

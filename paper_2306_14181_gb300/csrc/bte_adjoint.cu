@@ -1,0 +1,295 @@
+// Discrete adjoint of the explicit DOM transient step (arXiv 2306.14181, Sec. 4).  The paper
+// has no adjoint; this is the exact transpose of the forward step of bte_kernels.cu /
+// bte_tiled.cu, derived by hand.  One step is e^{n+1} = F(e^n, T_L(e^n)) with T_L of
+// Eq. (BTE_get_e0) linear in e, so for J = sum_i p_i T_L,i(e^N)
+//   lambda^N           = dT_L/de^T p,
+//   lambda^n           = dF/de^T lambda^{n+1} + dT_L/de^T mu^{n+1},
+//   mu^{n+1}_i         = sum_{k,d} lambda^{n+1}_{k,d,i} dt C_k/(W tau_k),
+//   dJ/dQ_i           += dt a_n sum_{k,d} lambda^{n+1}_{k,d,i} C_k/(sum C W),
+//   dJ/dlog tau_k     += sum_{d,i} lambda^{n+1} (-dt/tau_k)(C_k T_L/W - e)
+//                        + sum_i mu^{n+1}_i (C_k T_L,i - sum_d w_d e_{k,d,i})/(tau_k D).
+// dF/de^T is a gather over the downwind-transposed stencil: a face with upwind cell m,
+// value F_m = u_m + L(u_m - u_l, u_r - u_m)/2, enters cell m with -|nu| and cell m+sg with
+// +|nu|, so its adjoint weight is phi_m = |nu| (lambda_{m+sg} - lambda_m), and cell j
+// collects phi_{j+sg} dF/du_l + phi_j dF/du_m + phi_{j-sg} dF/du_r, the limiter Jacobian
+// evaluated at e^n.  Ghost values transpose as: periodic -> wrap; thermalizing incoming -> 0;
+// outgoing (thermalizing or diffuse wall) -> the wall cell itself; specular -> the mirrored
+// direction's cells (gathered from that plane's faces next to the wall); diffuse incoming ->
+// spread back over the wall cell's outgoing directions with weights w (s.n) / sum_in w|s.n|.
+// One thread per (cell, band) loops over the band's directions, as the generic forward does.
+#include "bte_device.cuh"
+#include "bte_adjoint.h"
+
+namespace bte {
+
+// Partial derivatives of the limiter L(a, b) (0 where ab <= 0).
+template <int LIM> __device__ __forceinline__ void lim_grad(float a, float b, float &La, float &Lb);
+template <> __device__ __forceinline__ void lim_grad<kLimFirst>(float, float, float &La, float &Lb) {
+    La = Lb = 0.f;
+}
+template <> __device__ __forceinline__ void lim_grad<kLimMinmod>(float a, float b, float &La, float &Lb) {
+    const bool on = a * b > 0.f, pa = fabsf(a) < fabsf(b);
+    La = on && pa ? 1.f : 0.f;
+    Lb = on && !pa ? 1.f : 0.f;
+}
+template <> __device__ __forceinline__ void lim_grad<kLimVanAlbada>(float a, float b, float &La, float &Lb) {
+    // L = ab(a+b)/(a^2+b^2):  dL/da = b^2 (2ab + b^2 - a^2)/(a^2+b^2)^2, symmetric in b
+    La = Lb = 0.f;
+    if (a * b > 0.f) {
+        const float q = fmaf(a, a, b * b);
+        const float rq = 1.f / q;
+        La = (b * b * rq) * ((2.f * a * b + b * b - a * a) * rq);
+        Lb = (a * a * rq) * ((2.f * a * b + a * a - b * b) * rq);
+    }
+}
+
+// dF/du_l, dF/du_m, dF/du_r of the face with upwind position m (orientation sg) of plane
+// (k, d) on the line of cell i along axis ax.
+template <class Cd, int LIM>
+__device__ __forceinline__ void face_grad(const StepArgs &a, const typename Cd::T *e, const BandConst &b, int k,
+                                          int d, long long base, long long i, const int c[3], int ax, int m, int sg,
+                                          float nu, float g[3]) {
+    const float ul = ext_value<Cd>(a, e, b, k, d, base, i, c, ax, m - sg, nu);
+    const float um = ext_value<Cd>(a, e, b, k, d, base, i, c, ax, m, nu);
+    const float ur = ext_value<Cd>(a, e, b, k, d, base, i, c, ax, m + sg, nu);
+    float La, Lb;
+    lim_grad<LIM>(um - ul, ur - um, La, Lb);
+    g[0] = -0.5f * La;
+    g[1] = 1.f + 0.5f * (La - Lb);
+    g[2] = 0.5f * Lb;
+}
+
+// lambda^{n+1} of plane base at position pos along ax through cell i: 0 outside the domain
+// (ghost cells are not updated), wrapped on a periodic axis.
+__device__ __forceinline__ float lam_at(const StepArgs &a, const float *lam, long long base, long long i,
+                                        const int c[3], int ax, int pos) {
+    const int n = a.n[ax];
+    if (pos < 0 || pos >= n) {
+        if (a.bc[2 * ax + (pos < 0 ? 0 : 1)] != kBcPeriodic) return 0.f;
+        pos = pos < 0 ? pos + n : pos - n;
+    }
+    return lam[base + i + (long long)(pos - c[ax]) * a.stride[ax]];
+}
+
+template <int S, int LIM>
+__global__ void __launch_bounds__(256) k_adj_step(const StepArgs a, const AdjArgs g) {
+    using Cd = Codec<S>;
+    using T = typename Cd::T;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.ncell) return;
+    const int k = blockIdx.y;
+    int c[3];
+    cell_coords(a, i, c);
+    const BandConst b = a.band[k];
+    const T *e = static_cast<const T *>(a.e_in);
+    const float *lam = g.lam_in;
+    const float mu = g.mu_in[i];
+    const float TLi = a.TL[i];
+    const float rho_i = rho_at<Cd>(a.R, a.invTs, i);
+
+    // Diffuse walls at this cell: adjoint of the incoming ghost value (both layers hold it),
+    // summed over the incoming directions of the band.
+    int wl[6];
+    const int nw = diffuse_walls_of(a, c, wl);
+    float gam[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int j = 0; j < nw; ++j) {
+        const int w = wl[j], ax = w >> 1, side = w & 1;
+        for (int d = 0; d < a.nd; ++d) {
+            const int plane = k * a.nd + d;
+            const float nu = a.nu[3 * plane + ax];
+            if (!(side == 0 ? nu > 0.f : nu < 0.f)) continue;
+            const int sg = nu > 0.f ? 1 : -1;
+            const long long base = (long long)plane * a.ncell;
+            const int f = c[ax];  // first cell of this orientation
+            float g1[3], g0[3];
+            face_grad<Cd, LIM>(a, e, b, k, d, base, i, c, ax, f - sg, sg, nu, g1);
+            face_grad<Cd, LIM>(a, e, b, k, d, base, i, c, ax, f, sg, nu, g0);
+            const float anu = fabsf(nu);
+            const float l0 = lam_at(a, lam, base, i, c, ax, f), l1 = lam_at(a, lam, base, i, c, ax, f + sg);
+            gam[j] += anu * l0 * (g1[0] + g1[1]) + anu * (l1 - l0) * g0[0];
+        }
+    }
+
+    float sq = 0.f, st = 0.f, sm = 0.f, se = 0.f;
+    for (int d = 0; d < a.nd; ++d) {
+        const int plane = k * a.nd + d;
+        const long long base = (long long)plane * a.ncell;
+        const float l = lam[base + i];
+        const float e0 = Cd::ld(e, base + i, b, rho_i);
+        sq += l;
+        st = fmaf(l, fmaf(b.ck, TLi, -e0), st);
+        se = fmaf(g.w[d], e0, se);
+        // relaxation -dt/tau e^n and the T_L coupling
+        float acc = fmaf(1.f - b.dtinv, l, a.wmom[plane] * a.invD * mu);
+        for (int ax = 0; ax < a.dim; ++ax) {
+            const float nu = a.nu[3 * plane + ax];
+            if (nu == 0.f) continue;
+            const int sg = nu > 0.f ? 1 : -1, n = a.n[ax], j = c[ax];
+            const float anu = fabsf(nu);
+            const bool per = a.bc[2 * ax] == kBcPeriodic;
+            float fg[3];
+            // face j+sg reads this cell as its upwind-left value (a face of the forward step
+            // only if its upwind cell is in the domain)
+            if (per || (j + sg >= 0 && j + sg < n)) {
+                face_grad<Cd, LIM>(a, e, b, k, d, base, i, c, ax, j + sg, sg, nu, fg);
+                acc += anu * (lam_at(a, lam, base, i, c, ax, j + 2 * sg) - lam_at(a, lam, base, i, c, ax, j + sg)) * fg[0];
+            }
+            // face j: this cell is its upwind value (and its downwind ghost when that ghost is
+            // the wall cell itself: a direction leaving through a thermalizing or diffuse wall)
+            face_grad<Cd, LIM>(a, e, b, k, d, base, i, c, ax, j, sg, nu, fg);
+            const float phj = anu * (lam_at(a, lam, base, i, c, ax, j + sg) - l);
+            acc += phj * fg[1];
+            if (!per && (j + sg < 0 || j + sg >= n)) {
+                const int bcd = a.bc[2 * ax + (sg > 0 ? 1 : 0)];
+                if (bcd == kBcIsothermal || bcd == kBcDiffuse) acc += phj * fg[2];
+            }
+            // face j-sg reads this cell as its downwind value
+            face_grad<Cd, LIM>(a, e, b, k, d, base, i, c, ax, j - sg, sg, nu, fg);
+            acc += anu * (l - lam_at(a, lam, base, i, c, ax, j - sg)) * fg[2];
+            // specular walls: faces of the mirrored direction that read this element as a ghost
+            for (int side = 0; side < 2; ++side) {
+                if (a.bc[2 * ax + side] != kBcSpecular) continue;
+                const int w0 = side ? n - 1 : 0, in = side ? -1 : 1;
+                const int layer = j == w0 ? 1 : (j == w0 + in ? 2 : 0);
+                if (layer == 0) continue;
+                const int dm = a.mirror[ax * a.nd + d];
+                const long long mbase = ((long long)k * a.nd + dm) * a.ncell;
+                const float num = a.nu[3 * (k * a.nd + dm) + ax];
+                if (num == 0.f) continue;
+                const int sgm = num > 0.f ? 1 : -1;
+                if (sgm == in) {
+                    // the mirrored direction enters through this wall: its ghosts w0 - sgm
+                    // (layer 1) and w0 - 2 sgm (layer 2) are this plane's cells w0, w0 + in
+                    float ga[3], gb[3];
+                    face_grad<Cd, LIM>(a, e, b, k, dm, mbase, i, c, ax, w0 - sgm, sgm, num, ga);
+                    const float la = anu * lam_at(a, lam, mbase, i, c, ax, w0);
+                    if (layer == 1) {
+                        face_grad<Cd, LIM>(a, e, b, k, dm, mbase, i, c, ax, w0, sgm, num, gb);
+                        const float lb = anu * (lam_at(a, lam, mbase, i, c, ax, w0 + sgm) -
+                                                lam_at(a, lam, mbase, i, c, ax, w0));
+                        acc += la * ga[1] + lb * gb[0];
+                    } else {
+                        acc += la * ga[0];
+                    }
+                } else if (layer == 1) {
+                    // the mirrored direction leaves through this wall: its downwind ghost is
+                    // this plane's wall cell
+                    face_grad<Cd, LIM>(a, e, b, k, dm, mbase, i, c, ax, w0, sgm, num, fg);
+                    acc -= anu * lam_at(a, lam, mbase, i, c, ax, w0) * fg[2];
+                }
+            }
+        }
+        // diffuse walls: this direction leaving through one spreads the ghost adjoint back
+        for (int jw = 0; jw < nw; ++jw) acc = fmaf(a.wdiff[wl[jw] * a.nd + d] * a.inv_den[wl[jw]], gam[jw], acc);
+        g.lam_out[base + i] = acc;
+        sm += acc;
+    }
+    g.pmu[(long long)k * a.ncell + i] = sm * (b.dtinv * b.ck);
+    g.pq[(long long)k * a.ncell + i] = sq;
+    g.pt[(long long)k * a.ncell + i] = fmaf(-b.dtinv, st, mu * (b.ck * g.W * TLi - se) * b.wtau * a.invD);
+}
+
+// lambda^N = dT_L/de^T p with the final T_L's own log-tau derivative: writes lam_out, pmu, pt
+// (pq = 0).
+template <int S>
+__global__ void __launch_bounds__(256) k_adj_init(const StepArgs a, const AdjArgs g, const float *probe) {
+    using Cd = Codec<S>;
+    using T = typename Cd::T;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.ncell) return;
+    const int k = blockIdx.y;
+    const BandConst b = a.band[k];
+    const T *e = static_cast<const T *>(a.e_in);
+    const float rho_i = rho_at<Cd>(a.R, a.invTs, i);
+    const float p = probe[i];
+    float sm = 0.f, se = 0.f;
+    for (int d = 0; d < a.nd; ++d) {
+        const int plane = k * a.nd + d;
+        const long long base = (long long)plane * a.ncell;
+        const float l = p * a.wmom[plane] * a.invD;
+        g.lam_out[base + i] = l;
+        sm += l;
+        se = fmaf(g.w[d], Cd::ld(e, base + i, b, rho_i), se);
+    }
+    g.pmu[(long long)k * a.ncell + i] = sm * (b.dtinv * b.ck);
+    g.pq[(long long)k * a.ncell + i] = 0.f;
+    g.pt[(long long)k * a.ncell + i] = p * (b.ck * g.W * a.TL[i] - se) * b.wtau * a.invD;
+}
+
+// mu^n_i = sum_k pmu[k][i] and dJ/dQ_i += a_n sum_k dt C_k/(sum C W) pq[k][i], in band order.
+__global__ void __launch_bounds__(256) k_adj_cells(const StepArgs a, const AdjArgs g, float amp, float *mu_out,
+                                                   double *gQ) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.ncell) return;
+    float m = 0.f;
+    double q = 0.0;
+    for (int k = 0; k < a.nb; ++k) {
+        m += g.pmu[(long long)k * a.ncell + i];
+        q += (double)a.band[k].srck * (double)g.pq[(long long)k * a.ncell + i];
+    }
+    mu_out[i] = m;
+    gQ[i] += (double)amp * q;
+}
+
+// dJ/dlog tau_k += sum_i pt[k][i]: fixed-range block sums in FP64, then the blocks in order.
+constexpr int kTauBlock = 256, kTauPerBlock = 8192;
+__global__ void __launch_bounds__(kTauBlock) k_adj_tau_blocks(const AdjArgs g, long long ncell, double *part,
+                                                              int nblk) {
+    __shared__ double sh[kTauBlock];
+    const int k = blockIdx.y;
+    const long long lo = (long long)blockIdx.x * kTauPerBlock;
+    const long long hi = lo + kTauPerBlock < ncell ? lo + kTauPerBlock : ncell;
+    double s = 0.0;
+    for (long long i = lo + threadIdx.x; i < hi; i += kTauBlock) s += (double)g.pt[(long long)k * ncell + i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = kTauBlock / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(long long)k * nblk + blockIdx.x] = sh[0];
+}
+
+__global__ void k_adj_tau_sum(const double *part, int nblk, int nb, double *gtau) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nb) return;
+    double s = 0.0;
+    for (int j = 0; j < nblk; ++j) s += part[(long long)k * nblk + j];
+    gtau[k] += s;
+}
+
+int adj_tau_blocks(long long ncell) { return (int)((ncell + kTauPerBlock - 1) / kTauPerBlock); }
+
+template <int S>
+static void adj_step_s(const StepArgs &a, const AdjArgs &g, int limiter, cudaStream_t s) {
+    const dim3 grid((unsigned)((a.ncell + 255) / 256), (unsigned)a.nb);
+    if (limiter == kLimFirst) k_adj_step<S, kLimFirst><<<grid, 256, 0, s>>>(a, g);
+    else if (limiter == kLimMinmod) k_adj_step<S, kLimMinmod><<<grid, 256, 0, s>>>(a, g);
+    else k_adj_step<S, kLimVanAlbada><<<grid, 256, 0, s>>>(a, g);
+}
+
+cudaError_t launch_adj_step(const StepArgs &a, const AdjArgs &g, int storage, int limiter, cudaStream_t s) {
+    if (storage == kStoreF32) adj_step_s<kStoreF32>(a, g, limiter, s);
+    else if (storage == kStoreF16) adj_step_s<kStoreF16>(a, g, limiter, s);
+    else adj_step_s<kStoreBF16>(a, g, limiter, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_init(const StepArgs &a, const AdjArgs &g, int storage, const float *probe, cudaStream_t s) {
+    const dim3 grid((unsigned)((a.ncell + 255) / 256), (unsigned)a.nb);
+    if (storage == kStoreF32) k_adj_init<kStoreF32><<<grid, 256, 0, s>>>(a, g, probe);
+    else if (storage == kStoreF16) k_adj_init<kStoreF16><<<grid, 256, 0, s>>>(a, g, probe);
+    else k_adj_init<kStoreBF16><<<grid, 256, 0, s>>>(a, g, probe);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_reduce(const StepArgs &a, const AdjArgs &g, float amp, float *mu_out, double *gQ,
+                              double *tau_part, double *gtau, cudaStream_t s) {
+    k_adj_cells<<<(unsigned)((a.ncell + 255) / 256), 256, 0, s>>>(a, g, amp, mu_out, gQ);
+    const int nblk = adj_tau_blocks(a.ncell);
+    k_adj_tau_blocks<<<dim3((unsigned)nblk, (unsigned)a.nb), kTauBlock, 0, s>>>(g, a.ncell, tau_part, nblk);
+    k_adj_tau_sum<<<(a.nb + 127) / 128, 128, 0, s>>>(tau_part, nblk, a.nb, gtau);
+    return cudaGetLastError();
+}
+
+}  // namespace bte

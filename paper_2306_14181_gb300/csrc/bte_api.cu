@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -15,6 +16,7 @@
 #include "../../include/bte.h"
 #include "bte_internal.h"
 #include "bte_tiled.h"
+#include "bte_adjoint.h"
 
 using namespace bte;
 
@@ -65,6 +67,10 @@ struct bte_ctx {
     long long step = 0;
     size_t device_bytes = 0;
     std::string err;
+    // adjoint: direction weights (FP32) and, with tracing on, the last bte_adjoint's timing
+    float *wf = nullptr;
+    double adj_ms = 0, adj_recompute_ms = 0;
+    long long adj_steps = 0, adj_recompute_steps = 0;
     // tracing: event triples (before forward, after forward, after finalize) per step
     bool prof = false;
     std::vector<cudaEvent_t> ev;
@@ -281,7 +287,7 @@ static bte_status refresh_moments(bte_ctx *c) {
 }
 
 static void free_all(bte_ctx *c) {
-    void *ptrs[] = {c->e[0], c->e[1], c->TL, c->R, c->Q, c->P, c->ediff[0], c->ediff[1], c->nu, c->wmom, c->wdiff,
+    void *ptrs[] = {c->wf, c->e[0], c->e[1], c->TL, c->R, c->Q, c->P, c->ediff[0], c->ediff[1], c->nu, c->wmom, c->wdiff,
                     c->iso, c->mirror_d, c->band, c->d_w, c->d_s, c->d_v, c->d_invtau, c->dg, c->dflag};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -501,6 +507,7 @@ extern "C" bte_status bte_create(const bte_grid *grid, const bte_bands *bands, c
     if ((st = dalloc(c, &c->mirror_d, mir.size())) != BTE_OK) return bail(st);
     if ((st = dalloc(c, &c->band, band.size())) != BTE_OK) return bail(st);
     if ((st = dalloc(c, &c->d_w, c->w.size())) != BTE_OK) return bail(st);
+    if ((st = dalloc(c, &c->wf, c->w.size())) != BTE_OK) return bail(st);
     if ((st = dalloc(c, &c->d_s, c->s.size())) != BTE_OK) return bail(st);
     if ((st = dalloc(c, &c->d_v, c->v.size())) != BTE_OK) return bail(st);
     if ((st = dalloc(c, &c->d_invtau, invtau.size())) != BTE_OK) return bail(st);
@@ -511,6 +518,10 @@ extern "C" bte_status bte_create(const bte_grid *grid, const bte_bands *bands, c
     if ((st = upload(c, c->mirror_d, mir.data(), mir.size())) != BTE_OK) return bail(st);
     if ((st = upload(c, c->band, band.data(), band.size())) != BTE_OK) return bail(st);
     if ((st = upload(c, c->d_w, c->w.data(), c->w.size())) != BTE_OK) return bail(st);
+    {
+        std::vector<float> wf(c->w.begin(), c->w.end());
+        if ((st = upload(c, c->wf, wf.data(), wf.size())) != BTE_OK) return bail(st);
+    }
     if ((st = upload(c, c->d_s, c->s.data(), c->s.size())) != BTE_OK) return bail(st);
     if ((st = upload(c, c->d_v, c->v.data(), c->v.size())) != BTE_OK) return bail(st);
     if ((st = upload(c, c->d_invtau, invtau.data(), invtau.size())) != BTE_OK) return bail(st);
@@ -863,5 +874,250 @@ extern "C" bte_status bte_energy_noalloc(bte_ctx *c, double *E_total, double wal
     if (wall_flux)
         for (int wl = 0; wl < 6; ++wl) wall_flux[wl] = (wl < 2 * c->dim) ? (V / L[wl >> 1]) * res[1 + wl] : 0.0;
     if (nonfinite) return fail(c, BTE_ENONFINITE, "the state holds a non-finite value");
+    return BTE_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Discrete adjoint with checkpointing (kernels: bte_adjoint.cu)
+// ------------------------------------------------------------------------------------------
+namespace {
+
+// Everything that resumes the forward step from a state: codes, their reference, T_L and
+// the wall ghost tables of that state, and the step index (source amplitude, rounding key).
+struct Snap {
+    void *e = nullptr;
+    float *R = nullptr, *TL = nullptr;
+    void *ediff = nullptr;
+    long long step = 0;
+};
+
+struct AdjWork {
+    bte_ctx *c;
+    size_t ediff_bytes = 0;
+    std::vector<void *> blocks;  // every device allocation of the call
+    ~AdjWork() {
+        for (void *p : blocks) cudaFree(p);
+    }
+    bool alloc(void **p, size_t bytes) {
+        if (cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) {
+            cudaGetLastError();
+            *p = nullptr;
+            return false;
+        }
+        blocks.push_back(*p);
+        return true;
+    }
+    bool snap(Snap &s) {
+        return alloc(&s.e, c->state_bytes) && alloc((void **)&s.R, c->ncell * sizeof(float)) &&
+               alloc((void **)&s.TL, c->ncell * sizeof(float)) && alloc(&s.ediff, ediff_bytes);
+    }
+};
+
+}  // namespace
+
+static bte_status snap_save(bte_ctx *c, Snap &s, size_t ediff_bytes) {
+    CU(c, cudaMemcpyAsync(s.e, c->e[c->cur], c->state_bytes, cudaMemcpyDeviceToDevice, c->stream));
+    CU(c, cudaMemcpyAsync(s.R, c->R, c->ncell * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    CU(c, cudaMemcpyAsync(s.TL, c->TL, c->ncell * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    CU(c, cudaMemcpyAsync(s.ediff, c->ediff[c->ecur], ediff_bytes, cudaMemcpyDeviceToDevice, c->stream));
+    s.step = c->step;
+    return BTE_OK;
+}
+
+static bte_status snap_restore(bte_ctx *c, const Snap &s, size_t ediff_bytes) {
+    CU(c, cudaMemcpyAsync(c->e[c->cur], s.e, c->state_bytes, cudaMemcpyDeviceToDevice, c->stream));
+    CU(c, cudaMemcpyAsync(c->R, s.R, c->ncell * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    CU(c, cudaMemcpyAsync(c->TL, s.TL, c->ncell * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    CU(c, cudaMemcpyAsync(c->ediff[c->ecur], s.ediff, ediff_bytes, cudaMemcpyDeviceToDevice, c->stream));
+    c->step = s.step;
+    return BTE_OK;
+}
+
+extern "C" bte_status bte_adjoint(bte_ctx *c, int nsteps, int ckpt_every, const double *probe, double *J,
+                                  double *dJ_dQ, double *dJ_dlogtau) {
+    if (!c) return fail(nullptr, BTE_EINVAL, "ctx is NULL");
+    if (!probe) return fail(c, BTE_EINVAL, "probe is NULL");
+    if (nsteps < 0) return fail(c, BTE_EINVAL, "nsteps must be >= 0");
+    if (ckpt_every < 0) return fail(c, BTE_EINVAL, "ckpt_every must be >= 0");
+    for (long long i = 0; i < c->ncell; ++i)
+        if (!std::isfinite(probe[i])) return fail(c, BTE_EINVAL, "probe holds a non-finite value at cell %lld", i);
+    const long long nc = c->ncell, nel = c->nelem;
+    int K = ckpt_every > 0 ? ckpt_every : std::max(1, (int)std::ceil(std::sqrt((double)std::max(nsteps, 1))));
+    K = std::max(1, std::min(K, std::max(nsteps, 1)));
+    const int nseg = nsteps > 0 ? (nsteps + K - 1) / K : 0;
+    AdjWork w;
+    w.c = c;
+    w.ediff_bytes = ((size_t)6 * c->nb * c->wc_max + 16) * c->elem_bytes;
+    // adjoint state and partials
+    float *lam[2], *mu[2], *pmu, *pq, *pt, *pr;
+    double *gQ, *gt, *tpart;
+    const int ntb = adj_tau_blocks(nc);
+    if (!w.alloc((void **)&lam[0], nel * sizeof(float)) || !w.alloc((void **)&lam[1], nel * sizeof(float)) ||
+        !w.alloc((void **)&mu[0], nc * sizeof(float)) || !w.alloc((void **)&mu[1], nc * sizeof(float)) ||
+        !w.alloc((void **)&pmu, (size_t)c->nb * nc * sizeof(float)) ||
+        !w.alloc((void **)&pq, (size_t)c->nb * nc * sizeof(float)) ||
+        !w.alloc((void **)&pt, (size_t)c->nb * nc * sizeof(float)) || !w.alloc((void **)&pr, nc * sizeof(float)) ||
+        !w.alloc((void **)&gQ, nc * sizeof(double)) || !w.alloc((void **)&gt, c->nb * sizeof(double)) ||
+        !w.alloc((void **)&tpart, (size_t)c->nb * ntb * sizeof(double)))
+        return fail(c, BTE_ENOMEM, "adjoint buffers do not fit in device memory");
+    // checkpoints: one per segment, then within a segment either every state (when K states
+    // fit in half of the free memory) or every K2 = ceil(sqrt K)-th state, its sub-segments
+    // recomputed into K2 more snapshots
+    const size_t snap_bytes = c->state_bytes + 2 * nc * sizeof(float) + w.ediff_bytes;
+    size_t mfree = 0, mtot = 0;
+    CU(c, cudaMemGetInfo(&mfree, &mtot));
+    const size_t fixed = (size_t)(nseg + 1) * snap_bytes;
+    int K2 = 1;
+    if (fixed + (size_t)K * snap_bytes > mfree / 2) K2 = (int)std::ceil(std::sqrt((double)K));
+    if (const char *env = std::getenv("BTE_ADJOINT_INNER_STRIDE")) {  // testing the two-level path
+        const int v = std::atoi(env);
+        if (v >= 1) K2 = std::min(v, K);
+    }
+    const int n2 = (K + K2 - 1) / K2;
+    std::vector<Snap> L1(nseg), L2(n2), L3(K2 > 1 ? K2 : 0);
+    Snap fin;
+    for (auto &s : L1)
+        if (!w.snap(s)) return fail(c, BTE_ENOMEM, "adjoint checkpoints do not fit in device memory");
+    for (auto &s : L2)
+        if (!w.snap(s)) return fail(c, BTE_ENOMEM, "adjoint checkpoints do not fit in device memory");
+    for (auto &s : L3)
+        if (!w.snap(s)) return fail(c, BTE_ENOMEM, "adjoint checkpoints do not fit in device memory");
+    if (!w.snap(fin)) return fail(c, BTE_ENOMEM, "adjoint checkpoints do not fit in device memory");
+    {
+        std::vector<float> pf(probe, probe + nc);
+        CU(c, cudaMemcpyAsync(pr, pf.data(), nc * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        CU(c, cudaMemsetAsync(gQ, 0, nc * sizeof(double), c->stream));
+        CU(c, cudaMemsetAsync(gt, 0, c->nb * sizeof(double), c->stream));
+        CU(c, cudaStreamSynchronize(c->stream));
+    }
+    const bool prof = c->prof;
+    c->prof = false;  // the forward steps of the adjoint are not traced as bte_step calls
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    double adj_ms = 0, rec_ms = 0;
+    long long adj_n = 0, rec_n = 0;
+    if (prof) {
+        CU(c, cudaEventCreate(&ev0));
+        CU(c, cudaEventCreate(&ev1));
+    }
+    auto timed_steps = [&](int n) -> bte_status {
+        if (n <= 0) return BTE_OK;
+        if (prof) CU(c, cudaEventRecord(ev0, c->stream));
+        bte_status st = bte_step(c, n);
+        if (st != BTE_OK) return st;
+        if (prof) {
+            float ms = 0;
+            CU(c, cudaEventRecord(ev1, c->stream));
+            CU(c, cudaEventSynchronize(ev1));
+            CU(c, cudaEventElapsedTime(&ms, ev0, ev1));
+            rec_ms += ms;
+            rec_n += n;
+        }
+        return BTE_OK;
+    };
+    int cur = 0;
+    AdjArgs g;
+    g.w = c->wf;
+    g.W = (float)c->W;
+    g.pmu = pmu;
+    g.pq = pq;
+    g.pt = pt;
+    auto adj_step = [&](const Snap &s) -> bte_status {
+        StepArgs a = make_args(c);
+        a.e_in = s.e;
+        a.R = s.R;
+        a.TL = s.TL;
+        a.ediff_in = s.ediff;
+        g.lam_in = lam[cur];
+        g.lam_out = lam[cur ^ 1];
+        g.mu_in = mu[cur];
+        if (prof) CU(c, cudaEventRecord(ev0, c->stream));
+        CU(c, launch_adj_step(a, g, c->storage, c->limiter, c->stream));
+        CU(c, launch_adj_reduce(a, g, (float)amplitude_at(c, s.step), mu[cur ^ 1], gQ, tpart, gt, c->stream));
+        if (prof) {
+            float ms = 0;
+            CU(c, cudaEventRecord(ev1, c->stream));
+            CU(c, cudaEventSynchronize(ev1));
+            CU(c, cudaEventElapsedTime(&ms, ev0, ev1));
+            adj_ms += ms;
+            ++adj_n;
+        }
+        cur ^= 1;
+        return BTE_OK;
+    };
+    bte_status st = BTE_OK;
+    auto run = [&]() -> bte_status {
+        // forward sweep, keeping the segment checkpoints
+        for (int s = 0; s < nseg; ++s) {
+            TRY(snap_save(c, L1[s], w.ediff_bytes));
+            TRY(timed_steps(std::min(K, nsteps - s * K)));
+        }
+        TRY(snap_save(c, fin, w.ediff_bytes));
+        // J = sum p T_L^N and lambda^N
+        {
+            std::vector<float> tl(nc);
+            CU(c, cudaMemcpyAsync(tl.data(), c->TL, nc * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+            CU(c, cudaStreamSynchronize(c->stream));
+            double jv = 0;
+            for (long long i = 0; i < nc; ++i) jv += probe[i] * (double)tl[i];
+            if (J) *J = jv;
+            StepArgs a = make_args(c);
+            a.e_in = c->e[c->cur];
+            g.lam_out = lam[cur];
+            g.lam_in = nullptr;
+            g.mu_in = nullptr;
+            CU(c, launch_adj_init(a, g, c->storage, pr, c->stream));
+            CU(c, launch_adj_reduce(a, g, 0.f, mu[cur], gQ, tpart, gt, c->stream));
+        }
+        // reverse sweep, segment by segment
+        for (int s = nseg - 1; s >= 0; --s) {
+            const int n0 = s * K, n1 = std::min(nsteps, n0 + K);
+            TRY(snap_restore(c, L1[s], w.ediff_bytes));
+            const int ns2 = (n1 - n0 + K2 - 1) / K2;
+            for (int m = n0; m < n1; ++m) {
+                if ((m - n0) % K2 == 0) TRY(snap_save(c, L2[(m - n0) / K2], w.ediff_bytes));
+                if ((m - n0) / K2 == ns2 - 1 && K2 > 1) break;  // the last sub-checkpoint is taken
+                if (m < n1 - 1) TRY(timed_steps(1));
+            }
+            if (K2 == 1) {
+                for (int m = n1 - 1; m >= n0; --m) TRY(adj_step(L2[m - n0]));
+                continue;
+            }
+            for (int sub = ns2 - 1; sub >= 0; --sub) {
+                const int m0 = n0 + sub * K2, m1 = std::min(n1, m0 + K2);
+                TRY(snap_restore(c, L2[sub], w.ediff_bytes));
+                for (int m = m0; m < m1; ++m) {
+                    TRY(snap_save(c, L3[m - m0], w.ediff_bytes));
+                    if (m < m1 - 1) TRY(timed_steps(1));
+                }
+                for (int m = m1 - 1; m >= m0; --m) TRY(adj_step(L3[m - m0]));
+            }
+        }
+        TRY(snap_restore(c, fin, w.ediff_bytes));
+        if (dJ_dQ) CU(c, cudaMemcpyAsync(dJ_dQ, gQ, nc * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        if (dJ_dlogtau) CU(c, cudaMemcpyAsync(dJ_dlogtau, gt, c->nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CU(c, cudaStreamSynchronize(c->stream));
+        return check_device_flags(c);
+    };
+    st = run();
+    c->prof = prof;
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    if (st == BTE_OK && prof) {
+        c->adj_ms = adj_ms;
+        c->adj_steps = adj_n;
+        c->adj_recompute_ms = rec_ms;
+        c->adj_recompute_steps = rec_n;
+    }
+    if (st != BTE_OK) cudaStreamSynchronize(c->stream);
+    return st;
+}
+
+extern "C" bte_status bte_adjoint_profile_read(bte_ctx *c, double *adj_ms, long long *adj_steps, double *fwd_ms,
+                                               long long *fwd_steps) {
+    if (!c) return fail(nullptr, BTE_EINVAL, "ctx is NULL");
+    if (adj_ms) *adj_ms = c->adj_ms;
+    if (adj_steps) *adj_steps = c->adj_steps;
+    if (fwd_ms) *fwd_ms = c->adj_recompute_ms;
+    if (fwd_steps) *fwd_steps = c->adj_recompute_steps;
     return BTE_OK;
 }

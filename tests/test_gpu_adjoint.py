@@ -1,0 +1,164 @@
+"""GPU discrete adjoint (through the C ABI) against the oracle's FP64 adjoint and central
+differences of the oracle's forward run: dJ/dQ and dJ/dlog tau within 1e-4 (relative to the
+largest component) for FP32 state."""
+import numpy as np
+import pytest
+
+from paper_2306_14181_gb300 import inputs
+from tests.support import gpu_ctx, oracle_problem, small_cfg
+
+pytestmark = pytest.mark.gpu
+
+ISO, DIF, SPE, PER = 0, 1, 2, 3
+TW = [0.3, -0.2, 0.1, 0.4, -0.3, 0.2]
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2306_14181_gb300 import build
+    build.build()
+
+
+CASES = [
+    (1, (40, 1, 1), [ISO, DIF, PER, PER, PER, PER], 1),
+    (1, (32, 1, 1), [SPE, ISO, PER, PER, PER, PER], 1),
+    (2, (24, 17, 1), [DIF, SPE, ISO, DIF, PER, PER], 1),
+    (2, (96, 13, 1), [SPE, SPE, ISO, DIF, PER, PER], 2),
+    (2, (128, 9, 1), [PER, PER, SPE, DIF, PER, PER], 2),
+    (3, (12, 9, 8), [SPE, SPE, PER, PER, DIF, ISO], 1),
+    (3, (96, 9, 7), [DIF, ISO, SPE, SPE, PER, PER], 2),
+]
+
+
+def _setup(dim, n, bc, limiter, kernel, nsteps, storage=0, seed=8):
+    cfg = small_cfg(dim, n, bc, Tw=TW, nb=2)
+    P = oracle_problem(cfg, limiter)
+    rng = np.random.default_rng(seed)
+    Q = (rng.random((P.nz, P.ny, P.nx)) * 2e17).astype(np.float32)
+    amps = np.linspace(1.0, 0.3, nsteps)
+    dT0 = rng.random((P.nz, P.ny, P.nx)) - 0.5
+    p = np.zeros((P.nz, P.ny, P.nx))
+    p[P.nz // 2:, P.ny // 2:, P.nx // 2:] = 1.0
+    p /= p.sum()
+    ctx = gpu_ctx(cfg, limiter=limiter, kernel=kernel, storage=storage)
+    return cfg, P, ctx, Q, amps, dT0, p
+
+
+def _gpu_adjoint(ctx, Q, amps, dT0, p, nsteps, ckpt=0):
+    from paper_2306_14181_gb300 import bte
+    bte.bte_init_temperature(ctx, dT0.reshape(-1))
+    bte.bte_set_source(ctx, Q, amps)
+    return bte.bte_adjoint(ctx, nsteps, p, ckpt)
+
+
+@pytest.mark.parametrize("limiter", [0, 1, 2])
+@pytest.mark.parametrize("dim,n,bc,kernel", CASES)
+def test_adjoint_matches_oracle_adjoint(dim, n, bc, kernel, limiter):
+    nsteps = 16
+    cfg, P, ctx, Q, amps, dT0, p = _setup(dim, n, bc, limiter, kernel, nsteps)
+    assert ctx.info.kernel == kernel
+    J, gQ, gt = _gpu_adjoint(ctx, Q, amps, dT0, p, nsteps, ckpt=5)
+    e0 = P.equilibrium(np.asarray(dT0, np.float32).astype(np.float64))
+    Jo, gQo, gto = P.adjoint(e0, nsteps, p, Q, amps)
+    assert abs(J - Jo) <= 1e-5 * abs(Jo)
+    assert np.max(np.abs(gQ - gQo)) <= TOL * np.max(np.abs(gQo))
+    assert np.max(np.abs(gt - gto)) <= TOL * np.max(np.abs(gto))
+
+
+def test_adjoint_matches_oracle_finite_differences():
+    """The GPU gradient against central differences of the oracle's FP64 forward run."""
+    nsteps = 16
+    cfg, P, ctx, Q, amps, dT0, p = _setup(2, (96, 13, 1), [SPE, SPE, ISO, DIF, PER, PER], 2, 2, nsteps)
+    J, gQ, gt = _gpu_adjoint(ctx, Q, amps, dT0, p, nsteps)
+    e0 = P.equilibrium(np.asarray(dT0, np.float32).astype(np.float64))
+
+    def Jo(Pp, Qq):
+        return float(np.sum(p * Pp.lattice_temperature(Pp.run(e0, nsteps, Qq, amps))))
+
+    rng = np.random.default_rng(3)
+    hq = 1e-4 * float(Q.max())
+    for ci in rng.choice(P.ncell, 4, replace=False):
+        Qp, Qm = Q.copy().reshape(-1), Q.copy().reshape(-1)
+        Qp[ci] = np.float32(Qp[ci] + hq)
+        Qm[ci] = np.float32(Qm[ci] - hq)
+        fd = (Jo(P, Qp.reshape(Q.shape)) - Jo(P, Qm.reshape(Q.shape))) / (float(Qp[ci]) - float(Qm[ci]))
+        assert abs(fd - gQ.reshape(-1)[ci]) <= TOL * np.max(np.abs(gQ))
+    for k in range(P.nb):
+        Js = []
+        for sgn in (1, -1):
+            tau = np.array(cfg["tau"], float)
+            tau[k] *= np.exp(sgn * 1e-4)
+            Js.append(Jo(oracle_problem(dict(cfg, tau=tau), 2), Q))
+        fd = (Js[0] - Js[1]) / 2e-4
+        assert abs(fd - gt[k]) <= TOL * np.max(np.abs(gt))
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_checkpoint_spacing_does_not_change_the_result(kernel):
+    """Recomputation from checkpoints is bitwise deterministic: every checkpoint spacing
+    gives the same gradients, and the context ends where bte_step would leave it."""
+    from paper_2306_14181_gb300 import bte
+    nsteps = 23
+    cfg, P, ctx, Q, amps, dT0, p = _setup(2, (96, 13, 1), [SPE, SPE, ISO, DIF, PER, PER], 2, kernel, nsteps)
+    out = []
+    for ck in (1, 4, 23, 0):
+        out.append(_gpu_adjoint(ctx, Q, amps, dT0, p, nsteps, ck))
+        assert ctx.info.kernel == kernel
+    state = bte.bte_get_state(ctx)
+    for J, gQ, gt in out[1:]:
+        assert J == out[0][0] and np.array_equal(gQ, out[0][1]) and np.array_equal(gt, out[0][2])
+    bte.bte_init_temperature(ctx, dT0.reshape(-1))
+    bte.bte_set_source(ctx, Q, amps)
+    bte.bte_step(ctx, nsteps)
+    assert np.array_equal(bte.bte_get_state(ctx), state)
+
+
+def test_two_level_recomputation(monkeypatch):
+    """Forcing the inner checkpoint stride (the path taken when a segment's states do not fit)
+    gives bitwise the same gradients."""
+    nsteps = 30
+    cfg, P, ctx, Q, amps, dT0, p = _setup(2, (96, 13, 1), [SPE, SPE, ISO, DIF, PER, PER], 2, 2, nsteps)
+    ref = _gpu_adjoint(ctx, Q, amps, dT0, p, nsteps, 10)
+    monkeypatch.setenv("BTE_ADJOINT_INNER_STRIDE", "3")
+    two = _gpu_adjoint(ctx, Q, amps, dT0, p, nsteps, 10)
+    assert two[0] == ref[0] and np.array_equal(two[1], ref[1]) and np.array_equal(two[2], ref[2])
+
+
+@pytest.mark.parametrize("storage,tol", [(1, 2e-3), (2, 1e-2)])
+def test_adjoint_with_16bit_state(storage, tol):
+    """FP16/BF16 coded state (FP32 adjoint): the gradients of the rounded trajectory against
+    the FP64 oracle's, within the storage's own accuracy."""
+    nsteps = 16
+    cfg, P, ctx, Q, amps, dT0, p = _setup(3, (96, 9, 7), [DIF, ISO, SPE, SPE, PER, PER], 2, 2, nsteps, storage=storage)
+    J, gQ, gt = _gpu_adjoint(ctx, Q, amps, dT0, p, nsteps)
+    e0 = P.equilibrium(np.asarray(dT0, np.float32).astype(np.float64))
+    Jo, gQo, gto = P.adjoint(e0, nsteps, p, Q, amps)
+    assert np.max(np.abs(gQ - gQo)) <= tol * np.max(np.abs(gQo))
+    assert np.max(np.abs(gt - gto)) <= tol * np.max(np.abs(gto))
+
+
+def test_autograd_function():
+    """torch.autograd through ProbeTemperature: the gradients are the adjoint's."""
+    import torch
+    from paper_2306_14181_gb300.autograd import probe_temperature
+    nsteps = 12
+    cfg = small_cfg(2, (96, 13, 1), [SPE, SPE, ISO, DIF, PER, PER], Tw=TW, nb=2)
+    P = oracle_problem(cfg, 2)
+    rng = np.random.default_rng(4)
+    Qn = (rng.random((P.nz, P.ny, P.nx)) * 2e17).astype(np.float32)
+    p = np.zeros((P.nz, P.ny, P.nx))
+    p[:, 8:, 40:56] = 1.0
+    p /= p.sum()
+    Q = torch.tensor(Qn, device="cuda", requires_grad=True)
+    log_tau = torch.tensor(np.log(cfg["tau"]), dtype=torch.float64, requires_grad=True)
+    problem = dict(cfg, probe=p, steps=nsteps, ckpt=4)
+    J = probe_temperature(Q, log_tau, problem)
+    (2.0 * J).backward()
+    Jo, gQo, gto = P.adjoint(P.equilibrium(0.0), nsteps, p, Qn)
+    assert abs(J.item() - Jo) <= 1e-5 * abs(Jo)
+    assert np.max(np.abs(Q.grad.cpu().numpy() - 2 * gQo)) <= TOL * np.max(np.abs(2 * gQo))
+    assert np.max(np.abs(log_tau.grad.numpy() - 2 * gto)) <= TOL * np.max(np.abs(2 * gto))

@@ -20,7 +20,7 @@ TW = [0.3, -0.2, 0.1, 0.4, -0.3, 0.2]
 GRIDS = [
     (1, (12, 1, 1), [ISO, DIF, PER, PER, PER, PER]),
     (1, (10, 1, 1), [SPE, ISO, PER, PER, PER, PER]),
-    (2, (7, 6, 1), [DIF, SPE, ISO, PER, PER, PER]),
+    (2, (7, 6, 1), [DIF, SPE, ISO, DIF, PER, PER]),
     (2, (6, 5, 1), [PER, PER, SPE, DIF, PER, PER]),
     (3, (5, 4, 4), [SPE, SPE, PER, PER, DIF, ISO]),
     (3, (4, 5, 3), [DIF, ISO, SPE, SPE, PER, PER]),
