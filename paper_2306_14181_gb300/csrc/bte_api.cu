@@ -421,7 +421,8 @@ extern "C" bte_status bte_create(const bte_grid *grid, const bte_bands *bands, c
     c->G = c->nb;
     if (c->kernel != BTE_KERNEL_GENERIC) {
         std::string why;
-        c->tiled = tiled_plan(c->dim, c->n, c->nb, c->nd, c->storage, c->limiter, c->bc, c->plan, why);
+        c->tiled = tiled_plan(c->dim, c->n, c->nb, c->nd, c->storage, c->limiter,
+                              c->rounding == BTE_ROUND_STOCHASTIC, c->bc, c->plan, why);
         if (!c->tiled && c->kernel == BTE_KERNEL_TILED) {
             c->err = "tiled kernel unavailable: " + why;
             return bail(BTE_EUNSUPPORTED);

@@ -39,14 +39,12 @@ __global__ void __launch_bounds__(256) k_finalize_tiled(const StepArgs a, const 
     const int ty = y / p.ty, tz = z / p.tz;
     const int tile = tz * p.nty + ty;
     const int li = ((z - tz * p.tz) * p.ty + (y - ty * p.ty)) * nx + x;
+    // the tile's segments: its units in part order, each unit's bands in order
+    const int g0 = p.tile_seg0[tile], g1 = p.tile_seg0[tile + 1];
+    const float *P = a.P + li;
     float s = 0.f;
-    for (int j = 0; j < p.J; ++j) {  // the tile's units in part order, each unit's bands in order
-        const int u = j * p.ntiles + tile;
-        const int p0 = part_begin(p, j), p1 = part_begin(p, j + 1);
-        if (p0 >= p1) continue;
-        const int g0 = p.unit_seg0[u], g1 = p.unit_seg0[u + 1];
-        for (int g = g0; g < g1; ++g) s += a.P[(size_t)g * p.tcells + li];
-    }
+    #pragma unroll 8
+    for (int g = g0; g < g1; ++g) s += P[(size_t)g * p.tcells];
     TL[i] = s * a.invD;
 }
 
@@ -54,9 +52,14 @@ __global__ void __launch_bounds__(256) k_finalize_tiled(const StepArgs a, const 
 // (sum over the band-k segments of the cell's tile) / sum_in w|s.n|.  With 16-bit storage the
 // value is coded against the wall cell's new reference rho = T_L^n / T_scale, and thermalizing
 // y/z walls get their emission C_k T_w / W coded the same way.
+struct WallList {
+    int w[6];
+};
+
 template <int S>
-__global__ void __launch_bounds__(256) k_ediff_tiled(const StepArgs a, const TiledArgs p, int wall) {
+__global__ void __launch_bounds__(256) k_ediff_tiled(const StepArgs a, const TiledArgs p, const WallList wls) {
     using T = typename St<S>::T;
+    const int wall = wls.w[blockIdx.z];
     const int ax = wall >> 1, side = wall & 1;
     const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
     const int n0 = ax == 0 ? ny : nx;            // fastest wall-cell coordinate extent
@@ -90,8 +93,12 @@ __global__ void __launch_bounds__(256) k_ediff_tiled(const StepArgs a, const Til
         v = s * a.inv_den[wall];
     }
     T *out = static_cast<T *>(a.ediff_out) + ((long long)wall * a.nb + k) * a.wc_max + j;
-    if constexpr (St<S>::kRef) *out = St<S>::enc(fmaf(v, b.inv_scale, -a.TL[((long long)z * ny + y) * nx + x] * a.invTs));
-    else *out = St<S>::enc(v);
+    if constexpr (St<S>::kRef) {
+        const uint32_t c = St<S>::enc(fmaf(v, b.inv_scale, -a.TL[((long long)z * ny + y) * nx + x] * a.invTs));
+        *reinterpret_cast<unsigned short *>(out) = (unsigned short)c;
+    } else {
+        *out = v;
+    }
 }
 
 // Per-plane constants the producer copies into each stage:
@@ -124,10 +131,10 @@ __global__ void k_fill_isorows(const StepArgs a, int nx, float *rows) {
 }
 
 // ---- dispatch -------------------------------------------------------------------------------
-StepKernel pick(int storage, int lim, int nx, int dim) {
+StepKernel pick(int storage, int lim, int nx, int dim, bool sr) {
     if (storage == kStoreF32) return dim == 2 ? pick_f32_2d(lim, nx) : pick_f32_3d(lim, nx);
-    if (storage == kStoreF16) return dim == 2 ? pick_f16_2d(lim, nx) : pick_f16_3d(lim, nx);
-    return dim == 2 ? pick_bf16_2d(lim, nx) : pick_bf16_3d(lim, nx);
+    if (storage == kStoreF16) return dim == 2 ? pick_f16_2d(lim, nx, sr) : pick_f16_3d(lim, nx, sr);
+    return dim == 2 ? pick_bf16_2d(lim, nx, sr) : pick_bf16_3d(lim, nx, sr);
 }
 
 template <class V>
@@ -151,8 +158,8 @@ using namespace tiled;
 // ------------------------------------------------------------------------------------------
 // host side
 // ------------------------------------------------------------------------------------------
-bool tiled_plan(int dim, const int n[3], int nb, int nd, int storage, int limiter, const int bc[6], TiledPlan &plan,
-                std::string &why) {
+bool tiled_plan(int dim, const int n[3], int nb, int nd, int storage, int limiter, bool sr, const int bc[6],
+                TiledPlan &plan, std::string &why) {
     plan = TiledPlan();
     if (dim != 2 && dim != 3) {
         why = "the tiled kernel covers 2-D and 3-D grids";
@@ -215,7 +222,7 @@ bool tiled_plan(int dim, const int n[3], int nb, int nd, int storage, int limite
     plan.acc_off = plan.bt_off + (int)((bt_bytes + 127) / 128 * 128);
     plan.rho_off = plan.acc_off + (int)((bt_bytes + 127) / 128 * 128);
     plan.smem = plan.rho_off + (int)rho_bytes;
-    plan.kernel = (void *)pick(storage, limiter, nx, dim);
+    plan.kernel = (void *)pick(storage, limiter, nx, dim, sr && storage != kStoreF32);
     if (!plan.kernel) {
         why = "no kernel instance";
         return false;
@@ -247,14 +254,20 @@ bool tiled_plan(int dim, const int n[3], int nb, int nd, int storage, int limite
     plan.J = std::min(plan.nctas / hcf, plan.np);
     plan.U = plan.ntiles * plan.J;
     if (plan.nctas > plan.U) plan.nctas = plan.U;
-    plan.h_unit_seg0.assign(plan.U + 1, 0);
-    for (int u = 0; u < plan.U; ++u) {
-        const int j = u / plan.ntiles;
-        const long long p0 = (long long)j * plan.np / plan.J, p1 = (long long)(j + 1) * plan.np / plan.J;
-        const int nseg = p1 > p0 ? (int)((p1 - 1) / nd - p0 / nd + 1) : 0;
-        plan.h_unit_seg0[u + 1] = plan.h_unit_seg0[u] + nseg;
+    // segment rows numbered tile by tile: [U] first row of each unit, then [ntiles + 1] tile starts
+    plan.h_unit_seg0.assign(plan.U + plan.ntiles + 1, 0);
+    int nsg = 0;
+    for (int t = 0; t < plan.ntiles; ++t) {
+        plan.h_unit_seg0[plan.U + t] = nsg;
+        for (int j = 0; j < plan.J; ++j) {
+            const long long p0 = (long long)j * plan.np / plan.J, p1 = (long long)(j + 1) * plan.np / plan.J;
+            const int nseg = p1 > p0 ? (int)((p1 - 1) / nd - p0 / nd + 1) : 0;
+            plan.h_unit_seg0[j * plan.ntiles + t] = nsg;
+            nsg += nseg;
+        }
     }
-    plan.G = plan.h_unit_seg0[plan.U];
+    plan.h_unit_seg0[plan.U + plan.ntiles] = nsg;
+    plan.G = nsg;
     plan.valid = 1;
     return true;
 }
@@ -302,6 +315,7 @@ static TiledArgs device_args(const TiledPlan &plan) {
     TiledArgs t;
     memset(&t, 0, sizeof t);
     t.unit_seg0 = plan.unit_seg0;
+    t.tile_seg0 = plan.unit_seg0 + plan.U;
     t.U = plan.U;
     t.J = plan.J;
     t.np = plan.np;
@@ -348,23 +362,31 @@ cudaError_t launch_finalize_tiled(const StepArgs &a, const TiledPlan &plan, int 
     const TiledArgs t = device_args(plan);
     const unsigned nblk = (unsigned)((a.ncell + 255) / 256);
     k_finalize_tiled<<<nblk, 256, 0, s>>>(a, t, TL_out);
+    // every wall that needs ghost values in one launch (z: the wall), x covering its cells
+    WallList wl;
+    int nw = 0;
+    long long nwc = 0;
     for (int w = 0; w < 2 * plan.dim; ++w) {
         if (!tiled_wall_pass(plan, a.bc, w)) continue;
         const int ax = w >> 1;
-        const long long nwc = ax == 0 ? (long long)a.n[1] * a.n[2]
-                                      : (ax == 1 ? (long long)a.n[0] * a.n[2] : (long long)a.n[0] * a.n[1]);
-        const dim3 g((unsigned)((nwc + 255) / 256), (unsigned)a.nb);
-        if (storage == kStoreF32) k_ediff_tiled<kStoreF32><<<g, 256, 0, s>>>(a, t, w);
-        else if (storage == kStoreF16) k_ediff_tiled<kStoreF16><<<g, 256, 0, s>>>(a, t, w);
-        else k_ediff_tiled<kStoreBF16><<<g, 256, 0, s>>>(a, t, w);
+        const long long m = ax == 0 ? (long long)a.n[1] * a.n[2]
+                                    : (ax == 1 ? (long long)a.n[0] * a.n[2] : (long long)a.n[0] * a.n[1]);
+        nwc = std::max(nwc, m);
+        wl.w[nw++] = w;
+    }
+    if (nw > 0) {
+        const dim3 g((unsigned)((nwc + 255) / 256), (unsigned)a.nb, (unsigned)nw);
+        if (storage == kStoreF32) k_ediff_tiled<kStoreF32><<<g, 256, 0, s>>>(a, t, wl);
+        else if (storage == kStoreF16) k_ediff_tiled<kStoreF16><<<g, 256, 0, s>>>(a, t, wl);
+        else k_ediff_tiled<kStoreBF16><<<g, 256, 0, s>>>(a, t, wl);
     }
     return cudaGetLastError();
 }
 
 int tiled_finalize_launches(const TiledPlan &plan, const int bc[6]) {
-    int n = 1;
-    for (int w = 0; w < 2 * plan.dim; ++w) n += tiled_wall_pass(plan, bc, w);
-    return n;
+    for (int w = 0; w < 2 * plan.dim; ++w)
+        if (tiled_wall_pass(plan, bc, w)) return 2;
+    return 1;
 }
 
 }  // namespace bte

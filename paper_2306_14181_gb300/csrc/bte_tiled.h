@@ -10,7 +10,8 @@ namespace bte {
 
 // Device-side view of the plan, passed by value to the kernels.
 struct TiledArgs {
-    const int *unit_seg0;  // [U + 1] first segment (row of P / PW) of each unit
+    const int *unit_seg0;  // [U] first segment (row of P / PW) of each unit
+    const int *tile_seg0;  // [ntiles + 1] segments of tile t are rows tile_seg0[t] .. tile_seg0[t+1]-1
     int U, J, np, ntiles;  // units, parts per tile, planes (nb*nd), tiles
     float *PW;             // diffuse-wall partials [G][nwd][tw]
     const float *hdr;      // per-plane constants [nb*nd][16] (see tiled_build_headers)
@@ -34,6 +35,8 @@ struct TiledArgs {
 // still in L2 when its neighbour needs them.  J = nctas / gcd(ntiles, nctas) makes the unit
 // count a multiple of the CTA count.  A segment is the run of one unit within one band; it
 // writes one row of moment partials P[seg][tile cells] and one row of diffuse-wall partials.
+// Segments are numbered tile by tile (parts in order, bands in order within a part), so a
+// tile's partials are one contiguous run of rows, summed in that order by the finalize.
 struct TiledPlan {
     int valid = 0;
     int dim = 0, vx = 0;
@@ -56,8 +59,8 @@ struct TiledPlan {
 
 // Shape check, tile geometry and the schedule (queries the current device for its SM count
 // and the kernel's occupancy).  false + reason if the grid cannot be tiled.
-bool tiled_plan(int dim, const int n[3], int nb, int nd, int storage, int limiter, const int bc[6], TiledPlan &plan,
-                std::string &why);
+bool tiled_plan(int dim, const int n[3], int nb, int nd, int storage, int limiter, bool sr, const int bc[6],
+                TiledPlan &plan, std::string &why);
 // Device copies of the schedule tables, the wall partials and the error flag, and the per-plane
 // constant records the producer copies into each stage (built from the step tables in a).
 bool tiled_setup(TiledPlan &plan, const StepArgs &a, std::string &why);

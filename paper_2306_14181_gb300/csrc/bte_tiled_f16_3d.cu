@@ -1,8 +1,10 @@
-// Instances of the tiled forward kernel: F16 storage, 3-D grids.
+// Instances of the tiled forward kernel: F16 codes rounded to nearest, 3-D grids.
 #include "bte_tiled_kernel.cuh"
 
 namespace bte {
 namespace tiled {
-StepKernel pick_f16_3d(int lim, int nx) { return pick_instance<kStoreF16, 3>(lim, nx); }
+StepKernel pick_f16_3d(int lim, int nx, bool sr) {
+    return sr ? pick_f16sr_3d(lim, nx) : pick_instance<kStoreF16, 3, false>(lim, nx);
+}
 }  // namespace tiled
 }  // namespace bte

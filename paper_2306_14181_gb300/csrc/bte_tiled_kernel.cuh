@@ -35,31 +35,38 @@ template <> struct Geo<3, 1> {
 template <int S> struct St;
 template <> struct St<kStoreF32> {
     using T = float;
+    using C = float;  // a code held in a register
     static constexpr bool kRef = false;
     static __device__ __forceinline__ float dec(T h, float) { return h; }
-    static __device__ __forceinline__ T enc(float v) { return v; }
-    static __device__ __forceinline__ T enc_sr(float v, uint32_t) { return v; }
+    static __device__ __forceinline__ float val(C c) { return c; }
+    static __device__ __forceinline__ C bits(T h) { return h; }
+    static __device__ __forceinline__ C enc(float v) { return v; }
+    static __device__ __forceinline__ C enc_sr(float v, uint32_t) { return v; }
 };
 template <> struct St<kStoreF16> {
     using T = __half;
+    using C = uint32_t;  // the code's 16 bits in the low half
     static constexpr bool kRef = true;
     static __device__ __forceinline__ float dec(T h, float rho) { return __half2float(h) + rho; }
-    static __device__ __forceinline__ T enc(float v) { return __float2half_rn(v); }
+    static __device__ __forceinline__ float val(C c) { return __half2float(__ushort_as_half((unsigned short)c)); }
+    static __device__ __forceinline__ C bits(T h) { return __half_as_ushort(h); }
+    static __device__ __forceinline__ C enc(float v) { return __half_as_ushort(__float2half_rn(v)); }
     // stochastic rounding: 13 random bits below binary16's 10 fraction bits, then truncation
     // (exact for normal binary16 values; round to nearest in the subnormal range)
-    static __device__ __forceinline__ T enc_sr(float v, uint32_t bits) {
-        return __float2half_rn(__uint_as_float((__float_as_uint(v) + (bits >> 19)) & 0xffffe000u));
+    static __device__ __forceinline__ C enc_sr(float v, uint32_t bits) {
+        return __half_as_ushort(__float2half_rn(__uint_as_float((__float_as_uint(v) + (bits >> 19)) & 0xffffe000u)));
     }
 };
 template <> struct St<kStoreBF16> {
     using T = __nv_bfloat16;
+    using C = uint32_t;
     static constexpr bool kRef = true;
     static __device__ __forceinline__ float dec(T h, float rho) { return __bfloat162float(h) + rho; }
-    static __device__ __forceinline__ T enc(float v) { return __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ float val(C c) { return __uint_as_float(c << 16); }
+    static __device__ __forceinline__ C bits(T h) { return __bfloat16_as_ushort(h); }
+    static __device__ __forceinline__ C enc(float v) { return __bfloat16_as_ushort(__float2bfloat16_rn(v)); }
     // stochastic rounding: 16 random bits below bfloat16's 7 fraction bits, then truncation
-    static __device__ __forceinline__ T enc_sr(float v, uint32_t bits) {
-        return __ushort_as_bfloat16((unsigned short)((__float_as_uint(v) + (bits >> 16)) >> 16));
-    }
+    static __device__ __forceinline__ C enc_sr(float v, uint32_t bits) { return (__float_as_uint(v) + (bits >> 16)) >> 16; }
 };
 
 // PTX approximate reciprocal (one MUFU operation, no special-case branches).
@@ -175,47 +182,62 @@ __device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;"
 
 // ---- VL-wide loads and stores ---------------------------------------------------------------
 // VL decoded values of a box row: p points at the codes, r at the same cells' references in the
-// shared reference box (read by the 16-bit instances only).
+// shared reference box (read by the 16-bit instances only).  Codes are taken from 32-bit words
+// in registers (no local arrays).
 template <int S, int VL>
 __device__ __forceinline__ void ld_row(float (&v)[VL], const typename St<S>::T *p, const float *r) {
-    using T = typename St<S>::T;
-    constexpr int B = VL * (int)sizeof(T);
-    alignas(16) T h[VL];
-    if constexpr (B == 16) {
-        *reinterpret_cast<uint4 *>(h) = *reinterpret_cast<const uint4 *>(p);
-    } else if constexpr (B == 8) {
-        *reinterpret_cast<uint2 *>(h) = *reinterpret_cast<const uint2 *>(p);
-    } else {
-        #pragma unroll
-        for (int j = 0; j < VL; ++j) h[j] = p[j];
-    }
-    float rr[VL];
-    if constexpr (St<S>::kRef) {
+    using Q = St<S>;
+    if constexpr (!Q::kRef) {
         if constexpr (VL == 4) {
-            const float4 f = *reinterpret_cast<const float4 *>(r);
-            rr[0] = f.x; rr[1] = f.y; rr[2] = f.z; rr[3] = f.w;
+            const float4 f = *reinterpret_cast<const float4 *>(p);
+            v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
         } else {
             #pragma unroll
-            for (int j = 0; j < VL; ++j) rr[j] = r[j];
+            for (int j = 0; j < VL; ++j) v[j] = p[j];
         }
     } else {
+        float f[VL], rr[VL];
+        if constexpr (VL == 4) {
+            const uint2 q = *reinterpret_cast<const uint2 *>(p);
+            f[0] = Q::val(q.x & 0xffffu); f[1] = Q::val(q.x >> 16);
+            f[2] = Q::val(q.y & 0xffffu); f[3] = Q::val(q.y >> 16);
+            const float4 g = *reinterpret_cast<const float4 *>(r);
+            rr[0] = g.x; rr[1] = g.y; rr[2] = g.z; rr[3] = g.w;
+        } else {
+            #pragma unroll
+            for (int j = 0; j < VL; ++j) {
+                f[j] = Q::val(Q::bits(p[j]));
+                rr[j] = r[j];
+            }
+        }
+        // h + rho, two at a time
         #pragma unroll
-        for (int j = 0; j < VL; ++j) rr[j] = 0.f;
+        for (int j = 0; j + 1 < VL; j += 2) {
+            const float2 d = __fadd2_rn(make_float2(f[j], f[j + 1]), make_float2(rr[j], rr[j + 1]));
+            v[j] = d.x;
+            v[j + 1] = d.y;
+        }
+        if constexpr (VL & 1) v[VL - 1] = f[VL - 1] + rr[VL - 1];
     }
-    #pragma unroll
-    for (int j = 0; j < VL; ++j) v[j] = St<S>::dec(h[j], rr[j]);
 }
 
 template <int S, int VL>
-__device__ __forceinline__ void st_row(typename St<S>::T *p, const typename St<S>::T (&h)[VL]) {
-    constexpr int B = VL * (int)sizeof(typename St<S>::T);
-    if constexpr (B == 16) {
-        *reinterpret_cast<uint4 *>(p) = *reinterpret_cast<const uint4 *>(h);
-    } else if constexpr (B == 8) {
-        *reinterpret_cast<uint2 *>(p) = *reinterpret_cast<const uint2 *>(h);
+__device__ __forceinline__ void st_row(typename St<S>::T *p, const typename St<S>::C (&c)[VL]) {
+    using Q = St<S>;
+    if constexpr (!Q::kRef) {
+        if constexpr (VL == 4) *reinterpret_cast<float4 *>(p) = make_float4(c[0], c[1], c[2], c[3]);
+        else {
+            #pragma unroll
+            for (int j = 0; j < VL; ++j) p[j] = c[j];
+        }
     } else {
-        #pragma unroll
-        for (int j = 0; j < VL; ++j) p[j] = h[j];
+        if constexpr (VL == 4) {
+            *reinterpret_cast<uint2 *>(p) = make_uint2(c[0] | (c[1] << 16), c[2] | (c[3] << 16));
+        } else {
+            unsigned short *ps = reinterpret_cast<unsigned short *>(p);
+            #pragma unroll
+            for (int j = 0; j < VL; ++j) ps[j] = (unsigned short)c[j];
+        }
     }
 }
 
@@ -354,9 +376,9 @@ __device__ void producer(const StepArgs &a, const TiledArgs &p, char *smem, uint
     bool more = cur.start(a, p);
     bool ahead_ok = ahead.start(a, p);
     for (int j = 0; j < p.ns && ahead_ok; ++j) ahead_ok = ahead.next(a, p);  // the plane-tile ns later
+    int s = 0;         // stage of plane-tile i = i mod ns
+    uint32_t ph = 0u;  // its use count parity = (i / ns) mod 2
     for (int i = 0; more; ++i, more = cur.next(a, p)) {
-        const int s = i % p.ns;
-        const uint32_t ph = (uint32_t)(i / p.ns) & 1u;
         if (i >= p.ns && !mbar_wait(&empty[s], ph ^ 1u, p.err, 2)) return;
         fence_proxy_async();
         __syncwarp();
@@ -445,6 +467,10 @@ __device__ void producer(const StepArgs &a, const TiledArgs &p, char *smem, uint
                 bulk_prefetch_l2(e + (long long)qp.plane * a.ncell + ((long long)z * ny + ylo) * NX, (uint32_t)(yhi - ylo) * rowb);
             ahead_ok = ahead.next(a, p);
         }
+        if (++s == p.ns) {
+            s = 0;
+            ph ^= 1u;
+        }
     }
 }
 
@@ -452,7 +478,7 @@ __device__ void producer(const StepArgs &a, const TiledArgs &p, char *smem, uint
 // Where an end lane of a warp takes its two x-neighbours from (besides the plain shuffle).
 enum { kGhShfl = 0, kGhSmem = 1, kGhSpec = 2, kGhDiff = 3, kGhConst = 4, kGhOwn = 5 };
 
-template <int S, int LIM, int VL, int WPR, int DIM>
+template <int S, int LIM, int VL, int WPR, int DIM, bool SR>
 __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs &p, const PT &q, const char *stage,
                                              int zl, int rb, int half, float *accsm, const float *btsm, float *wsm,
                                              const float *rbox) {
@@ -481,8 +507,7 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
     // second ghost layer of a thermalizing or diffuse wall holds the wall value coded against
     // the wall cell's reference, as the first layer does
     const int dyR = sy * NX, dzR = sz * RY * NX;
-    const bool sr = REF && a.sr;
-    const uint32_t pkey = sr ? plane_key(a.srkey, q.plane) : 0u;
+    const uint32_t pkey = SR ? plane_key(a.srkey, q.plane) : 0u;
     int ro = ((DIM == 3 ? zl + 2 : 0) * RY + yl0 + 2) * NX;
     int ry2 = 2 * dyR, rz2 = 2 * dzR;
     if constexpr (REF) {
@@ -622,16 +647,16 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
             #pragma unroll
             for (int v = 0; v < VL; ++v) { bt[v] = btsm[c + v]; ac[v] = accsm[c + v]; }
         }
-        T h[VL];
+        typename St<S>::C h[VL];
         float es[VL];
         const long long grow = ((long long)z * ny + y) * NX;  // global index of the row's first cell
         #pragma unroll
         for (int v = 0; v < VL; ++v) {
             // FP32: e^{n+1}.  16-bit: bt carries -rho_new, so en is already the new code's value
             const float en = fmaf(-dtinv, w0[v], w0[v] - div[v]) + bt[v];
-            if constexpr (REF) h[v] = sr ? St<S>::enc_sr(en, mix32(pkey ^ (uint32_t)(grow + x0 + v))) : St<S>::enc(en);
+            if constexpr (SR) h[v] = St<S>::enc_sr(en, mix32(pkey ^ (uint32_t)(grow + x0 + v)));
             else h[v] = St<S>::enc(en);
-            es[v] = St<S>::dec(h[v], 0.f);
+            es[v] = St<S>::val(h[v]);
             ac[v] = fmaf(wm, es[v], ac[v]);
         }
         if constexpr (VL == 4) *reinterpret_cast<float4 *>(accsm + c) = make_float4(ac[0], ac[1], ac[2], ac[3]);
@@ -756,7 +781,7 @@ __device__ __forceinline__ void fill_ref_box(const StepArgs &a, const PT &q, flo
     }
 }
 
-template <int S, int LIM, int VL, int WPR, int DIM>
+template <int S, int LIM, int VL, int WPR, int DIM, bool SR>
 __device__ void consumer(const StepArgs &a, const TiledArgs &p, char *smem, uint64_t *full, uint64_t *empty) {
     constexpr bool REF = St<S>::kRef;
     constexpr int NX = 32 * VL * WPR, TY = Geo<DIM, WPR>::TY, NCW = Geo<DIM, WPR>::NCW;
@@ -770,6 +795,8 @@ __device__ void consumer(const StepArgs &a, const TiledArgs &p, char *smem, uint
     float *accsm = reinterpret_cast<float *>(smem + p.acc_off);
     float *rbox = reinterpret_cast<float *>(smem + p.rho_off);
     int seg = -1, cur_unit = -1, cur_band = -1;
+    int s = 0;         // stage of plane-tile i = i mod ns
+    uint32_t ph = 0u;  // its use count parity = (i / ns) mod 2
     float wsum = 0.f;  // sum of w_d / tau_k over the segment's planes (16-bit storage)
     PT cur{};
     Cursor<DIM, WPR> c;
@@ -810,20 +837,24 @@ __device__ void consumer(const StepArgs &a, const TiledArgs &p, char *smem, uint
                 }
             }
         }
-        const int s = i % p.ns;
-        const uint32_t ph = (uint32_t)(i / p.ns) & 1u;
         if (!mbar_wait(&full[s], ph, p.err, 1)) return;
         const char *stage = smem + p.stage0 + (size_t)s * p.stage_bytes;
         if constexpr (REF) wsum += reinterpret_cast<const float *>(stage + p.hdr_off)[3];
         if (zl < q.nzt && rb < q.nyt)
-            rows_of_warp<S, LIM, VL, WPR, DIM>(a, p, q, stage, zl, rb, half, accsm, btsm, wsm, rbox);
+            rows_of_warp<S, LIM, VL, WPR, DIM, SR>(a, p, q, stage, zl, rb, half, accsm, btsm, wsm, rbox);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
+        if (++s == p.ns) {
+            s = 0;
+            ph ^= 1u;
+        }
     }
     if (seg >= 0) flush_segment<REF, VL, WPR, DIM>(a, p, seg, cur, accsm, wsm, wsum);
 }
 
-template <int S, int LIM, int VL, int WPR, int DIM>
+// SR: 16-bit codes rounded stochastically (a separate instance, so the round-to-nearest one
+// carries none of the hashing)
+template <int S, int LIM, int VL, int WPR, int DIM, bool SR>
 __global__ void __launch_bounds__((Geo<DIM, WPR>::NCW + 1) * 32, 1) k_step_tiled(const StepArgs a, const TiledArgs p) {
     extern __shared__ __align__(128) char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
@@ -843,36 +874,40 @@ __global__ void __launch_bounds__((Geo<DIM, WPR>::NCW + 1) * 32, 1) k_step_tiled
     if ((int)(threadIdx.x >> 5) == Geo<DIM, WPR>::NCW)
         producer<S, VL, WPR, DIM>(a, p, smem, full, empty);
     else
-        consumer<S, LIM, VL, WPR, DIM>(a, p, smem, full, empty);
+        consumer<S, LIM, VL, WPR, DIM, SR>(a, p, smem, full, empty);
 }
 
 typedef void (*StepKernel)(const StepArgs, const TiledArgs);
 
 // nx = 96: VL 3, one warp per row; nx = 128: VL 4, one warp; nx = 256 (2-D only): VL 4, two warps
-template <int S, int LIM, int DIM>
+template <int S, int LIM, int DIM, bool SR>
 StepKernel pick_nx(int nx) {
-    if (nx == 96) return k_step_tiled<S, LIM, 3, 1, DIM>;
-    if (nx == 128) return k_step_tiled<S, LIM, 4, 1, DIM>;
+    if (nx == 96) return k_step_tiled<S, LIM, 3, 1, DIM, SR>;
+    if (nx == 128) return k_step_tiled<S, LIM, 4, 1, DIM, SR>;
     if constexpr (DIM == 2) {
-        if (nx == 256) return k_step_tiled<S, LIM, 4, 2, DIM>;
+        if (nx == 256) return k_step_tiled<S, LIM, 4, 2, DIM, SR>;
     }
     return nullptr;
 }
 
-template <int S, int DIM>
+template <int S, int DIM, bool SR>
 StepKernel pick_instance(int lim, int nx) {
-    if (lim == kLimFirst) return pick_nx<S, kLimFirst, DIM>(nx);
-    if (lim == kLimMinmod) return pick_nx<S, kLimMinmod, DIM>(nx);
-    return pick_nx<S, kLimVanAlbada, DIM>(nx);
+    if (lim == kLimFirst) return pick_nx<S, kLimFirst, DIM, SR>(nx);
+    if (lim == kLimMinmod) return pick_nx<S, kLimMinmod, DIM, SR>(nx);
+    return pick_nx<S, kLimVanAlbada, DIM, SR>(nx);
 }
 
-// one definition per instantiation unit
+// one definition per instantiation unit (sr: stochastic rounding of 16-bit codes)
 StepKernel pick_f32_2d(int lim, int nx);
 StepKernel pick_f32_3d(int lim, int nx);
-StepKernel pick_f16_2d(int lim, int nx);
-StepKernel pick_f16_3d(int lim, int nx);
-StepKernel pick_bf16_2d(int lim, int nx);
-StepKernel pick_bf16_3d(int lim, int nx);
+StepKernel pick_f16_2d(int lim, int nx, bool sr);
+StepKernel pick_f16_3d(int lim, int nx, bool sr);
+StepKernel pick_bf16_2d(int lim, int nx, bool sr);
+StepKernel pick_bf16_3d(int lim, int nx, bool sr);
+StepKernel pick_f16sr_2d(int lim, int nx);
+StepKernel pick_f16sr_3d(int lim, int nx);
+StepKernel pick_bf16sr_2d(int lim, int nx);
+StepKernel pick_bf16sr_3d(int lim, int nx);
 
 }  // namespace tiled
 }  // namespace bte
