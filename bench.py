@@ -105,6 +105,11 @@ class Dist:
             self.dist.destroy_process_group()
 
 
+def whole_job_rate(units_per_step, steps, world, t_max_ms):
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return units_per_step * steps * world / (t_max_ms / 1e3)
+
+
 # ------------------------------------------------------------------------------------------
 # clocks during the timed region
 # ------------------------------------------------------------------------------------------
@@ -327,7 +332,7 @@ def run_gb300(args):
     fwd_ms, nfwd, fin_ms, nfin = bte.bte_profile_read(ctx)
     bte.bte_profile(ctx, False)
     t_max = d.max(t_ms)
-    value = info.nelem * args.steps * d.world / (t_max / 1e3)
+    value = whole_job_rate(info.nelem, args.steps, d.world, t_max)
 
     # roofline of the forward kernel: algorithmic bytes = read e + write e per update
     peak, peak_kind = hbm_peak()
