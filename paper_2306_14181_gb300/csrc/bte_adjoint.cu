@@ -128,24 +128,42 @@ __global__ void __launch_bounds__(256) k_adj_step(const StepArgs a, const AdjArg
             const float anu = fabsf(nu);
             const bool per = a.bc[2 * ax] == kBcPeriodic;
             float fg[3];
+            // the stencil u_{-2..2} = e(j + m sg) (ghosts by the wall rules) and
+            // lambda_{-1..2}; the three faces that read this cell are F_{j-sg} = (u-2, u-1, u0),
+            // F_j = (u-1, u0, u1) and F_{j+sg} = (u0, u1, u2)
+            const float um2 = ext_value<Cd>(a, e, b, k, d, base, i, c, ax, j - 2 * sg, nu);
+            const float um1 = ext_value<Cd>(a, e, b, k, d, base, i, c, ax, j - sg, nu);
+            const float u0 = e0;
+            const float up1 = ext_value<Cd>(a, e, b, k, d, base, i, c, ax, j + sg, nu);
+            const float lm1 = lam_at(a, lam, base, i, c, ax, j - sg), lp1 = lam_at(a, lam, base, i, c, ax, j + sg);
             // face j+sg reads this cell as its upwind-left value (a face of the forward step
             // only if its upwind cell is in the domain)
             if (per || (j + sg >= 0 && j + sg < n)) {
-                face_grad<Cd, LIM>(a, e, b, k, d, base, i, c, ax, j + sg, sg, nu, fg);
-                acc += anu * (lam_at(a, lam, base, i, c, ax, j + 2 * sg) - lam_at(a, lam, base, i, c, ax, j + sg)) * fg[0];
+                const float up2 = ext_value<Cd>(a, e, b, k, d, base, i, c, ax, j + 2 * sg, nu);
+                float La, Lb;
+                lim_grad<LIM>(up1 - u0, up2 - up1, La, Lb);
+                acc += anu * (lam_at(a, lam, base, i, c, ax, j + 2 * sg) - lp1) * (-0.5f * La);
             }
             // face j: this cell is its upwind value (and its downwind ghost when that ghost is
             // the wall cell itself: a direction leaving through a thermalizing or diffuse wall)
-            face_grad<Cd, LIM>(a, e, b, k, d, base, i, c, ax, j, sg, nu, fg);
-            const float phj = anu * (lam_at(a, lam, base, i, c, ax, j + sg) - l);
+            {
+                float La, Lb;
+                lim_grad<LIM>(u0 - um1, up1 - u0, La, Lb);
+                fg[1] = 1.f + 0.5f * (La - Lb);
+                fg[2] = 0.5f * Lb;
+            }
+            const float phj = anu * (lp1 - l);
             acc += phj * fg[1];
             if (!per && (j + sg < 0 || j + sg >= n)) {
                 const int bcd = a.bc[2 * ax + (sg > 0 ? 1 : 0)];
                 if (bcd == kBcIsothermal || bcd == kBcDiffuse) acc += phj * fg[2];
             }
             // face j-sg reads this cell as its downwind value
-            face_grad<Cd, LIM>(a, e, b, k, d, base, i, c, ax, j - sg, sg, nu, fg);
-            acc += anu * (l - lam_at(a, lam, base, i, c, ax, j - sg)) * fg[2];
+            {
+                float La, Lb;
+                lim_grad<LIM>(um1 - um2, u0 - um1, La, Lb);
+                acc += anu * (l - lm1) * (0.5f * Lb);
+            }
             // specular walls: faces of the mirrored direction that read this element as a ghost
             for (int side = 0; side < 2; ++side) {
                 if (a.bc[2 * ax + side] != kBcSpecular) continue;
@@ -190,7 +208,7 @@ __global__ void __launch_bounds__(256) k_adj_step(const StepArgs a, const AdjArg
 }
 
 // lambda^N = dT_L/de^T p with the final T_L's own log-tau derivative: writes lam_out, pmu, pt
-// (pq = 0).
+// and pq = sum_d lambda^N.
 template <int S>
 __global__ void __launch_bounds__(256) k_adj_init(const StepArgs a, const AdjArgs g, const float *probe) {
     using Cd = Codec<S>;
@@ -212,7 +230,7 @@ __global__ void __launch_bounds__(256) k_adj_init(const StepArgs a, const AdjArg
         se = fmaf(g.w[d], Cd::ld(e, base + i, b, rho_i), se);
     }
     g.pmu[(long long)k * a.ncell + i] = sm * (b.dtinv * b.ck);
-    g.pq[(long long)k * a.ncell + i] = 0.f;
+    g.pq[(long long)k * a.ncell + i] = sm;
     g.pt[(long long)k * a.ncell + i] = p * (b.ck * g.W * a.TL[i] - se) * b.wtau * a.invD;
 }
 
@@ -259,6 +277,234 @@ __global__ void k_adj_tau_sum(const double *part, int nblk, int nb, double *gtau
 }
 
 int adj_tau_blocks(long long ncell) { return (int)((ncell + kTauPerBlock - 1) / kTauPerBlock); }
+
+
+// ------------------------------------------------------------------------------------------
+// Wall pass of the tiled adjoint: along axis ax, one thread per (band, line of cells) adds the
+// faces next to a non-periodic wall that read a ghost value (the first cell's in-face F_{f-sg}
+// and out-face F_f for directions entering through the wall, the last cell's out-face F_l for
+// directions leaving through it) and the ghost transposes: thermalizing incoming -> nothing,
+// outgoing -> the wall cell itself, specular -> the mirrored direction's wall and next cells,
+// diffuse incoming -> spread over the wall cell's outgoing directions.  Axis passes run one
+// after another (corner cells are touched by two).  The per-cell sums of the additions for
+// cells 0, 1, n-2, n-1 of the line go to corr[k][slot][line] for the finalize.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ int wall_slot(int pos, int n) { return pos < 2 ? pos : 2 + pos - (n - 2); }
+
+constexpr int kWallThreads = 64, kWallMaxDirs = 256;
+int adj_walls_max_dirs() { return kWallMaxDirs; }
+
+template <int S, int LIM>
+__global__ void __launch_bounds__(kWallThreads) k_adj_walls(const StepArgs a, const AdjArgs g, int ax, float *lam_out,
+                                                            float *corr, long long nlines) {
+    using Cd = Codec<S>;
+    using T = typename Cd::T;
+    // per direction and side: own-plane additions to the wall cell (layer 0) and the next cell
+    // (layer 1), and the adjoints of ghost layers 1 and 2
+    __shared__ float own[2][2][kWallMaxDirs], gh1[2][kWallMaxDirs], gh2[2][kWallMaxDirs], tot[4][kWallMaxDirs];
+    __shared__ float gam[2];
+    const long long line = blockIdx.x;
+    const int k = blockIdx.y;
+    const int n = a.n[ax];
+    int c[3];
+    {
+        const int o1 = ax == 0 ? 1 : 0, o2 = ax == 2 ? 1 : 2;
+        c[ax] = 0;
+        c[o1] = (int)(line % a.n[o1]);
+        c[o2] = (int)(line / a.n[o1]);
+    }
+    const long long i0 = ((long long)c[2] * a.n[1] + c[1]) * a.n[0] + c[0];
+    const long long st = a.stride[ax];
+    const BandConst b = a.band[k];
+    const T *e = static_cast<const T *>(a.e_in);
+    const float *lam = g.lam_in;
+    // phase 1: every direction's faces next to the two walls
+    for (int d = threadIdx.x; d < a.nd; d += blockDim.x) {
+        const int plane = k * a.nd + d;
+        const float nu = a.nu[3 * plane + ax];
+        const int sg = nu > 0.f ? 1 : -1;
+        const float anu = fabsf(nu);
+        const long long base = (long long)plane * a.ncell;
+        for (int side = 0; side < 2; ++side) {
+            own[side][0][d] = own[side][1][d] = gh1[side][d] = gh2[side][d] = 0.f;
+            if (a.bc[2 * ax + side] == kBcPeriodic || nu == 0.f) continue;
+            const int w0 = side ? n - 1 : 0, in = side ? -1 : 1;
+            int cw[3] = {c[0], c[1], c[2]};
+            cw[ax] = w0;
+            const long long iw = i0 + (long long)w0 * st;
+            if (sg == in) {
+                // entering through this wall: first cell w0, faces F_{w0-sg} and F_{w0}
+                float ga[3], gb[3];
+                face_grad<Cd, LIM>(a, e, b, k, d, base, iw, cw, ax, w0 - sg, sg, nu, ga);
+                face_grad<Cd, LIM>(a, e, b, k, d, base, iw, cw, ax, w0, sg, nu, gb);
+                const float l0 = lam_at(a, lam, base, iw, cw, ax, w0), l1 = lam_at(a, lam, base, iw, cw, ax, w0 + sg);
+                const float pa = anu * l0, pb = anu * (l1 - l0);
+                own[side][0][d] = pa * ga[2] + pb * gb[1];
+                own[side][1][d] = pb * gb[2];
+                gh1[side][d] = pa * ga[1] + pb * gb[0];
+                gh2[side][d] = pa * ga[0];
+            } else {
+                // leaving through this wall: last cell w0, face F_{w0} reads ghost layer 1
+                float gc[3];
+                face_grad<Cd, LIM>(a, e, b, k, d, base, iw, cw, ax, w0, sg, nu, gc);
+                const float ph = -anu * lam_at(a, lam, base, iw, cw, ax, w0);
+                own[side][1][d] = ph * gc[0];
+                own[side][0][d] = ph * gc[1];
+                gh1[side][d] = ph * gc[2];
+            }
+        }
+    }
+    __syncthreads();
+    // diffuse walls: the incoming directions' ghost adjoints, summed in direction order
+    if (threadIdx.x < 2) {
+        const int side = threadIdx.x, wall = 2 * ax + side;
+        float s = 0.f;
+        if (a.bc[wall] == kBcDiffuse)
+            for (int d = 0; d < a.nd; ++d) {
+                const float nu = a.nu[3 * (k * a.nd + d) + ax];
+                if (side == 0 ? nu > 0.f : nu < 0.f) s += gh1[side][d] + gh2[side][d];
+            }
+        gam[side] = s;
+    }
+    __syncthreads();
+    // phase 2: each direction's total at positions 0, 1, n-2, n-1 of the line, the ghost
+    // transposes included; one thread per direction writes its plane, so every element has
+    // a single writer
+    for (int d = threadIdx.x; d < a.nd; d += blockDim.x) {
+        const int plane = k * a.nd + d;
+        const float nu = a.nu[3 * plane + ax];
+        float dv[4] = {0.f, 0.f, 0.f, 0.f};  // by wall_slot
+        for (int side = 0; side < 2; ++side) {
+            const int wall = 2 * ax + side, bc = a.bc[wall];
+            if (bc == kBcPeriodic) continue;
+            const int w0 = side ? n - 1 : 0, in = side ? -1 : 1;
+            float v0 = own[side][0][d], v1 = own[side][1][d];
+            const bool leaving = nu != 0.f && (nu > 0.f ? 1 : -1) != in;
+            if (bc == kBcSpecular) {
+                // this plane's cells are the mirrored direction's ghosts
+                const int dm = a.mirror[ax * a.nd + d];
+                v0 += gh1[side][dm];
+                v1 += gh2[side][dm];
+            } else if (leaving) {
+                v0 += gh1[side][d];  // the outgoing ghost is the wall cell itself
+            }
+            if (bc == kBcDiffuse) v0 = fmaf(a.wdiff[wall * a.nd + d] * a.inv_den[wall], gam[side], v0);
+            dv[wall_slot(w0, n)] += v0;
+            dv[wall_slot(w0 + in, n)] += v1;
+        }
+        const long long pb = (long long)plane * a.ncell + i0;
+        #pragma unroll
+        for (int sl = 0; sl < 4; ++sl) {
+            tot[sl][d] = dv[sl];
+            const int pos = sl < 2 ? sl : n - 2 + (sl - 2);
+            if (dv[sl] != 0.f && (sl < 2 || pos >= 2)) lam_out[pb + (long long)pos * st] += dv[sl];
+        }
+    }
+    __syncthreads();
+    // per-position sums over the directions, in order, for the finalize
+    if (threadIdx.x < 4) {
+        float sacc = 0.f;
+        for (int d = 0; d < a.nd; ++d) sacc += tot[threadIdx.x][d];
+        corr[((long long)k * 4 + threadIdx.x) * nlines + line] = sacc;
+    }
+}
+
+// Tiled finalize: mu^n_i = sum of the tile's segment rows (Pm) plus the wall corrections;
+// q^n_i likewise (Pq); dJ/dQ_i += amp q^n_i; the band-independent log-tau sum
+// sum_i mu^{n+1}_i T_L,i^n in FP64 block partials.
+__global__ void __launch_bounds__(256) k_adj_tfinal(const StepArgs a, AdjTFinal f, float amp, float *mu_out,
+                                                    double *gQ, double *mt_part) {
+    __shared__ double sh[256];
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double mt = 0.0;
+    if (i < a.ncell) {
+        const int nx = a.n[0], ny = a.n[1];
+        const int c[3] = {(int)(i % nx), (int)((i / nx) % ny), (int)(i / ((long long)nx * ny))};
+        const int ty = c[1] / f.ty, tz = c[2] / f.tz;
+        const int tile = tz * f.nty + ty;
+        const int li = ((c[2] - tz * f.tz) * f.ty + (c[1] - ty * f.ty)) * nx + c[0];
+        float m = 0.f, q = 0.f;
+        for (int s = f.tile_seg0[tile]; s < f.tile_seg0[tile + 1]; ++s) {
+            m += f.Pm[(size_t)s * f.tcells + li];
+            q += f.Pq[(size_t)s * f.tcells + li];
+        }
+        for (int ax = 0; ax < a.dim; ++ax) {
+            if (a.bc[2 * ax] == kBcPeriodic) continue;
+            const int n = a.n[ax], pos = c[ax];
+            if (pos >= 2 && pos < n - 2) continue;
+            const int o1 = ax == 0 ? 1 : 0, o2 = ax == 2 ? 1 : 2;
+            const long long nl = (long long)a.n[o1] * a.n[o2], line = (long long)c[o2] * a.n[o1] + c[o1];
+            const int sl = wall_slot(pos, n);
+            for (int k = 0; k < a.nb; ++k) {
+                const float v = f.corr[ax][((long long)k * 4 + sl) * nl + line];
+                const BandConst b = a.band[k];
+                m = fmaf(b.dtinv * b.ck, v, m);
+                q = fmaf(b.srck, v, q);
+            }
+        }
+        mu_out[i] = m;
+        gQ[i] += (double)amp * (double)q;
+        mt = (double)f.mu_in[i] * (double)a.TL[i];
+    }
+    sh[threadIdx.x] = mt;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) mt_part[blockIdx.x] = sh[0];
+}
+
+// dJ/dlog tau_k += sum over band k's segments of (-dt/tau_k Ps0 - Ps1/(tau_k D))
+//                 + C_k/(tau_k D) sum_i mu^{n+1}_i T_L,i^n, all in a fixed order.
+__global__ void k_adj_ttau(const StepArgs a, AdjTFinal f, const double *mt_part, int nmt, double W, double *gtau) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= a.nb) return;
+    const BandConst b = a.band[k];
+    double mt = 0.0;
+    for (int j = 0; j < nmt; ++j) mt += mt_part[j];
+    double s = 0.0;
+    for (int g = 0; g < f.G; ++g) {
+        if (f.seg_band[g] != k) continue;
+        s += -(double)b.dtinv * (double)f.Ps[2 * g] - (double)f.Ps[2 * g + 1] * (double)b.wtau * (double)a.invD;
+    }
+    s += (double)b.ck * W * (double)b.wtau * (double)a.invD * mt;
+    gtau[k] += s;
+}
+
+cudaError_t launch_adj_walls(const StepArgs &a, const AdjArgs &g, int storage, int limiter, float *lam_out,
+                             float *const corr[3], cudaStream_t s) {
+    for (int ax = 0; ax < a.dim; ++ax) {
+        if (a.bc[2 * ax] == kBcPeriodic) continue;
+        const int o1 = ax == 0 ? 1 : 0, o2 = ax == 2 ? 1 : 2;
+        const long long nl = (long long)a.n[o1] * a.n[o2];
+        const dim3 grid((unsigned)nl, (unsigned)a.nb);
+#define BTE_ADJW(SS, LL) k_adj_walls<SS, LL><<<grid, kWallThreads, 0, s>>>(a, g, ax, lam_out, corr[ax], nl)
+        if (storage == kStoreF32) {
+            if (limiter == kLimFirst) BTE_ADJW(kStoreF32, kLimFirst);
+            else if (limiter == kLimMinmod) BTE_ADJW(kStoreF32, kLimMinmod);
+            else BTE_ADJW(kStoreF32, kLimVanAlbada);
+        } else if (storage == kStoreF16) {
+            if (limiter == kLimFirst) BTE_ADJW(kStoreF16, kLimFirst);
+            else if (limiter == kLimMinmod) BTE_ADJW(kStoreF16, kLimMinmod);
+            else BTE_ADJW(kStoreF16, kLimVanAlbada);
+        } else {
+            if (limiter == kLimFirst) BTE_ADJW(kStoreBF16, kLimFirst);
+            else if (limiter == kLimMinmod) BTE_ADJW(kStoreBF16, kLimMinmod);
+            else BTE_ADJW(kStoreBF16, kLimVanAlbada);
+        }
+#undef BTE_ADJW
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_tfinal(const StepArgs &a, const AdjTFinal &f, float amp, float *mu_out, double *gQ,
+                              double *mt_part, double W, double *gtau, cudaStream_t s) {
+    const int nblk = (int)((a.ncell + 255) / 256);
+    k_adj_tfinal<<<nblk, 256, 0, s>>>(a, f, amp, mu_out, gQ, mt_part);
+    k_adj_ttau<<<(a.nb + 63) / 64, 64, 0, s>>>(a, f, mt_part, nblk, W, gtau);
+    return cudaGetLastError();
+}
 
 template <int S>
 static void adj_step_s(const StepArgs &a, const AdjArgs &g, int limiter, cudaStream_t s) {

@@ -2,6 +2,7 @@
 #pragma once
 
 #include "bte_internal.h"
+#include "bte_tiled.h"
 
 namespace bte {
 
@@ -25,5 +26,28 @@ cudaError_t launch_adj_init(const StepArgs &a, const AdjArgs &g, int storage, co
 cudaError_t launch_adj_reduce(const StepArgs &a, const AdjArgs &g, float amp, float *mu_out, double *gQ,
                               double *tau_part, double *gtau, cudaStream_t s);
 int adj_tau_blocks(long long ncell);
+int adj_walls_max_dirs();  // directions the tiled adjoint's wall pass handles
+
+// Tiled adjoint (bte_adjoint_tiled*.cu): segment partials and their finalize.
+struct AdjTFinal {
+    const int *tile_seg0;  // [ntiles + 1] the tile's segment rows
+    const int *seg_band;   // [G] band of each segment
+    const float *Pm, *Pq;  // [G][tcells]
+    const float *Ps;       // [G][2]
+    const float *mu_in;    // mu^{n+1}
+    const float *corr[3];  // wall corrections per axis [nb][4][lines]
+    int G, tcells, ty, tz, nty;
+};
+// Wall pass along every non-periodic axis (one launch per axis; corr[ax]: nb * 4 * lines floats).
+cudaError_t launch_adj_walls(const StepArgs &a, const AdjArgs &g, int storage, int limiter, float *lam_out,
+                             float *const corr[3], cudaStream_t s);
+// mu^n, dJ/dQ += amp q^n, dJ/dlog tau from the segment scalars (mt_part: ceil(ncell/256) doubles).
+// The tiled adjoint step on the forward plan's tiles and schedule: lambda^n (interior and
+// periodic faces), segment rows Pm, Pq ([G][tcells]) and Ps ([G][2]).
+cudaError_t launch_adj_tiled(const StepArgs &a, const TiledPlan &plan, const float *lam_in, float *lam_out,
+                             const float *mu_in, float *Pm, float *Pq, float *Ps, const float *w, int storage,
+                             int limiter, cudaStream_t s);
+cudaError_t launch_adj_tfinal(const StepArgs &a, const AdjTFinal &f, float amp, float *mu_out, double *gQ,
+                              double *mt_part, double W, double *gtau, cudaStream_t s);
 
 }  // namespace bte

@@ -1,0 +1,438 @@
+// Tiled adjoint step (the transpose of the forward step; the algebra is in bte_adjoint.cu), on
+// the forward kernel's tiles and plane-synchronous unit schedule.  Included by the
+// instantiation units bte_adjoint_tiled_<storage>.cu.
+//
+// Face form of the transpose: a face with upwind position m (orientation sg along an axis)
+// has value F_m = u_m + L(u_m - u_l, u_r - u_m)/2 and enters cell m with -|nu|, cell m+sg with
+// +|nu|; with phi_m = |nu| (lambda_{m+sg} - lambda_m) it adds
+//   A_m = phi_m dF/du_l to cell m-sg,  B_m = phi_m dF/du_m to cell m,  C_m = phi_m dF/du_r to m+sg.
+// The limiter's partials are homogeneous of degree 0, so faces are evaluated on e / s_k
+// directly for 16-bit codes.  This kernel takes every face whose three values lie in the
+// domain (or wrap on a periodic axis): y faces streamed in registers from upwind to downwind
+// (one new face per row), x faces per lane (neighbour values by shuffles), z faces per
+// element.  The faces next to a non-periodic wall that read a ghost value (the first cell's
+// in-face and out-face, the last cell's out-face) and every ghost transpose are added by
+// k_adj_walls afterwards, which keeps this kernel free of wall rules.  Values come straight
+// from global memory (neighbouring units' rows are L2-resident).
+#pragma once
+
+#include "bte_adjoint.h"
+#include "bte_tiled_kernel.cuh"
+
+namespace bte {
+namespace tiled {
+
+template <int LIM> __device__ __forceinline__ void adj_lim_grad(float a, float b, float &La, float &Lb);
+template <> __device__ __forceinline__ void adj_lim_grad<kLimFirst>(float, float, float &La, float &Lb) {
+    La = Lb = 0.f;
+}
+template <> __device__ __forceinline__ void adj_lim_grad<kLimMinmod>(float a, float b, float &La, float &Lb) {
+    const bool on = a * b > 0.f, pa = fabsf(a) < fabsf(b);
+    La = on && pa ? 1.f : 0.f;
+    Lb = on && !pa ? 1.f : 0.f;
+}
+template <> __device__ __forceinline__ void adj_lim_grad<kLimVanAlbada>(float a, float b, float &La, float &Lb) {
+    // L = ab(a+b)/(a^2+b^2): dL/da = b^2 (2ab + b^2 - a^2)/(a^2+b^2)^2, symmetric in b
+    const float ab = a * b, aa = a * a, bb = b * b;
+    const float rq = rcp_approx(aa + bb);
+    const float t = 2.f * ab;
+    const float la = (bb * rq) * ((t + bb - aa) * rq);
+    const float lb = (aa * rq) * ((t + aa - bb) * rq);
+    La = ab > 1e-30f ? la : 0.f;
+    Lb = ab > 1e-30f ? lb : 0.f;
+}
+
+// A, B, C of a face with values (ul, um, ur) and weight phi.
+template <int LIM>
+__device__ __forceinline__ void face_terms(float ul, float um, float ur, float phi, float &A, float &B, float &C) {
+    float La, Lb;
+    adj_lim_grad<LIM>(um - ul, ur - um, La, Lb);
+    A = -0.5f * La * phi;
+    B = fmaf(0.5f * (La - Lb), phi, phi);
+    C = 0.5f * Lb * phi;
+}
+
+// Row index of position pos along an axis of n cells: itself, the wrapped row on a periodic
+// axis, or -1 outside a wall (faces reading it belong to the wall pass).
+__device__ __forceinline__ int adj_row(int pos, int n, bool per) {
+    if (pos >= 0 && pos < n) return pos;
+    if (!per) return -1;
+    return pos < 0 ? pos + n : pos - n;
+}
+
+// VL values of e (16-bit: e / s_k = h + rho) at global cell index `cell` of plane `base`.
+template <int S, int VL>
+__device__ __forceinline__ void adj_ld_e(float (&v)[VL], const StepArgs &a, const typename St<S>::T *e, long long base,
+                                         long long cell) {
+    using Q = St<S>;
+    if constexpr (!Q::kRef) {
+        if constexpr (VL == 4) {
+            const float4 f = *reinterpret_cast<const float4 *>(e + base + cell);
+            v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+        } else {
+            #pragma unroll
+            for (int j = 0; j < VL; ++j) v[j] = e[base + cell + j];
+        }
+    } else {
+        if constexpr (VL == 4) {
+            const uint2 q = *reinterpret_cast<const uint2 *>(e + base + cell);
+            const float4 r = *reinterpret_cast<const float4 *>(a.R + cell);
+            v[0] = fmaf(r.x, a.invTs, Q::val(q.x & 0xffffu));
+            v[1] = fmaf(r.y, a.invTs, Q::val(q.x >> 16));
+            v[2] = fmaf(r.z, a.invTs, Q::val(q.y & 0xffffu));
+            v[3] = fmaf(r.w, a.invTs, Q::val(q.y >> 16));
+        } else {
+            #pragma unroll
+            for (int j = 0; j < VL; ++j) v[j] = fmaf(a.R[cell + j], a.invTs, Q::val(Q::bits(e[base + cell + j])));
+        }
+    }
+}
+
+template <int VL>
+__device__ __forceinline__ void adj_ld_l(float (&v)[VL], const float *lam, long long idx) {
+    if constexpr (VL == 4) {
+        const float4 f = *reinterpret_cast<const float4 *>(lam + idx);
+        v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+    } else {
+        #pragma unroll
+        for (int j = 0; j < VL; ++j) v[j] = lam[idx + j];
+    }
+}
+
+// One value of e / s_k (or lambda) at x position xp of a row (used by the end lanes of a warp).
+template <int S>
+__device__ __forceinline__ float adj_e1(const StepArgs &a, const typename St<S>::T *e, long long base, long long cell) {
+    using Q = St<S>;
+    if constexpr (!Q::kRef) return e[base + cell];
+    else return fmaf(a.R[cell], a.invTs, Q::val(Q::bits(e[base + cell])));
+}
+
+// x faces of one lane: upwind cell m = x0-1+f, f = 0 .. VL+1 (orientation SX); index i of ex /
+// lx is position x0-2+i.  A face is taken when its three values are in the domain or wrap.
+// Cell x0+j (face index j+1) gets A of face x0+j+SX, B of face x0+j, C of face x0+j-SX.
+template <int LIM, int VL, int SX>
+__device__ __forceinline__ void adj_xfaces(const float (&ex)[VL + 4], const float (&lx)[VL + 4], int x0, int NX,
+                                           bool perx, float anx, float (&acc)[VL]) {
+    float fA[VL + 2], fB[VL + 2], fC[VL + 2];
+    #pragma unroll
+    for (int f = 0; f < VL + 2; ++f) {
+        const int m = x0 - 1 + f;
+        const bool ok = perx || (m >= 1 && m + 1 < NX);
+        float A = 0.f, B = 0.f, C = 0.f;
+        if (ok) face_terms<LIM>(ex[f + 1 - SX], ex[f + 1], ex[f + 1 + SX], anx * (lx[f + 1 + SX] - lx[f + 1]), A, B, C);
+        fA[f] = A;
+        fB[f] = B;
+        fC[f] = C;
+    }
+    #pragma unroll
+    for (int j = 0; j < VL; ++j) acc[j] += fA[j + 1 + SX] + fB[j + 1] + fC[j + 1 - SX];
+}
+
+struct AdjTiledArgs {
+    const float *lam_in;  // lambda^{n+1}
+    float *lam_out;       // lambda^n
+    const float *mu_in;   // mu^{n+1} [ncell]
+    float *Pm, *Pq;       // per segment rows [G][tcells]: sum_d lambda^n dt C_k/(W tau_k), sum_d lambda^n dt C_k/(sum C W)
+    float *Ps;            // per segment [G][2]: sum lambda^{n+1} (C_k T_L/W - e), sum w_d mu^{n+1} e
+    const float *w;       // [nd]
+};
+
+// The rows one warp streams for one plane-tile.
+template <int S, int LIM, int VL, int WPR, int DIM>
+__device__ __forceinline__ void adj_rows(const StepArgs &a, const AdjTiledArgs &g, const PT &q, int zl, int rb, int half,
+                                         float *accm, float *accq, float &s1, float &s2) {
+    using T = typename St<S>::T;
+    constexpr int NX = 32 * VL * WPR, TY = Geo<DIM, WPR>::TY;
+    const int lane = threadIdx.x & 31, x0 = (half * 32 + lane) * VL;
+    const int ny = a.n[1], nz = a.n[2];
+    const int plane = q.plane;
+    const long long base = (long long)plane * a.ncell;
+    const BandConst b = a.band[q.k];
+    const float nux = a.nu[3 * plane], nuy = a.nu[3 * plane + 1], nuz = DIM == 3 ? a.nu[3 * plane + 2] : 0.f;
+    const float anx = fabsf(nux), any = fabsf(nuy), anz = fabsf(nuz);
+    const int sx = nux > 0.f ? 1 : -1, sy = nuy > 0.f ? 1 : -1, sz = nuz > 0.f ? 1 : -1;
+    const bool perx = a.bc[0] == kBcPeriodic, pery = a.bc[2] == kBcPeriodic, perz = DIM == 3 && a.bc[4] == kBcPeriodic;
+    const float diag = 1.f - b.dtinv, wmD = a.wmom[plane] * a.invD, wd = g.w[q.d];
+    const float sc = St<S>::kRef ? b.scale : 1.f;  // e = sc * (value in the kernel)
+    const float bm = b.dtinv * b.ck, bq = b.srck;
+    const T *e = static_cast<const T *>(a.e_in);
+    const float *lam = g.lam_in;
+    const int nrows = min(kR, q.nyt - rb);
+    const int z = q.z0 + zl;
+    // streaming order along y: t = 0 .. nrows-1 are this warp's rows, upwind to downwind
+    const int y0w = q.y0 + (sy > 0 ? rb : rb + nrows - 1);
+    auto cell_of = [&](int zz, int yy) { return ((long long)zz * ny + yy) * NX + x0; };
+
+    // y window: e at t-2 .. t+2 (rows), lambda at t-1 .. t+2; faces F_{t+1} computed per step
+    float e_m2[VL], e_m1[VL], e_0[VL], e_p1[VL], e_p2[VL], l_m1[VL], l_0[VL], l_p1[VL], l_p2[VL];
+    float Bprev[VL], Cprev[VL], Cprev2[VL];  // B_t (face t), C_{t-1} (face t-1), C_{t-2}
+    bool ok_m2, ok_m1, ok_0, ok_p1, ok_p2;
+    auto load_row = [&](float (&ev)[VL], float (&lv)[VL], int t, bool &ok) {
+        const int yy = adj_row(y0w + t * sy, ny, pery);
+        ok = yy >= 0;
+        if (ok) {
+            const long long cl = cell_of(z, yy);
+            adj_ld_e<S, VL>(ev, a, e, base, cl);
+            adj_ld_l<VL>(lv, lam, base + cl);
+        } else {
+            #pragma unroll
+            for (int j = 0; j < VL; ++j) ev[j] = lv[j] = 0.f;
+        }
+    };
+    float dummy[VL];
+    load_row(e_m2, dummy, -2, ok_m2);
+    load_row(e_m1, l_m1, -1, ok_m1);
+    load_row(e_0, l_0, 0, ok_0);
+    load_row(e_p1, l_p1, 1, ok_p1);
+    // faces t-1 = -1 (values -2, -1, 0) and t = 0 (values -1, 0, 1)
+    #pragma unroll
+    for (int j = 0; j < VL; ++j) {
+        float A, B, C;
+        if (ok_m2 && ok_m1 && ok_0) face_terms<LIM>(e_m2[j], e_m1[j], e_0[j], any * (l_0[j] - l_m1[j]), A, B, C);
+        else A = B = C = 0.f;
+        Cprev[j] = C;  // C_{-1} goes to row 0
+        if (ok_m1 && ok_0 && ok_p1) face_terms<LIM>(e_m1[j], e_0[j], e_p1[j], any * (l_p1[j] - l_0[j]), A, B, C);
+        else A = B = C = 0.f;
+        Bprev[j] = B;  // B_0 goes to row 0
+        Cprev2[j] = C; // C_0 goes to row 1
+    }
+    #pragma unroll
+    for (int t = 0; t < kR; ++t) {
+        if (t >= nrows) break;
+        const int y = y0w + t * sy;
+        const long long cl = cell_of(z, y);
+        load_row(e_p2, l_p2, t + 2, ok_p2);
+        float acc[VL];
+        // y: face t+1 (values t, t+1, t+2) adds A to row t
+        #pragma unroll
+        for (int j = 0; j < VL; ++j) {
+            float A, B, C;
+            if (ok_0 && ok_p1 && ok_p2) face_terms<LIM>(e_0[j], e_p1[j], e_p2[j], any * (l_p2[j] - l_p1[j]), A, B, C);
+            else A = B = C = 0.f;
+            acc[j] = A + Bprev[j] + Cprev[j];
+            Cprev[j] = Cprev2[j];
+            Bprev[j] = B;
+            Cprev2[j] = C;
+        }
+        // x: values e and lambda at x0-2 .. x0+VL+1 from the neighbour lanes; the end lanes of
+        // a warp read theirs (wrapped on a periodic axis; positions outside a wall are never
+        // used: the faces reading them belong to the wall pass)
+        {
+            float ex[VL + 4], lx[VL + 4];
+            #pragma unroll
+            for (int j = 0; j < VL; ++j) {
+                ex[j + 2] = e_0[j];
+                lx[j + 2] = l_0[j];
+            }
+            const int lft = (lane + 31) & 31, rgt = (lane + 1) & 31;
+            ex[0] = __shfl_sync(0xffffffffu, e_0[VL - 2], lft);
+            ex[1] = __shfl_sync(0xffffffffu, e_0[VL - 1], lft);
+            ex[VL + 2] = __shfl_sync(0xffffffffu, e_0[0], rgt);
+            ex[VL + 3] = __shfl_sync(0xffffffffu, e_0[1], rgt);
+            lx[0] = __shfl_sync(0xffffffffu, l_0[VL - 2], lft);
+            lx[1] = __shfl_sync(0xffffffffu, l_0[VL - 1], lft);
+            lx[VL + 2] = __shfl_sync(0xffffffffu, l_0[0], rgt);
+            lx[VL + 3] = __shfl_sync(0xffffffffu, l_0[1], rgt);
+            const bool lo = lane == 0, hi = lane == 31;
+            if ((lo && (half > 0 || perx)) || (hi && (half < WPR - 1 || perx))) {
+                const long long rowc = ((long long)z * ny + y) * NX;
+                const int xa = lo ? (x0 - 2 + NX) % NX : (x0 + VL) % NX;
+                const int xb = lo ? (x0 - 1 + NX) % NX : (x0 + VL + 1) % NX;
+                const float ea = adj_e1<S>(a, e, base, rowc + xa), eb = adj_e1<S>(a, e, base, rowc + xb);
+                const float la = lam[base + rowc + xa], lb = lam[base + rowc + xb];
+                if (lo) {
+                    ex[0] = ea; ex[1] = eb; lx[0] = la; lx[1] = lb;
+                } else {
+                    ex[VL + 2] = ea; ex[VL + 3] = eb; lx[VL + 2] = la; lx[VL + 3] = lb;
+                }
+            }
+            if (sx > 0) adj_xfaces<LIM, VL, 1>(ex, lx, x0, NX, perx, anx, acc);
+            else adj_xfaces<LIM, VL, -1>(ex, lx, x0, NX, perx, anx, acc);
+        }
+        if constexpr (DIM == 3) {
+            // z: faces z-sz (values z-2sz, z-sz, z), z (z-sz, z, z+sz), z+sz (z, z+sz, z+2sz)
+            float zv[5][VL], zl4[4][VL];
+            bool zok[5];
+            #pragma unroll
+            for (int r = 0; r < 5; ++r) {
+                const int zz = adj_row(z + (r - 2) * sz, nz, perz);
+                zok[r] = zz >= 0;
+                if (r == 2) {
+                    #pragma unroll
+                    for (int j = 0; j < VL; ++j) zv[r][j] = e_0[j];
+                } else if (zok[r]) {
+                    adj_ld_e<S, VL>(zv[r], a, e, base, cell_of(zz, y));
+                } else {
+                    #pragma unroll
+                    for (int j = 0; j < VL; ++j) zv[r][j] = 0.f;
+                }
+                if (r >= 1) {
+                    if (r == 2) {
+                        #pragma unroll
+                        for (int j = 0; j < VL; ++j) zl4[1][j] = l_0[j];
+                    } else if (zok[r]) {
+                        adj_ld_l<VL>(zl4[r - 1], lam, base + cell_of(zz, y));
+                    } else {
+                        #pragma unroll
+                        for (int j = 0; j < VL; ++j) zl4[r - 1][j] = 0.f;
+                    }
+                }
+            }
+            #pragma unroll
+            for (int j = 0; j < VL; ++j) {
+                float A, B, C;
+                if (zok[0] && zok[1]) {  // face z-sz: C to this cell
+                    face_terms<LIM>(zv[0][j], zv[1][j], zv[2][j], anz * (zl4[1][j] - zl4[0][j]), A, B, C);
+                    acc[j] += C;
+                }
+                if (zok[1] && zok[3]) {  // face z: B
+                    face_terms<LIM>(zv[1][j], zv[2][j], zv[3][j], anz * (zl4[2][j] - zl4[1][j]), A, B, C);
+                    acc[j] += B;
+                }
+                if (zok[3] && zok[4]) {  // face z+sz: A
+                    face_terms<LIM>(zv[2][j], zv[3][j], zv[4][j], anz * (zl4[3][j] - zl4[2][j]), A, B, C);
+                    acc[j] += A;
+                }
+            }
+        }
+        // relaxation, T_L coupling; store; per-cell and per-segment partials
+        float mu[VL], tl[VL];
+        adj_ld_l<VL>(mu, g.mu_in, cl);
+        adj_ld_l<VL>(tl, a.TL, cl);
+        float out[VL];
+        const int c = (zl * TY + (y - q.y0)) * NX + x0;
+        #pragma unroll
+        for (int j = 0; j < VL; ++j) {
+            const float lv = l_0[j];
+            out[j] = fmaf(diag, lv, fmaf(wmD, mu[j], acc[j]));
+            const float ev = sc * e_0[j];
+            s1 = fmaf(lv, fmaf(b.ck, tl[j], -ev), s1);
+            s2 = fmaf(wd * mu[j], ev, s2);
+            accm[c + j] = fmaf(bm, out[j], accm[c + j]);
+            accq[c + j] = fmaf(bq, out[j], accq[c + j]);
+        }
+        if constexpr (VL == 4)
+            *reinterpret_cast<float4 *>(g.lam_out + base + cl) = make_float4(out[0], out[1], out[2], out[3]);
+        else {
+            #pragma unroll
+            for (int j = 0; j < VL; ++j) g.lam_out[base + cl + j] = out[j];
+        }
+        // slide the window
+        #pragma unroll
+        for (int j = 0; j < VL; ++j) {
+            e_m2[j] = e_m1[j];
+            e_m1[j] = e_0[j];
+            e_0[j] = e_p1[j];
+            e_p1[j] = e_p2[j];
+            l_m1[j] = l_0[j];
+            l_0[j] = l_p1[j];
+            l_p1[j] = l_p2[j];
+        }
+        ok_m2 = ok_m1;
+        ok_m1 = ok_0;
+        ok_0 = ok_p1;
+        ok_p1 = ok_p2;
+    }
+}
+
+template <int S, int LIM, int VL, int WPR, int DIM>
+__global__ void __launch_bounds__(Geo<DIM, WPR>::NCW * 32, 1) k_adj_tiled(const StepArgs a, const TiledArgs p,
+                                                                          const AdjTiledArgs g) {
+    constexpr int NX = 32 * VL * WPR, TY = Geo<DIM, WPR>::TY, NCW = Geo<DIM, WPR>::NCW;
+    extern __shared__ __align__(128) char smem[];
+    float *accm = reinterpret_cast<float *>(smem);
+    float *accq = accm + p.tcells;
+    float *red = accq + p.tcells;  // [2][NCW]
+    for (int j = threadIdx.x; j < 2 * p.tcells; j += blockDim.x) accm[j] = 0.f;
+    __syncthreads();
+    int zl, rb, half;
+    warp_place<VL, WPR, DIM>(zl, rb, half);
+    const int lane = threadIdx.x & 31, x0 = (half * 32 + lane) * VL;
+    int seg = -1, cur_unit = -1, cur_band = -1;
+    PT cur{};
+    float s1 = 0.f, s2 = 0.f;
+    auto flush = [&]() {
+        float *Pm = g.Pm + (size_t)seg * p.tcells, *Pq = g.Pq + (size_t)seg * p.tcells;
+        #pragma unroll
+        for (int r = 0; r < kR; ++r) {
+            const int yl = rb + r;
+            const int c = (zl * TY + yl) * NX + x0;
+            if (yl < cur.nyt && zl < cur.nzt) {
+                #pragma unroll
+                for (int v = 0; v < VL; ++v) {
+                    Pm[c + v] = accm[c + v];
+                    Pq[c + v] = accq[c + v];
+                }
+            }
+            #pragma unroll
+            for (int v = 0; v < VL; ++v) accm[c + v] = accq[c + v] = 0.f;
+        }
+        // segment scalars: warp sums, then warp 0 adds the warps in order
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+        if (lane == 0) {
+            red[threadIdx.x >> 5] = s1;
+            red[NCW + (threadIdx.x >> 5)] = s2;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t1 = 0.f, t2 = 0.f;
+            for (int w = 0; w < NCW; ++w) {
+                t1 += red[w];
+                t2 += red[NCW + w];
+            }
+            g.Ps[2 * seg] = t1;
+            g.Ps[2 * seg + 1] = t2;
+        }
+        __syncthreads();
+        s1 = s2 = 0.f;
+    };
+    Cursor<DIM, WPR> c;
+    bool more = c.start(a, p);
+    for (; more; more = c.next(a, p)) {
+        const PT q = c.q;
+        if (c.u != cur_unit || q.k != cur_band) {
+            if (seg >= 0) flush();
+            seg = p.unit_seg0[c.u] + q.k - c.p0 / a.nd;
+            cur_unit = c.u;
+            cur_band = q.k;
+            cur = q;
+        }
+        if (zl < q.nzt && rb < q.nyt) adj_rows<S, LIM, VL, WPR, DIM>(a, g, q, zl, rb, half, accm, accq, s1, s2);
+    }
+    if (seg >= 0) flush();
+}
+
+typedef void (*AdjKernel)(const StepArgs, const TiledArgs, const AdjTiledArgs);
+
+template <int S, int LIM, int DIM>
+AdjKernel adj_pick_nx(int nx) {
+    if (nx == 96) return k_adj_tiled<S, LIM, 3, 1, DIM>;
+    if (nx == 128) return k_adj_tiled<S, LIM, 4, 1, DIM>;
+    if constexpr (DIM == 2) {
+        if (nx == 256) return k_adj_tiled<S, LIM, 4, 2, DIM>;
+    }
+    return nullptr;
+}
+
+template <int S>
+AdjKernel adj_pick_instance(int lim, int nx, int dim) {
+    if (dim == 2) {
+        if (lim == kLimFirst) return adj_pick_nx<S, kLimFirst, 2>(nx);
+        if (lim == kLimMinmod) return adj_pick_nx<S, kLimMinmod, 2>(nx);
+        return adj_pick_nx<S, kLimVanAlbada, 2>(nx);
+    }
+    if (lim == kLimFirst) return adj_pick_nx<S, kLimFirst, 3>(nx);
+    if (lim == kLimMinmod) return adj_pick_nx<S, kLimMinmod, 3>(nx);
+    return adj_pick_nx<S, kLimVanAlbada, 3>(nx);
+}
+
+AdjKernel adj_pick_f32(int lim, int nx, int dim);
+AdjKernel adj_pick_f16(int lim, int nx, int dim);
+AdjKernel adj_pick_bf16(int lim, int nx, int dim);
+
+}  // namespace tiled
+}  // namespace bte

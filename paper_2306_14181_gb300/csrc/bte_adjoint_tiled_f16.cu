@@ -1,0 +1,8 @@
+// Instances of the tiled adjoint kernel: F16 storage, 2-D and 3-D grids.
+#include "bte_adjoint_tiled.cuh"
+
+namespace bte {
+namespace tiled {
+AdjKernel adj_pick_f16(int lim, int nx, int dim) { return adj_pick_instance<kStoreF16>(lim, nx, dim); }
+}  // namespace tiled
+}  // namespace bte

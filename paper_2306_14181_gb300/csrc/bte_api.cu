@@ -984,6 +984,24 @@ extern "C" bte_status bte_adjoint(bte_ctx *c, int nsteps, int ckpt_every, const 
     for (auto &s : L3)
         if (!w.snap(s)) return fail(c, BTE_ENOMEM, "adjoint checkpoints do not fit in device memory");
     if (!w.snap(fin)) return fail(c, BTE_ENOMEM, "adjoint checkpoints do not fit in device memory");
+    // tiled adjoint: segment partials, wall corrections, block partials of sum mu T_L
+    float *Pm = nullptr, *Pq = nullptr, *Ps = nullptr, *corr[3] = {nullptr, nullptr, nullptr};
+    double *mtp = nullptr;
+    const bool tiled_adj = c->tiled && c->nd <= adj_walls_max_dirs();
+    if (tiled_adj) {
+        const size_t gt_rows = (size_t)std::max(1, c->plan.G);
+        if (!w.alloc((void **)&Pm, gt_rows * c->plan.tcells * sizeof(float)) ||
+            !w.alloc((void **)&Pq, gt_rows * c->plan.tcells * sizeof(float)) ||
+            !w.alloc((void **)&Ps, 2 * gt_rows * sizeof(float)) ||
+            !w.alloc((void **)&mtp, (size_t)((nc + 255) / 256) * sizeof(double)))
+            return fail(c, BTE_ENOMEM, "adjoint buffers do not fit in device memory");
+        for (int ax = 0; ax < c->dim; ++ax) {
+            if (c->bc[2 * ax] == BTE_BC_PERIODIC) continue;
+            const long long lines = nc / c->n[ax];
+            if (!w.alloc((void **)&corr[ax], (size_t)c->nb * 4 * lines * sizeof(float)))
+                return fail(c, BTE_ENOMEM, "adjoint buffers do not fit in device memory");
+        }
+    }
     {
         std::vector<float> pf(probe, probe + nc);
         CU(c, cudaMemcpyAsync(pr, pf.data(), nc * sizeof(float), cudaMemcpyHostToDevice, c->stream));
@@ -1016,6 +1034,7 @@ extern "C" bte_status bte_adjoint(bte_ctx *c, int nsteps, int ckpt_every, const 
         return BTE_OK;
     };
     int cur = 0;
+    long long base_step = c->step;
     AdjArgs g;
     g.w = c->wf;
     g.W = (float)c->W;
@@ -1032,8 +1051,31 @@ extern "C" bte_status bte_adjoint(bte_ctx *c, int nsteps, int ckpt_every, const 
         g.lam_out = lam[cur ^ 1];
         g.mu_in = mu[cur];
         if (prof) CU(c, cudaEventRecord(ev0, c->stream));
-        CU(c, launch_adj_step(a, g, c->storage, c->limiter, c->stream));
-        CU(c, launch_adj_reduce(a, g, (float)amplitude_at(c, s.step), mu[cur ^ 1], gQ, tpart, gt, c->stream));
+        if (tiled_adj) {
+            // interior and periodic faces on the tiles, then the faces next to each wall, then
+            // mu^n, dJ/dQ (the q^n of lambda^n with the amplitude of step n-1) and dJ/dlog tau
+            CU(c, launch_adj_tiled(a, c->plan, lam[cur], lam[cur ^ 1], mu[cur], Pm, Pq, Ps, c->wf, c->storage,
+                                   c->limiter, c->stream));
+            CU(c, launch_adj_walls(a, g, c->storage, c->limiter, lam[cur ^ 1], corr, c->stream));
+            AdjTFinal f;
+            f.tile_seg0 = c->plan.unit_seg0 + c->plan.U;
+            f.seg_band = c->plan.seg_band;
+            f.Pm = Pm;
+            f.Pq = Pq;
+            f.Ps = Ps;
+            f.mu_in = mu[cur];
+            for (int ax = 0; ax < 3; ++ax) f.corr[ax] = corr[ax];
+            f.G = c->plan.G;
+            f.tcells = c->plan.tcells;
+            f.ty = c->plan.ty;
+            f.tz = c->plan.tz;
+            f.nty = c->plan.nty;
+            const float amp_prev = s.step > base_step ? (float)amplitude_at(c, s.step - 1) : 0.f;
+            CU(c, launch_adj_tfinal(a, f, amp_prev, mu[cur ^ 1], gQ, mtp, c->W, gt, c->stream));
+        } else {
+            CU(c, launch_adj_step(a, g, c->storage, c->limiter, c->stream));
+            CU(c, launch_adj_reduce(a, g, (float)amplitude_at(c, s.step), mu[cur ^ 1], gQ, tpart, gt, c->stream));
+        }
         if (prof) {
             float ms = 0;
             CU(c, cudaEventRecord(ev1, c->stream));
@@ -1048,6 +1090,7 @@ extern "C" bte_status bte_adjoint(bte_ctx *c, int nsteps, int ckpt_every, const 
     bte_status st = BTE_OK;
     auto run = [&]() -> bte_status {
         // forward sweep, keeping the segment checkpoints
+        base_step = c->step;
         for (int s = 0; s < nseg; ++s) {
             TRY(snap_save(c, L1[s], w.ediff_bytes));
             TRY(timed_steps(std::min(K, nsteps - s * K)));
@@ -1067,7 +1110,10 @@ extern "C" bte_status bte_adjoint(bte_ctx *c, int nsteps, int ckpt_every, const 
             g.lam_in = nullptr;
             g.mu_in = nullptr;
             CU(c, launch_adj_init(a, g, c->storage, pr, c->stream));
-            CU(c, launch_adj_reduce(a, g, 0.f, mu[cur], gQ, tpart, gt, c->stream));
+            // the tiled path takes dJ/dQ of step N-1 from q^N here; the generic step kernel
+            // takes it from lambda^{n+1} itself
+            const float amp_last = tiled_adj && nsteps > 0 ? (float)amplitude_at(c, c->step - 1) : 0.f;
+            CU(c, launch_adj_reduce(a, g, amp_last, mu[cur], gQ, tpart, gt, c->stream));
         }
         // reverse sweep, segment by segment
         for (int s = nseg - 1; s >= 0; --s) {

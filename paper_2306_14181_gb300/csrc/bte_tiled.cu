@@ -274,6 +274,18 @@ bool tiled_plan(int dim, const int n[3], int nb, int nd, int storage, int limite
 
 bool tiled_setup(TiledPlan &plan, const StepArgs &a, std::string &why) {
     if (!upload_vec(&plan.unit_seg0, plan.h_unit_seg0, why)) return false;
+    // band of every segment row (the adjoint's per-band sums)
+    {
+        std::vector<int> sb(std::max(1, plan.G), 0);
+        for (int u = 0; u < plan.U; ++u) {
+            const int j = u / plan.ntiles;
+            const long long p0 = (long long)j * plan.np / plan.J, p1 = (long long)(j + 1) * plan.np / plan.J;
+            if (p1 <= p0) continue;
+            const int b0 = (int)(p0 / a.nd), b1 = (int)((p1 - 1) / a.nd);
+            for (int k = b0; k <= b1; ++k) sb[plan.h_unit_seg0[u] + k - b0] = k;
+        }
+        if (!upload_vec(&plan.seg_band, sb, why)) return false;
+    }
     const size_t npw = std::max<size_t>(1, (size_t)plan.G * plan.nwd * plan.tw);
     if (cudaMalloc((void **)&plan.PW, npw * sizeof(float)) != cudaSuccess ||
         cudaMemset(plan.PW, 0, npw * sizeof(float)) != cudaSuccess ||
@@ -301,17 +313,18 @@ bool tiled_setup(TiledPlan &plan, const StepArgs &a, std::string &why) {
 }
 
 void tiled_free(TiledPlan &plan) {
-    void *ptrs[] = {plan.unit_seg0, plan.PW, plan.err, plan.hdr, plan.isorow};
+    void *ptrs[] = {plan.unit_seg0, plan.seg_band, plan.PW, plan.err, plan.hdr, plan.isorow};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     plan.unit_seg0 = nullptr;
+    plan.seg_band = nullptr;
     plan.isorow = nullptr;
     plan.PW = nullptr;
     plan.err = nullptr;
     plan.hdr = nullptr;
 }
 
-static TiledArgs device_args(const TiledPlan &plan) {
+TiledArgs tiled_device_args(const TiledPlan &plan) {
     TiledArgs t;
     memset(&t, 0, sizeof t);
     t.unit_seg0 = plan.unit_seg0;
@@ -347,7 +360,7 @@ static TiledArgs device_args(const TiledPlan &plan) {
 
 cudaError_t launch_step_tiled(const StepArgs &a, const TiledPlan &plan, cudaStream_t s) {
     StepKernel kf = (StepKernel)plan.kernel;
-    kf<<<plan.nctas, plan.threads, plan.smem, s>>>(a, device_args(plan));
+    kf<<<plan.nctas, plan.threads, plan.smem, s>>>(a, tiled_device_args(plan));
     return cudaGetLastError();
 }
 
@@ -359,7 +372,7 @@ static bool tiled_wall_pass(const TiledPlan &plan, const int bc[6], int w) {
 
 cudaError_t launch_finalize_tiled(const StepArgs &a, const TiledPlan &plan, int storage, float *TL_out,
                                   cudaStream_t s) {
-    const TiledArgs t = device_args(plan);
+    const TiledArgs t = tiled_device_args(plan);
     const unsigned nblk = (unsigned)((a.ncell + 255) / 256);
     k_finalize_tiled<<<nblk, 256, 0, s>>>(a, t, TL_out);
     // every wall that needs ghost values in one launch (z: the wall), x covering its cells

@@ -50,6 +50,7 @@ struct TiledPlan {
     int U = 0, J = 0, np = 0;
     std::vector<int> h_unit_seg0;
     int *unit_seg0 = nullptr;
+    int *seg_band = nullptr;  // [G] band of each segment row
     float *PW = nullptr;
     float *hdr = nullptr;
     void *isorow = nullptr;
@@ -65,6 +66,7 @@ bool tiled_plan(int dim, const int n[3], int nb, int nd, int storage, int limite
 // constant records the producer copies into each stage (built from the step tables in a).
 bool tiled_setup(TiledPlan &plan, const StepArgs &a, std::string &why);
 void tiled_free(TiledPlan &plan);
+TiledArgs tiled_device_args(const TiledPlan &plan);
 cudaError_t launch_step_tiled(const StepArgs &a, const TiledPlan &plan, cudaStream_t s);
 cudaError_t launch_finalize_tiled(const StepArgs &a, const TiledPlan &plan, int storage, float *TL_out,
                                   cudaStream_t s);
