@@ -157,6 +157,7 @@ __device__ __forceinline__ void adj_rows(const StepArgs &a, const AdjTiledArgs &
     const float bm = b.dtinv * b.ck, bq = b.srck;
     const T *e = static_cast<const T *>(a.e_in);
     const float *lam = g.lam_in;
+    constexpr int kR = Geo<DIM, WPR>::KR;
     const int nrows = min(kR, q.nyt - rb);
     const int z = q.z0 + zl;
     // streaming order along y: t = 0 .. nrows-1 are this warp's rows, upwind to downwind
@@ -354,7 +355,7 @@ __global__ void __launch_bounds__(Geo<DIM, WPR>::NCW * 32, 1) k_adj_tiled(const 
     auto flush = [&]() {
         float *Pm = g.Pm + (size_t)seg * p.tcells, *Pq = g.Pq + (size_t)seg * p.tcells;
         #pragma unroll
-        for (int r = 0; r < kR; ++r) {
+        for (int r = 0; r < Geo<DIM, WPR>::KR; ++r) {
             const int yl = rb + r;
             const int c = (zl * TY + yl) * NX + x0;
             if (yl < cur.nyt && zl < cur.nzt) {

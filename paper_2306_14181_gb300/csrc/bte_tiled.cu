@@ -174,7 +174,7 @@ bool tiled_plan(int dim, const int n[3], int nb, int nd, int storage, int limite
     const int wpr = nx == 256 ? 2 : 1;
     const int ncw = dim == 2 ? Geo<2, 1>::NCW : Geo<3, 1>::NCW;
     const int TZ = dim == 2 ? Geo<2, 1>::TZ : Geo<3, 1>::TZ;
-    const int TY = ncw / (TZ * wpr) * kR;
+    const int TY = dim == 3 ? Geo<3, 1>::TY : (wpr == 2 ? Geo<2, 2>::TY : Geo<2, 1>::TY);
     plan.vx = nx / 32;
     plan.dim = dim;
     plan.storage = storage;

@@ -10,20 +10,20 @@
 namespace bte {
 namespace tiled {
 
-constexpr int kR = 4;                                 // rows streamed by one warp
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
 constexpr int kHdrFloats = 16;                        // per-plane constants written by the producer
 
 // Tile geometry: a lane holds VL consecutive cells of a row, WPR warps cover a row of
-// nx = 32 VL WPR cells; NCW consumer warps stream kR rows each; 2-D tiles are TY rows, 3-D
-// tiles TY rows by TZ slices.  2-D CTAs run 16 consumer warps (96 registers a thread), 3-D
-// ones 12 (128 registers; the z-stencil needs more live values).
+// nx = 32 VL WPR cells; NCW consumer warps stream KR rows each; 2-D tiles are TY rows, 3-D
+// tiles TY rows by TZ slices.  2-D CTAs run 16 consumer warps of 4 rows (96 registers a
+// thread; 8 warps of 8 rows, with 224 registers, measured 35% slower: too few warps to hide
+// latency), 3-D ones 12 warps of 4 rows (128; the z-stencil needs more live values).
 template <int DIM, int WPR> struct Geo;
 template <int WPR> struct Geo<2, WPR> {
-    static constexpr int NCW = 16, TZ = 1, TY = NCW / WPR * kR;
+    static constexpr int NCW = 16, KR = 4, TZ = 1, TY = NCW / WPR * KR;
 };
 template <> struct Geo<3, 1> {
-    static constexpr int NCW = 12, TZ = 6, TY = NCW / TZ * kR;
+    static constexpr int NCW = 12, KR = 4, TZ = 6, TY = NCW / TZ * KR;
 };
 
 // Storage codecs.  FP32 storage keeps e.  16-bit storage keeps h = round(e / s_k - rho_i) with
@@ -493,6 +493,7 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
     const float dtinv = hd[4], sc = hd[5];
     const float any = fabsf(nuy), anz = fabsf(nuz);
     const int sy = nuy > 0.f ? 1 : -1, sz = nuz > 0.f ? 1 : -1;
+    constexpr int kR = Geo<DIM, WPR>::KR;
     const int nrows = min(kR, q.nyt - rb);
     const int yl0 = sy > 0 ? rb : rb + nrows - 1;  // first row in streaming (upwind-to-downwind) order
     const int ybox0 = q.y0 - (sy > 0 ? 2 : 1);
@@ -712,7 +713,7 @@ __device__ __forceinline__ void warp_place(int &zl, int &rb, int &half) {
     half = warp % WPR;
     const int u = warp / WPR;
     zl = u % Geo<DIM, WPR>::TZ;
-    rb = (u / Geo<DIM, WPR>::TZ) * kR;
+    rb = (u / Geo<DIM, WPR>::TZ) * Geo<DIM, WPR>::KR;
 }
 
 // End of a segment: this thread's moment partials to P[seg], the diffuse-wall partials of
@@ -734,7 +735,7 @@ __device__ __forceinline__ void flush_segment(const StepArgs &a, const TiledArgs
         wck = wsum * b.ck;
     }
     #pragma unroll
-    for (int r = 0; r < kR; ++r) {
+    for (int r = 0; r < Geo<DIM, WPR>::KR; ++r) {
         const int yl = rb + r;
         const int c = (zl * TY + yl) * NX + x0;
         if (yl < q.nyt && zl < q.nzt) {
@@ -821,7 +822,7 @@ __device__ void consumer(const StepArgs &a, const TiledArgs &p, char *smem, uint
             // (16-bit: in units of s_k, less the new code reference rho_new = T_L^n / T_scale)
             const BandConst b = a.band[q.k];
             #pragma unroll
-            for (int r = 0; r < kR; ++r) {
+            for (int r = 0; r < Geo<DIM, WPR>::KR; ++r) {
                 const int yl = rb + r;
                 if (yl < q.nyt && zl < q.nzt) {
                     const long long i0 = ((long long)(q.z0 + zl) * ny + (q.y0 + yl)) * NX + x0;
