@@ -32,7 +32,7 @@ METRIC = "cell·dir·band updates/s and % HBM roofline; adjoint/forward step tim
 UNIT = "cell·dir·band updates/s"
 FALLBACK_HBM_GBS = 6800.0
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
-KERNEL = {"auto": 0, "generic": 1, "tiled": 2}
+KERNEL = {"auto": 0, "generic": 1, "tiled": 2, "persistent": 3}
 
 
 def workloads():
@@ -309,7 +309,7 @@ def run_gb300(args):
                                 stream=stream.cuda_stream, T_scale=args.t_scale,
                                 rounding=1 if args.rounding == "stochastic" else 0, seed=1)
     info = ctx.info
-    kernel_name = "tiled" if info.kernel == bte.BTE_KERNEL_TILED else "generic"
+    kernel_name = {bte.BTE_KERNEL_TILED: "tiled", bte.BTE_KERNEL_PERSISTENT: "persistent"}.get(info.kernel, "generic")
     if Q is not None:
         bte.bte_set_source(ctx, torch.from_numpy(Q.reshape(-1)).cuda(), amps)
     bte.bte_step(ctx, args.warmup)
@@ -336,14 +336,22 @@ def run_gb300(args):
 
     # roofline of the forward kernel: algorithmic bytes = read e + write e per update
     peak, peak_kind = hbm_peak()
-    bytes_per_launch = info.nelem * 2 * info.elem_bytes
+    persistent = info.kernel == bte.BTE_KERNEL_PERSISTENT
+    # a persistent launch covers all the steps of its bte_step call
+    steps_per_launch = args.steps / max(nfwd, 1) if persistent else 1
+    bytes_per_launch = info.nelem * 2 * info.elem_bytes * steps_per_launch
     fwd_avg_s = fwd_ms / max(nfwd, 1) / 1e3
     achieved = bytes_per_launch / fwd_avg_s / 1e9
     traffic = measured_traffic(args.workload, args.storage, kernel_name)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "forward step (%s)" % kernel_name, "peak_source": peak_kind,
-                "bytes_per_launch": bytes_per_launch, "kernel_ms": fwd_avg_s * 1e3,
+    roofline = {"bound": "latency" if persistent else "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "forward step (%s)" % kernel_name,
+                "peak_source": peak_kind, "bytes_per_launch": bytes_per_launch, "kernel_ms": fwd_avg_s * 1e3,
                 "finalize_ms": fin_ms / max(nfin, 1)}
+    if persistent:
+        # the state stays in shared memory: report the step time, not a DRAM fraction
+        roofline["us_per_step"] = fwd_avg_s * 1e6 / steps_per_launch
+        roofline["note"] = "one single-CTA launch per bte_step call; the state never leaves shared memory"
+        roofline["finalize_ms"] = 0.0
 
     # end to end through the C ABI with host buffers: upload the step's source (pinned), step,
     # read the step's lattice temperature back
@@ -404,7 +412,7 @@ def run_gb300(args):
                        **({"rounding": args.rounding, "T_scale": args.t_scale} if args.storage != "f32" else {}),
                        "updates_per_step": info.nelem, "l2": "state %.2f GB > L2, no flush" % (info.state_bytes / 1e9),
                        "parallelism": "replicas" if d.world > 1 else "single"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(nfwd + nfin),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(nfwd if persistent else nfwd + nfin),
             "clocks": ck}
     if adjoint is not None:
         line["adjoint"] = adjoint

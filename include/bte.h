@@ -93,9 +93,13 @@ enum { BTE_ROUND_NEAREST = 0, BTE_ROUND_STOCHASTIC = 1 };
 
 /* Which forward kernel to run. */
 enum {
-    BTE_KERNEL_AUTO = 0,    /* the tiled kernel where its shape limits allow, else generic */
-    BTE_KERNEL_GENERIC = 1, /* one thread per (cell, band); any grid shape */
-    BTE_KERNEL_TILED = 2    /* shared-memory tiled kernel; BTE_EUNSUPPORTED if the grid does not fit */
+    BTE_KERNEL_AUTO = 0,       /* persistent for small 1-D FP32 problems, else tiled where its shape
+                                  limits allow, else generic */
+    BTE_KERNEL_GENERIC = 1,    /* one thread per (cell, band); any grid shape */
+    BTE_KERNEL_TILED = 2,      /* shared-memory tiled kernel; BTE_EUNSUPPORTED if the grid does not fit */
+    BTE_KERNEL_PERSISTENT = 3  /* 1-D, FP32 storage, state in one CTA's shared memory for all the steps
+                                  of a bte_step call (two block barriers a step, one launch a call);
+                                  BTE_EUNSUPPORTED otherwise */
 };
 
 typedef struct bte_ctx bte_ctx;

@@ -21,7 +21,7 @@ BTE_BC_ISOTHERMAL, BTE_BC_DIFFUSE, BTE_BC_SPECULAR, BTE_BC_PERIODIC = 0, 1, 2, 3
 BTE_STORE_F32, BTE_STORE_F16, BTE_STORE_BF16 = 0, 1, 2
 BTE_LIM_FIRST_ORDER, BTE_LIM_MINMOD, BTE_LIM_VANALBADA = 0, 1, 2
 BTE_ROUND_NEAREST, BTE_ROUND_STOCHASTIC = 0, 1
-BTE_KERNEL_AUTO, BTE_KERNEL_GENERIC, BTE_KERNEL_TILED = 0, 1, 2
+BTE_KERNEL_AUTO, BTE_KERNEL_GENERIC, BTE_KERNEL_TILED, BTE_KERNEL_PERSISTENT = 0, 1, 2, 3
 
 # every entry point include/bte.h declares
 EXPORTS = ["bte_create", "bte_destroy", "bte_last_error", "bte_init_temperature", "bte_set_source", "bte_step",

@@ -61,6 +61,10 @@ struct bte_ctx {
     // tiled-kernel plan
     TiledPlan plan;
     bool tiled = false;
+    // persistent single-CTA path (small 1-D FP32 problems): per-call source amplitudes
+    bool persist = false;
+    float *d_amp = nullptr;
+    size_t d_amp_n = 0;
     // source
     bool has_source = false, has_amp = false;
     std::vector<double> amp;
@@ -287,7 +291,7 @@ static bte_status refresh_moments(bte_ctx *c) {
 }
 
 static void free_all(bte_ctx *c) {
-    void *ptrs[] = {c->wf, c->e[0], c->e[1], c->TL, c->R, c->Q, c->P, c->ediff[0], c->ediff[1], c->nu, c->wmom, c->wdiff,
+    void *ptrs[] = {c->d_amp, c->wf, c->e[0], c->e[1], c->TL, c->R, c->Q, c->P, c->ediff[0], c->ediff[1], c->nu, c->wmom, c->wdiff,
                     c->iso, c->mirror_d, c->band, c->d_w, c->d_s, c->d_v, c->d_invtau, c->dg, c->dflag};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -377,7 +381,7 @@ extern "C" bte_status bte_create(const bte_grid *grid, const bte_bands *bands, c
     if (opts->storage < BTE_STORE_F32 || opts->storage > BTE_STORE_BF16) return fail(nullptr, BTE_EINVAL, "bad storage");
     if (opts->limiter < BTE_LIM_FIRST_ORDER || opts->limiter > BTE_LIM_VANALBADA)
         return fail(nullptr, BTE_EINVAL, "bad limiter");
-    if (opts->kernel < BTE_KERNEL_AUTO || opts->kernel > BTE_KERNEL_TILED) return fail(nullptr, BTE_EINVAL, "bad kernel");
+    if (opts->kernel < BTE_KERNEL_AUTO || opts->kernel > BTE_KERNEL_PERSISTENT) return fail(nullptr, BTE_EINVAL, "bad kernel");
     if (opts->rounding != BTE_ROUND_NEAREST && opts->rounding != BTE_ROUND_STOCHASTIC)
         return fail(nullptr, BTE_EINVAL, "bad rounding");
     c->dt = opts->dt;
@@ -419,7 +423,24 @@ extern "C" bte_status bte_create(const bte_grid *grid, const bte_bands *bands, c
     const int nplanes = c->nb * c->nd;
     // kernel plan
     c->G = c->nb;
-    if (c->kernel != BTE_KERNEL_GENERIC) {
+    {
+        // a 1-D FP32 state that fits in one CTA's shared memory runs persistent
+        const size_t np = (size_t)c->nb * c->nd;
+        const size_t ps = (2 * np * c->n[0] + c->n[0] + 2 * c->nb + 5 * np + 8 * (size_t)c->n[0]) * sizeof(float);
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+            cudaGetLastError();
+            optin = 0;
+        }
+        const bool fits = c->dim == 1 && c->storage == BTE_STORE_F32 && ps <= (size_t)optin;
+        if (c->kernel == BTE_KERNEL_PERSISTENT && !fits) {
+            c->err = "persistent kernel unavailable: it needs a 1-D FP32 state that fits in shared memory";
+            return bail(BTE_EUNSUPPORTED);
+        }
+        c->persist = fits && (c->kernel == BTE_KERNEL_AUTO || c->kernel == BTE_KERNEL_PERSISTENT);
+    }
+    if (c->kernel != BTE_KERNEL_GENERIC && !c->persist) {
         std::string why;
         c->tiled = tiled_plan(c->dim, c->n, c->nb, c->nd, c->storage, c->limiter,
                               c->rounding == BTE_ROUND_STOCHASTIC, c->bc, c->plan, why);
@@ -607,9 +628,36 @@ extern "C" bte_status bte_set_source(bte_ctx *c, const float *Q, int on_device, 
     return BTE_OK;
 }
 
+// All nsteps steps in one persistent single-CTA launch (1-D FP32 states in shared memory).
+static bte_status step_persistent(bte_ctx *c, int nsteps) {
+    if ((size_t)nsteps > c->d_amp_n) {
+        if (c->d_amp) cudaFree(c->d_amp);
+        c->d_amp = nullptr;
+        c->d_amp_n = 0;
+        CU(c, cudaMalloc((void **)&c->d_amp, (size_t)nsteps * sizeof(float)));
+        c->d_amp_n = nsteps;
+    }
+    std::vector<float> amps(nsteps);
+    for (int s = 0; s < nsteps; ++s) amps[s] = (float)amplitude_at(c, c->step + s);
+    CU(c, cudaMemcpyAsync(c->d_amp, amps.data(), nsteps * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    StepArgs a = make_args(c);
+    cudaEvent_t ev;
+    if (c->prof) TRY(prof_event(c, &ev));
+    CU(c, launch_persist_1d(a, c->limiter, nsteps, c->d_amp, static_cast<float *>(c->e[c->cur]), c->TL,
+                            static_cast<float *>(c->ediff[c->ecur]), c->stream));
+    if (c->prof) {
+        TRY(prof_event(c, &ev));
+        TRY(prof_event(c, &ev));
+    }
+    // (a copy from pageable memory has left `amps` when cudaMemcpyAsync returns)
+    c->step += nsteps;
+    return BTE_OK;
+}
+
 extern "C" bte_status bte_step(bte_ctx *c, int nsteps) {
     if (!c) return fail(nullptr, BTE_EINVAL, "ctx is NULL");
     if (nsteps < 0) return fail(c, BTE_EINVAL, "n must be >= 0");
+    if (c->persist) return nsteps > 0 ? step_persistent(c, nsteps) : BTE_OK;
     for (int s = 0; s < nsteps; ++s) {
         StepArgs a = make_args(c);
         a.amp = (float)amplitude_at(c, c->step);
@@ -808,7 +856,7 @@ extern "C" bte_status bte_get_info(const bte_ctx *c, bte_info *info) {
     info->elem_bytes = (int)c->elem_bytes;
     info->storage = c->storage;
     info->limiter = c->limiter;
-    info->kernel = c->tiled ? BTE_KERNEL_TILED : BTE_KERNEL_GENERIC;
+    info->kernel = c->persist ? BTE_KERNEL_PERSISTENT : (c->tiled ? BTE_KERNEL_TILED : BTE_KERNEL_GENERIC);
     info->dt = c->dt;
     info->W = c->W;
     info->step = c->step;

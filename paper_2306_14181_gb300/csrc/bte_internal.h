@@ -77,6 +77,12 @@ cudaError_t launch_fill(const StepArgs &a, int storage, const double *dT0, float
 cudaError_t launch_moment_only(const StepArgs &a, int storage, cudaStream_t s);
 cudaError_t launch_step_generic(const StepArgs &a, int storage, int limiter, cudaStream_t s);
 cudaError_t launch_finalize(const StepArgs &a, int G, float *TL_out, cudaStream_t s);
+// Persistent single-CTA run of nsteps steps of a 1-D FP32 problem (bte_persist.cu): e_io in
+// place, T_L and the diffuse-wall values of the final state out; amps[s] the source amplitude
+// of step s of the call.
+size_t persist_1d_smem(const StepArgs &a);
+cudaError_t launch_persist_1d(const StepArgs &a, int limiter, int nsteps, const float *amps, float *e_io,
+                              float *tl_out, float *ediff_out, cudaStream_t s);
 // Decoded state values e (FP32, [nb*nd][ncell]) of e_in into out (device).
 cudaError_t launch_decode(const StepArgs &a, int storage, float *out, cudaStream_t s);
 

@@ -25,6 +25,8 @@ def _built():
 
 CASES = [
     (1, (40, 1, 1), [ISO, DIF, PER, PER, PER, PER], 1),
+    (1, (40, 1, 1), [ISO, DIF, PER, PER, PER, PER], 3),
+    (1, (36, 1, 1), [SPE, SPE, PER, PER, PER, PER], 3),
     (1, (32, 1, 1), [SPE, ISO, PER, PER, PER, PER], 1),
     (2, (24, 17, 1), [DIF, SPE, ISO, DIF, PER, PER], 1),
     (2, (96, 13, 1), [SPE, SPE, ISO, DIF, PER, PER], 2),
