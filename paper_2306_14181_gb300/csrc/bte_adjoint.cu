@@ -17,6 +17,8 @@
 // direction's cells (gathered from that plane's faces next to the wall); diffuse incoming ->
 // spread back over the wall cell's outgoing directions with weights w (s.n) / sum_in w|s.n|.
 // One thread per (cell, band) loops over the band's directions, as the generic forward does.
+#include <algorithm>
+
 #include "bte_device.cuh"
 #include "bte_adjoint.h"
 
@@ -291,20 +293,19 @@ int adj_tau_blocks(long long ncell) { return (int)((ncell + kTauPerBlock - 1) / 
 // ------------------------------------------------------------------------------------------
 __device__ __forceinline__ int wall_slot(int pos, int n) { return pos < 2 ? pos : 2 + pos - (n - 2); }
 
-constexpr int kWallThreads = 64, kWallMaxDirs = 256;
-int adj_walls_max_dirs() { return kWallMaxDirs; }
+// Phase 1: one thread per (line, direction, band), threads along the lines (coalesced for y and
+// z walls).  scratch[((k nd + d) 8 + 4 side + j) nlines + line], j = 0, 1: additions to the
+// wall cell and the next cell of the same plane; j = 2, 3: adjoints of ghost layers 1 and 2.
+constexpr int kWallThreads = 128;
 
 template <int S, int LIM>
-__global__ void __launch_bounds__(kWallThreads) k_adj_walls(const StepArgs a, const AdjArgs g, int ax, float *lam_out,
-                                                            float *corr, long long nlines) {
+__global__ void __launch_bounds__(kWallThreads) k_adj_walls_a(const StepArgs a, const AdjArgs g, int ax,
+                                                              float *scratch, long long nlines) {
     using Cd = Codec<S>;
     using T = typename Cd::T;
-    // per direction and side: own-plane additions to the wall cell (layer 0) and the next cell
-    // (layer 1), and the adjoints of ghost layers 1 and 2
-    __shared__ float own[2][2][kWallMaxDirs], gh1[2][kWallMaxDirs], gh2[2][kWallMaxDirs], tot[4][kWallMaxDirs];
-    __shared__ float gam[2];
-    const long long line = blockIdx.x;
-    const int k = blockIdx.y;
+    const long long line = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (line >= nlines) return;
+    const int d = blockIdx.y, k = blockIdx.z;
     const int n = a.n[ax];
     int c[3];
     {
@@ -318,16 +319,15 @@ __global__ void __launch_bounds__(kWallThreads) k_adj_walls(const StepArgs a, co
     const BandConst b = a.band[k];
     const T *e = static_cast<const T *>(a.e_in);
     const float *lam = g.lam_in;
-    // phase 1: every direction's faces next to the two walls
-    for (int d = threadIdx.x; d < a.nd; d += blockDim.x) {
-        const int plane = k * a.nd + d;
-        const float nu = a.nu[3 * plane + ax];
-        const int sg = nu > 0.f ? 1 : -1;
-        const float anu = fabsf(nu);
-        const long long base = (long long)plane * a.ncell;
-        for (int side = 0; side < 2; ++side) {
-            own[side][0][d] = own[side][1][d] = gh1[side][d] = gh2[side][d] = 0.f;
-            if (a.bc[2 * ax + side] == kBcPeriodic || nu == 0.f) continue;
+    const int plane = k * a.nd + d;
+    const float nu = a.nu[3 * plane + ax];
+    const int sg = nu > 0.f ? 1 : -1;
+    const float anu = fabsf(nu);
+    const long long base = (long long)plane * a.ncell;
+    float *out = scratch + (long long)plane * 8 * nlines + line;
+    for (int side = 0; side < 2; ++side) {
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        if (a.bc[2 * ax + side] != kBcPeriodic && nu != 0.f) {
             const int w0 = side ? n - 1 : 0, in = side ? -1 : 1;
             int cw[3] = {c[0], c[1], c[2]};
             cw[ax] = w0;
@@ -339,73 +339,101 @@ __global__ void __launch_bounds__(kWallThreads) k_adj_walls(const StepArgs a, co
                 face_grad<Cd, LIM>(a, e, b, k, d, base, iw, cw, ax, w0, sg, nu, gb);
                 const float l0 = lam_at(a, lam, base, iw, cw, ax, w0), l1 = lam_at(a, lam, base, iw, cw, ax, w0 + sg);
                 const float pa = anu * l0, pb = anu * (l1 - l0);
-                own[side][0][d] = pa * ga[2] + pb * gb[1];
-                own[side][1][d] = pb * gb[2];
-                gh1[side][d] = pa * ga[1] + pb * gb[0];
-                gh2[side][d] = pa * ga[0];
+                v[0] = pa * ga[2] + pb * gb[1];
+                v[1] = pb * gb[2];
+                v[2] = pa * ga[1] + pb * gb[0];
+                v[3] = pa * ga[0];
             } else {
                 // leaving through this wall: last cell w0, face F_{w0} reads ghost layer 1
                 float gc[3];
                 face_grad<Cd, LIM>(a, e, b, k, d, base, iw, cw, ax, w0, sg, nu, gc);
                 const float ph = -anu * lam_at(a, lam, base, iw, cw, ax, w0);
-                own[side][1][d] = ph * gc[0];
-                own[side][0][d] = ph * gc[1];
-                gh1[side][d] = ph * gc[2];
+                v[1] = ph * gc[0];
+                v[0] = ph * gc[1];
+                v[2] = ph * gc[2];
             }
         }
+        #pragma unroll
+        for (int j = 0; j < 4; ++j) out[(long long)(4 * side + j) * nlines] = v[j];
     }
+}
+
+// Phase 2: one block per (line, band), threads over the directions: the ghost transposes
+// (specular: the mirrored direction's ghost adjoints; thermalizing or diffuse outgoing: the
+// direction's own; diffuse incoming: summed over the entering directions, in order, and spread
+// over the leaving ones), each direction's additions written to lambda^n by its own thread,
+// and the per-position sums over the directions, in order, to corr.  Dynamic shared memory:
+// 8 nd floats.
+__global__ void __launch_bounds__(kWallThreads) k_adj_walls_b(const StepArgs a, int ax, const float *scratch,
+                                                              float *lam_out, float *corr, long long nlines) {
+    extern __shared__ float wsh[];
+    const int nd = a.nd;
+    float *gh = wsh;            // [side][layer][d]: ghost adjoints
+    float *tot = wsh + 4 * nd;  // [slot][d]
+    __shared__ float gam[2];
+    const long long line = blockIdx.x;
+    const int k = blockIdx.y;
+    const int n = a.n[ax];
+    int c[3];
+    {
+        const int o1 = ax == 0 ? 1 : 0, o2 = ax == 2 ? 1 : 2;
+        c[ax] = 0;
+        c[o1] = (int)(line % a.n[o1]);
+        c[o2] = (int)(line / a.n[o1]);
+    }
+    const long long i0 = ((long long)c[2] * a.n[1] + c[1]) * a.n[0] + c[0];
+    const long long st = a.stride[ax];
+    auto sc = [&](int d, int j) { return scratch[((long long)(k * nd + d) * 8 + j) * nlines + line]; };
+    for (int d = threadIdx.x; d < nd; d += blockDim.x)
+        for (int side = 0; side < 2; ++side) {
+            gh[(2 * side) * nd + d] = sc(d, 4 * side + 2);
+            gh[(2 * side + 1) * nd + d] = sc(d, 4 * side + 3);
+        }
     __syncthreads();
-    // diffuse walls: the incoming directions' ghost adjoints, summed in direction order
     if (threadIdx.x < 2) {
-        const int side = threadIdx.x, wall = 2 * ax + side;
-        float s = 0.f;
-        if (a.bc[wall] == kBcDiffuse)
-            for (int d = 0; d < a.nd; ++d) {
-                const float nu = a.nu[3 * (k * a.nd + d) + ax];
-                if (side == 0 ? nu > 0.f : nu < 0.f) s += gh1[side][d] + gh2[side][d];
+        const int side = threadIdx.x, in = side ? -1 : 1;
+        float sum = 0.f;
+        if (a.bc[2 * ax + side] == kBcDiffuse)
+            for (int d = 0; d < nd; ++d) {
+                const float nu = a.nu[3 * (k * nd + d) + ax];
+                if (nu != 0.f && (nu > 0.f ? 1 : -1) == in) sum += gh[(2 * side) * nd + d] + gh[(2 * side + 1) * nd + d];
             }
-        gam[side] = s;
+        gam[side] = sum;
     }
     __syncthreads();
-    // phase 2: each direction's total at positions 0, 1, n-2, n-1 of the line, the ghost
-    // transposes included; one thread per direction writes its plane, so every element has
-    // a single writer
-    for (int d = threadIdx.x; d < a.nd; d += blockDim.x) {
-        const int plane = k * a.nd + d;
-        const float nu = a.nu[3 * plane + ax];
-        float dv[4] = {0.f, 0.f, 0.f, 0.f};  // by wall_slot
+    for (int d = threadIdx.x; d < nd; d += blockDim.x) {
+        const float nu = a.nu[3 * (k * nd + d) + ax];
+        float dv[4] = {0.f, 0.f, 0.f, 0.f};
         for (int side = 0; side < 2; ++side) {
             const int wall = 2 * ax + side, bc = a.bc[wall];
             if (bc == kBcPeriodic) continue;
             const int w0 = side ? n - 1 : 0, in = side ? -1 : 1;
-            float v0 = own[side][0][d], v1 = own[side][1][d];
+            float v0 = sc(d, 4 * side), v1 = sc(d, 4 * side + 1);
             const bool leaving = nu != 0.f && (nu > 0.f ? 1 : -1) != in;
             if (bc == kBcSpecular) {
-                // this plane's cells are the mirrored direction's ghosts
-                const int dm = a.mirror[ax * a.nd + d];
-                v0 += gh1[side][dm];
-                v1 += gh2[side][dm];
+                const int dm = a.mirror[ax * nd + d];
+                v0 += gh[(2 * side) * nd + dm];
+                v1 += gh[(2 * side + 1) * nd + dm];
             } else if (leaving) {
-                v0 += gh1[side][d];  // the outgoing ghost is the wall cell itself
+                v0 += gh[(2 * side) * nd + d];
             }
-            if (bc == kBcDiffuse) v0 = fmaf(a.wdiff[wall * a.nd + d] * a.inv_den[wall], gam[side], v0);
+            if (bc == kBcDiffuse) v0 = fmaf(a.wdiff[wall * nd + d] * a.inv_den[wall], gam[side], v0);
             dv[wall_slot(w0, n)] += v0;
             dv[wall_slot(w0 + in, n)] += v1;
         }
-        const long long pb = (long long)plane * a.ncell + i0;
+        const long long pb = (long long)(k * nd + d) * a.ncell + i0;
         #pragma unroll
         for (int sl = 0; sl < 4; ++sl) {
-            tot[sl][d] = dv[sl];
+            tot[sl * nd + d] = dv[sl];
             const int pos = sl < 2 ? sl : n - 2 + (sl - 2);
             if (dv[sl] != 0.f && (sl < 2 || pos >= 2)) lam_out[pb + (long long)pos * st] += dv[sl];
         }
     }
     __syncthreads();
-    // per-position sums over the directions, in order, for the finalize
     if (threadIdx.x < 4) {
-        float sacc = 0.f;
-        for (int d = 0; d < a.nd; ++d) sacc += tot[threadIdx.x][d];
-        corr[((long long)k * 4 + threadIdx.x) * nlines + line] = sacc;
+        float sum = 0.f;
+        for (int d = 0; d < nd; ++d) sum += tot[threadIdx.x * nd + d];
+        corr[((long long)k * 4 + threadIdx.x) * nlines + line] = sum;
     }
 }
 
@@ -456,30 +484,41 @@ __global__ void __launch_bounds__(256) k_adj_tfinal(const StepArgs a, AdjTFinal 
 }
 
 // dJ/dlog tau_k += sum over band k's segments of (-dt/tau_k Ps0 - Ps1/(tau_k D))
-//                 + C_k/(tau_k D) sum_i mu^{n+1}_i T_L,i^n, all in a fixed order.
-__global__ void k_adj_ttau(const StepArgs a, AdjTFinal f, const double *mt_part, int nmt, double W, double *gtau) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= a.nb) return;
+//                 + C_k/(tau_k D) sum_i mu^{n+1}_i T_L,i^n: one block per band, each thread a fixed
+// strided subset, then a fixed-order tree.
+constexpr int kTauThreads = 256;
+__global__ void __launch_bounds__(kTauThreads) k_adj_ttau(const StepArgs a, AdjTFinal f, const double *mt_part, int nmt,
+                                                          double W, double *gtau) {
+    __shared__ double sh[2][kTauThreads];
+    const int k = blockIdx.x;
     const BandConst b = a.band[k];
-    double mt = 0.0;
-    for (int j = 0; j < nmt; ++j) mt += mt_part[j];
-    double s = 0.0;
-    for (int g = 0; g < f.G; ++g) {
-        if (f.seg_band[g] != k) continue;
-        s += -(double)b.dtinv * (double)f.Ps[2 * g] - (double)f.Ps[2 * g + 1] * (double)b.wtau * (double)a.invD;
+    double s = 0.0, mt = 0.0;
+    for (int g = threadIdx.x; g < f.G; g += kTauThreads)
+        if (f.seg_band[g] == k)
+            s += -(double)b.dtinv * (double)f.Ps[2 * g] - (double)f.Ps[2 * g + 1] * (double)b.wtau * (double)a.invD;
+    for (int j = threadIdx.x; j < nmt; j += kTauThreads) mt += mt_part[j];
+    sh[0][threadIdx.x] = s;
+    sh[1][threadIdx.x] = mt;
+    __syncthreads();
+    for (int h = kTauThreads / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + h];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + h];
+        }
+        __syncthreads();
     }
-    s += (double)b.ck * W * (double)b.wtau * (double)a.invD * mt;
-    gtau[k] += s;
+    if (threadIdx.x == 0) gtau[k] += sh[0][0] + (double)b.ck * W * (double)b.wtau * (double)a.invD * sh[1][0];
 }
 
 cudaError_t launch_adj_walls(const StepArgs &a, const AdjArgs &g, int storage, int limiter, float *lam_out,
-                             float *const corr[3], cudaStream_t s) {
+                             float *const corr[3], float *scratch, cudaStream_t s) {
     for (int ax = 0; ax < a.dim; ++ax) {
         if (a.bc[2 * ax] == kBcPeriodic) continue;
         const int o1 = ax == 0 ? 1 : 0, o2 = ax == 2 ? 1 : 2;
         const long long nl = (long long)a.n[o1] * a.n[o2];
-        const dim3 grid((unsigned)nl, (unsigned)a.nb);
-#define BTE_ADJW(SS, LL) k_adj_walls<SS, LL><<<grid, kWallThreads, 0, s>>>(a, g, ax, lam_out, corr[ax], nl)
+        const unsigned nbl = (unsigned)((nl + kWallThreads - 1) / kWallThreads);
+        const dim3 ga(nbl, (unsigned)a.nd, (unsigned)a.nb), gb((unsigned)nl, (unsigned)a.nb);
+#define BTE_ADJW(SS, LL) k_adj_walls_a<SS, LL><<<ga, kWallThreads, 0, s>>>(a, g, ax, scratch, nl)
         if (storage == kStoreF32) {
             if (limiter == kLimFirst) BTE_ADJW(kStoreF32, kLimFirst);
             else if (limiter == kLimMinmod) BTE_ADJW(kStoreF32, kLimMinmod);
@@ -494,15 +533,29 @@ cudaError_t launch_adj_walls(const StepArgs &a, const AdjArgs &g, int storage, i
             else BTE_ADJW(kStoreBF16, kLimVanAlbada);
         }
 #undef BTE_ADJW
+        const int tb = std::min(kWallThreads, (a.nd + 31) / 32 * 32);  // no idle warp for nd < 128
+        k_adj_walls_b<<<gb, tb, (size_t)8 * a.nd * sizeof(float), s>>>(a, ax, scratch, lam_out, corr[ax], nl);
     }
     return cudaGetLastError();
+}
+
+int adj_walls_max_dirs() { return 6144; }  // 8 nd floats of dynamic shared memory <= 192 KB
+
+long long adj_walls_scratch_floats(const StepArgs &a) {
+    long long m = 0;
+    for (int ax = 0; ax < a.dim; ++ax) {
+        if (a.bc[2 * ax] == kBcPeriodic) continue;
+        const int o1 = ax == 0 ? 1 : 0, o2 = ax == 2 ? 1 : 2;
+        m = std::max(m, (long long)a.n[o1] * a.n[o2]);
+    }
+    return m * 8 * (long long)a.nb * a.nd;
 }
 
 cudaError_t launch_adj_tfinal(const StepArgs &a, const AdjTFinal &f, float amp, float *mu_out, double *gQ,
                               double *mt_part, double W, double *gtau, cudaStream_t s) {
     const int nblk = (int)((a.ncell + 255) / 256);
     k_adj_tfinal<<<nblk, 256, 0, s>>>(a, f, amp, mu_out, gQ, mt_part);
-    k_adj_ttau<<<(a.nb + 63) / 64, 64, 0, s>>>(a, f, mt_part, nblk, W, gtau);
+    k_adj_ttau<<<a.nb, kTauThreads, 0, s>>>(a, f, mt_part, nblk, W, gtau);
     return cudaGetLastError();
 }
 

@@ -26,7 +26,6 @@ cudaError_t launch_adj_init(const StepArgs &a, const AdjArgs &g, int storage, co
 cudaError_t launch_adj_reduce(const StepArgs &a, const AdjArgs &g, float amp, float *mu_out, double *gQ,
                               double *tau_part, double *gtau, cudaStream_t s);
 int adj_tau_blocks(long long ncell);
-int adj_walls_max_dirs();  // directions the tiled adjoint's wall pass handles
 
 // Tiled adjoint (bte_adjoint_tiled*.cu): segment partials and their finalize.
 struct AdjTFinal {
@@ -38,9 +37,12 @@ struct AdjTFinal {
     const float *corr[3];  // wall corrections per axis [nb][4][lines]
     int G, tcells, ty, tz, nty;
 };
-// Wall pass along every non-periodic axis (one launch per axis; corr[ax]: nb * 4 * lines floats).
+// Wall pass along every non-periodic axis (two launches per axis; corr[ax]: nb * 4 * lines
+// floats; scratch: adj_walls_scratch_floats(a) floats).
 cudaError_t launch_adj_walls(const StepArgs &a, const AdjArgs &g, int storage, int limiter, float *lam_out,
-                             float *const corr[3], cudaStream_t s);
+                             float *const corr[3], float *scratch, cudaStream_t s);
+long long adj_walls_scratch_floats(const StepArgs &a);
+int adj_walls_max_dirs();  // directions the wall pass's combine phase holds in shared memory
 // mu^n, dJ/dQ += amp q^n, dJ/dlog tau from the segment scalars (mt_part: ceil(ncell/256) doubles).
 // The tiled adjoint step on the forward plan's tiles and schedule: lambda^n (interior and
 // periodic faces), segment rows Pm, Pq ([G][tcells]) and Ps ([G][2]).

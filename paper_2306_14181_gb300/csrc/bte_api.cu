@@ -1036,12 +1036,14 @@ extern "C" bte_status bte_adjoint(bte_ctx *c, int nsteps, int ckpt_every, const 
     float *Pm = nullptr, *Pq = nullptr, *Ps = nullptr, *corr[3] = {nullptr, nullptr, nullptr};
     double *mtp = nullptr;
     const bool tiled_adj = c->tiled && c->nd <= adj_walls_max_dirs();
+    float *wscr = nullptr;
     if (tiled_adj) {
         const size_t gt_rows = (size_t)std::max(1, c->plan.G);
         if (!w.alloc((void **)&Pm, gt_rows * c->plan.tcells * sizeof(float)) ||
             !w.alloc((void **)&Pq, gt_rows * c->plan.tcells * sizeof(float)) ||
             !w.alloc((void **)&Ps, 2 * gt_rows * sizeof(float)) ||
-            !w.alloc((void **)&mtp, (size_t)((nc + 255) / 256) * sizeof(double)))
+            !w.alloc((void **)&mtp, (size_t)((nc + 255) / 256) * sizeof(double)) ||
+            !w.alloc((void **)&wscr, (size_t)std::max(1LL, adj_walls_scratch_floats(make_args(c))) * sizeof(float)))
             return fail(c, BTE_ENOMEM, "adjoint buffers do not fit in device memory");
         for (int ax = 0; ax < c->dim; ++ax) {
             if (c->bc[2 * ax] == BTE_BC_PERIODIC) continue;
@@ -1104,7 +1106,7 @@ extern "C" bte_status bte_adjoint(bte_ctx *c, int nsteps, int ckpt_every, const 
             // mu^n, dJ/dQ (the q^n of lambda^n with the amplitude of step n-1) and dJ/dlog tau
             CU(c, launch_adj_tiled(a, c->plan, lam[cur], lam[cur ^ 1], mu[cur], Pm, Pq, Ps, c->wf, c->storage,
                                    c->limiter, c->stream));
-            CU(c, launch_adj_walls(a, g, c->storage, c->limiter, lam[cur ^ 1], corr, c->stream));
+            CU(c, launch_adj_walls(a, g, c->storage, c->limiter, lam[cur ^ 1], corr, wscr, c->stream));
             AdjTFinal f;
             f.tile_seg0 = c->plan.unit_seg0 + c->plan.U;
             f.seg_band = c->plan.seg_band;
