@@ -178,10 +178,11 @@ def hbm_peak():
 
 
 def kernel_source_hash():
+    """Hash of the tiled forward kernel's sources (the kernel the traffic figure describes)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2306_14181_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
+        if (name.startswith("bte_tiled") and name.endswith((".cu", ".cuh", ".h"))) or name == "bte_internal.h":
             h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()[:12]
 

@@ -309,8 +309,21 @@ __device__ __forceinline__ void adj_rows(const StepArgs &a, const AdjTiledArgs &
             const float ev = sc * e_0[j];
             s1 = fmaf(lv, fmaf(b.ck, tl[j], -ev), s1);
             s2 = fmaf(wd * mu[j], ev, s2);
-            accm[c + j] = fmaf(bm, out[j], accm[c + j]);
-            accq[c + j] = fmaf(bq, out[j], accq[c + j]);
+        }
+        // per-cell partials (four contiguous floats per lane move as one 16-byte access, free
+        // of bank conflicts)
+        if constexpr (VL == 4) {
+            float4 m = *reinterpret_cast<float4 *>(accm + c), qq = *reinterpret_cast<float4 *>(accq + c);
+            m.x = fmaf(bm, out[0], m.x); m.y = fmaf(bm, out[1], m.y); m.z = fmaf(bm, out[2], m.z); m.w = fmaf(bm, out[3], m.w);
+            qq.x = fmaf(bq, out[0], qq.x); qq.y = fmaf(bq, out[1], qq.y); qq.z = fmaf(bq, out[2], qq.z); qq.w = fmaf(bq, out[3], qq.w);
+            *reinterpret_cast<float4 *>(accm + c) = m;
+            *reinterpret_cast<float4 *>(accq + c) = qq;
+        } else {
+            #pragma unroll
+            for (int j = 0; j < VL; ++j) {
+                accm[c + j] = fmaf(bm, out[j], accm[c + j]);
+                accq[c + j] = fmaf(bq, out[j], accq[c + j]);
+            }
         }
         if constexpr (VL == 4)
             *reinterpret_cast<float4 *>(g.lam_out + base + cl) = make_float4(out[0], out[1], out[2], out[3]);
@@ -358,15 +371,24 @@ __global__ void __launch_bounds__(Geo<DIM, WPR>::NCW * 32, 1) k_adj_tiled(const 
         for (int r = 0; r < Geo<DIM, WPR>::KR; ++r) {
             const int yl = rb + r;
             const int c = (zl * TY + yl) * NX + x0;
-            if (yl < cur.nyt && zl < cur.nzt) {
-                #pragma unroll
-                for (int v = 0; v < VL; ++v) {
-                    Pm[c + v] = accm[c + v];
-                    Pq[c + v] = accq[c + v];
+            if constexpr (VL == 4) {
+                if (yl < cur.nyt && zl < cur.nzt) {
+                    *reinterpret_cast<float4 *>(Pm + c) = *reinterpret_cast<const float4 *>(accm + c);
+                    *reinterpret_cast<float4 *>(Pq + c) = *reinterpret_cast<const float4 *>(accq + c);
                 }
+                *reinterpret_cast<float4 *>(accm + c) = make_float4(0.f, 0.f, 0.f, 0.f);
+                *reinterpret_cast<float4 *>(accq + c) = make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+                if (yl < cur.nyt && zl < cur.nzt) {
+                    #pragma unroll
+                    for (int v = 0; v < VL; ++v) {
+                        Pm[c + v] = accm[c + v];
+                        Pq[c + v] = accq[c + v];
+                    }
+                }
+                #pragma unroll
+                for (int v = 0; v < VL; ++v) accm[c + v] = accq[c + v] = 0.f;
             }
-            #pragma unroll
-            for (int v = 0; v < VL; ++v) accm[c + v] = accq[c + v] = 0.f;
         }
         // segment scalars: warp sums, then warp 0 adds the warps in order
         #pragma unroll
