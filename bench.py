@@ -287,6 +287,20 @@ def run_reference(args):
     d.close()
 
 
+def l2_note(info):
+    """How the timed steps relate to L2: each step reads one state copy and writes the other."""
+    import torch
+    from paper_2306_14181_gb300 import bte
+    l2 = getattr(torch.cuda.get_device_properties(torch.cuda.current_device()), "L2_cache_size", 0) or (126 << 20)
+    ws = 2 * info.state_bytes
+    if info.kernel == bte.BTE_KERNEL_PERSISTENT:
+        return "state held in shared memory for the whole call; no DRAM traffic to flush"
+    if ws > l2:
+        return "step reads %.2f GB and writes %.2f GB (> %d MB L2), no flush" % (
+            info.state_bytes / 1e9, info.state_bytes / 1e9, l2 >> 20)
+    return "step working set %.0f MB fits the %d MB L2: steps run L2-warm, no flush" % (ws / 2**20, l2 >> 20)
+
+
 def make_workload(args):
     kw = {} if args.nb is None else {"nb": args.nb}
     return workloads()[args.workload](**kw)
@@ -411,7 +425,7 @@ def run_gb300(args):
             "config": {"workload": cfg["name"], "grid": list(cfg["n"]), "bands": info.nbands, "dirs": info.ndirs,
                        "storage": args.storage, "limiter": args.limiter, "kernel": kernel_name,
                        **({"rounding": args.rounding, "T_scale": args.t_scale} if args.storage != "f32" else {}),
-                       "updates_per_step": info.nelem, "l2": "state %.2f GB > L2, no flush" % (info.state_bytes / 1e9),
+                       "updates_per_step": info.nelem, "l2": l2_note(info),
                        "parallelism": "replicas" if d.world > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(nfwd if persistent else nfwd + nfin),
             "clocks": ck}
