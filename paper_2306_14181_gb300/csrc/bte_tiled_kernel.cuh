@@ -76,8 +76,10 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
-// Limiter; the van Albada ratio uses the approximate reciprocal and a select (pairs with
-// ab <= 1e-30 get a zero slope, so a selected denominator is always a normal number).
+// Limiter.  Van Albada, L = max(ab, 0) (a + b) / (a^2 + b^2 + 1e-30): the approximate
+// reciprocal of a denominator that is always a normal number, and no compare or select (pairs
+// with ab <= 0 give a zero numerator; the 1e-30 changes L by a relative 1e-30 / (a^2 + b^2)).
+constexpr float kVaTiny = 1e-30f;
 template <int LIM> __device__ __forceinline__ float lim(float a, float b);
 template <> __device__ __forceinline__ float lim<kLimFirst>(float, float) { return 0.f; }
 template <> __device__ __forceinline__ float lim<kLimMinmod>(float a, float b) {
@@ -85,9 +87,7 @@ template <> __device__ __forceinline__ float lim<kLimMinmod>(float a, float b) {
     return a * b > 0.f ? m : 0.f;
 }
 template <> __device__ __forceinline__ float lim<kLimVanAlbada>(float a, float b) {
-    const float ab = a * b;
-    const float r = ab * (a + b) * rcp_approx(fmaf(a, a, b * b));
-    return ab > 1e-30f ? r : 0.f;
+    return fmaxf(a * b, 0.f) * (a + b) * rcp_approx(fmaf(a, a, fmaf(b, b, kVaTiny)));
 }
 // face value e_m + L(e_m - e_l, e_r - e_m) / 2 at the upwind cell m
 template <int LIM> __device__ __forceinline__ float face(float ul, float um, float ur) {
@@ -95,25 +95,25 @@ template <int LIM> __device__ __forceinline__ float face(float ul, float um, flo
 }
 
 // The same for two independent faces with the packed FP32x2 instructions of sm_100+ (each
-// lane-pair operation rounds exactly like the scalar one).
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+// lane-pair operation rounds exactly like the scalar one).  a - b as one fused a + (-1) b,
+// which rounds once, like a subtraction.
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.f), a); }
 
 template <int LIM> __device__ __forceinline__ float2 face2(float2 ul, float2 um, float2 ur);
 template <> __device__ __forceinline__ float2 face2<kLimFirst>(float2, float2 um, float2) { return um; }
 template <> __device__ __forceinline__ float2 face2<kLimMinmod>(float2 ul, float2 um, float2 ur) {
     const float2 a = sub2(um, ul), b = sub2(ur, um);
     const float2 L = make_float2(lim<kLimMinmod>(a.x, b.x), lim<kLimMinmod>(a.y, b.y));
-    return __ffma2_rn(make_float2(0.5f, 0.5f), L, um);
+    return __ffma2_rn(f2(0.5f), L, um);
 }
 template <> __device__ __forceinline__ float2 face2<kLimVanAlbada>(float2 ul, float2 um, float2 ur) {
     const float2 a = sub2(um, ul), b = sub2(ur, um);
     const float2 ab = __fmul2_rn(a, b);
-    const float2 num = __fmul2_rn(ab, __fadd2_rn(a, b));
-    const float2 den = __ffma2_rn(a, a, __fmul2_rn(b, b));
-    float2 L = __fmul2_rn(num, make_float2(rcp_approx(den.x), rcp_approx(den.y)));
-    L.x = ab.x > 1e-30f ? L.x : 0.f;
-    L.y = ab.y > 1e-30f ? L.y : 0.f;
-    return __ffma2_rn(make_float2(0.5f, 0.5f), L, um);
+    const float2 num = __fmul2_rn(make_float2(fmaxf(ab.x, 0.f), fmaxf(ab.y, 0.f)), __fadd2_rn(a, b));
+    const float2 den = __ffma2_rn(a, a, __ffma2_rn(b, b, f2(kVaTiny)));
+    const float2 L = __fmul2_rn(num, make_float2(rcp_approx(den.x), rcp_approx(den.y)));
+    return __ffma2_rn(f2(0.5f), L, um);
 }
 
 // out[i] = face(ul[i], um[i], ur[i]) for i < N, two at a time
@@ -561,9 +561,16 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
             rx1 = (sd == 0 ? 0 : NX - SD::V) + gi1;
         } else if (leaving) {
             gmode = kGhOwn;
+            // FP32: read the lane's own end cell from the box row (same value, no select)
+            if constexpr (!REF) gi0 = gi1 = sd == 0 ? 0 : VL - 1;
         } else if (bc == kBcIsothermal) {
             gmode = kGhConst;
             gc = hd[7 + sd];
+            // FP32: read the emission value from the plane's constants (no select)
+            if constexpr (!REF) {
+                gptr = reinterpret_cast<const T *>(hd + 7 + sd);
+                gstep = 0;
+            }
         } else {
             gptr = SD::dcol(side, sd, zl) + (int)(dcol_src(a, sd, q.k, z, q.y0) & (SD::V - 1)) + yl0;
             gstep = sy;
@@ -590,11 +597,9 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
         if (j >= nrows) break;
         const int y = q.y0 + yl0 + j * sy;
         ld_row<S, VL>(wp1, box + o + dy + x0, rbox + ro + dyR + x0);
-        float div[VL], fout[VL];
+        float fout[VL];
         // y: out face between y and y + sy (upwind y); the in face is the previous row's out face
         faces<LIM, VL>(wm1, w0, wp1, fout);
-        #pragma unroll
-        for (int v = 0; v < VL; ++v) div[v] = any * (fout[v] - fin[v]);
         // x: neighbours from the adjacent lanes, the end lanes as decided above
         float ex[VL + 4];
         #pragma unroll
@@ -611,9 +616,11 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
                 r1 = rbox[ro + rx1];
             }
             float g0 = St<S>::dec(gp[gi0], r0), g1 = St<S>::dec(gp[gi1], r1);
-            const float own = lane == 0 ? w0[0] : w0[VL - 1];
-            g0 = gmode == kGhConst ? gc : (gmode == kGhOwn ? own : g0);
-            g1 = gmode == kGhConst ? gc : (gmode == kGhOwn ? own : g1);
+            if constexpr (REF) {
+                const float own = lane == 0 ? w0[0] : w0[VL - 1];
+                g0 = gmode == kGhConst ? gc : (gmode == kGhOwn ? own : g0);
+                g1 = gmode == kGhConst ? gc : (gmode == kGhOwn ? own : g1);
+            }
             const bool l0 = gmode != kGhShfl && lane == 0, l31 = gmode != kGhShfl && lane == 31;
             ex[1] = l0 ? g0 : ex[1];
             ex[0] = l0 ? g1 : ex[0];
@@ -624,18 +631,17 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
         float F[VL + 1];
         if (nux > 0.f) faces<LIM, VL + 1>(ex, ex + 1, ex + 2, F);       // upwind cell x0+j
         else faces<LIM, VL + 1>(ex + 3, ex + 2, ex + 1, F);             // upwind cell x0+j+1
+        float gx[VL];
         #pragma unroll
-        for (int v = 0; v < VL; ++v) div[v] = fmaf(nux, F[v + 1] - F[v], div[v]);
+        for (int v = 0; v < VL; ++v) gx[v] = F[v + 1] - F[v];
+        float zo[VL], zi[VL];
         if constexpr (DIM == 3) {
             float zm1[VL], zm2[VL], zp1[VL];
             ld_row<S, VL>(zm1, box + o - dz + x0, rbox + ro - dzR + x0);
             ld_row<S, VL>(zm2, box + o - 2 * dz + x0, rbox + ro - rz2 + x0);
             ld_row<S, VL>(zp1, box + o + dz + x0, rbox + ro + dzR + x0);
-            float zo[VL], zi[VL];
             faces<LIM, VL>(zm1, w0, zp1, zo);
             faces<LIM, VL>(zm2, zm1, w0, zi);
-            #pragma unroll
-            for (int v = 0; v < VL; ++v) div[v] = fmaf(anz, zo[v] - zi[v], div[v]);
         }
         // update, store, moment and diffuse-wall partials
         float bt[VL], ac[VL];
@@ -649,17 +655,44 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
             for (int v = 0; v < VL; ++v) { bt[v] = btsm[c + v]; ac[v] = accsm[c + v]; }
         }
         typename St<S>::C h[VL];
-        float es[VL];
+        float en[VL], es[VL];
         const long long grow = ((long long)z * ny + y) * NX;  // global index of the row's first cell
+        // FP32: e^{n+1} = e - dt/tau e + bt - |nu_y| (F_out - F_in) - nu_x (F_{v+1} - F_v)
+        // [- |nu_z| (F_zout - F_zin)].  16-bit: bt carries -rho_new, so en is already the new code's
+        // value.  Two cells at a time.
+        #pragma unroll
+        for (int v = 0; v + 1 < VL; v += 2) {
+            const float2 u = make_float2(w0[v], w0[v + 1]);
+            float2 t = __fadd2_rn(__ffma2_rn(f2(-dtinv), u, u), make_float2(bt[v], bt[v + 1]));
+            t = __ffma2_rn(f2(-any), sub2(make_float2(fout[v], fout[v + 1]), make_float2(fin[v], fin[v + 1])), t);
+            t = __ffma2_rn(f2(-nux), make_float2(gx[v], gx[v + 1]), t);
+            if constexpr (DIM == 3)
+                t = __ffma2_rn(f2(-anz), sub2(make_float2(zo[v], zo[v + 1]), make_float2(zi[v], zi[v + 1])), t);
+            en[v] = t.x;
+            en[v + 1] = t.y;
+        }
+        if constexpr (VL & 1) {
+            constexpr int v = VL - 1;
+            float t = fmaf(-dtinv, w0[v], w0[v]) + bt[v];
+            t = fmaf(-any, fout[v] - fin[v], t);
+            t = fmaf(-nux, gx[v], t);
+            if constexpr (DIM == 3) t = fmaf(-anz, zo[v] - zi[v], t);
+            en[v] = t;
+        }
         #pragma unroll
         for (int v = 0; v < VL; ++v) {
-            // FP32: e^{n+1}.  16-bit: bt carries -rho_new, so en is already the new code's value
-            const float en = fmaf(-dtinv, w0[v], w0[v] - div[v]) + bt[v];
-            if constexpr (SR) h[v] = St<S>::enc_sr(en, mix32(pkey ^ (uint32_t)(grow + x0 + v)));
-            else h[v] = St<S>::enc(en);
+            if constexpr (SR) h[v] = St<S>::enc_sr(en[v], mix32(pkey ^ (uint32_t)(grow + x0 + v)));
+            else h[v] = St<S>::enc(en[v]);
             es[v] = St<S>::val(h[v]);
-            ac[v] = fmaf(wm, es[v], ac[v]);
         }
+        // moment partials, two cells at a time
+        #pragma unroll
+        for (int v = 0; v + 1 < VL; v += 2) {
+            const float2 m = __ffma2_rn(f2(wm), make_float2(es[v], es[v + 1]), make_float2(ac[v], ac[v + 1]));
+            ac[v] = m.x;
+            ac[v + 1] = m.y;
+        }
+        if constexpr (VL & 1) ac[VL - 1] = fmaf(wm, es[VL - 1], ac[VL - 1]);
         if constexpr (VL == 4) *reinterpret_cast<float4 *>(accsm + c) = make_float4(ac[0], ac[1], ac[2], ac[3]);
         else {
             #pragma unroll
