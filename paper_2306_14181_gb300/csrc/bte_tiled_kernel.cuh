@@ -16,8 +16,11 @@ constexpr int kHdrFloats = 16;                        // per-plane constants wri
 // Tile geometry: a lane holds VL consecutive cells of a row, WPR warps cover a row of
 // nx = 32 VL WPR cells; NCW consumer warps stream KR rows each; 2-D tiles are TY rows, 3-D
 // tiles TY rows by TZ slices.  2-D CTAs run 16 consumer warps of 4 rows (96 registers a
-// thread; 8 warps of 8 rows, with 224 registers, measured 35% slower: too few warps to hide
-// latency), 3-D ones 12 warps of 4 rows (128; the z-stencil needs more live values).
+// thread), 3-D ones 12 warps of 4 rows (128; the z-stencil needs more live values).  Fewer,
+// wider warps on 256-cell rows measured slower: 8 warps of 8 rows at 4 cells a lane (224
+// registers) by 35%, and 8 warps of 4 rows at 8 cells a lane (142 registers; 40 instead of 50
+// instructions per update, but issue slots 40% busy instead of 61%, and twice the shared-memory
+// bank conflicts from the 32-byte lane stride) by 23%: 9 resident warps cannot hide latency.
 template <int DIM, int WPR> struct Geo;
 template <int WPR> struct Geo<2, WPR> {
     static constexpr int NCW = 16, KR = 4, TZ = 1, TY = NCW / WPR * KR;
