@@ -187,7 +187,7 @@ bool tiled_plan(int dim, const int n[3], int nb, int nd, int storage, int limite
     }
     plan.ty = TY;
     plan.tz = TZ;
-    plan.threads = (ncw + 1) * 32;
+    plan.threads = (ncw + kProducerWarps) * 32;
     plan.nty = (n[1] + TY - 1) / TY;
     plan.ntz = dim == 3 ? (n[2] + TZ - 1) / TZ : 1;
     plan.ntiles = plan.nty * plan.ntz;

@@ -22,12 +22,33 @@ constexpr int kHdrFloats = 16;                        // per-plane constants wri
 // instructions per update, but issue slots 40% busy instead of 61%, and twice the shared-memory
 // bank conflicts from the 32-byte lane stride) by 23%: 9 resident warps cannot hide latency.
 template <int DIM, int WPR> struct Geo;
+// The producer is a warpgroup of its own (one working warp, three idle) so that registers can
+// move between the two roles: at launch every thread gets 65536 / threads (rounded down to a
+// multiple of 8); the producer warpgroup then gives back all but RP a thread and the consumer
+// warpgroups take RC.  2-D: 640 threads x 96 = 61440 at launch, 16 x 32 x 104 + 4 x 32 x 56 =
+// 60416 after; 3-D: 512 x 128 = 65536 at launch, 12 x 32 x 152 + 4 x 32 x 56 = 65536 after.
+// Per SM sub-partition (warps w, w + 4, ...): 2-D 4 x 32 x 104 + 32 x 56 = 15104, 3-D 3 x 32 x
+// 152 + 32 x 56 = 16384, within its 16384 registers.  (A 17th warp alone would cap every
+// thread at 96 registers: five warps share one sub-partition.)
 template <int WPR> struct Geo<2, WPR> {
     static constexpr int NCW = 16, KR = 4, TZ = 1, TY = NCW / WPR * KR;
+    static constexpr int RC = 104, RP = 56;
 };
 template <> struct Geo<3, 1> {
     static constexpr int NCW = 12, KR = 4, TZ = 6, TY = NCW / TZ * KR;
+    static constexpr int RC = 152, RP = 56;
 };
+constexpr int kProducerWarps = 4;  // one warpgroup
+template <int DIM, int WPR> constexpr int launch_regs() {
+    return 65536 / ((Geo<DIM, WPR>::NCW + kProducerWarps) * 32) / 8 * 8;
+}
+static_assert(Geo<2, 2>::NCW % 4 == 0 && Geo<3, 1>::NCW % 4 == 0, "consumers fill whole warpgroups");
+static_assert(Geo<2, 2>::NCW * 32 * Geo<2, 2>::RC + kProducerWarps * 32 * Geo<2, 2>::RP <=
+                  (Geo<2, 2>::NCW + kProducerWarps) * 32 * launch_regs<2, 2>(), "2-D register split");
+static_assert(Geo<3, 1>::NCW * 32 * Geo<3, 1>::RC + kProducerWarps * 32 * Geo<3, 1>::RP <=
+                  (Geo<3, 1>::NCW + kProducerWarps) * 32 * launch_regs<3, 1>(), "3-D register split");
+static_assert((Geo<2, 2>::NCW / 4) * 32 * Geo<2, 2>::RC + 32 * Geo<2, 2>::RP <= 16384 &&
+                  (Geo<3, 1>::NCW / 4) * 32 * Geo<3, 1>::RC + 32 * Geo<3, 1>::RP <= 16384, "per sub-partition");
 
 // Storage codecs.  FP32 storage keeps e.  16-bit storage keeps h = round(e / s_k - rho_i) with
 // rho_i = R_i / T_scale the cell's code reference (the departure from band k's equilibrium at
@@ -481,7 +502,9 @@ __device__ void producer(const StepArgs &a, const TiledArgs &p, char *smem, uint
 // Where an end lane of a warp takes its two x-neighbours from (besides the plain shuffle).
 enum { kGhShfl = 0, kGhSmem = 1, kGhSpec = 2, kGhDiff = 3, kGhConst = 4, kGhOwn = 5 };
 
-template <int S, int LIM, int VL, int WPR, int DIM, bool SR>
+// SY, SX: signs of the direction's y and x components (+1 when positive, else -1), fixed per
+// instance so that row steps are constants and the x faces need no orientation branch.
+template <int S, int LIM, int VL, int WPR, int DIM, bool SR, int SY, int SX>
 __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs &p, const PT &q, const char *stage,
                                              int zl, int rb, int half, float *accsm, const float *btsm, float *wsm,
                                              const float *rbox) {
@@ -495,7 +518,8 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
     const float nux = h0.x, nuy = h0.y, nuz = h0.z, wm = h0.w;
     const float dtinv = hd[4], sc = hd[5];
     const float any = fabsf(nuy), anz = fabsf(nuz);
-    const int sy = nuy > 0.f ? 1 : -1, sz = nuz > 0.f ? 1 : -1;
+    constexpr int sy = SY;
+    const int sz = nuz > 0.f ? 1 : -1;
     constexpr int kR = Geo<DIM, WPR>::KR;
     const int nrows = min(kR, q.nyt - rb);
     const int yl0 = sy > 0 ? rb : rb + nrows - 1;  // first row in streaming (upwind-to-downwind) order
@@ -632,7 +656,7 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
         }
         // faces F_j between x0+j and x0+j+1, j = -1..VL-1 (index j+1); flux in signed form
         float F[VL + 1];
-        if (nux > 0.f) faces<LIM, VL + 1>(ex, ex + 1, ex + 2, F);       // upwind cell x0+j
+        if constexpr (SX > 0) faces<LIM, VL + 1>(ex, ex + 1, ex + 2, F);  // upwind cell x0+j
         else faces<LIM, VL + 1>(ex + 3, ex + 2, ex + 1, F);             // upwind cell x0+j+1
         float gx[VL];
         #pragma unroll
@@ -877,8 +901,17 @@ __device__ void consumer(const StepArgs &a, const TiledArgs &p, char *smem, uint
         if (!mbar_wait(&full[s], ph, p.err, 1)) return;
         const char *stage = smem + p.stage0 + (size_t)s * p.stage_bytes;
         if constexpr (REF) wsum += reinterpret_cast<const float *>(stage + p.hdr_off)[3];
-        if (zl < q.nzt && rb < q.nyt)
-            rows_of_warp<S, LIM, VL, WPR, DIM, SR>(a, p, q, stage, zl, rb, half, accsm, btsm, wsm, rbox);
+        if (zl < q.nzt && rb < q.nyt) {
+            const float *hd = reinterpret_cast<const float *>(stage + p.hdr_off);
+            const bool px = hd[0] > 0.f, py = hd[1] > 0.f;  // the signs rows_of_warp takes
+            if (py) {
+                if (px) rows_of_warp<S, LIM, VL, WPR, DIM, SR, 1, 1>(a, p, q, stage, zl, rb, half, accsm, btsm, wsm, rbox);
+                else rows_of_warp<S, LIM, VL, WPR, DIM, SR, 1, -1>(a, p, q, stage, zl, rb, half, accsm, btsm, wsm, rbox);
+            } else {
+                if (px) rows_of_warp<S, LIM, VL, WPR, DIM, SR, -1, 1>(a, p, q, stage, zl, rb, half, accsm, btsm, wsm, rbox);
+                else rows_of_warp<S, LIM, VL, WPR, DIM, SR, -1, -1>(a, p, q, stage, zl, rb, half, accsm, btsm, wsm, rbox);
+            }
+        }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
         if (++s == p.ns) {
@@ -892,7 +925,7 @@ __device__ void consumer(const StepArgs &a, const TiledArgs &p, char *smem, uint
 // SR: 16-bit codes rounded stochastically (a separate instance, so the round-to-nearest one
 // carries none of the hashing)
 template <int S, int LIM, int VL, int WPR, int DIM, bool SR>
-__global__ void __launch_bounds__((Geo<DIM, WPR>::NCW + 1) * 32, 1) k_step_tiled(const StepArgs a, const TiledArgs p) {
+__global__ void __launch_bounds__((Geo<DIM, WPR>::NCW + kProducerWarps) * 32, 1) k_step_tiled(const StepArgs a, const TiledArgs p) {
     extern __shared__ __align__(128) char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint64_t *empty = full + p.ns;
@@ -908,10 +941,14 @@ __global__ void __launch_bounds__((Geo<DIM, WPR>::NCW + 1) * 32, 1) k_step_tiled
     float *accsm = reinterpret_cast<float *>(smem + p.acc_off);
     for (int j = threadIdx.x; j < p.tcells; j += blockDim.x) accsm[j] = 0.f;
     __syncthreads();
-    if ((int)(threadIdx.x >> 5) == Geo<DIM, WPR>::NCW)
-        producer<S, VL, WPR, DIM>(a, p, smem, full, empty);
-    else
+    const int warp = (int)(threadIdx.x >> 5);
+    if (warp >= Geo<DIM, WPR>::NCW) {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(Geo<DIM, WPR>::RP));
+        if (warp == Geo<DIM, WPR>::NCW) producer<S, VL, WPR, DIM>(a, p, smem, full, empty);
+    } else {
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(Geo<DIM, WPR>::RC));
         consumer<S, LIM, VL, WPR, DIM, SR>(a, p, smem, full, empty);
+    }
 }
 
 typedef void (*StepKernel)(const StepArgs, const TiledArgs);
