@@ -611,6 +611,9 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
     const float wz = DIM == 3 ? (z == 0 ? hd[13] : (z == nz - 1 ? hd[14] : 0.f)) : 0.f;
     float *wzp = wsm + (z == 0 ? max(p.wslot[4], 0) : max(p.wslot[5], 0)) * p.tw + yl0 * NX + x0;
     const float wy0 = hd[11], wy1 = hd[12];
+    // the rows of this warp on the y walls, as loop indices in streaming order (-1: none)
+    const int ys0 = q.y0 + yl0;
+    const int jw0 = wy0 != 0.f ? -ys0 * sy : -1, jw1 = wy1 != 0.f ? (ny - 1 - ys0) * sy : -1;
     float *wy0p = wsm + max(p.wslot[2], 0) * p.tw + zl * NX + x0;
     float *wy1p = wsm + max(p.wslot[3], 0) * p.tw + zl * NX + x0;
 
@@ -735,9 +738,9 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
             if constexpr (REF) ev = sc * (ev + a.TL[grow + x0 + xe] * a.invTs);
             wxp[j * sy] += wx * ev;
         }
-        const float wy = y == 0 ? wy0 : (y == ny - 1 ? wy1 : 0.f);  // uniform across the warp
-        if (wy != 0.f) {
-            float *w = y == 0 ? wy0p : wy1p;
+        if (j == jw0 || j == jw1) {  // uniform across the warp
+            const float wy = j == jw0 ? wy0 : wy1;
+            float *w = j == jw0 ? wy0p : wy1p;
             #pragma unroll
             for (int v = 0; v < VL; ++v) {
                 float ev = es[v];
