@@ -13,7 +13,9 @@ cudaError_t launch_adj_tiled(const StepArgs &a, const TiledPlan &plan, const flo
                                          : adj_pick_bf16(limiter, plan.nx, plan.dim);
     if (!k) return cudaErrorInvalidConfiguration;
     const int ncw = plan.dim == 2 ? Geo<2, 1>::NCW : Geo<3, 1>::NCW;
-    const size_t smem = (size_t)2 * plan.tcells * sizeof(float) + 2 * ncw * sizeof(float);
+    // accumulators of mu and of the source gradient, the block reduction, and in 3-D the z-face
+    // terms passed between slices (two plane-tile parities of A and C)
+    const size_t smem = (size_t)(plan.dim == 3 ? 6 : 2) * plan.tcells * sizeof(float) + 2 * ncw * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     AdjTiledArgs g;

@@ -128,6 +128,57 @@ __device__ __forceinline__ void adj_xfaces(const float (&ex)[VL + 4], const floa
     for (int j = 0; j < VL; ++j) acc[j] += fA[j + 1 + SX] + fB[j + 1] + fC[j + 1 - SX];
 }
 
+// x faces of one lane when one warp covers a row (WPR = 1): the lane takes the faces whose
+// upwind cells are its own, x0 .. x0+VL-1, and receives by shuffle the one term of each
+// neighbour lane's end face that lands on its cells (the A of the face downwind of its last
+// cell ... in orientation SX: cell x0+j gets A of face x0+j+SX, B of face x0+j, C of face
+// x0+j-SX).  The row's two ends meet by the same shuffles, which is the wrap of a periodic
+// axis; on a wall axis those end faces read ghost values and belong to the wall pass (zero).
+template <int LIM, int VL, int SX>
+__device__ __forceinline__ void adj_xfaces_w(const float (&e0)[VL], const float (&l0)[VL], int x0, int NX, bool perx,
+                                             float anx, int lane, float (&acc)[VL]) {
+    const int lft = (lane + 31) & 31, rgt = (lane + 1) & 31;
+    float ex[VL + 2], lx[VL + 2];  // positions x0-1 .. x0+VL
+    #pragma unroll
+    for (int j = 0; j < VL; ++j) {
+        ex[j + 1] = e0[j];
+        lx[j + 1] = l0[j];
+    }
+    ex[0] = __shfl_sync(0xffffffffu, e0[VL - 1], lft);
+    ex[VL + 1] = __shfl_sync(0xffffffffu, e0[0], rgt);
+    if constexpr (SX > 0) {
+        lx[VL + 1] = __shfl_sync(0xffffffffu, l0[0], rgt);
+        lx[0] = 0.f;
+    } else {
+        lx[0] = __shfl_sync(0xffffffffu, l0[VL - 1], lft);
+        lx[VL + 1] = 0.f;
+    }
+    float fA[VL], fB[VL], fC[VL];
+    #pragma unroll
+    for (int f = 0; f < VL; ++f) {
+        const int m = x0 + f;
+        const bool ok = perx || (m >= 1 && m + 1 < NX);
+        float A = 0.f, B = 0.f, C = 0.f;
+        if (ok) face_terms<LIM>(ex[f + 1 - SX], ex[f + 1], ex[f + 1 + SX], anx * (lx[f + 1 + SX] - lx[f + 1]), A, B, C);
+        fA[f] = A;
+        fB[f] = B;
+        fC[f] = C;
+    }
+    // A of the face at x0+VL-1+SX... from the lane downwind, C of the face upwind from the lane upwind
+    float nA = __shfl_sync(0xffffffffu, SX > 0 ? fA[0] : fA[VL - 1], SX > 0 ? rgt : lft);
+    float nC = __shfl_sync(0xffffffffu, SX > 0 ? fC[VL - 1] : fC[0], SX > 0 ? lft : rgt);
+    if (!perx) {
+        if (lane == (SX > 0 ? 31 : 0)) nA = 0.f;
+        if (lane == (SX > 0 ? 0 : 31)) nC = 0.f;
+    }
+    #pragma unroll
+    for (int j = 0; j < VL; ++j) {
+        const float ta = SX > 0 ? (j + 1 < VL ? fA[j + 1 < VL ? j + 1 : 0] : nA) : (j >= 1 ? fA[j >= 1 ? j - 1 : 0] : nA);
+        const float tc = SX > 0 ? (j >= 1 ? fC[j >= 1 ? j - 1 : 0] : nC) : (j + 1 < VL ? fC[j + 1 < VL ? j + 1 : 0] : nC);
+        acc[j] += ta + fB[j] + tc;
+    }
+}
+
 struct AdjTiledArgs {
     const float *lam_in;  // lambda^{n+1}
     float *lam_out;       // lambda^n
@@ -138,9 +189,35 @@ struct AdjTiledArgs {
 };
 
 // The rows one warp streams for one plane-tile.
+// lambda^n of VL cells to global memory, and their per-cell partials of mu and of the source
+// gradient (four contiguous floats per lane move as one 16-byte access, free of bank conflicts)
+template <int VL>
+__device__ __forceinline__ void adj_emit(const AdjTiledArgs &g, float *accm, float *accq, int c, long long gi, float bm,
+                                         float bq, const float (&out)[VL]) {
+    if constexpr (VL == 4) {
+        float4 m = *reinterpret_cast<float4 *>(accm + c), qq = *reinterpret_cast<float4 *>(accq + c);
+        m.x = fmaf(bm, out[0], m.x); m.y = fmaf(bm, out[1], m.y); m.z = fmaf(bm, out[2], m.z); m.w = fmaf(bm, out[3], m.w);
+        qq.x = fmaf(bq, out[0], qq.x); qq.y = fmaf(bq, out[1], qq.y); qq.z = fmaf(bq, out[2], qq.z); qq.w = fmaf(bq, out[3], qq.w);
+        *reinterpret_cast<float4 *>(accm + c) = m;
+        *reinterpret_cast<float4 *>(accq + c) = qq;
+        *reinterpret_cast<float4 *>(g.lam_out + gi) = make_float4(out[0], out[1], out[2], out[3]);
+    } else {
+        #pragma unroll
+        for (int j = 0; j < VL; ++j) {
+            accm[c + j] = fmaf(bm, out[j], accm[c + j]);
+            accq[c + j] = fmaf(bq, out[j], accq[c + j]);
+            g.lam_out[gi + j] = out[j];
+        }
+    }
+}
+
+// 3-D: each warp evaluates the z face at its own slice (values z-sz, z, z+sz), keeps B, and
+// passes A (for slice z-sz) and C (for slice z+sz) through xa / xa + tcells; after a barrier
+// of the consumer warps it adds the terms its neighbour slices left for it.  The tile's two
+// edge slices evaluate the face just outside the tile themselves.
 template <int S, int LIM, int VL, int WPR, int DIM>
 __device__ __forceinline__ void adj_rows(const StepArgs &a, const AdjTiledArgs &g, const PT &q, int zl, int rb, int half,
-                                         float *accm, float *accq, float &s1, float &s2) {
+                                         float *accm, float *accq, float &s1, float &s2, float *xa) {
     using T = typename St<S>::T;
     constexpr int NX = 32 * VL * WPR, TY = Geo<DIM, WPR>::TY;
     const int lane = threadIdx.x & 31, x0 = (half * 32 + lane) * VL;
@@ -180,6 +257,8 @@ __device__ __forceinline__ void adj_rows(const StepArgs &a, const AdjTiledArgs &
             for (int j = 0; j < VL; ++j) ev[j] = lv[j] = 0.f;
         }
     };
+    float outp[DIM == 3 ? kR : 1][VL];  // 3-D: this warp's outputs before the z exchange
+    const int p_tcells = TY * Geo<DIM, WPR>::TZ * NX;
     float dummy[VL];
     load_row(e_m2, dummy, -2, ok_m2);
     load_row(e_m1, l_m1, -1, ok_m1);
@@ -218,7 +297,10 @@ __device__ __forceinline__ void adj_rows(const StepArgs &a, const AdjTiledArgs &
         // x: values e and lambda at x0-2 .. x0+VL+1 from the neighbour lanes; the end lanes of
         // a warp read theirs (wrapped on a periodic axis; positions outside a wall are never
         // used: the faces reading them belong to the wall pass)
-        {
+        if constexpr (WPR == 1) {
+            if (sx > 0) adj_xfaces_w<LIM, VL, 1>(e_0, l_0, x0, NX, perx, anx, lane, acc);
+            else adj_xfaces_w<LIM, VL, -1>(e_0, l_0, x0, NX, perx, anx, lane, acc);
+        } else {
             float ex[VL + 4], lx[VL + 4];
             #pragma unroll
             for (int j = 0; j < VL; ++j) {
@@ -250,49 +332,59 @@ __device__ __forceinline__ void adj_rows(const StepArgs &a, const AdjTiledArgs &
             if (sx > 0) adj_xfaces<LIM, VL, 1>(ex, lx, x0, NX, perx, anx, acc);
             else adj_xfaces<LIM, VL, -1>(ex, lx, x0, NX, perx, anx, acc);
         }
+        const int c = (zl * TY + (y - q.y0)) * NX + x0;
         if constexpr (DIM == 3) {
-            // z: faces z-sz (values z-2sz, z-sz, z), z (z-sz, z, z+sz), z+sz (z, z+sz, z+2sz)
-            float zv[5][VL], zl4[4][VL];
-            bool zok[5];
+            // z: the face at this slice (values z-sz, z, z+sz) gives B here, A to slice z-sz and
+            // C to slice z+sz; a tile-edge slice also takes the face just outside the tile
+            // (z-sz: values z-2sz, z-sz, z, its C; z+sz: values z, z+sz, z+2sz, its A)
+            const bool in_up = zl - sz >= 0 && zl - sz < q.nzt, in_dn = zl + sz >= 0 && zl + sz < q.nzt;
+            const int z1 = adj_row(z - sz, nz, perz), z3 = adj_row(z + sz, nz, perz);
+            float e1[VL], e3[VL], l3[VL];
+            if (z1 >= 0) adj_ld_e<S, VL>(e1, a, e, base, cell_of(z1, y));
+            if (z3 >= 0) {
+                adj_ld_e<S, VL>(e3, a, e, base, cell_of(z3, y));
+                adj_ld_l<VL>(l3, lam, base + cell_of(z3, y));
+            }
+            float xA[VL], xC[VL];
             #pragma unroll
-            for (int r = 0; r < 5; ++r) {
-                const int zz = adj_row(z + (r - 2) * sz, nz, perz);
-                zok[r] = zz >= 0;
-                if (r == 2) {
-                    #pragma unroll
-                    for (int j = 0; j < VL; ++j) zv[r][j] = e_0[j];
-                } else if (zok[r]) {
-                    adj_ld_e<S, VL>(zv[r], a, e, base, cell_of(zz, y));
-                } else {
-                    #pragma unroll
-                    for (int j = 0; j < VL; ++j) zv[r][j] = 0.f;
-                }
-                if (r >= 1) {
-                    if (r == 2) {
-                        #pragma unroll
-                        for (int j = 0; j < VL; ++j) zl4[1][j] = l_0[j];
-                    } else if (zok[r]) {
-                        adj_ld_l<VL>(zl4[r - 1], lam, base + cell_of(zz, y));
-                    } else {
-                        #pragma unroll
-                        for (int j = 0; j < VL; ++j) zl4[r - 1][j] = 0.f;
-                    }
-                }
+            for (int j = 0; j < VL; ++j) {
+                float A = 0.f, B = 0.f, C = 0.f;
+                if (z1 >= 0 && z3 >= 0) face_terms<LIM>(e1[j], e_0[j], e3[j], anz * (l3[j] - l_0[j]), A, B, C);
+                acc[j] += B;
+                xA[j] = A;
+                xC[j] = C;
             }
             #pragma unroll
             for (int j = 0; j < VL; ++j) {
-                float A, B, C;
-                if (zok[0] && zok[1]) {  // face z-sz: C to this cell
-                    face_terms<LIM>(zv[0][j], zv[1][j], zv[2][j], anz * (zl4[1][j] - zl4[0][j]), A, B, C);
-                    acc[j] += C;
+                xa[c + j] = xA[j];
+                xa[p_tcells + c + j] = xC[j];
+            }
+            if (!in_up) {
+                const int z0 = adj_row(z - 2 * sz, nz, perz);
+                if (z0 >= 0 && z1 >= 0) {
+                    float e0v[VL], l1[VL];
+                    adj_ld_e<S, VL>(e0v, a, e, base, cell_of(z0, y));
+                    adj_ld_l<VL>(l1, lam, base + cell_of(z1, y));
+                    #pragma unroll
+                    for (int j = 0; j < VL; ++j) {
+                        float A, B, C;
+                        face_terms<LIM>(e0v[j], e1[j], e_0[j], anz * (l_0[j] - l1[j]), A, B, C);
+                        acc[j] += C;
+                    }
                 }
-                if (zok[1] && zok[3]) {  // face z: B
-                    face_terms<LIM>(zv[1][j], zv[2][j], zv[3][j], anz * (zl4[2][j] - zl4[1][j]), A, B, C);
-                    acc[j] += B;
-                }
-                if (zok[3] && zok[4]) {  // face z+sz: A
-                    face_terms<LIM>(zv[2][j], zv[3][j], zv[4][j], anz * (zl4[3][j] - zl4[2][j]), A, B, C);
-                    acc[j] += A;
+            }
+            if (!in_dn) {
+                const int z4 = adj_row(z + 2 * sz, nz, perz);
+                if (z3 >= 0 && z4 >= 0) {
+                    float e4[VL], l4[VL];
+                    adj_ld_e<S, VL>(e4, a, e, base, cell_of(z4, y));
+                    adj_ld_l<VL>(l4, lam, base + cell_of(z4, y));
+                    #pragma unroll
+                    for (int j = 0; j < VL; ++j) {
+                        float A, B, C;
+                        face_terms<LIM>(e_0[j], e3[j], e4[j], anz * (l4[j] - l3[j]), A, B, C);
+                        acc[j] += A;
+                    }
                 }
             }
         }
@@ -301,7 +393,6 @@ __device__ __forceinline__ void adj_rows(const StepArgs &a, const AdjTiledArgs &
         adj_ld_l<VL>(mu, g.mu_in, cl);
         adj_ld_l<VL>(tl, a.TL, cl);
         float out[VL];
-        const int c = (zl * TY + (y - q.y0)) * NX + x0;
         #pragma unroll
         for (int j = 0; j < VL; ++j) {
             const float lv = l_0[j];
@@ -310,26 +401,11 @@ __device__ __forceinline__ void adj_rows(const StepArgs &a, const AdjTiledArgs &
             s1 = fmaf(lv, fmaf(b.ck, tl[j], -ev), s1);
             s2 = fmaf(wd * mu[j], ev, s2);
         }
-        // per-cell partials (four contiguous floats per lane move as one 16-byte access, free
-        // of bank conflicts)
-        if constexpr (VL == 4) {
-            float4 m = *reinterpret_cast<float4 *>(accm + c), qq = *reinterpret_cast<float4 *>(accq + c);
-            m.x = fmaf(bm, out[0], m.x); m.y = fmaf(bm, out[1], m.y); m.z = fmaf(bm, out[2], m.z); m.w = fmaf(bm, out[3], m.w);
-            qq.x = fmaf(bq, out[0], qq.x); qq.y = fmaf(bq, out[1], qq.y); qq.z = fmaf(bq, out[2], qq.z); qq.w = fmaf(bq, out[3], qq.w);
-            *reinterpret_cast<float4 *>(accm + c) = m;
-            *reinterpret_cast<float4 *>(accq + c) = qq;
+        if constexpr (DIM == 3) {
+            #pragma unroll
+            for (int j = 0; j < VL; ++j) outp[t][j] = out[j];
         } else {
-            #pragma unroll
-            for (int j = 0; j < VL; ++j) {
-                accm[c + j] = fmaf(bm, out[j], accm[c + j]);
-                accq[c + j] = fmaf(bq, out[j], accq[c + j]);
-            }
-        }
-        if constexpr (VL == 4)
-            *reinterpret_cast<float4 *>(g.lam_out + base + cl) = make_float4(out[0], out[1], out[2], out[3]);
-        else {
-            #pragma unroll
-            for (int j = 0; j < VL; ++j) g.lam_out[base + cl + j] = out[j];
+            adj_emit<VL>(g, accm, accq, c, base + cl, bm, bq, out);
         }
         // slide the window
         #pragma unroll
@@ -347,6 +423,26 @@ __device__ __forceinline__ void adj_rows(const StepArgs &a, const AdjTiledArgs &
         ok_0 = ok_p1;
         ok_p1 = ok_p2;
     }
+    if constexpr (DIM == 3) {
+        consumer_sync<Geo<DIM, WPR>::NCW>();  // every slice's A and C of this plane-tile are written
+        const bool in_up = zl - sz >= 0 && zl - sz < q.nzt, in_dn = zl + sz >= 0 && zl + sz < q.nzt;
+        const int dzc = sz * TY * NX;
+        #pragma unroll
+        for (int t = 0; t < kR; ++t) {
+            if (t >= nrows) break;
+            const int y = y0w + t * sy;
+            const int c = (zl * TY + (y - q.y0)) * NX + x0;
+            float out[VL];
+            #pragma unroll
+            for (int j = 0; j < VL; ++j) {
+                float v = outp[t][j];
+                if (in_up) v += xa[p_tcells + c - dzc + j];  // C of the face at slice z-sz
+                if (in_dn) v += xa[c + dzc + j];             // A of the face at slice z+sz
+                out[j] = v;
+            }
+            adj_emit<VL>(g, accm, accq, c, base + cell_of(z, y), bm, bq, out);
+        }
+    }
 }
 
 template <int S, int LIM, int VL, int WPR, int DIM>
@@ -357,6 +453,8 @@ __global__ void __launch_bounds__(Geo<DIM, WPR>::NCW * 32, 1) k_adj_tiled(const 
     float *accm = reinterpret_cast<float *>(smem);
     float *accq = accm + p.tcells;
     float *red = accq + p.tcells;  // [2][NCW]
+    // 3-D: z-face terms passed between slices, [2 plane-tile parities][A, C][tcells]
+    float *xbuf = red + 2 * NCW;
     for (int j = threadIdx.x; j < 2 * p.tcells; j += blockDim.x) accm[j] = 0.f;
     __syncthreads();
     int zl, rb, half;
@@ -415,7 +513,7 @@ __global__ void __launch_bounds__(Geo<DIM, WPR>::NCW * 32, 1) k_adj_tiled(const 
     };
     Cursor<DIM, WPR> c;
     bool more = c.start(a, p);
-    for (; more; more = c.next(a, p)) {
+    for (int i = 0; more; ++i, more = c.next(a, p)) {
         const PT q = c.q;
         if (c.u != cur_unit || q.k != cur_band) {
             if (seg >= 0) flush();
@@ -424,7 +522,9 @@ __global__ void __launch_bounds__(Geo<DIM, WPR>::NCW * 32, 1) k_adj_tiled(const 
             cur_band = q.k;
             cur = q;
         }
-        if (zl < q.nzt && rb < q.nyt) adj_rows<S, LIM, VL, WPR, DIM>(a, g, q, zl, rb, half, accm, accq, s1, s2);
+        float *xa = xbuf + (size_t)(i & 1) * 2 * p.tcells;
+        if (zl < q.nzt && rb < q.nyt) adj_rows<S, LIM, VL, WPR, DIM>(a, g, q, zl, rb, half, accm, accq, s1, s2, xa);
+        else if constexpr (DIM == 3) consumer_sync<NCW>();  // the z exchange's barrier
     }
     if (seg >= 0) flush();
 }

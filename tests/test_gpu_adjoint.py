@@ -33,6 +33,8 @@ CASES = [
     (2, (128, 9, 1), [PER, PER, SPE, DIF, PER, PER], 2),
     (3, (12, 9, 8), [SPE, SPE, PER, PER, DIF, ISO], 1),
     (3, (96, 9, 7), [DIF, ISO, SPE, SPE, PER, PER], 2),
+    # z walls across three z-tiles of 6, 6 and 1 slices; periodic x at 4 cells a lane
+    (3, (128, 10, 13), [PER, PER, SPE, DIF, ISO, DIF], 2),
 ]
 
 
