@@ -13,9 +13,17 @@ cudaError_t launch_adj_tiled(const StepArgs &a, const TiledPlan &plan, const flo
                                          : adj_pick_bf16(limiter, plan.nx, plan.dim);
     if (!k) return cudaErrorInvalidConfiguration;
     const int ncw = plan.dim == 2 ? Geo<2, 1>::NCW : Geo<3, 1>::NCW;
-    // accumulators of mu and of the source gradient, the block reduction, and in 3-D the z-face
-    // terms passed between slices (two plane-tile parities of A and C)
-    const size_t smem = (size_t)(plan.dim == 3 ? 6 : 2) * plan.tcells * sizeof(float) + 2 * ncw * sizeof(float);
+    // accumulators of mu and of the source gradient and the block reduction; in 3-D the z-face
+    // terms passed between slices and the plane-tile's box of e and lambda; with 16-bit storage
+    // the unit's reference box, and mu and T_L of the tile, each where it still fits
+    const size_t box = (size_t)(plan.ty + 4) * (plan.dim == 3 ? plan.tz + 4 : 1) * plan.nx;
+    const size_t limit = (size_t)227 * 1024 / sizeof(float);
+    size_t nf = (size_t)2 * plan.tcells + 2 * ncw + (plan.dim == 3 ? (size_t)2 * plan.tcells + 2 * box : 0);
+    const bool cache_r = storage != kStoreF32 && (plan.dim == 2 || nf + box <= limit);
+    if (cache_r) nf += box;
+    const bool cache_mt = nf + (size_t)2 * plan.tcells <= limit;
+    if (cache_mt) nf += (size_t)2 * plan.tcells;
+    const size_t smem = nf * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     AdjTiledArgs g;
@@ -26,6 +34,8 @@ cudaError_t launch_adj_tiled(const StepArgs &a, const TiledPlan &plan, const flo
     g.Pq = Pq;
     g.Ps = Ps;
     g.w = w;
+    g.cache_r = cache_r ? 1 : 0;
+    g.cache_mt = cache_mt ? 1 : 0;
     k<<<plan.nctas, ncw * 32, smem, s>>>(a, tiled_device_args(plan), g);
     return cudaGetLastError();
 }

@@ -9,11 +9,13 @@
 // The limiter's partials are homogeneous of degree 0, so faces are evaluated on e / s_k
 // directly for 16-bit codes.  This kernel takes every face whose three values lie in the
 // domain (or wrap on a periodic axis): y faces streamed in registers from upwind to downwind
-// (one new face per row), x faces per lane (neighbour values by shuffles), z faces per
-// element.  The faces next to a non-periodic wall that read a ghost value (the first cell's
-// in-face and out-face, the last cell's out-face) and every ghost transpose are added by
-// k_adj_walls afterwards, which keeps this kernel free of wall rules.  Values come straight
-// from global memory (neighbouring units' rows are L2-resident).
+// (one new face per row), x faces per lane with the neighbour lanes' values and end-face terms
+// by shuffles, and in 3-D one z face per cell, shared between neighbouring slices through
+// shared memory.  The faces next to a non-periodic wall that read a ghost value (the first
+// cell's in-face and out-face, the last cell's out-face) and every ghost transpose are added
+// by k_adj_walls afterwards, which keeps this kernel free of wall rules.  2-D rows come
+// straight from global memory (neighbouring units' rows are L2-resident); a 3-D plane-tile is
+// first staged, with its two-cell halo, in shared memory by all warps together.
 #pragma once
 
 #include "bte_adjoint.h"
@@ -60,10 +62,11 @@ __device__ __forceinline__ int adj_row(int pos, int n, bool per) {
     return pos < 0 ? pos + n : pos - n;
 }
 
-// VL values of e (16-bit: e / s_k = h + rho) at global cell index `cell` of plane `base`.
+// VL values of e (16-bit: e / s_k = h + rho) at global cell index `cell` of plane `base`; rho
+// points at the same cells' references R / T_scale in the unit's shared reference box.
 template <int S, int VL>
-__device__ __forceinline__ void adj_ld_e(float (&v)[VL], const StepArgs &a, const typename St<S>::T *e, long long base,
-                                         long long cell) {
+__device__ __forceinline__ void adj_ld_e(float (&v)[VL], const typename St<S>::T *e, long long base, long long cell,
+                                         const float *rho) {
     using Q = St<S>;
     if constexpr (!Q::kRef) {
         if constexpr (VL == 4) {
@@ -76,14 +79,14 @@ __device__ __forceinline__ void adj_ld_e(float (&v)[VL], const StepArgs &a, cons
     } else {
         if constexpr (VL == 4) {
             const uint2 q = *reinterpret_cast<const uint2 *>(e + base + cell);
-            const float4 r = *reinterpret_cast<const float4 *>(a.R + cell);
-            v[0] = fmaf(r.x, a.invTs, Q::val(q.x & 0xffffu));
-            v[1] = fmaf(r.y, a.invTs, Q::val(q.x >> 16));
-            v[2] = fmaf(r.z, a.invTs, Q::val(q.y & 0xffffu));
-            v[3] = fmaf(r.w, a.invTs, Q::val(q.y >> 16));
+            const float4 r = *reinterpret_cast<const float4 *>(rho);
+            v[0] = r.x + Q::val(q.x & 0xffffu);
+            v[1] = r.y + Q::val(q.x >> 16);
+            v[2] = r.z + Q::val(q.y & 0xffffu);
+            v[3] = r.w + Q::val(q.y >> 16);
         } else {
             #pragma unroll
-            for (int j = 0; j < VL; ++j) v[j] = fmaf(a.R[cell + j], a.invTs, Q::val(Q::bits(e[base + cell + j])));
+            for (int j = 0; j < VL; ++j) v[j] = rho[j] + Q::val(Q::bits(e[base + cell + j]));
         }
     }
 }
@@ -186,9 +189,10 @@ struct AdjTiledArgs {
     float *Pm, *Pq;       // per segment rows [G][tcells]: sum_d lambda^n dt C_k/(W tau_k), sum_d lambda^n dt C_k/(sum C W)
     float *Ps;            // per segment [G][2]: sum lambda^{n+1} (C_k T_L/W - e), sum w_d mu^{n+1} e
     const float *w;       // [nd]
+    int cache_r;          // 16-bit references of the unit's box held in shared memory
+    int cache_mt;         // mu^{n+1} and T_L^n of the unit's tile held in shared memory
 };
 
-// The rows one warp streams for one plane-tile.
 // lambda^n of VL cells to global memory, and their per-cell partials of mu and of the source
 // gradient (four contiguous floats per lane move as one 16-byte access, free of bank conflicts)
 template <int VL>
@@ -211,24 +215,24 @@ __device__ __forceinline__ void adj_emit(const AdjTiledArgs &g, float *accm, flo
     }
 }
 
-// 3-D: each warp evaluates the z face at its own slice (values z-sz, z, z+sz), keeps B, and
-// passes A (for slice z-sz) and C (for slice z+sz) through xa / xa + tcells; after a barrier
-// of the consumer warps it adds the terms its neighbour slices left for it.  The tile's two
-// edge slices evaluate the face just outside the tile themselves.
+// 2-D: the rows one warp streams for one plane-tile, values straight from global memory (the
+// 16-bit references, mu and T_L from the unit's shared copies).
 template <int S, int LIM, int VL, int WPR, int DIM>
 __device__ __forceinline__ void adj_rows(const StepArgs &a, const AdjTiledArgs &g, const PT &q, int zl, int rb, int half,
-                                         float *accm, float *accq, float &s1, float &s2, float *xa) {
+                                         float *accm, float *accq, float &s1, float &s2, const float *rbox,
+                                         const float *mtbox) {
+    static_assert(DIM == 2, "3-D plane-tiles go through adj_tile3");
     using T = typename St<S>::T;
     constexpr int NX = 32 * VL * WPR, TY = Geo<DIM, WPR>::TY;
     const int lane = threadIdx.x & 31, x0 = (half * 32 + lane) * VL;
-    const int ny = a.n[1], nz = a.n[2];
+    const int ny = a.n[1];
     const int plane = q.plane;
     const long long base = (long long)plane * a.ncell;
     const BandConst b = a.band[q.k];
-    const float nux = a.nu[3 * plane], nuy = a.nu[3 * plane + 1], nuz = DIM == 3 ? a.nu[3 * plane + 2] : 0.f;
-    const float anx = fabsf(nux), any = fabsf(nuy), anz = fabsf(nuz);
-    const int sx = nux > 0.f ? 1 : -1, sy = nuy > 0.f ? 1 : -1, sz = nuz > 0.f ? 1 : -1;
-    const bool perx = a.bc[0] == kBcPeriodic, pery = a.bc[2] == kBcPeriodic, perz = DIM == 3 && a.bc[4] == kBcPeriodic;
+    const float nux = a.nu[3 * plane], nuy = a.nu[3 * plane + 1];
+    const float anx = fabsf(nux), any = fabsf(nuy);
+    const int sx = nux > 0.f ? 1 : -1, sy = nuy > 0.f ? 1 : -1;
+    const bool perx = a.bc[0] == kBcPeriodic, pery = a.bc[2] == kBcPeriodic;
     const float diag = 1.f - b.dtinv, wmD = a.wmom[plane] * a.invD, wd = g.w[q.d];
     const float sc = St<S>::kRef ? b.scale : 1.f;  // e = sc * (value in the kernel)
     const float bm = b.dtinv * b.ck, bq = b.srck;
@@ -240,6 +244,12 @@ __device__ __forceinline__ void adj_rows(const StepArgs &a, const AdjTiledArgs &
     // streaming order along y: t = 0 .. nrows-1 are this warp's rows, upwind to downwind
     const int y0w = q.y0 + (sy > 0 ? rb : rb + nrows - 1);
     auto cell_of = [&](int zz, int yy) { return ((long long)zz * ny + yy) * NX + x0; };
+    // this lane's cells of (unwrapped) row yu of slice zu in the reference box: rows y0-2 ..
+    // y0+TY+1 (and slices z0-2 .. z0+TZ+1 in 3-D)
+    constexpr int RY = TY + 4;
+    auto rho_at = [&](int zu, int yu) {
+        return rbox + ((DIM == 3 ? zu - (q.z0 - 2) : 0) * RY + (yu - (q.y0 - 2))) * NX + x0;
+    };
 
     // y window: e at t-2 .. t+2 (rows), lambda at t-1 .. t+2; faces F_{t+1} computed per step
     float e_m2[VL], e_m1[VL], e_0[VL], e_p1[VL], e_p2[VL], l_m1[VL], l_0[VL], l_p1[VL], l_p2[VL];
@@ -250,14 +260,13 @@ __device__ __forceinline__ void adj_rows(const StepArgs &a, const AdjTiledArgs &
         ok = yy >= 0;
         if (ok) {
             const long long cl = cell_of(z, yy);
-            adj_ld_e<S, VL>(ev, a, e, base, cl);
+            adj_ld_e<S, VL>(ev, e, base, cl, rho_at(z, y0w + t * sy));
             adj_ld_l<VL>(lv, lam, base + cl);
         } else {
             #pragma unroll
             for (int j = 0; j < VL; ++j) ev[j] = lv[j] = 0.f;
         }
     };
-    float outp[DIM == 3 ? kR : 1][VL];  // 3-D: this warp's outputs before the z exchange
     const int p_tcells = TY * Geo<DIM, WPR>::TZ * NX;
     float dummy[VL];
     load_row(e_m2, dummy, -2, ok_m2);
@@ -333,65 +342,15 @@ __device__ __forceinline__ void adj_rows(const StepArgs &a, const AdjTiledArgs &
             else adj_xfaces<LIM, VL, -1>(ex, lx, x0, NX, perx, anx, acc);
         }
         const int c = (zl * TY + (y - q.y0)) * NX + x0;
-        if constexpr (DIM == 3) {
-            // z: the face at this slice (values z-sz, z, z+sz) gives B here, A to slice z-sz and
-            // C to slice z+sz; a tile-edge slice also takes the face just outside the tile
-            // (z-sz: values z-2sz, z-sz, z, its C; z+sz: values z, z+sz, z+2sz, its A)
-            const bool in_up = zl - sz >= 0 && zl - sz < q.nzt, in_dn = zl + sz >= 0 && zl + sz < q.nzt;
-            const int z1 = adj_row(z - sz, nz, perz), z3 = adj_row(z + sz, nz, perz);
-            float e1[VL], e3[VL], l3[VL];
-            if (z1 >= 0) adj_ld_e<S, VL>(e1, a, e, base, cell_of(z1, y));
-            if (z3 >= 0) {
-                adj_ld_e<S, VL>(e3, a, e, base, cell_of(z3, y));
-                adj_ld_l<VL>(l3, lam, base + cell_of(z3, y));
-            }
-            float xA[VL], xC[VL];
-            #pragma unroll
-            for (int j = 0; j < VL; ++j) {
-                float A = 0.f, B = 0.f, C = 0.f;
-                if (z1 >= 0 && z3 >= 0) face_terms<LIM>(e1[j], e_0[j], e3[j], anz * (l3[j] - l_0[j]), A, B, C);
-                acc[j] += B;
-                xA[j] = A;
-                xC[j] = C;
-            }
-            #pragma unroll
-            for (int j = 0; j < VL; ++j) {
-                xa[c + j] = xA[j];
-                xa[p_tcells + c + j] = xC[j];
-            }
-            if (!in_up) {
-                const int z0 = adj_row(z - 2 * sz, nz, perz);
-                if (z0 >= 0 && z1 >= 0) {
-                    float e0v[VL], l1[VL];
-                    adj_ld_e<S, VL>(e0v, a, e, base, cell_of(z0, y));
-                    adj_ld_l<VL>(l1, lam, base + cell_of(z1, y));
-                    #pragma unroll
-                    for (int j = 0; j < VL; ++j) {
-                        float A, B, C;
-                        face_terms<LIM>(e0v[j], e1[j], e_0[j], anz * (l_0[j] - l1[j]), A, B, C);
-                        acc[j] += C;
-                    }
-                }
-            }
-            if (!in_dn) {
-                const int z4 = adj_row(z + 2 * sz, nz, perz);
-                if (z3 >= 0 && z4 >= 0) {
-                    float e4[VL], l4[VL];
-                    adj_ld_e<S, VL>(e4, a, e, base, cell_of(z4, y));
-                    adj_ld_l<VL>(l4, lam, base + cell_of(z4, y));
-                    #pragma unroll
-                    for (int j = 0; j < VL; ++j) {
-                        float A, B, C;
-                        face_terms<LIM>(e_0[j], e3[j], e4[j], anz * (l4[j] - l3[j]), A, B, C);
-                        acc[j] += A;
-                    }
-                }
-            }
-        }
         // relaxation, T_L coupling; store; per-cell and per-segment partials
         float mu[VL], tl[VL];
-        adj_ld_l<VL>(mu, g.mu_in, cl);
-        adj_ld_l<VL>(tl, a.TL, cl);
+        if (mtbox) {
+            adj_ld_l<VL>(mu, mtbox, c);
+            adj_ld_l<VL>(tl, mtbox + p_tcells, c);
+        } else {
+            adj_ld_l<VL>(mu, g.mu_in, cl);
+            adj_ld_l<VL>(tl, a.TL, cl);
+        }
         float out[VL];
         #pragma unroll
         for (int j = 0; j < VL; ++j) {
@@ -401,12 +360,7 @@ __device__ __forceinline__ void adj_rows(const StepArgs &a, const AdjTiledArgs &
             s1 = fmaf(lv, fmaf(b.ck, tl[j], -ev), s1);
             s2 = fmaf(wd * mu[j], ev, s2);
         }
-        if constexpr (DIM == 3) {
-            #pragma unroll
-            for (int j = 0; j < VL; ++j) outp[t][j] = out[j];
-        } else {
-            adj_emit<VL>(g, accm, accq, c, base + cl, bm, bq, out);
-        }
+        adj_emit<VL>(g, accm, accq, c, base + cl, bm, bq, out);
         // slide the window
         #pragma unroll
         for (int j = 0; j < VL; ++j) {
@@ -423,9 +377,229 @@ __device__ __forceinline__ void adj_rows(const StepArgs &a, const AdjTiledArgs &
         ok_0 = ok_p1;
         ok_p1 = ok_p2;
     }
-    if constexpr (DIM == 3) {
-        consumer_sync<Geo<DIM, WPR>::NCW>();  // every slice's A and C of this plane-tile are written
-        const bool in_up = zl - sz >= 0 && zl - sz < q.nzt, in_dn = zl + sz >= 0 && zl + sz < q.nzt;
+}
+
+// ---- 3-D plane-tiles: the box staged in shared memory ------------------------------------------
+// Box of a 3-D plane-tile: rows y0-2 .. y0+TY+1 by slices z0-2 .. z0+TZ+1 of every x, index
+// ((z - z0 + 2) RY + (y - y0 + 2)) NX + x (the reference box's layout).  All warps fill it with
+// 16-byte loads, e (16-bit: decoded against the references) in Eb and lambda^{n+1} in Lb;
+// positions beyond a wall hold 0 and are never used, and the corners (a halo row of a halo
+// slice) are not read at all.
+template <int S, int VL, int WPR, int DIM>
+__device__ __forceinline__ void adj_stage_box(const StepArgs &a, const AdjTiledArgs &g, const PT &q, const float *rbox,
+                                              float *Eb, float *Lb) {
+    using T = typename St<S>::T;
+    using Q = St<S>;
+    constexpr int NX = 32 * VL * WPR, TY = Geo<DIM, WPR>::TY, TZ = Geo<DIM, WPR>::TZ;
+    constexpr int RY = TY + 4, RZ = TZ + 4, NG = NX / 4, NT = Geo<DIM, WPR>::NCW * 32;
+    static_assert(NX % 4 == 0, "rows move in groups of four cells");
+    const int ny = a.n[1], nz = a.n[2];
+    const bool pery = a.bc[2] == kBcPeriodic, perz = a.bc[4] == kBcPeriodic;
+    const long long base = (long long)q.plane * a.ncell;
+    const T *e = static_cast<const T *>(a.e_in);
+    for (int gi = threadIdx.x; gi < RZ * RY * NG; gi += NT) {
+        const int xg = gi % NG, by = (gi / NG) % RY, bz = gi / (NG * RY);
+        if ((by < 2 || by >= TY + 2) && (bz < 2 || bz >= TZ + 2)) continue;
+        const int idx = (bz * RY + by) * NX + 4 * xg;
+        const int yy = adj_row(q.y0 - 2 + by, ny, pery), zz = adj_row(q.z0 - 2 + bz, nz, perz);
+        float4 ev = make_float4(0.f, 0.f, 0.f, 0.f), lv = ev;
+        if (yy >= 0 && zz >= 0) {
+            const long long cell = ((long long)zz * ny + yy) * NX + 4 * xg;
+            lv = *reinterpret_cast<const float4 *>(g.lam_in + base + cell);
+            if constexpr (Q::kRef) {
+                const uint2 h = *reinterpret_cast<const uint2 *>(e + base + cell);
+                float4 r;
+                if (rbox) {
+                    r = *reinterpret_cast<const float4 *>(rbox + idx);
+                } else {
+                    const float4 R = *reinterpret_cast<const float4 *>(a.R + cell);
+                    r = make_float4(R.x * a.invTs, R.y * a.invTs, R.z * a.invTs, R.w * a.invTs);
+                }
+                ev = make_float4(r.x + Q::val(h.x & 0xffffu), r.y + Q::val(h.x >> 16), r.z + Q::val(h.y & 0xffffu),
+                                 r.w + Q::val(h.y >> 16));
+            } else {
+                ev = *reinterpret_cast<const float4 *>(e + base + cell);
+            }
+        }
+        *reinterpret_cast<float4 *>(Eb + idx) = ev;
+        *reinterpret_cast<float4 *>(Lb + idx) = lv;
+    }
+}
+
+template <int VL>
+__device__ __forceinline__ void ld_box(float (&v)[VL], const float *p) {
+    if constexpr (VL == 4) {
+        const float4 f = *reinterpret_cast<const float4 *>(p);
+        v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+    } else {
+        #pragma unroll
+        for (int j = 0; j < VL; ++j) v[j] = p[j];
+    }
+}
+
+// One 3-D plane-tile, called by every warp of the block.  (0) All warps stage the box.  (1)
+// Each warp streams its rows along y from the box: y faces in registers, x faces by shuffle,
+// and the z face at its own slice (values z-sz, z, z+sz), whose B stays here while A (for
+// slice z-sz) and C (for slice z+sz) go to xa / xa + tcells; a tile-edge slice also takes the
+// face just outside the tile.  (2) After the second barrier each warp adds the terms its
+// neighbour slices left and writes lambda^n.  The two barriers also order the reuse of the
+// box and of xa by the next plane-tile.
+template <int S, int LIM, int VL, int WPR, int DIM>
+__device__ __forceinline__ void adj_tile3(const StepArgs &a, const AdjTiledArgs &g, const PT &q, int zl, int rb, int half,
+                                          float *accm, float *accq, float &s1, float &s2, float *xa, const float *rbox,
+                                          const float *mtbox, float *Eb, float *Lb) {
+    static_assert(DIM == 3, "3-D plane-tiles");
+    constexpr int NX = 32 * VL * WPR, TY = Geo<DIM, WPR>::TY, TZ = Geo<DIM, WPR>::TZ, NCW = Geo<DIM, WPR>::NCW;
+    constexpr int RY = TY + 4, kR = Geo<DIM, WPR>::KR, TC = TY * TZ * NX;
+    adj_stage_box<S, VL, WPR, DIM>(a, g, q, rbox, Eb, Lb);
+    consumer_sync<NCW>();  // the box is complete
+    const bool act = zl < q.nzt && rb < q.nyt;
+    const int lane = threadIdx.x & 31, x0 = (half * 32 + lane) * VL;
+    const int ny = a.n[1], nz = a.n[2];
+    const int plane = q.plane;
+    const long long base = (long long)plane * a.ncell;
+    const BandConst b = a.band[q.k];
+    const float nux = a.nu[3 * plane], nuy = a.nu[3 * plane + 1], nuz = a.nu[3 * plane + 2];
+    const float anx = fabsf(nux), any = fabsf(nuy), anz = fabsf(nuz);
+    const int sx = nux > 0.f ? 1 : -1, sy = nuy > 0.f ? 1 : -1, sz = nuz > 0.f ? 1 : -1;
+    const bool perx = a.bc[0] == kBcPeriodic, pery = a.bc[2] == kBcPeriodic, perz = a.bc[4] == kBcPeriodic;
+    const float diag = 1.f - b.dtinv, wmD = a.wmom[plane] * a.invD, wd = g.w[q.d];
+    const float sc = St<S>::kRef ? b.scale : 1.f;  // e = sc * (value in the kernel)
+    const float bm = b.dtinv * b.ck, bq = b.srck;
+    const int nrows = act ? min(kR, q.nyt - rb) : 0;
+    const int z = q.z0 + zl;
+    const int y0w = q.y0 + (sy > 0 ? rb : rb + nrows - 1);
+    // this lane's cells of (unwrapped) row yu at slice offset dzs from z in the box
+    auto box_at = [&](const float *B, int dzs, int yu) { return B + ((zl + 2 + dzs) * RY + (yu - q.y0 + 2)) * NX + x0; };
+    const bool in_up = zl - sz >= 0 && zl - sz < q.nzt, in_dn = zl + sz >= 0 && zl + sz < q.nzt;
+    const bool zok1 = adj_row(z - sz, nz, perz) >= 0, zok3 = adj_row(z + sz, nz, perz) >= 0;
+    const bool zok0 = adj_row(z - 2 * sz, nz, perz) >= 0, zok4 = adj_row(z + 2 * sz, nz, perz) >= 0;
+    float outp[kR][VL];
+    if (act) {
+        // y window: e at t-2 .. t+2 (rows), lambda at t-1 .. t+2; faces F_{t+1} computed per step
+        float e_m2[VL], e_m1[VL], e_0[VL], e_p1[VL], e_p2[VL], l_m1[VL], l_0[VL], l_p1[VL], l_p2[VL];
+        float Bprev[VL], Cprev[VL], Cprev2[VL];
+        bool ok_m2, ok_m1, ok_0, ok_p1, ok_p2;
+        auto load_row = [&](float (&ev)[VL], float (&lv)[VL], int t, bool &ok, bool withl) {
+            const int yu = y0w + t * sy;
+            ok = adj_row(yu, ny, pery) >= 0;
+            ld_box<VL>(ev, box_at(Eb, 0, yu));
+            if (withl) ld_box<VL>(lv, box_at(Lb, 0, yu));
+        };
+        float dummy[VL];
+        load_row(e_m2, dummy, -2, ok_m2, false);
+        load_row(e_m1, l_m1, -1, ok_m1, true);
+        load_row(e_0, l_0, 0, ok_0, true);
+        load_row(e_p1, l_p1, 1, ok_p1, true);
+        #pragma unroll
+        for (int j = 0; j < VL; ++j) {
+            float A, B, C;
+            if (ok_m2 && ok_m1 && ok_0) face_terms<LIM>(e_m2[j], e_m1[j], e_0[j], any * (l_0[j] - l_m1[j]), A, B, C);
+            else A = B = C = 0.f;
+            Cprev[j] = C;
+            if (ok_m1 && ok_0 && ok_p1) face_terms<LIM>(e_m1[j], e_0[j], e_p1[j], any * (l_p1[j] - l_0[j]), A, B, C);
+            else A = B = C = 0.f;
+            Bprev[j] = B;
+            Cprev2[j] = C;
+        }
+        #pragma unroll
+        for (int t = 0; t < kR; ++t) {
+            if (t >= nrows) break;
+            const int y = y0w + t * sy;
+            const int c = (zl * TY + (y - q.y0)) * NX + x0;
+            load_row(e_p2, l_p2, t + 2, ok_p2, true);
+            float acc[VL];
+            #pragma unroll
+            for (int j = 0; j < VL; ++j) {
+                float A, B, C;
+                if (ok_0 && ok_p1 && ok_p2) face_terms<LIM>(e_0[j], e_p1[j], e_p2[j], any * (l_p2[j] - l_p1[j]), A, B, C);
+                else A = B = C = 0.f;
+                acc[j] = A + Bprev[j] + Cprev[j];
+                Cprev[j] = Cprev2[j];
+                Bprev[j] = B;
+                Cprev2[j] = C;
+            }
+            if (sx > 0) adj_xfaces_w<LIM, VL, 1>(e_0, l_0, x0, NX, perx, anx, lane, acc);
+            else adj_xfaces_w<LIM, VL, -1>(e_0, l_0, x0, NX, perx, anx, lane, acc);
+            // z: the face at this slice, and the tile-edge faces
+            {
+                float e1[VL], e3[VL], l3[VL];
+                ld_box<VL>(e1, box_at(Eb, -sz, y));
+                ld_box<VL>(e3, box_at(Eb, sz, y));
+                ld_box<VL>(l3, box_at(Lb, sz, y));
+                float xA[VL], xC[VL];
+                #pragma unroll
+                for (int j = 0; j < VL; ++j) {
+                    float A = 0.f, B = 0.f, C = 0.f;
+                    if (zok1 && zok3) face_terms<LIM>(e1[j], e_0[j], e3[j], anz * (l3[j] - l_0[j]), A, B, C);
+                    acc[j] += B;
+                    xA[j] = A;
+                    xC[j] = C;
+                }
+                #pragma unroll
+                for (int j = 0; j < VL; ++j) {
+                    xa[c + j] = xA[j];
+                    xa[TC + c + j] = xC[j];
+                }
+                if (!in_up && zok0 && zok1) {
+                    float e0v[VL], l1[VL];
+                    ld_box<VL>(e0v, box_at(Eb, -2 * sz, y));
+                    ld_box<VL>(l1, box_at(Lb, -sz, y));
+                    #pragma unroll
+                    for (int j = 0; j < VL; ++j) {
+                        float A, B, C;
+                        face_terms<LIM>(e0v[j], e1[j], e_0[j], anz * (l_0[j] - l1[j]), A, B, C);
+                        acc[j] += C;
+                    }
+                }
+                if (!in_dn && zok3 && zok4) {
+                    float e4[VL], l4[VL];
+                    ld_box<VL>(e4, box_at(Eb, 2 * sz, y));
+                    ld_box<VL>(l4, box_at(Lb, 2 * sz, y));
+                    #pragma unroll
+                    for (int j = 0; j < VL; ++j) {
+                        float A, B, C;
+                        face_terms<LIM>(e_0[j], e3[j], e4[j], anz * (l4[j] - l3[j]), A, B, C);
+                        acc[j] += A;
+                    }
+                }
+            }
+            // relaxation, T_L coupling and the segment scalars
+            float mu[VL], tl[VL];
+            const long long cl = ((long long)z * ny + y) * NX + x0;
+            if (mtbox) {
+                adj_ld_l<VL>(mu, mtbox, c);
+                adj_ld_l<VL>(tl, mtbox + TC, c);
+            } else {
+                adj_ld_l<VL>(mu, g.mu_in, cl);
+                adj_ld_l<VL>(tl, a.TL, cl);
+            }
+            #pragma unroll
+            for (int j = 0; j < VL; ++j) {
+                const float lv = l_0[j];
+                outp[t][j] = fmaf(diag, lv, fmaf(wmD, mu[j], acc[j]));
+                const float ev = sc * e_0[j];
+                s1 = fmaf(lv, fmaf(b.ck, tl[j], -ev), s1);
+                s2 = fmaf(wd * mu[j], ev, s2);
+            }
+            #pragma unroll
+            for (int j = 0; j < VL; ++j) {
+                e_m2[j] = e_m1[j];
+                e_m1[j] = e_0[j];
+                e_0[j] = e_p1[j];
+                e_p1[j] = e_p2[j];
+                l_m1[j] = l_0[j];
+                l_0[j] = l_p1[j];
+                l_p1[j] = l_p2[j];
+            }
+            ok_m2 = ok_m1;
+            ok_m1 = ok_0;
+            ok_0 = ok_p1;
+            ok_p1 = ok_p2;
+        }
+    }
+    consumer_sync<NCW>();  // every slice's A and C of this plane-tile are written
+    if (act) {
         const int dzc = sz * TY * NX;
         #pragma unroll
         for (int t = 0; t < kR; ++t) {
@@ -436,11 +610,44 @@ __device__ __forceinline__ void adj_rows(const StepArgs &a, const AdjTiledArgs &
             #pragma unroll
             for (int j = 0; j < VL; ++j) {
                 float v = outp[t][j];
-                if (in_up) v += xa[p_tcells + c - dzc + j];  // C of the face at slice z-sz
-                if (in_dn) v += xa[c + dzc + j];             // A of the face at slice z+sz
+                if (in_up) v += xa[TC + c - dzc + j];  // C of the face at slice z-sz
+                if (in_dn) v += xa[c + dzc + j];       // A of the face at slice z+sz
                 out[j] = v;
             }
-            adj_emit<VL>(g, accm, accq, c, base + cell_of(z, y), bm, bq, out);
+            adj_emit<VL>(g, accm, accq, c, base + ((long long)z * ny + y) * NX + x0, bm, bq, out);
+        }
+    }
+}
+
+// A unit's shared copies: the code references R / T_scale of rows y0-2 .. y0+TY+1 (and slices
+// z0-2 .. z0+TZ+1) of every x, wrapped on a periodic axis (positions beyond a wall are never
+// read: faces reading them belong to the wall pass), and mu^{n+1}, T_L^n of the tile's cells.
+template <int S, int VL, int WPR, int DIM>
+__device__ void adj_fill_boxes(const StepArgs &a, const AdjTiledArgs &g, const PT &q, float *rbox, float *mtbox) {
+    constexpr int NX = 32 * VL * WPR, TY = Geo<DIM, WPR>::TY, TZ = Geo<DIM, WPR>::TZ;
+    constexpr int RY = TY + 4, RZ = DIM == 3 ? TZ + 4 : 1, NT = Geo<DIM, WPR>::NCW * 32;
+    const int ny = a.n[1], nz = a.n[2];
+    const bool pery = a.bc[2] == kBcPeriodic, perz = DIM == 3 && a.bc[4] == kBcPeriodic;
+    if constexpr (St<S>::kRef) {
+        for (int idx = threadIdx.x; idx < RZ * RY * NX; idx += NT) {
+            const int x = idx % NX, ry = (idx / NX) % RY, rz = idx / (NX * RY);
+            const int y = adj_row(q.y0 - 2 + ry, ny, pery);
+            const int z = DIM == 3 ? adj_row(q.z0 - 2 + rz, nz, perz) : 0;
+            rbox[idx] = (y >= 0 && z >= 0) ? a.R[((long long)z * ny + y) * NX + x] * a.invTs : 0.f;
+        }
+    }
+    if (mtbox) {
+        constexpr int TC = TY * TZ * NX;
+        for (int idx = threadIdx.x; idx < TC; idx += NT) {
+            const int x = idx % NX, yl = (idx / NX) % TY, zl = idx / (NX * TY);
+            float mu = 0.f, tl = 0.f;
+            if (yl < q.nyt && zl < q.nzt) {
+                const long long cell = ((long long)(q.z0 + zl) * ny + q.y0 + yl) * NX + x;
+                mu = g.mu_in[cell];
+                tl = a.TL[cell];
+            }
+            mtbox[idx] = mu;
+            mtbox[TC + idx] = tl;
         }
     }
 }
@@ -453,8 +660,15 @@ __global__ void __launch_bounds__(Geo<DIM, WPR>::NCW * 32, 1) k_adj_tiled(const 
     float *accm = reinterpret_cast<float *>(smem);
     float *accq = accm + p.tcells;
     float *red = accq + p.tcells;  // [2][NCW]
-    // 3-D: z-face terms passed between slices, [2 plane-tile parities][A, C][tcells]
+    // 3-D: the z-face terms passed between slices [A, C][tcells], then the plane-tile's box of
+    // e and of lambda^{n+1}
+    constexpr int RB = (TY + 4) * (DIM == 3 ? Geo<DIM, WPR>::TZ + 4 : 1) * NX;
     float *xbuf = red + 2 * NCW;
+    float *Eb = xbuf + (DIM == 3 ? 2 * p.tcells : 0), *Lb = Eb + RB;
+    // 16-bit storage: the unit's reference box (where it fits); then, if they fit, mu and T_L of
+    // the tile
+    float *rbox = g.cache_r ? (DIM == 3 ? Lb + RB : xbuf) : nullptr;
+    float *mtbox = g.cache_mt ? (rbox ? rbox + RB : (DIM == 3 ? Lb + RB : xbuf)) : nullptr;
     for (int j = threadIdx.x; j < 2 * p.tcells; j += blockDim.x) accm[j] = 0.f;
     __syncthreads();
     int zl, rb, half;
@@ -513,18 +727,23 @@ __global__ void __launch_bounds__(Geo<DIM, WPR>::NCW * 32, 1) k_adj_tiled(const 
     };
     Cursor<DIM, WPR> c;
     bool more = c.start(a, p);
-    for (int i = 0; more; ++i, more = c.next(a, p)) {
+    for (; more; more = c.next(a, p)) {
         const PT q = c.q;
         if (c.u != cur_unit || q.k != cur_band) {
-            if (seg >= 0) flush();
+            if (seg >= 0) flush();  // ends with a block barrier: no warp reads the old unit's boxes
+            if (c.u != cur_unit && (rbox || mtbox)) {
+                adj_fill_boxes<S, VL, WPR, DIM>(a, g, q, rbox, mtbox);
+                __syncthreads();
+            }
             seg = p.unit_seg0[c.u] + q.k - c.p0 / a.nd;
             cur_unit = c.u;
             cur_band = q.k;
             cur = q;
         }
-        float *xa = xbuf + (size_t)(i & 1) * 2 * p.tcells;
-        if (zl < q.nzt && rb < q.nyt) adj_rows<S, LIM, VL, WPR, DIM>(a, g, q, zl, rb, half, accm, accq, s1, s2, xa);
-        else if constexpr (DIM == 3) consumer_sync<NCW>();  // the z exchange's barrier
+        if constexpr (DIM == 3)
+            adj_tile3<S, LIM, VL, WPR, DIM>(a, g, q, zl, rb, half, accm, accq, s1, s2, xbuf, rbox, mtbox, Eb, Lb);
+        else if (zl < q.nzt && rb < q.nyt)
+            adj_rows<S, LIM, VL, WPR, DIM>(a, g, q, zl, rb, half, accm, accq, s1, s2, rbox, mtbox);
     }
     if (seg >= 0) flush();
 }
