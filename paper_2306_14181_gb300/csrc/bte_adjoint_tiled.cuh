@@ -397,32 +397,48 @@ __device__ __forceinline__ void adj_stage_box(const StepArgs &a, const AdjTiledA
     const bool pery = a.bc[2] == kBcPeriodic, perz = a.bc[4] == kBcPeriodic;
     const long long base = (long long)q.plane * a.ncell;
     const T *e = static_cast<const T *>(a.e_in);
-    for (int gi = threadIdx.x; gi < RZ * RY * NG; gi += NT) {
-        const int xg = gi % NG, by = (gi / NG) % RY, bz = gi / (NG * RY);
-        if ((by < 2 || by >= TY + 2) && (bz < 2 || bz >= TZ + 2)) continue;
-        const int idx = (bz * RY + by) * NX + 4 * xg;
-        const int yy = adj_row(q.y0 - 2 + by, ny, pery), zz = adj_row(q.z0 - 2 + bz, nz, perz);
-        float4 ev = make_float4(0.f, 0.f, 0.f, 0.f), lv = ev;
-        if (yy >= 0 && zz >= 0) {
-            const long long cell = ((long long)zz * ny + yy) * NX + 4 * xg;
-            lv = *reinterpret_cast<const float4 *>(g.lam_in + base + cell);
-            if constexpr (Q::kRef) {
-                const uint2 h = *reinterpret_cast<const uint2 *>(e + base + cell);
-                float4 r;
-                if (rbox) {
-                    r = *reinterpret_cast<const float4 *>(rbox + idx);
+    // groups of four cells, UB per thread in flight before their stores
+    constexpr int TOT = RZ * RY * NG, UB = 8;
+    for (int g0 = 0; g0 < TOT; g0 += UB * NT) {
+        float4 ev[UB], lv[UB];
+        #pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            ev[u] = lv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            const int gi = g0 + u * NT + (int)threadIdx.x;
+            const int xg = gi % NG, by = (gi / NG) % RY, bz = gi / (NG * RY);
+            const int yy = adj_row(q.y0 - 2 + by, ny, pery), zz = adj_row(q.z0 - 2 + bz, nz, perz);
+            const bool corner = (by < 2 || by >= TY + 2) && (bz < 2 || bz >= TZ + 2);
+            if (gi < TOT && !corner && yy >= 0 && zz >= 0) {
+                const int idx = (bz * RY + by) * NX + 4 * xg;
+                const long long cell = ((long long)zz * ny + yy) * NX + 4 * xg;
+                lv[u] = *reinterpret_cast<const float4 *>(g.lam_in + base + cell);
+                if constexpr (Q::kRef) {
+                    const uint2 h = *reinterpret_cast<const uint2 *>(e + base + cell);
+                    float4 r;
+                    if (rbox) {
+                        r = *reinterpret_cast<const float4 *>(rbox + idx);
+                    } else {
+                        const float4 R = *reinterpret_cast<const float4 *>(a.R + cell);
+                        r = make_float4(R.x * a.invTs, R.y * a.invTs, R.z * a.invTs, R.w * a.invTs);
+                    }
+                    ev[u] = make_float4(r.x + Q::val(h.x & 0xffffu), r.y + Q::val(h.x >> 16),
+                                        r.z + Q::val(h.y & 0xffffu), r.w + Q::val(h.y >> 16));
                 } else {
-                    const float4 R = *reinterpret_cast<const float4 *>(a.R + cell);
-                    r = make_float4(R.x * a.invTs, R.y * a.invTs, R.z * a.invTs, R.w * a.invTs);
+                    ev[u] = *reinterpret_cast<const float4 *>(e + base + cell);
                 }
-                ev = make_float4(r.x + Q::val(h.x & 0xffffu), r.y + Q::val(h.x >> 16), r.z + Q::val(h.y & 0xffffu),
-                                 r.w + Q::val(h.y >> 16));
-            } else {
-                ev = *reinterpret_cast<const float4 *>(e + base + cell);
             }
         }
-        *reinterpret_cast<float4 *>(Eb + idx) = ev;
-        *reinterpret_cast<float4 *>(Lb + idx) = lv;
+        #pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            const int gi = g0 + u * NT + (int)threadIdx.x;
+            const int xg = gi % NG, by = (gi / NG) % RY, bz = gi / (NG * RY);
+            const bool corner = (by < 2 || by >= TY + 2) && (bz < 2 || bz >= TZ + 2);
+            if (gi < TOT && !corner) {
+                const int idx = (bz * RY + by) * NX + 4 * xg;
+                *reinterpret_cast<float4 *>(Eb + idx) = ev[u];
+                *reinterpret_cast<float4 *>(Lb + idx) = lv[u];
+            }
+        }
     }
 }
 
