@@ -103,6 +103,8 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // Limiter.  Van Albada, L = max(ab, 0) (a + b) / (a^2 + b^2 + 1e-30): the approximate
 // reciprocal of a denominator that is always a normal number, and no compare or select (pairs
 // with ab <= 0 give a zero numerator; the 1e-30 changes L by a relative 1e-30 / (a^2 + b^2)).
+// max(ab, 0) is taken as (ab + |ab|) / 2, an add on the FMA pipe instead of a min/max on the
+// busier ALU pipe; the factors of 2 are exact, so the result is the same.
 constexpr float kVaTiny = 1e-30f;
 template <int LIM> __device__ __forceinline__ float lim(float a, float b);
 template <> __device__ __forceinline__ float lim<kLimFirst>(float, float) { return 0.f; }
@@ -111,7 +113,8 @@ template <> __device__ __forceinline__ float lim<kLimMinmod>(float a, float b) {
     return a * b > 0.f ? m : 0.f;
 }
 template <> __device__ __forceinline__ float lim<kLimVanAlbada>(float a, float b) {
-    return fmaxf(a * b, 0.f) * (a + b) * rcp_approx(fmaf(a, a, fmaf(b, b, kVaTiny)));
+    const float ab = a * b;
+    return 0.5f * ((ab + fabsf(ab)) * (a + b)) * rcp_approx(fmaf(a, a, fmaf(b, b, kVaTiny)));
 }
 // face value e_m + L(e_m - e_l, e_r - e_m) / 2 at the upwind cell m
 template <int LIM> __device__ __forceinline__ float face(float ul, float um, float ur) {
@@ -134,10 +137,11 @@ template <> __device__ __forceinline__ float2 face2<kLimMinmod>(float2 ul, float
 template <> __device__ __forceinline__ float2 face2<kLimVanAlbada>(float2 ul, float2 um, float2 ur) {
     const float2 a = sub2(um, ul), b = sub2(ur, um);
     const float2 ab = __fmul2_rn(a, b);
-    const float2 num = __fmul2_rn(make_float2(fmaxf(ab.x, 0.f), fmaxf(ab.y, 0.f)), __fadd2_rn(a, b));
+    // (ab + |ab|) = 2 max(ab, 0), the 2 taken out by the final 1/4
+    const float2 num = __fmul2_rn(make_float2(ab.x + fabsf(ab.x), ab.y + fabsf(ab.y)), __fadd2_rn(a, b));
     const float2 den = __ffma2_rn(a, a, __ffma2_rn(b, b, f2(kVaTiny)));
     const float2 L = __fmul2_rn(num, make_float2(rcp_approx(den.x), rcp_approx(den.y)));
-    return __ffma2_rn(f2(0.5f), L, um);
+    return __ffma2_rn(f2(0.25f), L, um);
 }
 
 // out[i] = face(ul[i], um[i], ur[i]) for i < N, two at a time
