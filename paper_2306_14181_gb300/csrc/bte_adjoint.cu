@@ -18,6 +18,7 @@
 // spread back over the wall cell's outgoing directions with weights w (s.n) / sum_in w|s.n|.
 // One thread per (cell, band) loops over the band's directions, as the generic forward does.
 #include <algorithm>
+#include <cstdlib>
 
 #include "bte_device.cuh"
 #include "bte_adjoint.h"
@@ -297,6 +298,7 @@ __device__ __forceinline__ int wall_slot(int pos, int n) { return pos < 2 ? pos 
 // z walls).  scratch[((k nd + d) 8 + 4 side + j) nlines + line], j = 0, 1: additions to the
 // wall cell and the next cell of the same plane; j = 2, 3: adjoints of ghost layers 1 and 2.
 constexpr int kWallThreads = 128;
+constexpr long long kWallLineThreads = 65536;  // (line, band) pairs from which phase 2 takes a thread each
 
 template <int S, int LIM>
 __global__ void __launch_bounds__(kWallThreads) k_adj_walls_a(const StepArgs a, const AdjArgs g, int ax,
@@ -358,7 +360,74 @@ __global__ void __launch_bounds__(kWallThreads) k_adj_walls_a(const StepArgs a, 
     }
 }
 
-// Phase 2: one block per (line, band), threads over the directions: the ghost transposes
+// Phase 2 for many lines: one thread per (line, band), threads along the lines, each looping
+// over the directions in order: the ghost transposes (specular: the mirrored direction's ghost adjoints;
+// thermalizing or diffuse outgoing: the direction's own; diffuse incoming: summed over the
+// entering directions, in order, and spread over the leaving ones), each direction's additions
+// added to lambda^n, and the per-position sums over the directions, in order, to corr.  Reads of
+// the scratch rows and, for y and z walls, the lambda^n updates are coalesced across threads.
+__global__ void __launch_bounds__(kWallThreads) k_adj_walls_bl(const StepArgs a, int ax, const float *scratch,
+                                                               float *lam_out, float *corr, long long nlines) {
+    const long long line = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (line >= nlines) return;
+    const int k = blockIdx.y;
+    const int nd = a.nd, n = a.n[ax];
+    int c[3];
+    {
+        const int o1 = ax == 0 ? 1 : 0, o2 = ax == 2 ? 1 : 2;
+        c[ax] = 0;
+        c[o1] = (int)(line % a.n[o1]);
+        c[o2] = (int)(line / a.n[o1]);
+    }
+    const long long i0 = ((long long)c[2] * a.n[1] + c[1]) * a.n[0] + c[0];
+    const long long st = a.stride[ax];
+    auto sc = [&](int d, int j) { return scratch[((long long)(k * nd + d) * 8 + j) * nlines + line]; };
+    float gam[2] = {0.f, 0.f};
+    for (int side = 0; side < 2; ++side) {
+        const int in = side ? -1 : 1;
+        if (a.bc[2 * ax + side] != kBcDiffuse) continue;
+        float sum = 0.f;
+        for (int d = 0; d < nd; ++d) {
+            const float nu = a.nu[3 * (k * nd + d) + ax];
+            if (nu != 0.f && (nu > 0.f ? 1 : -1) == in) sum += sc(d, 4 * side + 2) + sc(d, 4 * side + 3);
+        }
+        gam[side] = sum;
+    }
+    float tot[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int d = 0; d < nd; ++d) {
+        const float nu = a.nu[3 * (k * nd + d) + ax];
+        float dv[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int side = 0; side < 2; ++side) {
+            const int wall = 2 * ax + side, bc = a.bc[wall];
+            if (bc == kBcPeriodic) continue;
+            const int w0 = side ? n - 1 : 0, in = side ? -1 : 1;
+            float v0 = sc(d, 4 * side), v1 = sc(d, 4 * side + 1);
+            const bool leaving = nu != 0.f && (nu > 0.f ? 1 : -1) != in;
+            if (bc == kBcSpecular) {
+                const int dm = a.mirror[ax * nd + d];
+                v0 += sc(dm, 4 * side + 2);
+                v1 += sc(dm, 4 * side + 3);
+            } else if (leaving) {
+                v0 += sc(d, 4 * side + 2);
+            }
+            if (bc == kBcDiffuse) v0 = fmaf(a.wdiff[wall * nd + d] * a.inv_den[wall], gam[side], v0);
+            dv[wall_slot(w0, n)] += v0;
+            dv[wall_slot(w0 + in, n)] += v1;
+        }
+        const long long pb = (long long)(k * nd + d) * a.ncell + i0;
+        #pragma unroll
+        for (int sl = 0; sl < 4; ++sl) {
+            tot[sl] += dv[sl];
+            const int pos = sl < 2 ? sl : n - 2 + (sl - 2);
+            if (dv[sl] != 0.f && (sl < 2 || pos >= 2)) lam_out[pb + (long long)pos * st] += dv[sl];
+        }
+    }
+    #pragma unroll
+    for (int sl = 0; sl < 4; ++sl) corr[((long long)k * 4 + sl) * nlines + line] = tot[sl];
+}
+
+// Phase 2 for few lines: one block per (line, band), threads over the directions (the same
+// sums, in the same order): the ghost transposes
 // (specular: the mirrored direction's ghost adjoints; thermalizing or diffuse outgoing: the
 // direction's own; diffuse incoming: summed over the entering directions, in order, and spread
 // over the leaving ones), each direction's additions written to lambda^n by its own thread,
@@ -517,7 +586,7 @@ cudaError_t launch_adj_walls(const StepArgs &a, const AdjArgs &g, int storage, i
         const int o1 = ax == 0 ? 1 : 0, o2 = ax == 2 ? 1 : 2;
         const long long nl = (long long)a.n[o1] * a.n[o2];
         const unsigned nbl = (unsigned)((nl + kWallThreads - 1) / kWallThreads);
-        const dim3 ga(nbl, (unsigned)a.nd, (unsigned)a.nb), gb((unsigned)nl, (unsigned)a.nb);
+        const dim3 ga(nbl, (unsigned)a.nd, (unsigned)a.nb);
 #define BTE_ADJW(SS, LL) k_adj_walls_a<SS, LL><<<ga, kWallThreads, 0, s>>>(a, g, ax, scratch, nl)
         if (storage == kStoreF32) {
             if (limiter == kLimFirst) BTE_ADJW(kStoreF32, kLimFirst);
@@ -533,8 +602,17 @@ cudaError_t launch_adj_walls(const StepArgs &a, const AdjArgs &g, int storage, i
             else BTE_ADJW(kStoreBF16, kLimVanAlbada);
         }
 #undef BTE_ADJW
-        const int tb = std::min(kWallThreads, (a.nd + 31) / 32 * 32);  // no idle warp for nd < 128
-        k_adj_walls_b<<<gb, tb, (size_t)8 * a.nd * sizeof(float), s>>>(a, ax, scratch, lam_out, corr[ax], nl);
+        // a thread per (line, band) when they fill the GPU many times over, else a block each
+        // (BTE_ADJ_WALL_LINES overrides the bound, for tests of both forms)
+        long long lines_min = kWallLineThreads;
+        if (const char *env = std::getenv("BTE_ADJ_WALL_LINES")) lines_min = std::atoll(env);
+        if (nl * a.nb >= lines_min) {
+            k_adj_walls_bl<<<dim3(nbl, (unsigned)a.nb), kWallThreads, 0, s>>>(a, ax, scratch, lam_out, corr[ax], nl);
+        } else {
+            const int tb = std::min(kWallThreads, (a.nd + 31) / 32 * 32);  // no idle warp for nd < 128
+            k_adj_walls_b<<<dim3((unsigned)nl, (unsigned)a.nb), tb, (size_t)8 * a.nd * sizeof(float), s>>>(
+                a, ax, scratch, lam_out, corr[ax], nl);
+        }
     }
     return cudaGetLastError();
 }

@@ -145,6 +145,23 @@ def test_adjoint_with_16bit_state(storage, tol):
     assert np.max(np.abs(gt - gto)) <= tol * np.max(np.abs(gto))
 
 
+@pytest.mark.parametrize("storage", [0, 1])
+def test_wall_combine_forms_agree(storage, monkeypatch):
+    """The diffuse/specular/isothermal wall pass combines the directions either with a thread per
+    (line, band) (many lines) or with a block per (line, band) (few lines); both sum in the same
+    order, so the gradients agree bit for bit (the second form is checked against the oracle by
+    the other cases)."""
+    nsteps = 6
+    out = []
+    for lines_min in ("0", str(1 << 40)):
+        monkeypatch.setenv("BTE_ADJ_WALL_LINES", lines_min)
+        cfg, P, ctx, Q, amps, dT0, p = _setup(3, (96, 9, 7), [DIF, ISO, SPE, SPE, ISO, DIF], 2, 2, nsteps,
+                                              storage=storage)
+        out.append(_gpu_adjoint(ctx, Q, amps, dT0, p, nsteps))
+    (J0, gQ0, gt0), (J1, gQ1, gt1) = out
+    assert J0 == J1 and np.array_equal(gQ0, gQ1) and np.array_equal(gt0, gt1)
+
+
 def test_autograd_function():
     """torch.autograd through ProbeTemperature: the gradients are the adjoint's."""
     import torch
