@@ -507,8 +507,10 @@ __device__ void producer(const StepArgs &a, const TiledArgs &p, char *smem, uint
 enum { kGhShfl = 0, kGhSmem = 1, kGhSpec = 2, kGhDiff = 3, kGhConst = 4, kGhOwn = 5 };
 
 // SY, SX: signs of the direction's y and x components (+1 when positive, else -1), fixed per
-// instance so that row steps are constants and the x faces need no orientation branch.
-template <int S, int LIM, int VL, int WPR, int DIM, bool SR, int SY, int SX>
+// instance so that row steps are constants and the x faces need no orientation branch.  FULL:
+// the warp's KR rows all lie in the tile (every tile but a ragged last one), so the row loop
+// carries no exit test.
+template <int S, int LIM, int VL, int WPR, int DIM, bool SR, int SY, int SX, bool FULL>
 __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs &p, const PT &q, const char *stage,
                                              int zl, int rb, int half, float *accsm, const float *btsm, float *wsm,
                                              const float *rbox) {
@@ -525,7 +527,7 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
     constexpr int sy = SY;
     const int sz = nuz > 0.f ? 1 : -1;
     constexpr int kR = Geo<DIM, WPR>::KR;
-    const int nrows = min(kR, q.nyt - rb);
+    const int nrows = FULL ? kR : min(kR, q.nyt - rb);
     const int yl0 = sy > 0 ? rb : rb + nrows - 1;  // first row in streaming (upwind-to-downwind) order
     const int ybox0 = q.y0 - (sy > 0 ? 2 : 1);
     const int zbox0 = DIM == 3 ? q.z0 - (sz > 0 ? 2 : 1) : 0;
@@ -628,7 +630,7 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
     faces<LIM, VL>(wm2, wm1, w0, fin);
     #pragma unroll
     for (int j = 0; j < kR; ++j) {
-        if (j >= nrows) break;
+        if (!FULL && j >= nrows) break;
         const int y = q.y0 + yl0 + j * sy;
         ld_row<S, VL>(wp1, box + o + dy + x0, rbox + ro + dyR + x0);
         float fout[VL];
@@ -911,13 +913,16 @@ __device__ void consumer(const StepArgs &a, const TiledArgs &p, char *smem, uint
         if (zl < q.nzt && rb < q.nyt) {
             const float *hd = reinterpret_cast<const float *>(stage + p.hdr_off);
             const bool px = hd[0] > 0.f, py = hd[1] > 0.f;  // the signs rows_of_warp takes
-            if (py) {
-                if (px) rows_of_warp<S, LIM, VL, WPR, DIM, SR, 1, 1>(a, p, q, stage, zl, rb, half, accsm, btsm, wsm, rbox);
-                else rows_of_warp<S, LIM, VL, WPR, DIM, SR, 1, -1>(a, p, q, stage, zl, rb, half, accsm, btsm, wsm, rbox);
+            const bool full = rb + Geo<DIM, WPR>::KR <= q.nyt;
+#define BTE_ROWS(SY_, SX_, F_) rows_of_warp<S, LIM, VL, WPR, DIM, SR, SY_, SX_, F_>(a, p, q, stage, zl, rb, half, accsm, btsm, wsm, rbox)
+            if (full) {
+                if (py) { if (px) BTE_ROWS(1, 1, true); else BTE_ROWS(1, -1, true); }
+                else { if (px) BTE_ROWS(-1, 1, true); else BTE_ROWS(-1, -1, true); }
             } else {
-                if (px) rows_of_warp<S, LIM, VL, WPR, DIM, SR, -1, 1>(a, p, q, stage, zl, rb, half, accsm, btsm, wsm, rbox);
-                else rows_of_warp<S, LIM, VL, WPR, DIM, SR, -1, -1>(a, p, q, stage, zl, rb, half, accsm, btsm, wsm, rbox);
+                if (py) { if (px) BTE_ROWS(1, 1, false); else BTE_ROWS(1, -1, false); }
+                else { if (px) BTE_ROWS(-1, 1, false); else BTE_ROWS(-1, -1, false); }
             }
+#undef BTE_ROWS
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
