@@ -177,13 +177,37 @@ def hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def code_only(text):
+    """C/C++/CUDA source without its comments and whitespace (a comment edit leaves the kernel
+    unchanged)."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        if text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        elif text[i] == '"':
+            j = i + 1
+            while j < n and text[j] != '"':
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        else:
+            out.append(text[i])
+            i += 1
+    return "".join("".join(out).split())
+
+
 def kernel_source_hash():
-    """Hash of the tiled forward kernel's sources (the kernel the traffic figure describes)."""
+    """Hash of the tiled forward kernel's code, comments and whitespace aside (the kernel the
+    traffic figure describes)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2306_14181_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
         if (name.startswith("bte_tiled") and name.endswith((".cu", ".cuh", ".h"))) or name == "bte_internal.h":
-            h.update(open(os.path.join(csrc, name), "rb").read())
+            h.update(code_only(open(os.path.join(csrc, name), encoding="utf-8").read()).encode())
     return h.hexdigest()[:12]
 
 

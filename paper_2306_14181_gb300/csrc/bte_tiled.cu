@@ -3,18 +3,20 @@
 //
 // Work unit: a plane-tile = one (band k, direction d) plane restricted to a spatial tile of full
 // x-rows (nx = 32 * VX cells) by TY rows (by TZ slices in 3-D).  Persistent CTAs take equal,
-// contiguous ranges of the tile-major list of plane-tiles.  In each CTA one producer warp moves
-// every box row the stencil needs into a ring of shared-memory stages with TMA bulk copies
-// (cp.async.bulk, completion counted on an mbarrier): the tile with its upwind-oriented halo
-// (two rows upwind, one downwind per axis) and, for rows outside the domain, the ghost rows of
-// Sec. 2.2 - the wrapped row (periodic), the mirrored direction's row (specular), the wall row
-// itself (outgoing directions), the diffuse-wall value row, or a constant (thermalizing wall).
-// Eight consumer warps own whole x-rows (VX cells per lane), take the x-stencil from warp
-// shuffles, stream y in registers and read z from shared memory, store e^{n+1} straight to
-// global memory and keep the T_L moment partials and the per-cell source terms in registers
-// for a whole segment (one tile and one band).  A segment's partials go to one row of P (and of
-// PW for diffuse walls); the finalize passes sum a tile's segments in a fixed order, so the
-// reduction is deterministic without atomics.  Every mbarrier wait is bounded.
+// contiguous ranges of the tile-major list of plane-tiles.  In each CTA one producer warp (of a
+// producer warpgroup that hands its spare registers to the consumers) moves every box row the
+// stencil needs into a ring of shared-memory stages with TMA bulk copies (cp.async.bulk,
+// completion counted on an mbarrier): the tile with its upwind-oriented halo (two rows upwind,
+// one downwind per axis) and, for rows outside the domain, the ghost rows of Sec. 2.2 - the
+// wrapped row (periodic), the mirrored direction's row (specular), the wall row itself
+// (outgoing directions), the diffuse-wall value row, or a constant (thermalizing wall).
+// Consumer warps (16 in 2-D, 12 in 3-D) own 4 rows of VL = 3 or 4 cells a lane (two warps per
+// 256-cell row), take the x-stencil from warp shuffles, stream y in registers and read z from
+// shared memory, store e^{n+1} straight to global memory, and keep the T_L moment partials and
+// the per-cell source terms in shared memory for a whole segment (one tile and one band).  A
+// segment's partials go to one row of P (and of PW for diffuse walls); the finalize passes sum
+// a tile's segments in a fixed order, so the reduction is deterministic without atomics.  Every
+// mbarrier wait is bounded.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 

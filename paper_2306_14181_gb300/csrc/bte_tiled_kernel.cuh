@@ -15,12 +15,13 @@ constexpr int kHdrFloats = 16;                        // per-plane constants wri
 
 // Tile geometry: a lane holds VL consecutive cells of a row, WPR warps cover a row of
 // nx = 32 VL WPR cells; NCW consumer warps stream KR rows each; 2-D tiles are TY rows, 3-D
-// tiles TY rows by TZ slices.  2-D CTAs run 16 consumer warps of 4 rows (96 registers a
-// thread), 3-D ones 12 warps of 4 rows (128; the z-stencil needs more live values).  Fewer,
-// wider warps on 256-cell rows measured slower: 8 warps of 8 rows at 4 cells a lane (224
-// registers) by 35%, and 8 warps of 4 rows at 8 cells a lane (142 registers; 40 instead of 50
-// instructions per update, but issue slots 40% busy instead of 61%, and twice the shared-memory
-// bank conflicts from the 32-byte lane stride) by 23%: 9 resident warps cannot hide latency.
+// tiles TY rows by TZ slices.  2-D CTAs run 16 consumer warps of 4 rows (104 registers a
+// thread after the split below), 3-D ones 12 warps of 4 rows (152; the z-stencil needs more
+// live values).  Fewer, wider warps on 256-cell rows measured slower: 8 warps of 8 rows at 4
+// cells a lane (224 registers) by 35%, and 8 warps of 4 rows at 8 cells a lane (142 registers;
+// 40 instead of 50 instructions per update, but issue slots 40% busy instead of 61%, and twice
+// the shared-memory bank conflicts from the 32-byte lane stride) by 23%: 9 resident warps
+// cannot hide latency.
 template <int DIM, int WPR> struct Geo;
 // The producer is a warpgroup of its own (one working warp, three idle) so that registers can
 // move between the two roles: at launch every thread gets 65536 / threads (rounded down to a

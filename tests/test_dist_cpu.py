@@ -57,3 +57,15 @@ def test_single_process_defaults():
     d = bench.Dist("gloo")
     assert d.world == 1 and d.rank == 0 and d.max(3.5) == 3.5
     assert bench.whole_job_rate(10, 2, 1, 4.0) == pytest.approx(10 * 2 / 0.004)
+
+
+def test_traffic_key_ignores_comments():
+    """The DRAM-traffic figure is keyed by the forward kernel's code with comments and
+    whitespace removed: a comment edit keeps the key, a code edit changes it."""
+    import bench
+    src = 'int a = 1; // one\n/* block\n comment */ const char *s = "// not a comment";\n'
+    assert bench.code_only(src) == bench.code_only('int a = 1;\nconst char *s = "// not a comment";')
+    assert bench.code_only(src) != bench.code_only(src.replace("a = 1", "a = 2"))
+    assert '"//notacomment"' in bench.code_only(src)
+    key = bench.kernel_source_hash()
+    assert len(key) == 12 and key == bench.kernel_source_hash()
