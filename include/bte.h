@@ -195,7 +195,10 @@ bte_status bte_init_temperature(bte_ctx *ctx, const double *dT0);
  * or device per on_device), split over bands in proportion to C_k and uniformly over
  * directions.  amp[n] (host, n_amp doubles) scales the source at step n (t_n = n dt); steps
  * n >= n_amp get amplitude 0.  amp = NULL means amplitude 1 at every step.  Q = NULL removes
- * the source. */
+ * the source.  A host Q is checked (BTE_EINVAL on a non-finite value, nothing changed) and
+ * copied into the context's pinned staging before the call returns, so the caller may reuse
+ * or free it at once; the upload itself is stream ordered and the call does not wait for
+ * steps already queued.  A device Q is copied in stream order and must stay valid until then. */
 bte_status bte_set_source(bte_ctx *ctx, const float *Q, int on_device, const double *amp, int n_amp);
 
 /* Advance n >= 0 steps of Eq. (disretized_transientBTE).  Each step is one fused pass of the
@@ -205,7 +208,7 @@ bte_status bte_set_source(bte_ctx *ctx, const float *Q, int on_device, const dou
 bte_status bte_step(bte_ctx *ctx, int n);
 
 /* The lattice temperature the last step formed (FP32 on the device), as doubles into dTL
- * (host, ncell).  Synchronises. */
+ * (host, ncell).  Synchronises (the copy goes through the context's pinned staging). */
 bte_status bte_lattice_temperature(bte_ctx *ctx, double *dTL);
 
 /* FP64 moments of the current state (Eq. getTQ and Eq. BTE_get_e0): dT (ncell), dTL (ncell)

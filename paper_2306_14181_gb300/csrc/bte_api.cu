@@ -65,6 +65,10 @@ struct bte_ctx {
     bool persist = false;
     float *d_amp = nullptr;
     size_t d_amp_n = 0;
+    // pinned host staging (allocated on first use): the source field on its way up, with the
+    // event that marks its upload read; the lattice temperature on its way down
+    float *h_src = nullptr, *h_tl = nullptr;
+    cudaEvent_t ev_src = nullptr;
     // source
     bool has_source = false, has_amp = false;
     std::vector<double> amp;
@@ -298,6 +302,11 @@ static void free_all(bte_ctx *c) {
     tiled_free(c->plan);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     c->ev.clear();
+    if (c->h_src) cudaFreeHost(c->h_src);
+    if (c->h_tl) cudaFreeHost(c->h_tl);
+    if (c->ev_src) cudaEventDestroy(c->ev_src);
+    c->h_src = c->h_tl = nullptr;
+    c->ev_src = nullptr;
 }
 
 static bte_status prof_event(bte_ctx *c, cudaEvent_t *out) {
@@ -616,12 +625,35 @@ extern "C" bte_status bte_set_source(bte_ctx *c, const float *Q, int on_device, 
         c->amp.clear();
         return BTE_OK;
     }
-    if (!on_device)
-        for (long long i = 0; i < c->ncell; ++i)
-            if (!std::isfinite(Q[i])) return fail(c, BTE_EINVAL, "Q holds a non-finite value at cell %lld", i);
-    CU(c, cudaMemcpyAsync(c->Q, Q, c->ncell * sizeof(float), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                          c->stream));
-    if (!on_device) CU(c, cudaStreamSynchronize(c->stream));  // the caller may free Q on return
+    if (on_device) {
+        CU(c, cudaMemcpyAsync(c->Q, Q, c->ncell * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+        // checked and copied in one pass into pinned staging (once the previous upload has read
+        // it), then uploaded in stream order: the caller may free Q on return, and nothing
+        // waits for the steps already queued
+        if (!c->h_src) {
+            CU(c, cudaMallocHost((void **)&c->h_src, c->ncell * sizeof(float)));
+            CU(c, cudaEventCreateWithFlags(&c->ev_src, cudaEventDisableTiming));
+        } else {
+            CU(c, cudaEventSynchronize(c->ev_src));
+        }
+        // the exponent field all ones marks an infinity or a NaN; an integer test and no early
+        // exit keep the loop vectorised
+        uint32_t nonfinite = 0;
+        const uint32_t *qb = reinterpret_cast<const uint32_t *>(Q);
+        uint32_t *hb = reinterpret_cast<uint32_t *>(c->h_src);
+        for (long long i = 0; i < c->ncell; ++i) {
+            const uint32_t v = qb[i];
+            nonfinite |= (uint32_t)((v & 0x7f800000u) == 0x7f800000u);
+            hb[i] = v;
+        }
+        if (nonfinite) {
+            for (long long i = 0; i < c->ncell; ++i)
+                if (!std::isfinite(Q[i])) return fail(c, BTE_EINVAL, "Q holds a non-finite value at cell %lld", i);
+        }
+        CU(c, cudaMemcpyAsync(c->Q, c->h_src, c->ncell * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        CU(c, cudaEventRecord(c->ev_src, c->stream));
+    }
     c->has_source = true;
     c->has_amp = amp != nullptr;
     c->amp.assign(amp ? amp : (const double *)nullptr, amp ? amp + n_amp : (const double *)nullptr);
@@ -716,9 +748,10 @@ extern "C" bte_status bte_synchronize(bte_ctx *c) {
 
 extern "C" bte_status bte_lattice_temperature(bte_ctx *c, double *dTL) {
     if (!c || !dTL) return fail(c, BTE_EINVAL, "NULL argument");
-    std::vector<float> t(c->ncell);
-    CU(c, cudaMemcpyAsync(t.data(), c->TL, c->ncell * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    if (!c->h_tl) CU(c, cudaMallocHost((void **)&c->h_tl, c->ncell * sizeof(float)));  // pinned: a direct copy
+    CU(c, cudaMemcpyAsync(c->h_tl, c->TL, c->ncell * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
     CU(c, cudaStreamSynchronize(c->stream));
+    const float *t = c->h_tl;
     for (long long i = 0; i < c->ncell; ++i) dTL[i] = t[i];
     return BTE_OK;
 }

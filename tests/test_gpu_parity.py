@@ -147,6 +147,40 @@ def test_gpu_energy_balance(bc):
         assert abs((E1 - E0) - rhs) <= 2e-6 * max(abs(E0), abs(rhs))
 
 
+def test_host_source_copied_before_return():
+    """bte_set_source copies a host source before it returns: overwriting the caller's array at
+    once changes nothing, a rejected (non-finite) source leaves the previous one in place, and of
+    two uploads in a row the second holds."""
+    from paper_2306_14181_gb300 import bte
+    cfg = small_cfg(2, (128, 24, 1), [DIF, SPE, ISO, DIF, PER, PER], Tw=[0.1, 0.2, 0.3, 0.4, 0, 0], nb=4,
+                    quad=("octant", 2, 3))
+    Q = (np.random.default_rng(5).random((1, 24, 128)) * 1e17).astype(np.float32)
+    a, b = gpu_ctx(cfg), gpu_ctx(cfg)
+    bte.bte_set_source(a, Q.copy())
+    Qb = Q.copy()
+    bte.bte_set_source(b, Qb)
+    Qb[...] = 3e38  # the caller reuses its buffer at once
+    bte.bte_step(a, 3)
+    bte.bte_step(b, 3)
+    assert np.array_equal(bte.bte_get_state(a), bte.bte_get_state(b))
+    bad = Q.copy()
+    bad.reshape(-1)[77] = np.nan
+    with pytest.raises(bte.BteError):
+        bte.bte_set_source(b, bad)
+    bte.bte_step(a, 2)
+    bte.bte_step(b, 2)
+    assert np.array_equal(bte.bte_get_state(a), bte.bte_get_state(b))
+    bte.bte_set_source(b, np.zeros_like(Q))
+    bte.bte_set_source(b, Q)
+    bte.bte_step(a, 2)
+    bte.bte_step(b, 2)
+    assert np.array_equal(bte.bte_get_state(a), bte.bte_get_state(b))
+    TLa, TLb = np.empty(3072), np.empty(3072)
+    bte.bte_lattice_temperature(a, TLa)
+    bte.bte_lattice_temperature(b, TLb)
+    assert np.array_equal(TLa, TLb) and np.all(np.isfinite(TLa))
+
+
 # The tiled kernel (full-row tiles: nx = 96, 128 or 256 in 2-D, 96 or 128 in 3-D); ragged tiles
 # in y and z, every wall type on every side, every limiter.
 TILED = [
