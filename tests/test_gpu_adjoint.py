@@ -31,6 +31,9 @@ CASES = [
     (2, (24, 17, 1), [DIF, SPE, ISO, DIF, PER, PER], 1),
     (2, (96, 13, 1), [SPE, SPE, ISO, DIF, PER, PER], 2),
     (2, (128, 9, 1), [PER, PER, SPE, DIF, PER, PER], 2),
+    # two warps per 256-cell row: the end lanes between them read their neighbours' values
+    (2, (256, 9, 1), [DIF, SPE, SPE, ISO, PER, PER], 2),
+    (2, (256, 7, 1), [PER, PER, ISO, DIF, PER, PER], 2),
     (3, (12, 9, 8), [SPE, SPE, PER, PER, DIF, ISO], 1),
     (3, (96, 9, 7), [DIF, ISO, SPE, SPE, PER, PER], 2),
     # z walls across three z-tiles of 6, 6 and 1 slices; periodic x at 4 cells a lane
