@@ -207,11 +207,12 @@ bool tiled_plan(int dim, const int n[3], int nb, int nd, int storage, int limite
         if (bc[w] == kBcDiffuse) plan.wslot[w] = plan.nwd++;
     const size_t wall_bytes = (size_t)std::max(1, plan.nwd) * plan.tw * sizeof(float);
     const size_t bt_bytes = (size_t)plan.tcells * sizeof(float);
+    const size_t acc_bytes = dim == 3 ? 0 : bt_bytes;  // 3-D consumers keep the moment partials in registers
     // 16-bit storage: the code references of the tile and its two-cell halo, one float per cell
     const size_t rho_bytes = storage == kStoreF32 ? 0 : (size_t)(TY + 4) * (dim == 3 ? TZ + 4 : 1) * nx * sizeof(float);
     plan.ns = 0;
-    for (int ns = 4; ns >= 2; --ns)
-        if (plan.stage0 + (size_t)ns * plan.stage_bytes + wall_bytes + 2 * bt_bytes + rho_bytes + 128 <= budget) {
+    for (int ns = 6; ns >= 2; --ns)
+        if (plan.stage0 + (size_t)ns * plan.stage_bytes + wall_bytes + bt_bytes + acc_bytes + rho_bytes + 128 <= budget) {
             plan.ns = ns;
             break;
         }
@@ -222,7 +223,7 @@ bool tiled_plan(int dim, const int n[3], int nb, int nd, int storage, int limite
     plan.wall_off = (int)(plan.stage0 + (size_t)plan.ns * plan.stage_bytes);
     plan.bt_off = plan.wall_off + (int)((wall_bytes + 127) / 128 * 128);
     plan.acc_off = plan.bt_off + (int)((bt_bytes + 127) / 128 * 128);
-    plan.rho_off = plan.acc_off + (int)((bt_bytes + 127) / 128 * 128);
+    plan.rho_off = plan.acc_off + (int)((acc_bytes + 127) / 128 * 128);
     plan.smem = plan.rho_off + (int)rho_bytes;
     plan.kernel = (void *)pick(storage, limiter, nx, dim, sr && storage != kStoreF32);
     if (!plan.kernel) {

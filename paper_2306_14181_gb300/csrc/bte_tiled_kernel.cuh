@@ -40,6 +40,10 @@ template <> struct Geo<3, 1> {
     static constexpr int RC = 152, RP = 56;
 };
 constexpr int kProducerWarps = 4;  // one warpgroup
+// Where a consumer keeps the moment partials of its cells for a segment: in registers in 3-D
+// (152 a thread leave room for KR x VL more; measured 3 % faster on the laser block), in shared
+// memory in 2-D (at 104 registers the 16 more live values cost 2 %).
+template <int DIM> constexpr bool kAccRegs = DIM == 3;
 template <int DIM, int WPR> constexpr int launch_regs() {
     return 65536 / ((Geo<DIM, WPR>::NCW + kProducerWarps) * 32) / 8 * 8;
 }
@@ -513,7 +517,8 @@ enum { kGhShfl = 0, kGhSmem = 1, kGhSpec = 2, kGhDiff = 3, kGhConst = 4, kGhOwn 
 // carries no exit test.
 template <int S, int LIM, int VL, int WPR, int DIM, bool SR, int SY, int SX, bool FULL>
 __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs &p, const PT &q, const char *stage,
-                                             int zl, int rb, int half, float *accsm, const float *btsm, float *wsm,
+                                             int zl, int rb, int half, float *accsm,
+                                             float (&acc)[Geo<DIM, WPR>::KR][VL], const float *btsm, float *wsm,
                                              const float *rbox) {
     using T = typename St<S>::T;
     constexpr bool REF = St<S>::kRef;
@@ -630,8 +635,11 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
     ld_row<S, VL>(w0, box + o + x0, rbox + ro + x0);
     faces<LIM, VL>(wm2, wm1, w0, fin);
     #pragma unroll
-    for (int j = 0; j < kR; ++j) {
-        if (!FULL && j >= nrows) break;
+    for (int jj = 0; jj < kR; ++jj) {
+        // r: the row's place in the warp's stretch (its accumulators); j: its place in the stream
+        const int r = SY > 0 ? jj : kR - 1 - jj;
+        if (!FULL && r >= nrows) continue;
+        const int j = SY > 0 ? r : nrows - 1 - r;
         const int y = q.y0 + yl0 + j * sy;
         ld_row<S, VL>(wp1, box + o + dy + x0, rbox + ro + dyR + x0);
         float fout[VL];
@@ -684,12 +692,20 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
         float bt[VL], ac[VL];
         if constexpr (VL == 4) {
             const float4 f = *reinterpret_cast<const float4 *>(btsm + c);
-            const float4 g = *reinterpret_cast<const float4 *>(accsm + c);
             bt[0] = f.x; bt[1] = f.y; bt[2] = f.z; bt[3] = f.w;
+        } else {
+            #pragma unroll
+            for (int v = 0; v < VL; ++v) bt[v] = btsm[c + v];
+        }
+        if constexpr (kAccRegs<DIM>) {
+            #pragma unroll
+            for (int v = 0; v < VL; ++v) ac[v] = acc[r][v];
+        } else if constexpr (VL == 4) {
+            const float4 g = *reinterpret_cast<const float4 *>(accsm + c);
             ac[0] = g.x; ac[1] = g.y; ac[2] = g.z; ac[3] = g.w;
         } else {
             #pragma unroll
-            for (int v = 0; v < VL; ++v) { bt[v] = btsm[c + v]; ac[v] = accsm[c + v]; }
+            for (int v = 0; v < VL; ++v) ac[v] = accsm[c + v];
         }
         typename St<S>::C h[VL];
         float en[VL], es[VL];
@@ -730,8 +746,12 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
             ac[v + 1] = m.y;
         }
         if constexpr (VL & 1) ac[VL - 1] = fmaf(wm, es[VL - 1], ac[VL - 1]);
-        if constexpr (VL == 4) *reinterpret_cast<float4 *>(accsm + c) = make_float4(ac[0], ac[1], ac[2], ac[3]);
-        else {
+        if constexpr (kAccRegs<DIM>) {
+            #pragma unroll
+            for (int v = 0; v < VL; ++v) acc[r][v] = ac[v];
+        } else if constexpr (VL == 4) {
+            *reinterpret_cast<float4 *>(accsm + c) = make_float4(ac[0], ac[1], ac[2], ac[3]);
+        } else {
             #pragma unroll
             for (int v = 0; v < VL; ++v) accsm[c + v] = ac[v];
         }
@@ -792,7 +812,8 @@ __device__ __forceinline__ void warp_place(int &zl, int &rb, int &half) {
 // values are s_k (h_d + rho_new), so P = s_k * sum + (sum_d w_d/tau) C_k T_L^n / W.
 template <bool REF, int VL, int WPR, int DIM>
 __device__ __forceinline__ void flush_segment(const StepArgs &a, const TiledArgs &p, int seg, const PT &q,
-                                              float *accsm, float *wsm, float wsum) {
+                                              float *accsm, float (&acc)[Geo<DIM, WPR>::KR][VL], float *wsm,
+                                              float wsum) {
     constexpr int NX = 32 * VL * WPR, TY = Geo<DIM, WPR>::TY, NCW = Geo<DIM, WPR>::NCW;
     int zl, rb, half;
     warp_place<VL, WPR, DIM>(zl, rb, half);
@@ -812,12 +833,16 @@ __device__ __forceinline__ void flush_segment(const StepArgs &a, const TiledArgs
             const long long g = ((long long)(q.z0 + zl) * a.n[1] + q.y0 + yl) * NX + x0;
             #pragma unroll
             for (int v = 0; v < VL; ++v) {
-                if constexpr (REF) P[c + v] = fmaf(sc, accsm[c + v], wck * a.TL[g + v]);
-                else P[c + v] = accsm[c + v];
+                const float m = kAccRegs<DIM> ? acc[r][v] : accsm[c + v];
+                if constexpr (REF) P[c + v] = fmaf(sc, m, wck * a.TL[g + v]);
+                else P[c + v] = m;
             }
         }
         #pragma unroll
-        for (int v = 0; v < VL; ++v) accsm[c + v] = 0.f;
+        for (int v = 0; v < VL; ++v) {
+            if constexpr (kAccRegs<DIM>) acc[r][v] = 0.f;
+            else accsm[c + v] = 0.f;
+        }
     }
     consumer_sync<NCW>();
     for (int idx = threadIdx.x; idx < p.nwd * p.tw; idx += NCW * 32) {
@@ -864,6 +889,11 @@ __device__ void consumer(const StepArgs &a, const TiledArgs &p, char *smem, uint
     float *wsm = reinterpret_cast<float *>(smem + p.wall_off);
     float *btsm = reinterpret_cast<float *>(smem + p.bt_off);
     float *accsm = reinterpret_cast<float *>(smem + p.acc_off);
+    float acc[Geo<DIM, WPR>::KR][VL];  // 3-D: this thread's moment partials of the current segment
+    #pragma unroll
+    for (int r = 0; r < Geo<DIM, WPR>::KR; ++r)
+        #pragma unroll
+        for (int v = 0; v < VL; ++v) acc[r][v] = 0.f;
     float *rbox = reinterpret_cast<float *>(smem + p.rho_off);
     int seg = -1, cur_unit = -1, cur_band = -1;
     int s = 0;         // stage of plane-tile i = i mod ns
@@ -875,7 +905,7 @@ __device__ void consumer(const StepArgs &a, const TiledArgs &p, char *smem, uint
     for (int i = 0; more; ++i, more = c.next(a, p)) {
         const PT q = c.q;
         if (c.u != cur_unit || q.k != cur_band) {
-            if (seg >= 0) flush_segment<REF, VL, WPR, DIM>(a, p, seg, cur, accsm, wsm, wsum);
+            if (seg >= 0) flush_segment<REF, VL, WPR, DIM>(a, p, seg, cur, accsm, acc, wsm, wsum);
             if constexpr (REF) {
                 // after the flush's barriers no warp reads the previous unit's references
                 if (c.u != cur_unit) {
@@ -915,7 +945,7 @@ __device__ void consumer(const StepArgs &a, const TiledArgs &p, char *smem, uint
             const float *hd = reinterpret_cast<const float *>(stage + p.hdr_off);
             const bool px = hd[0] > 0.f, py = hd[1] > 0.f;  // the signs rows_of_warp takes
             const bool full = rb + Geo<DIM, WPR>::KR <= q.nyt;
-#define BTE_ROWS(SY_, SX_, F_) rows_of_warp<S, LIM, VL, WPR, DIM, SR, SY_, SX_, F_>(a, p, q, stage, zl, rb, half, accsm, btsm, wsm, rbox)
+#define BTE_ROWS(SY_, SX_, F_) rows_of_warp<S, LIM, VL, WPR, DIM, SR, SY_, SX_, F_>(a, p, q, stage, zl, rb, half, accsm, acc, btsm, wsm, rbox)
             if (full) {
                 if (py) { if (px) BTE_ROWS(1, 1, true); else BTE_ROWS(1, -1, true); }
                 else { if (px) BTE_ROWS(-1, 1, true); else BTE_ROWS(-1, -1, true); }
@@ -932,7 +962,7 @@ __device__ void consumer(const StepArgs &a, const TiledArgs &p, char *smem, uint
             ph ^= 1u;
         }
     }
-    if (seg >= 0) flush_segment<REF, VL, WPR, DIM>(a, p, seg, cur, accsm, wsm, wsum);
+    if (seg >= 0) flush_segment<REF, VL, WPR, DIM>(a, p, seg, cur, accsm, acc, wsm, wsum);
 }
 
 // SR: 16-bit codes rounded stochastically (a separate instance, so the round-to-nearest one
@@ -951,8 +981,10 @@ __global__ void __launch_bounds__((Geo<DIM, WPR>::NCW + kProducerWarps) * 32, 1)
     }
     float *wsm = reinterpret_cast<float *>(smem + p.wall_off);
     for (int j = threadIdx.x; j < p.nwd * p.tw; j += blockDim.x) wsm[j] = 0.f;
-    float *accsm = reinterpret_cast<float *>(smem + p.acc_off);
-    for (int j = threadIdx.x; j < p.tcells; j += blockDim.x) accsm[j] = 0.f;
+    if constexpr (!kAccRegs<DIM>) {
+        float *accsm = reinterpret_cast<float *>(smem + p.acc_off);
+        for (int j = threadIdx.x; j < p.tcells; j += blockDim.x) accsm[j] = 0.f;
+    }
     __syncthreads();
     const int warp = (int)(threadIdx.x >> 5);
     if (warp >= Geo<DIM, WPR>::NCW) {
