@@ -631,12 +631,9 @@ extern "C" bte_status bte_set_source(bte_ctx *c, const float *Q, int on_device, 
         // checked and copied in one pass into pinned staging (once the previous upload has read
         // it), then uploaded in stream order: the caller may free Q on return, and nothing
         // waits for the steps already queued
-        if (!c->h_src) {
-            CU(c, cudaMallocHost((void **)&c->h_src, c->ncell * sizeof(float)));
-            CU(c, cudaEventCreateWithFlags(&c->ev_src, cudaEventDisableTiming));
-        } else {
-            CU(c, cudaEventSynchronize(c->ev_src));
-        }
+        if (!c->h_src) CU(c, cudaMallocHost((void **)&c->h_src, c->ncell * sizeof(float)));
+        if (!c->ev_src) CU(c, cudaEventCreateWithFlags(&c->ev_src, cudaEventDisableTiming));
+        else CU(c, cudaEventSynchronize(c->ev_src));  // the previous upload has read the staging
         // the exponent field all ones marks an infinity or a NaN; an integer test and no early
         // exit keep the loop vectorised
         uint32_t nonfinite = 0;
