@@ -451,7 +451,7 @@ def run_gb300(args):
                        **({"rounding": args.rounding, "T_scale": args.t_scale} if args.storage != "f32" else {}),
                        "updates_per_step": info.nelem, "l2": l2_note(info),
                        "parallelism": "replicas" if d.world > 1 else "single"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(nfwd if persistent else nfwd + nfin),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(nfwd if persistent else nfwd * info.launches_per_step),
             "clocks": ck}
     if adjoint is not None:
         line["adjoint"] = adjoint

@@ -167,6 +167,8 @@ typedef struct {
     double W;               /* sum_d w_d */
     long long step;         /* steps taken since bte_init_temperature / bte_set_state */
     size_t device_bytes;    /* device memory held by the context */
+    int launches_per_step;  /* kernel launches of one step (bte_step(ctx, 1)); the persistent 1-D
+                               kernel launches once per bte_step call, whatever n */
 } bte_info;
 
 /* Create a context: validate, build the quadrature, band tables and mirror maps on the host,

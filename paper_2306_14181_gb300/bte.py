@@ -67,7 +67,7 @@ class bte_info(ct.Structure):
                 ("ndirs", ct.c_int), ("ncell", ct.c_longlong), ("nelem", ct.c_longlong),
                 ("state_bytes", ct.c_size_t), ("elem_bytes", ct.c_int), ("storage", ct.c_int),
                 ("limiter", ct.c_int), ("kernel", ct.c_int), ("dt", ct.c_double), ("W", ct.c_double),
-                ("step", ct.c_longlong), ("device_bytes", ct.c_size_t)]
+                ("step", ct.c_longlong), ("device_bytes", ct.c_size_t), ("launches_per_step", ct.c_int)]
 
 
 _lib = None

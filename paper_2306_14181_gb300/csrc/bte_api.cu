@@ -22,6 +22,10 @@ using namespace bte;
 
 static thread_local std::string g_create_error;
 
+namespace bte {
+int tiled_finalize_launches(const TiledPlan &plan, const int bc[6]);  // kernels launch_finalize_tiled launches
+}  // namespace bte
+
 struct bte_ctx {
     // problem
     int dim = 0, n[3] = {1, 1, 1};
@@ -891,6 +895,8 @@ extern "C" bte_status bte_get_info(const bte_ctx *c, bte_info *info) {
     info->W = c->W;
     info->step = c->step;
     info->device_bytes = c->device_bytes;
+    // forward + finalize passes (the tiled finalize adds one for walls that need ghost values)
+    info->launches_per_step = c->persist ? 1 : 1 + (c->tiled ? tiled_finalize_launches(c->plan, c->bc) : 1);
     return BTE_OK;
 }
 
