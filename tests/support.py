@@ -69,3 +69,10 @@ def run_both(cfg, e0, nsteps, Q=None, amps=None, limiter=2, storage=0, kernel=0,
     _, gTL, _ = bte.bte_moments(ctx)
     eo = P.run(start, nsteps, Q, amps)
     return ctx, g, gTL, eo, P.lattice_temperature(eo)
+
+
+def fused_TL(ctx):
+    """The lattice temperature the step itself formed (the forward kernel's FP32 moment and the
+    finalize pass), as opposed to the FP64 recomputation of bte_moments."""
+    from paper_2306_14181_gb300 import bte
+    return bte.bte_lattice_temperature(ctx).reshape(ctx.shape[2:])

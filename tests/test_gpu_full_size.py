@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 from paper_2306_14181_gb300 import inputs
-from tests.support import gpu_ctx, oracle_problem
+from tests.support import fused_TL, gpu_ctx, oracle_problem, rel_linf
 
 pytestmark = pytest.mark.gpu
 
@@ -61,6 +61,11 @@ def _check(cfg, warm, seed):
     got = e_n1[pts[:, 0] * P.nd + pts[:, 1], pts[:, 2]].astype(np.float64)
     scale = np.max(np.abs(e64))
     assert np.max(np.abs(got - ref)) <= TOL * scale
+    # the T_L the step formed (FP32 moment partials and the finalize pass) against the oracle's
+    # T_L of the stored state e^{n+1} (Eq. BTE_get_e0)
+    del e64
+    oTL = P.lattice_temperature(e_n1.astype(np.float64).reshape(P.shape))
+    assert rel_linf(fused_TL(ctx), oTL) <= TOL
 
 
 def test_hotspot_2d_full_size_sampled():

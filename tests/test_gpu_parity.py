@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from paper_2306_14181_gb300 import inputs
-from tests.support import oracle_problem, oracle_quadrature, rel_linf, run_both, small_cfg, gpu_ctx
+from tests.support import fused_TL, gpu_ctx, oracle_problem, oracle_quadrature, rel_linf, run_both, small_cfg
 
 pytestmark = pytest.mark.gpu
 
@@ -60,6 +60,7 @@ def test_p12_tiny_grid_elementwise(dim, n, bc, _, limiter):
     ctx, g, gTL, eo, oTL = run_both(cfg, e0, 10, Q, amps, limiter=limiter)
     assert rel_linf(g, eo) <= TOL
     assert rel_linf(gTL, oTL) <= TOL
+    assert rel_linf(fused_TL(ctx), oTL) <= TOL
 
 
 # The 1-D film is unusually sensitive to per-step perturbations: its stiffest bands relax in a
@@ -207,6 +208,7 @@ def test_tiled_kernel_elementwise(dim, n, bc, limiter):
     assert ctx.info.kernel == bte.BTE_KERNEL_TILED
     assert rel_linf(g, eo) <= TOL
     assert rel_linf(gTL, oTL) <= TOL
+    assert rel_linf(fused_TL(ctx), oTL) <= TOL
 
 
 @pytest.mark.parametrize("dim,n,bc", [TILED[0], TILED[4]])
@@ -246,6 +248,7 @@ def test_hotspot_2d_tiled_workload_shape():
     ctx, g, gTL, eo, oTL = run_both(cfg, np.zeros(P.shape), 300, Q)
     assert ctx.info.kernel == bte.BTE_KERNEL_TILED
     assert rel_linf(gTL, oTL) <= TOL
+    assert rel_linf(fused_TL(ctx), oTL) <= TOL
 
 
 def test_laser_3d_tiled_subsample():
@@ -259,6 +262,7 @@ def test_laser_3d_tiled_subsample():
     ctx, g, gTL, eo, oTL = run_both(cfg, np.zeros(P.shape), 60, Q, amps)
     assert ctx.info.kernel == bte.BTE_KERNEL_TILED
     assert rel_linf(gTL, oTL) <= TOL
+    assert rel_linf(fused_TL(ctx), oTL) <= TOL
 
 
 # 16-bit storage: codes h with e = s_k (h + R / T_scale) against the per-cell reference R (the

@@ -390,3 +390,39 @@ def test_multid_time_step_keeps_maximum_principle(dim, n, quad, limiter):
     for _ in range(6):
         e = P.run(e, 4)
         assert e.min() >= lo - 1e-12 * hi and e.max() <= hi * (1 + 1e-12)
+
+
+# ---------------------------------------------------------------------------------------
+# Sampled step: orc_step_points (the checker of the full-size GPU tests) forms T_L at one
+# cell and e^{n+1} at one (k, d, cell) with its own index decoding; it must give exactly the
+# elements of the whole-grid step (Eq. disretized_transientBTE with Eq. BTE_get_e0).
+# ---------------------------------------------------------------------------------------
+def _point_samples(P, n, seed):
+    """n random (k, d, cell) triples plus every plane at each corner cell of the domain."""
+    rng = np.random.default_rng(seed)
+    pts = [np.stack([rng.integers(0, P.nb, n), rng.integers(0, P.nd, n), rng.integers(0, P.ncell, n)], axis=1)]
+    zs = (0, P.nz - 1)
+    ys = (0, P.ny - 1)
+    xs = (0, 1, P.nx - 1)
+    for z in zs:
+        for y in ys:
+            for x in xs:
+                i = (z * P.ny + y) * P.nx + x
+                kk, dd = np.meshgrid(np.arange(P.nb), np.arange(P.nd), indexing="ij")
+                pts.append(np.stack([kk.ravel(), dd.ravel(), np.full(kk.size, i)], axis=1))
+    return np.concatenate(pts)
+
+
+@pytest.mark.parametrize("limiter", [LIM_FIRST_ORDER, LIM_MINMOD, LIM_VANALBADA])
+@pytest.mark.parametrize("dim,n,bc", P2_CASES)
+def test_step_points_equal_whole_step(dim, n, bc, limiter):
+    cfg = small_cfg(dim, n, bc, Tw=[0.3, -0.2, 0.1, 0.4, -0.3, 0.2])
+    P = oracle_problem(cfg, limiter)
+    e = inputs.random_state(P.shape, 21) * 1e3
+    Q = (np.random.default_rng(4).random((P.nz, P.ny, P.nx)) * 1e17).astype(np.float32)
+    amp = 0.6
+    full = P.step(e, Q, amp).reshape(P.nb * P.nd, P.ncell)
+    pts = _point_samples(P, 400, 9)
+    got = P.step_points(e, pts, Q, amp)
+    want = full[pts[:, 0] * P.nd + pts[:, 1], pts[:, 2]]
+    assert np.array_equal(got, want)
