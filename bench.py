@@ -3,9 +3,12 @@
 
 One "step" is one time step of Eq. (disretized_transientBTE) over the whole workload: the
 fused forward kernel over every (band, direction, cell) plus the T_L finalize pass.  Default
-workload: the 2-D hot spot (256x256 cells, 40 bands, 128 directions, FP32 state), the
-configuration the updates/s figure is quoted on.  Inputs are resident in HBM before the timed
-region; the state (1.34 GB) is larger than L2, so no L2 flush is needed between steps.
+workload: the 3-D laser-heated block (128x128x64 cells, 40 bands, 96 directions, FP32 state),
+the largest of the paper-shaped configurations that runs on one GPU.  Inputs are resident in
+HBM before the timed region; the state (16.1 GB a copy) is far larger than L2, so no flush is
+needed between steps.  The same run then measures, one context at a time, the sub-records:
+the laser block with 16-bit storage, the 2-D hot spot (FP32 and 16-bit) and the adjoint/forward
+step-time ratio of the two adjoint workloads.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--storage f32|f16|bf16]
   python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
@@ -52,7 +55,7 @@ def parse():
     p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    p.add_argument("--workload", default="hotspot_2d")
+    p.add_argument("--workload", default="laser_3d")
     p.add_argument("--storage", default="f32", choices=sorted(STORAGE))
     p.add_argument("--kernel", default="auto", choices=sorted(KERNEL))
     p.add_argument("--rounding", default="nearest", choices=["nearest", "stochastic"],
@@ -67,6 +70,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--nb", type=int, default=None, help="override the workload's band count (profiling runs)")
+    p.add_argument("--no-sub-records", action="store_true",
+                   help="skip the sub-records (the other workloads and storage forms, the adjoint ratios)")
     a = p.parse_args()
     if a.warmup < 3:
         p.error("--warmup must be >= 3")
@@ -228,42 +233,40 @@ def measured_traffic(workload, storage, kernel_name):
 # ------------------------------------------------------------------------------------------
 # the oracle on the host cores (CPU baseline and the reference arm)
 # ------------------------------------------------------------------------------------------
-def oracle_for(cfg, ny_sample=None, limiter=2):
+def oracle_for(cfg, sample_n=None, limiter=2):
     from oracle import Problem
     from oracle import quadrature as oq
     c = dict(cfg)
-    if ny_sample is not None and c["dim"] >= 2 and ny_sample < c["n"][c["dim"] - 1]:
-        n = list(c["n"])
-        n[c["dim"] - 1] = ny_sample
-        c["n"] = tuple(n)
+    if sample_n is not None:
+        c["n"] = tuple(sample_n)
     s, w, mirror = oq.polar_1d(c["quad"][1]) if c["quad"][0] == "gl1d" else oq.octant_rule(c["quad"][1], c["quad"][2])
     return c, Problem(c["dim"], c["n"], c["h"], c["C"], c["v"], c["tau"], s, w, mirror, c["bc"], c["Tw"], c["dt"],
                       limiter)
 
 
-def cpu_sample_size(cfg):
-    """Cells along the slowest axis of the host sample: about 40 M updates per oracle step."""
-    if cfg["dim"] == 1:
-        return None
-    per_row = cfg["nb"] * (8 * cfg["quad"][1] * cfg["quad"][2]) * cfg["n"][0] * (cfg["n"][1] if cfg["dim"] == 3 else 1)
-    return max(2, min(cfg["n"][cfg["dim"] - 1], int(40e6 // per_row)))
+def cpu_sample_grid(cfg, updates):
+    """Grid of the host sample: the workload with its slowest axes cut (down to 2 cells) until a
+    step has about `updates` (band, direction, cell) updates.  All bands and directions are kept."""
+    n = list(cfg["n"])
+    per_cell = cfg["nb"] * (cfg["quad"][1] if cfg["quad"][0] == "gl1d" else 8 * cfg["quad"][1] * cfg["quad"][2])
+    for ax in reversed(range(1, cfg["dim"])):
+        rest = per_cell * math.prod(n) // n[ax]
+        n[ax] = max(2, min(n[ax], int(updates // max(rest, 1))))
+    return tuple(n)
 
 
-def time_oracle(cfg, seconds, limiter=2):
-    """Oracle steps on a slab of the workload until `seconds` of host time is used."""
+def time_oracle(cfg, seconds, limiter=2, updates=40e6, max_steps=None):
+    """Oracle steps on a cut of the workload until `seconds` of host time is used (at least one)."""
     from paper_2306_14181_gb300 import inputs
-    c, P = oracle_for(cfg, cpu_sample_size(cfg), limiter)
-    Q = None
-    if cfg.get("source") is not None:
-        c2 = dict(c)
-        Q = inputs.source_field(c2)
+    c, P = oracle_for(cfg, cpu_sample_grid(cfg, updates), limiter)
+    Q = inputs.source_field(c) if cfg.get("source") is not None else None
     e = P.equilibrium(0.0)
     nel = P.nb * P.nd * P.ncell
     t0 = time.perf_counter()
     e = P.step(e, Q, 1.0)
     t1 = time.perf_counter()
     n = 1
-    while t1 - t0 < seconds:
+    while t1 - t0 < seconds and (max_steps is None or n < max_steps):
         e = P.step(e, Q, 1.0)
         n += 1
         t1 = time.perf_counter()
@@ -273,6 +276,23 @@ def time_oracle(cfg, seconds, limiter=2):
 def omp_threads():
     v = os.environ.get("OMP_NUM_THREADS")
     return int(v) if v else (os.cpu_count() or 1)
+
+
+def time_oracle_one_thread(workload, seconds, limiter):
+    """The oracle on one host thread (a child process with OMP_NUM_THREADS=1, so the OpenMP
+    runtime of this process keeps its thread count)."""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "cfg = bench.workloads()[%r](); v, n, g, t = bench.time_oracle(cfg, %r, %r, 4e6, 50); "
+            "print(json.dumps([v, n, list(g), t]))" % (ROOT, workload, float(seconds), int(limiter)))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                           timeout=seconds * 4 + 120)
+        v, n, g, t = json.loads(r.stdout.strip().splitlines()[-1])
+    except (subprocess.SubprocessError, ValueError, IndexError, OSError):
+        return None
+    return {"value": v, "unit": UNIT, "cores": 1,
+            "sample": "%d FP64 oracle steps on a %s cut of the workload, %.1f s" % (n, "x".join(map(str, g)), t)}
 
 
 # ------------------------------------------------------------------------------------------
@@ -285,7 +305,9 @@ def run_reference(args):
     cfg = make_workload(args)
     from oracle import build_oracle
     build_oracle()
-    c, P = oracle_for(cfg, cpu_sample_size(cfg), args.limiter)
+    # about 75 s of oracle work at ~2e8 updates/s over the whole --steps + --warmup run
+    updates = min(4e7, max(2e6, 1.5e10 / (args.steps + args.warmup)))
+    c, P = oracle_for(cfg, cpu_sample_grid(cfg, updates), args.limiter)
     from paper_2306_14181_gb300 import inputs
     Q = inputs.source_field(c) if cfg.get("source") is not None else None
     e = P.equilibrium(0.0)
@@ -297,11 +319,11 @@ def run_reference(args):
     t = time.perf_counter() - t0
     nel = P.nb * P.nd * P.ncell
     value = nel * args.steps / t
-    sample = "%d oracle steps on a %s slab of %s (all bands and directions)" % (args.steps, "x".join(map(str, c["n"])),
-                                                                              cfg["name"])
+    sample = "%d oracle steps on a %s cut of %s (all bands and directions)" % (args.steps, "x".join(map(str, c["n"])),
+                                                                             cfg["name"])
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "storage": "f64", "data": "synthetic",
             "config": {"workload": cfg["name"], "sample_grid": list(c["n"]), "bands": c["nb"], "dirs": P.nd,
                        "limiter": args.limiter},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": omp_threads(), "kind": "oracle", "sample": sample},
@@ -330,67 +352,168 @@ def make_workload(args):
     return workloads()[args.workload](**kw)
 
 
+def kernel_name_of(info):
+    from paper_2306_14181_gb300 import bte
+    return {bte.BTE_KERNEL_TILED: "tiled", bte.BTE_KERNEL_PERSISTENT: "persistent"}.get(info.kernel, "generic")
+
+
+def make_context(cfg, storage, limiter, kernel, T_scale, rounding, amps_len):
+    """A context of the workload with its source field (device) and amplitudes set."""
+    import torch
+    from paper_2306_14181_gb300 import bte, inputs
+    Q = inputs.source_field(cfg)
+    amps = inputs.source_amplitudes(cfg, amps_len)
+    stream = torch.cuda.current_stream()
+    ctx = bte.bte_from_workload(cfg, storage=storage, limiter=limiter, kernel=kernel, stream=stream.cuda_stream,
+                                T_scale=T_scale, rounding=rounding, seed=1)
+    if Q is not None:
+        bte.bte_set_source(ctx, torch.from_numpy(Q.reshape(-1)).cuda(), amps)
+    return ctx, Q, amps
+
+
+def timed_forward(ctx, steps, d=None, clocks=None):
+    """Device time of `steps` bte_step calls (CUDA events on the context's stream) with the
+    library's per-launch tracing: (total ms, forward ms, forward launches, finalize ms,
+    finalize launches)."""
+    import torch
+    from paper_2306_14181_gb300 import bte
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    if d is not None:
+        d.barrier()
+    torch.cuda.synchronize()
+    if clocks is not None:
+        clocks.start()
+    bte.bte_profile(ctx, True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    bte.bte_step(ctx, steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if d is not None:
+        d.barrier()
+    torch.cuda.synchronize()
+    ck = clocks.stop() if clocks is not None else None
+    fwd_ms, nfwd, fin_ms, nfin = bte.bte_profile_read(ctx)
+    bte.bte_profile(ctx, False)
+    bte.bte_synchronize(ctx)  # a bounded wait that gave up is reported here
+    return ev0.elapsed_time(ev1), fwd_ms, nfwd, fin_ms, nfin, ck
+
+
+def roofline_of(info, steps, fwd_ms, nfwd, fin_ms, nfin, peak, peak_kind, traffic=None):
+    """Roofline of the forward kernel: algorithmic bytes = read e + write e per update, over the
+    mean device time of one launch."""
+    from paper_2306_14181_gb300 import bte
+    persistent = info.kernel == bte.BTE_KERNEL_PERSISTENT
+    # a persistent launch covers all the steps of its bte_step call
+    steps_per_launch = steps / max(nfwd, 1) if persistent else 1
+    bytes_per_launch = info.nelem * 2 * info.elem_bytes * steps_per_launch
+    fwd_avg_s = fwd_ms / max(nfwd, 1) / 1e3
+    achieved = bytes_per_launch / fwd_avg_s / 1e9
+    r = {"bound": "latency" if persistent else "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+         "frac": achieved / peak, "traffic": traffic, "kernel": "forward step (%s)" % kernel_name_of(info),
+         "peak_source": peak_kind, "bytes_per_launch": bytes_per_launch, "kernel_ms": fwd_avg_s * 1e3,
+         "finalize_ms": fin_ms / max(nfin, 1)}
+    if persistent:
+        # the state stays in shared memory: report the step time, not a DRAM fraction
+        r["us_per_step"] = fwd_avg_s * 1e6 / steps_per_launch
+        r["note"] = "one single-CTA launch per bte_step call; the state never leaves shared memory"
+        r["finalize_ms"] = 0.0
+    return r
+
+
+def adjoint_record(ctx, cfg, info, fwd_step_ms, nadj, kck, Q, amps, peak):
+    """One traced bte_adjoint call (forward sweep + checkpointed reverse sweep) of J = mean T_L
+    over the workload's probe: adjoint-step and forward-step device times and their ratio."""
+    import numpy as np
+    import torch
+    from paper_2306_14181_gb300 import bte, inputs
+    probe = inputs.probe_weights(cfg)
+    bte.bte_init_temperature(ctx, None)
+    if Q is not None:
+        bte.bte_set_source(ctx, torch.from_numpy(Q.reshape(-1)).cuda(), amps)
+    torch.cuda.synchronize()
+    bte.bte_profile(ctx, True)
+    t0 = time.perf_counter()
+    J, gQ, gt = bte.bte_adjoint(ctx, nadj, probe, kck)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    adj_ms, nadj_k, rec_ms, nrec = bte.bte_adjoint_profile_read(ctx)
+    bte.bte_profile(ctx, False)
+    adj_step = adj_ms / max(nadj_k, 1)
+    adj_bytes = info.nelem * (8 + info.elem_bytes)
+    return {"steps": nadj, "ckpt": kck, "J": J, "adj_step_ms": adj_step, "fwd_step_ms": fwd_step_ms,
+            "ratio": adj_step / fwd_step_ms, "recompute_steps": nrec, "recompute_ms": rec_ms, "wall_s": wall,
+            "bytes_per_adj_step": adj_bytes, "achieved_gbs": adj_bytes / (adj_step / 1e3) / 1e9,
+            "frac": adj_bytes / (adj_step / 1e3) / 1e9 / peak,
+            "grad_finite": bool(np.all(np.isfinite(gQ)) and np.all(np.isfinite(gt)))}
+
+
+# Sub-records measured in the same run after the headline, one context at a time: (workload,
+# storage, T_scale, timed forward steps, adjoint steps or None, checkpoint spacing).  The 3-D
+# adjoint runs 100 of its 1000 steps (checkpoints every 50) to keep the run within minutes.
+SUB_RECORDS = [
+    ("laser_3d", "f16", 1.0, 30, None, None),
+    ("hotspot_2d", "f32", 1.0, 100, None, None),
+    ("hotspot_2d", "f16", 10.0, 100, None, None),
+    ("film_adjoint_2d", "f32", 1.0, 100, 2000, 100),
+    ("block_adjoint_3d", "f16", 1.0, 10, 100, 50),
+]
+
+
+def sub_record(args, name, storage, T_scale, steps, nadj, kck, peak, peak_kind):
+    import gc
+    import torch
+    from paper_2306_14181_gb300 import bte
+    cfg = workloads()[name]()
+    warm = 3
+    ctx, Q, amps = make_context(cfg, STORAGE[storage], args.limiter, KERNEL["auto"], T_scale, 0,
+                                warm + steps + 8)
+    info = ctx.info
+    bte.bte_step(ctx, warm)
+    t_ms, fwd_ms, nfwd, fin_ms, nfin, _ = timed_forward(ctx, steps)
+    rec = {"workload": cfg["name"], "storage": storage, "kernel": kernel_name_of(info), "steps": steps,
+           "warmup": warm, "ms_per_step": t_ms / steps, "value": info.nelem * steps / (t_ms / 1e3), "unit": UNIT,
+           "updates_per_step": info.nelem,
+           "roofline": roofline_of(info, steps, fwd_ms, nfwd, fin_ms, nfin, peak, peak_kind)}
+    if storage != "f32":
+        rec["T_scale"] = T_scale
+    if nadj is not None:
+        fwd_step = (fwd_ms / max(nfwd, 1)) + fin_ms / max(nfin, 1)
+        rec["adjoint"] = adjoint_record(ctx, cfg, info, fwd_step, nadj, kck, Q, amps, peak)
+    bte.bte_destroy(ctx)
+    del ctx
+    gc.collect()
+    torch.cuda.empty_cache()
+    return rec
+
+
 def run_gb300(args):
+    import gc
     import numpy as np
     import torch
 
     d = Dist("nccl")
     torch.cuda.set_device(d.local)
-    from paper_2306_14181_gb300 import bte, build, inputs
+    from paper_2306_14181_gb300 import bte, build
     build.build()
     cfg = make_workload(args)
     storage = STORAGE[args.storage]
-    Q = inputs.source_field(cfg)
     total = args.warmup + args.steps + args.e2e_steps + 8
-    amps = inputs.source_amplitudes(cfg, total)
-    stream = torch.cuda.current_stream()
-    ctx = bte.bte_from_workload(cfg, storage=storage, limiter=args.limiter, kernel=KERNEL[args.kernel],
-                                stream=stream.cuda_stream, T_scale=args.t_scale,
-                                rounding=1 if args.rounding == "stochastic" else 0, seed=1)
+    ctx, Q, amps = make_context(cfg, storage, args.limiter, KERNEL[args.kernel], args.t_scale,
+                                1 if args.rounding == "stochastic" else 0, total)
     info = ctx.info
-    kernel_name = {bte.BTE_KERNEL_TILED: "tiled", bte.BTE_KERNEL_PERSISTENT: "persistent"}.get(info.kernel, "generic")
-    if Q is not None:
-        bte.bte_set_source(ctx, torch.from_numpy(Q.reshape(-1)).cuda(), amps)
+    kernel_name = kernel_name_of(info)
     bte.bte_step(ctx, args.warmup)
-    torch.cuda.synchronize()
-    d.barrier()
-    torch.cuda.synchronize()
     clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
-    bte.bte_profile(ctx, True)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    bte.bte_step(ctx, args.steps)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    d.barrier()
-    torch.cuda.synchronize()
-    ck = clocks.stop()
-    t_ms = ev0.elapsed_time(ev1)
-    fwd_ms, nfwd, fin_ms, nfin = bte.bte_profile_read(ctx)
-    bte.bte_profile(ctx, False)
+    t_ms, fwd_ms, nfwd, fin_ms, nfin, ck = timed_forward(ctx, args.steps, d, clocks)
     t_max = d.max(t_ms)
     value = whole_job_rate(info.nelem, args.steps, d.world, t_max)
-
-    # roofline of the forward kernel: algorithmic bytes = read e + write e per update
     peak, peak_kind = hbm_peak()
     persistent = info.kernel == bte.BTE_KERNEL_PERSISTENT
-    # a persistent launch covers all the steps of its bte_step call
-    steps_per_launch = args.steps / max(nfwd, 1) if persistent else 1
-    bytes_per_launch = info.nelem * 2 * info.elem_bytes * steps_per_launch
-    fwd_avg_s = fwd_ms / max(nfwd, 1) / 1e3
-    achieved = bytes_per_launch / fwd_avg_s / 1e9
-    traffic = measured_traffic(args.workload, args.storage, kernel_name)
-    roofline = {"bound": "latency" if persistent else "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": "forward step (%s)" % kernel_name,
-                "peak_source": peak_kind, "bytes_per_launch": bytes_per_launch, "kernel_ms": fwd_avg_s * 1e3,
-                "finalize_ms": fin_ms / max(nfin, 1)}
-    if persistent:
-        # the state stays in shared memory: report the step time, not a DRAM fraction
-        roofline["us_per_step"] = fwd_avg_s * 1e6 / steps_per_launch
-        roofline["note"] = "one single-CTA launch per bte_step call; the state never leaves shared memory"
-        roofline["finalize_ms"] = 0.0
+    roofline = roofline_of(info, args.steps, fwd_ms, nfwd, fin_ms, nfin, peak, peak_kind,
+                           measured_traffic(args.workload, args.storage, kernel_name))
 
     # end to end through the C ABI with host buffers: upload the step's source (pinned), step,
     # read the step's lattice temperature back
@@ -411,50 +534,46 @@ def run_gb300(args):
         e2e = {"value": info.nelem * args.e2e_steps * d.world / te, "unit": UNIT,
                "h2d_bytes_per_step": int(info.ncell * 4 if Qh is not None else 0),
                "d2h_bytes_per_step": int(info.ncell * 4)}
-    # adjoint workloads: one bte_adjoint call (forward sweep + checkpointed reverse sweep) of
-    # J = mean T_L over the probe, traced: adjoint-step and forward-step device times
+    # adjoint workloads as the headline: one traced bte_adjoint call
     adjoint = None
     if "probe" in cfg:
         nadj = args.adj_steps if args.adj_steps is not None else cfg["steps"]
         kck = args.ckpt if args.ckpt is not None else cfg.get("ckpt", 0)
-        probe = inputs.probe_weights(cfg)
-        bte.bte_init_temperature(ctx, None)
-        if Q is not None:
-            bte.bte_set_source(ctx, torch.from_numpy(Q.reshape(-1)).cuda(), amps)
-        torch.cuda.synchronize()
-        bte.bte_profile(ctx, True)
-        t0 = time.perf_counter()
-        J, gQ, gt = bte.bte_adjoint(ctx, nadj, probe, kck)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-        adj_ms, nadj_k, rec_ms, nrec = bte.bte_adjoint_profile_read(ctx)
-        bte.bte_profile(ctx, False)
-        adj_step = adj_ms / max(nadj_k, 1)
-        fwd_step = fwd_avg_s * 1e3 + fin_ms / max(nfin, 1)
-        adj_bytes = info.nelem * (8 + info.elem_bytes)
-        adjoint = {"steps": nadj, "ckpt": kck, "J": J, "adj_step_ms": adj_step, "fwd_step_ms": fwd_step,
-                   "ratio": adj_step / fwd_step, "recompute_steps": nrec, "recompute_ms": rec_ms, "wall_s": wall,
-                   "bytes_per_adj_step": adj_bytes, "achieved_gbs": adj_bytes / (adj_step / 1e3) / 1e9,
-                   "frac": adj_bytes / (adj_step / 1e3) / 1e9 / peak,
-                   "grad_finite": bool(np.all(np.isfinite(gQ)) and np.all(np.isfinite(gt)))}
-    cpu = None
-    if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:
-        v, n, grid, secs = time_oracle(cfg, args.cpu_seconds, args.limiter)
-        cpu = {"value": v, "unit": UNIT, "cores": omp_threads(), "kind": "oracle",
-               "sample": "%d FP64 oracle steps on a %s slab of the workload (all bands and directions), %.1f s"
-                         % (n, "x".join(map(str, grid)), secs)}
+        fwd_step = fwd_ms / max(nfwd, 1) + fin_ms / max(nfin, 1)
+        adjoint = adjoint_record(ctx, cfg, info, fwd_step, nadj, kck, Q, amps, peak)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": d.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32", "storage": args.storage, "data": "synthetic",
             "config": {"workload": cfg["name"], "grid": list(cfg["n"]), "bands": info.nbands, "dirs": info.ndirs,
                        "storage": args.storage, "limiter": args.limiter, "kernel": kernel_name,
                        **({"rounding": args.rounding, "T_scale": args.t_scale} if args.storage != "f32" else {}),
                        "updates_per_step": info.nelem, "l2": l2_note(info),
                        "parallelism": "replicas" if d.world > 1 else "single"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(nfwd if persistent else nfwd * info.launches_per_step),
-            "clocks": ck}
+            "roofline": roofline, "cpu_baseline": None, "e2e": e2e,
+            "gpu_launches": int(nfwd if persistent else nfwd * info.launches_per_step), "clocks": ck}
     if adjoint is not None:
         line["adjoint"] = adjoint
+    bte.bte_destroy(ctx)
+    del ctx
+    gc.collect()
+    torch.cuda.empty_cache()
+    # the other workloads, storage forms and the adjoint ratios (one GPU runs only)
+    if d.world == 1 and not args.no_sub_records:
+        subs = []
+        for name, st, ts, steps, nadj, kck in SUB_RECORDS:
+            if name == args.workload and st == args.storage and nadj is None:
+                continue
+            subs.append(sub_record(args, name, st, ts, steps, nadj, kck, peak, peak_kind))
+        line["sub_records"] = subs
+    if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:
+        v, n, grid, secs = time_oracle(cfg, args.cpu_seconds, args.limiter)
+        cpu = {"value": v, "unit": UNIT, "cores": omp_threads(), "kind": "oracle",
+               "sample": "%d FP64 oracle steps on a %s cut of the workload (all bands and directions), %.1f s"
+                         % (n, "x".join(map(str, grid)), secs)}
+        one = time_oracle_one_thread(args.workload, min(args.cpu_seconds, 10.0), args.limiter)
+        if one is not None:
+            cpu["single_thread"] = one
+        line["cpu_baseline"] = cpu
     if d.rank == 0:
         print(json.dumps(line), flush=True)
     d.barrier()

@@ -45,7 +45,7 @@ typedef enum {
     BTE_ECUDA = 3,         /* a CUDA runtime call failed (message in bte_last_error) */
     BTE_ESTATE = 4,        /* call not valid in the context's current state */
     BTE_ENONFINITE = 5,    /* a non-finite value was found in the state or an output */
-    BTE_ETIMEOUT = 6,      /* reserved: a bounded device wait gave up */
+    BTE_ETIMEOUT = 6,      /* a bounded device wait gave up (see bte_set_wait_limit) */
     BTE_EUNSUPPORTED = 7   /* valid request this build does not implement */
 } bte_status;
 
@@ -289,8 +289,21 @@ bte_status bte_adjoint_profile_read(bte_ctx *ctx, double *adj_ms, long long *adj
 bte_status bte_get_info(const bte_ctx *ctx, bte_info *info);
 bte_status bte_get_quadrature(const bte_ctx *ctx, double *s, double *w);
 
-/* Wait for all work issued on the context's stream. */
+/* Wait for all work issued on the context's stream.  Returns BTE_ETIMEOUT (once) when a
+ * bounded device wait of a step issued since the last such report gave up. */
 bte_status bte_synchronize(bte_ctx *ctx);
+
+/* Time limit of the bounded waits in the tiled forward kernel (a control of this library; the
+ * paper has no counterpart).  Each warp of that kernel waits on shared-memory barriers for its
+ * data (consumers) or for a free stage (producer); a wait that lasts longer than limit_ns
+ * nanoseconds gives up, the CTA stops its arithmetic but finishes its schedule, every bulk copy
+ * it issued is waited for (2 s at most) before it exits, and the launch ends.  That step's
+ * output is invalid: the next call that synchronises the stream (bte_synchronize, or a call
+ * returning data to the host) returns BTE_ETIMEOUT once and clears the flag, and the context
+ * stays usable (bte_set_state or bte_init_temperature gives a valid state again).
+ * limit_ns <= 0 restores the default of 2 s.  Takes effect at the next bte_step; other kernels
+ * hold no such waits.  Never fails for a valid ctx. */
+bte_status bte_set_wait_limit(bte_ctx *ctx, long long limit_ns);
 
 /* Kernel tracing with CUDA events on the context's stream.  bte_profile(ctx, 1) clears the
  * counters and starts recording an event pair around every forward-step launch and every

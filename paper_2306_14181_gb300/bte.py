@@ -27,7 +27,8 @@ BTE_KERNEL_AUTO, BTE_KERNEL_GENERIC, BTE_KERNEL_TILED, BTE_KERNEL_PERSISTENT = 0
 EXPORTS = ["bte_create", "bte_destroy", "bte_last_error", "bte_init_temperature", "bte_set_source", "bte_step",
            "bte_lattice_temperature", "bte_moments", "bte_energy", "bte_get_state", "bte_set_state",
            "bte_get_values", "bte_adjoint", "bte_adjoint_profile_read",
-           "bte_get_info", "bte_get_quadrature", "bte_synchronize", "bte_profile", "bte_profile_read", "bte_energy_noalloc"]
+           "bte_get_info", "bte_get_quadrature", "bte_synchronize", "bte_profile", "bte_profile_read", "bte_energy_noalloc",
+           "bte_set_wait_limit"]
 
 _STATUS = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESTATE", 5: "ENONFINITE", 6: "ETIMEOUT", 7: "EUNSUPPORTED"}
 
@@ -104,6 +105,7 @@ def load():
     lib.bte_get_info.argtypes = [P, ct.POINTER(bte_info)]
     lib.bte_get_quadrature.argtypes = [P, dp, dp]
     lib.bte_synchronize.argtypes = [P]
+    lib.bte_set_wait_limit.argtypes = [P, ct.c_longlong]
     lib.bte_profile.argtypes = [P, ct.c_int]
     lib.bte_profile_read.argtypes = [P, dp, ct.POINTER(ct.c_longlong), dp, ct.POINTER(ct.c_longlong)]
     for name in EXPORTS:
@@ -229,6 +231,11 @@ def bte_step(ctx, n=1):
 
 def bte_synchronize(ctx):
     _check(load().bte_synchronize(ctx.handle), ctx.handle)
+
+
+def bte_set_wait_limit(ctx, limit_ns=0):
+    """Limit (ns) of the tiled forward kernel's bounded waits; 0 restores the default 2 s."""
+    _check(load().bte_set_wait_limit(ctx.handle, int(limit_ns)), ctx.handle)
 
 
 def bte_lattice_temperature(ctx, out=None):

@@ -747,6 +747,12 @@ extern "C" bte_status bte_synchronize(bte_ctx *c) {
     return check_device_flags(c);
 }
 
+extern "C" bte_status bte_set_wait_limit(bte_ctx *c, long long limit_ns) {
+    if (!c) return fail(nullptr, BTE_EINVAL, "ctx is NULL");
+    c->plan.wait_ns = limit_ns > 0 ? (unsigned long long)limit_ns : 2000000000ull;
+    return BTE_OK;
+}
+
 extern "C" bte_status bte_lattice_temperature(bte_ctx *c, double *dTL) {
     if (!c || !dTL) return fail(c, BTE_EINVAL, "NULL argument");
     if (!c->h_tl) CU(c, cudaMallocHost((void **)&c->h_tl, c->ncell * sizeof(float)));  // pinned: a direct copy

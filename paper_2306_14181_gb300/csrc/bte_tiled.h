@@ -26,6 +26,7 @@ struct TiledArgs {
     int ty, tz;            // tile extents (rows, slices)
     int tcells;            // cells of a full tile (row length of P)
     int chunk;             // rows per bulk copy of a box slice
+    unsigned long long wait_ns;  // limit of a bounded mbarrier wait (ns)
 };
 
 // Plane-synchronous schedule of the tiled forward kernel.  The plane list (k*nd + d) of every
@@ -56,6 +57,7 @@ struct TiledPlan {
     void *isorow = nullptr;
     int storage = 0, nx = 0, chunk = 4;
     int *err = nullptr;
+    unsigned long long wait_ns = 2000000000ull;  // bounded-wait limit (bte_set_wait_limit)
 };
 
 // Shape check, tile geometry and the schedule (queries the current device for its SM count

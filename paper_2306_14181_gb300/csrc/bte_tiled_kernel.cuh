@@ -10,7 +10,8 @@
 namespace bte {
 namespace tiled {
 
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s: the drain limit, and the default of TiledArgs::wait_ns
+constexpr int kAbortOff = 112;  // byte offset of the CTA's abort word in shared memory (after <= 6 + 6 mbarriers)
 constexpr int kHdrFloats = 16;                        // per-plane constants written by the producer
 
 // Tile geometry: a lane holds VL consecutive cells of a row, WPR warps cover a row of
@@ -187,19 +188,30 @@ __device__ __forceinline__ unsigned long long gtimer() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// Wait for phase `parity` of the barrier, giving up after kWaitLimitNs: the error word gets
-// `code` and the caller stops its work.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int code) {
+// Wait for phase `parity` of the barrier, giving up after limit_ns nanoseconds: the error word
+// gets `code` and false is returned.  The callers never leave the CTA's schedule on a false
+// return (see the abort word below), so a give-up cannot strand another warp at a barrier.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int code,
+                                          unsigned long long limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = gtimer();
     while (!mbar_try_wait(bar, parity)) {
-        if (gtimer() - t0 > kWaitLimitNs) {
+        if (gtimer() - t0 > limit_ns) {
             atomicOr(err, code);
             return false;
         }
     }
     return true;
 }
+// The CTA's abort word (shared memory): set once any warp's bounded wait gave up.  From then on
+// the producer issues no more copies and the consumers skip their waits and their arithmetic
+// but still walk the whole schedule, so every warp reaches each named barrier and each stage
+// release the same number of times and the kernel ends.  The step's output is invalid and the
+// host reports BTE_ETIMEOUT.
+__device__ __forceinline__ bool cta_aborted(const char *smem) {
+    return __any_sync(0xffffffffu, *reinterpret_cast<const volatile int *>(smem + kAbortOff) != 0);
+}
+__device__ __forceinline__ void cta_abort(char *smem) { *reinterpret_cast<volatile int *>(smem + kAbortOff) = 1; }
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                      su32(dst)),
@@ -411,8 +423,19 @@ __device__ void producer(const StepArgs &a, const TiledArgs &p, char *smem, uint
     for (int j = 0; j < p.ns && ahead_ok; ++j) ahead_ok = ahead.next(a, p);  // the plane-tile ns later
     int s = 0;         // stage of plane-tile i = i mod ns
     uint32_t ph = 0u;  // its use count parity = (i / ns) mod 2
+    int issued = 0;    // plane-tiles whose copies were issued
     for (int i = 0; more; ++i, more = cur.next(a, p)) {
-        if (i >= p.ns && !mbar_wait(&empty[s], ph ^ 1u, p.err, 2)) return;
+        if (cta_aborted(smem)) break;
+        if (i >= p.ns) {
+            // the consumers released the stage, and the copies of its previous use have landed
+            // (at once in a normal run: the consumers waited for them; after an abort they may not)
+            bool ok = mbar_wait(&empty[s], ph ^ 1u, p.err, 2, p.wait_ns);
+            ok = ok && mbar_wait(&full[s], ph ^ 1u, p.err, 2, kWaitLimitNs);
+            if (!__all_sync(0xffffffffu, ok)) {
+                cta_abort(smem);
+                break;
+            }
+        }
         fence_proxy_async();
         __syncwarp();
         const PT &q = cur.q;
@@ -488,6 +511,7 @@ __device__ void producer(const StepArgs &a, const TiledArgs &p, char *smem, uint
                 }
         }
         mbar_arrive(&full[s]);
+        issued = i + 1;
         // pull the rows of a later plane-tile towards L2 (no shared memory involved)
         if (ahead_ok) {
             const PT &qp = ahead.q;
@@ -505,6 +529,9 @@ __device__ void producer(const StepArgs &a, const TiledArgs &p, char *smem, uint
             ph ^= 1u;
         }
     }
+    // Before the CTA exits, every bulk copy it issued has landed: the last use of each stage
+    // (bounded; a copy that never lands leaves the error flag set).
+    for (int j = max(issued - p.ns, 0); j < issued; ++j) mbar_wait(&full[j % p.ns], (uint32_t)(j / p.ns) & 1u, p.err, 2, kWaitLimitNs);
 }
 
 // ---- consumer warps -----------------------------------------------------------------------
@@ -938,10 +965,20 @@ __device__ void consumer(const StepArgs &a, const TiledArgs &p, char *smem, uint
                 }
             }
         }
-        if (!mbar_wait(&full[s], ph, p.err, 1)) return;
+        // warp-uniform: the stage's copies landed (fast path), else wait unless a warp of the
+        // CTA has given up.  After an abort a stage may pass the test with stale contents; the
+        // arithmetic on it reads only in-bounds addresses and the step is reported invalid.
+        bool ok = __all_sync(0xffffffffu, mbar_try_wait(&full[s], ph));
+        if (!ok) {
+            ok = !cta_aborted(smem);
+            if (ok) ok = __all_sync(0xffffffffu, mbar_wait(&full[s], ph, p.err, 1, p.wait_ns));
+            if (!ok && lane == 0) cta_abort(smem);
+        }
         const char *stage = smem + p.stage0 + (size_t)s * p.stage_bytes;
-        if constexpr (REF) wsum += reinterpret_cast<const float *>(stage + p.hdr_off)[3];
-        if (zl < q.nzt && rb < q.nyt) {
+        if constexpr (REF) {
+            if (ok) wsum += reinterpret_cast<const float *>(stage + p.hdr_off)[3];
+        }
+        if (ok && zl < q.nzt && rb < q.nyt) {
             const float *hd = reinterpret_cast<const float *>(stage + p.hdr_off);
             const bool px = hd[0] > 0.f, py = hd[1] > 0.f;  // the signs rows_of_warp takes
             const bool full = rb + Geo<DIM, WPR>::KR <= q.nyt;
@@ -977,6 +1014,7 @@ __global__ void __launch_bounds__((Geo<DIM, WPR>::NCW + kProducerWarps) * 32, 1)
             mbar_init(&full[s], 32);
             mbar_init(&empty[s], Geo<DIM, WPR>::NCW);
         }
+        *reinterpret_cast<int *>(smem + kAbortOff) = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     float *wsm = reinterpret_cast<float *>(smem + p.wall_off);

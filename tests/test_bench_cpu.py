@@ -1,5 +1,5 @@
 """bench.py's reference arm on the host cores (no GPU): the FP64 oracle timed on a bounded sample
-of the hot-spot workload, printed as one JSON line with the contract's keys."""
+of the 3-D laser workload, printed as one JSON line with the contract's keys."""
 import json
 import os
 import subprocess
@@ -18,7 +18,7 @@ def test_reference_arm_json_line():
                 "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert key in line
     assert line["value"] > 0 and line["higher_is_better"] is True and line["steps"] == 1
-    assert line["config"]["workload"].startswith("hotspot_2d")
+    assert line["config"]["workload"].startswith("laser_3d")
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
     e2e = line["e2e"]
