@@ -135,10 +135,18 @@ typedef struct {
     const double *w;
 } bte_quadrature;
 
-/* Wall types and thermalizing-wall temperatures (offsets from T_ref, K). */
+/* Wall types and thermalizing-wall temperatures (offsets from T_ref, K).
+ * dT_jump[a]: temperature difference (K) across the periodic pair of axis a, Sec. 2.2 (iv):
+ * the ghost values of the -a wall are the wrapped values plus C_k dT_jump[a] / W and those of
+ * the +a wall the wrapped values minus it (every direction, both ghost layers), so that a
+ * uniform gradient dT_jump[a] / L_a along +a is represented exactly; dT_jump[a] > 0 means the -a
+ * side is the warmer one and heat flows towards +a.  Must be 0 on an axis that is not periodic
+ * (BTE_EINVAL otherwise).  A non-zero jump runs the generic kernels (bte_info.kernel says so);
+ * BTE_EUNSUPPORTED when options.kernel asks for the tiled or persistent kernel. */
 typedef struct {
     int type[6];
     double T_wall[6];
+    double dT_jump[3];
 } bte_boundaries;
 
 typedef struct {
@@ -263,6 +271,22 @@ bte_status bte_set_state(bte_ctx *ctx, const void *src, size_t bytes, const floa
  * temporary device buffer of the same size; the context's stream is synchronised. */
 bte_status bte_get_values(bte_ctx *ctx, float *dst, int on_device);
 
+/* Residuals of the transient solver's loop condition (Sec. 4.1, Algorithm 2).  bte_residuals
+ * runs nsteps >= 1 steps and returns, for the last two states n and n+1 of the call,
+ *   eps_T = sqrt(sum_i (T_i^n - T_i^{n+1})^2 / N) / T_max,
+ *   eps_q = sqrt(sum_i (|q|_i^n - |q|_i^{n+1})^2 / N) / |q|_max,
+ * with T and q of Eq. (getTQ) formed in FP64 on the device, N the number of cells,
+ * T_max = max_i (T_ref + T_i^{n+1}) (absolute temperature, as the paper's solver works in) and
+ * |q|_max = max_i |q_i^{n+1}|; a ratio whose numerator is 0 is 0.  Outputs are host doubles (may
+ * be NULL); the stream is synchronised.  Diagnostic buffers are allocated on first use.
+ * bte_run_steady repeats bte_residuals(check_every) until eps_T < tol_T and eps_q < tol_q, or
+ * until max_steps steps have run (the last stretch may be shorter); it returns the steps it ran
+ * and the last residuals.  Both report BTE_ENONFINITE for a non-finite state and BTE_ETIMEOUT
+ * as bte_synchronize does. */
+bte_status bte_residuals(bte_ctx *ctx, int nsteps, double *eps_T, double *eps_q);
+bte_status bte_run_steady(bte_ctx *ctx, long long max_steps, int check_every, double tol_T, double tol_q,
+                          long long *steps_done, double *eps_T, double *eps_q);
+
 /* Discrete adjoint (the exact transpose of the step; the paper has no adjoint) of
  *     J = sum_i probe_i T_L,i   after nsteps steps from the context's current state,
  * T_L of Eq. (BTE_get_e0).  Runs the nsteps forward steps (the context ends in the state
@@ -302,8 +326,12 @@ bte_status bte_synchronize(bte_ctx *ctx);
  * returning data to the host) returns BTE_ETIMEOUT once and clears the flag, and the context
  * stays usable (bte_set_state or bte_init_temperature gives a valid state again).
  * limit_ns <= 0 restores the default of 2 s.  Takes effect at the next bte_step; other kernels
- * hold no such waits.  Never fails for a valid ctx. */
-bte_status bte_set_wait_limit(bte_ctx *ctx, long long limit_ns);
+ * hold no such waits.
+ * stall_test (failure-detection test, normally 0): 1 makes every consumer warp's first wait of
+ * the next tiled forward launch wait on a barrier that nothing completes, 2 does the same for
+ * the producer warp (3: both); that wait gives up after limit_ns and the launch ends as above.
+ * It applies to one launch only and is then cleared.  BTE_EINVAL for stall_test outside 0..3. */
+bte_status bte_set_wait_limit(bte_ctx *ctx, long long limit_ns, int stall_test);
 
 /* Kernel tracing with CUDA events on the context's stream.  bte_profile(ctx, 1) clears the
  * counters and starts recording an event pair around every forward-step launch and every

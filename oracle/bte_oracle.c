@@ -27,6 +27,11 @@
  *   - Boundaries (Sec. 2.2) are imposed through two ghost layers per wall.
  *   - The volumetric source is split over bands and directions in proportion to
  *     the heat capacity and uniformly in angle: Qdot_{k,d,i} = a(t_n) Q_i C_k/(sum C W).
+ *   - A periodic pair may carry a temperature difference dT (Sec. 2.2 (iv)): the
+ *     ghosts of the -a wall hold the wrapped values plus C_k dT/W, those of the +a
+ *     wall the wrapped values minus C_k dT/W (every direction and both ghost layers:
+ *     the ghost region is the periodic image of the domain shifted by the jump, so a
+ *     uniform gradient is represented exactly).  dT > 0: the -a side is warmer.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -53,6 +58,7 @@ typedef struct {
     double Tw[6];              /* isothermal wall temperature minus T_ref (K) */
     double dt;
     int limiter;
+    double jump[3];            /* temperature difference across each periodic pair (K), Sec. 2.2 (iv) */
 } orc_problem;
 
 /* ------------------------------------------------------------------------- */
@@ -92,6 +98,13 @@ static double sum_C_over_tau(const orc_problem *P) {
 }
 
 #define EIDX(P, k, d, i) ((((long)(k) * (P)->nd + (d)) * ncell_of(P)) + (i))
+
+/* Offset of a periodic ghost of band k on the side `side` of axis a, Sec. 2.2 (iv):
+ * e(r_B1) = e(r_B2) + C dT / 4 pi with 4 pi -> W; B1 = the -a wall. */
+static double periodic_jump(const orc_problem *P, int k, int a, int side) {
+    const double off = P->C[k] * P->jump[a] / total_weight(P);
+    return side == 0 ? off : -off;
+}
 
 /* Slope limiter of the two one-sided differences a (upwind side) and b (downwind side). */
 static double limiter(int kind, double a, double b) {
@@ -207,7 +220,7 @@ static double ext_value(const orc_problem *P, const double *e, const double *edi
     switch (P->bc[wall]) {
     case ORC_BC_PERIODIC:
         cc[a] = ((p % n) + n) % n;
-        return e[EIDX(P, k, d, cidx(P, cc))];
+        return e[EIDX(P, k, d, cidx(P, cc))] + periodic_jump(P, k, a, side);
     case ORC_BC_ISOTHERMAL:
         if (incoming) return P->C[k] * P->Tw[wall] / total_weight(P);
         cc[a] = wallpos;
@@ -493,7 +506,7 @@ static int ext_deps(const orc_problem *P, int k, int d, int a, const int c[3], i
 }
 
 /* Homogeneous part of an extended value of a perturbation de (thermalizing-wall
- * emission is a constant, so its perturbation is 0). */
+ * emission and the periodic jump are constants, so their perturbation is 0). */
 static double ext_value_lin(const orc_problem *P, const double *de, const double *dediff, int k, int d, int a,
                             const int c[3], int p) {
     const int n = extent(P, a);
@@ -503,6 +516,7 @@ static double ext_value_lin(const orc_problem *P, const double *de, const double
         const double sa = P->s[3 * d + a];
         const int incoming = side == 0 ? (sa > 0.0) : (sa < 0.0);
         if (P->bc[wall] == ORC_BC_ISOTHERMAL && incoming) return 0.0;
+        if (P->bc[wall] == ORC_BC_PERIODIC) return ext_value(P, de, dediff, k, d, a, c, p) - periodic_jump(P, k, a, side);
     }
     return ext_value(P, de, dediff, k, d, a, c, p);
 }

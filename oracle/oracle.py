@@ -7,6 +7,7 @@ Boundary codes: 0 isothermal, 1 diffuse, 2 specular, 3 periodic; walls ordered
 -x, +x, -y, +y, -z, +z.  Limiter codes: 0 first order, 1 minmod, 2 van Albada.
 """
 import ctypes as ct
+import math
 import os
 import subprocess
 import threading
@@ -47,6 +48,7 @@ class _Prob(ct.Structure):
         ("mirror", ct.POINTER(ct.c_int)),
         ("bc", ct.c_int * 6), ("Tw", ct.c_double * 6),
         ("dt", ct.c_double), ("limiter", ct.c_int),
+        ("jump", ct.c_double * 3),
     ]
 
 
@@ -83,7 +85,7 @@ def _fp(a):
 class Problem:
     """One discretised problem: grid, bands, quadrature, walls, time step and limiter."""
 
-    def __init__(self, dim, n, h, C, v, tau, s, w, mirror, bc, Tw, dt, limiter=LIM_VANALBADA):
+    def __init__(self, dim, n, h, C, v, tau, s, w, mirror, bc, Tw, dt, limiter=LIM_VANALBADA, jump=None):
         self.dim = int(dim)
         self.nx, self.ny, self.nz = (int(t) for t in n)
         self.dx, self.dy, self.dz = (float(t) for t in h)
@@ -98,11 +100,16 @@ class Problem:
         self.Tw = [float(t) for t in Tw]
         self.dt = float(dt)
         self.limiter = int(limiter)
+        # temperature difference across each periodic pair (Sec. 2.2 (iv)); 0 on other axes
+        self.jump = [float(t) for t in (jump if jump is not None else (0.0, 0.0, 0.0))]
+        for a in range(3):
+            assert self.jump[a] == 0.0 or self.bc[2 * a] == BC_PERIODIC, "a jump needs a periodic pair"
         self._lib = load_oracle()
         self._p = _Prob(self.dim, self.nx, self.ny, self.nz, self.dx, self.dy, self.dz, self.nb, self.nd,
                         _dp(self.C), _dp(self.v), _dp(self.tau), _dp(self.s), _dp(self.w),
                         self.mirror.ctypes.data_as(ct.POINTER(ct.c_int)),
-                        (ct.c_int * 6)(*self.bc), (ct.c_double * 6)(*self.Tw), self.dt, self.limiter)
+                        (ct.c_int * 6)(*self.bc), (ct.c_double * 6)(*self.Tw), self.dt, self.limiter,
+                        (ct.c_double * 3)(*self.jump))
 
     # -- sizes ---------------------------------------------------------------------------
     @property
@@ -225,6 +232,24 @@ class Problem:
         if rc != 0:
             raise MemoryError("oracle adjoint: trajectory does not fit in memory")
         return float(J[0]), gQ.reshape(self.nz, self.ny, self.nx), gt
+
+    def residuals(self, e_n, e_n1, Tref):
+        """The loop condition of the transient solver (Sec. 4.1, Algorithm 2) between consecutive
+        states: eps_T = sqrt(sum_i (T_i^n - T_i^{n+1})^2 / N) / T_max and eps_q the same for |q|,
+        T and q of Eq. (getTQ); T_max is the largest absolute temperature Tref + T_i^{n+1} and
+        |q|_max the largest |q_i^{n+1}|."""
+        T0, _, q0 = self.moments(e_n)
+        T1, _, q1 = self.moments(e_n1)
+        N = T0.size
+        qm0 = np.sqrt((q0 ** 2).sum(axis=0))
+        qm1 = np.sqrt((q1 ** 2).sum(axis=0))
+        num_T = math.sqrt(float(((T0 - T1) ** 2).sum()) / N)
+        num_q = math.sqrt(float(((qm0 - qm1) ** 2).sum()) / N)
+        Tmax = float(np.max(np.abs(Tref + T1)))
+        qmax = float(np.max(qm1))
+        eps_T = 0.0 if num_T == 0.0 else num_T / Tmax
+        eps_q = 0.0 if num_q == 0.0 else num_q / qmax
+        return eps_T, eps_q
 
     @property
     def cell_volume(self):

@@ -28,7 +28,7 @@ EXPORTS = ["bte_create", "bte_destroy", "bte_last_error", "bte_init_temperature"
            "bte_lattice_temperature", "bte_moments", "bte_energy", "bte_get_state", "bte_set_state",
            "bte_get_values", "bte_adjoint", "bte_adjoint_profile_read",
            "bte_get_info", "bte_get_quadrature", "bte_synchronize", "bte_profile", "bte_profile_read", "bte_energy_noalloc",
-           "bte_set_wait_limit"]
+           "bte_set_wait_limit", "bte_residuals", "bte_run_steady"]
 
 _STATUS = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESTATE", 5: "ENONFINITE", 6: "ETIMEOUT", 7: "EUNSUPPORTED"}
 
@@ -55,7 +55,7 @@ class bte_quadrature(ct.Structure):
 
 
 class bte_boundaries(ct.Structure):
-    _fields_ = [("type", ct.c_int * 6), ("T_wall", ct.c_double * 6)]
+    _fields_ = [("type", ct.c_int * 6), ("T_wall", ct.c_double * 6), ("dT_jump", ct.c_double * 3)]
 
 
 class bte_options(ct.Structure):
@@ -105,7 +105,10 @@ def load():
     lib.bte_get_info.argtypes = [P, ct.POINTER(bte_info)]
     lib.bte_get_quadrature.argtypes = [P, dp, dp]
     lib.bte_synchronize.argtypes = [P]
-    lib.bte_set_wait_limit.argtypes = [P, ct.c_longlong]
+    lib.bte_set_wait_limit.argtypes = [P, ct.c_longlong, ct.c_int]
+    lib.bte_residuals.argtypes = [P, ct.c_int, dp, dp]
+    lib.bte_run_steady.argtypes = [P, ct.c_longlong, ct.c_int, ct.c_double, ct.c_double,
+                                   ct.POINTER(ct.c_longlong), dp, dp]
     lib.bte_profile.argtypes = [P, ct.c_int]
     lib.bte_profile_read.argtypes = [P, dp, ct.POINTER(ct.c_longlong), dp, ct.POINTER(ct.c_longlong)]
     for name in EXPORTS:
@@ -163,8 +166,10 @@ def _current_stream():
 
 
 def bte_create(dim, n, h, C, vabs, tau, quad, bc, T_wall, dt, storage=BTE_STORE_F32, limiter=BTE_LIM_VANALBADA,
-               T_scale=1.0, rounding=BTE_ROUND_NEAREST, stream=None, seed=0, kernel=BTE_KERNEL_AUTO, Tref=300.0):
-    """bte_create.  quad: ("gl1d", n) | ("octant", ntheta, nphi) | ("explicit", s[nd,3], w[nd])."""
+               T_scale=1.0, rounding=BTE_ROUND_NEAREST, stream=None, seed=0, kernel=BTE_KERNEL_AUTO, Tref=300.0,
+               dT_jump=None):
+    """bte_create.  quad: ("gl1d", n) | ("octant", ntheta, nphi) | ("explicit", s[nd,3], w[nd]);
+    dT_jump: temperature difference (K) across each periodic pair (None: none)."""
     lib = load()
     C = np.ascontiguousarray(C, dtype=np.float64)
     vabs = np.ascontiguousarray(vabs, dtype=np.float64)
@@ -181,7 +186,9 @@ def bte_create(dim, n, h, C, vabs, tau, quad, bc, T_wall, dt, storage=BTE_STORE_
         w = np.ascontiguousarray(quad[2], dtype=np.float64)
         keep += [s, w]
         q = bte_quadrature(BTE_QUAD_EXPLICIT, 0, 0, w.size, _dp(s), _dp(w))
-    wl = bte_boundaries((ct.c_int * 6)(*[int(x) for x in bc]), (ct.c_double * 6)(*[float(x) for x in T_wall]))
+    jmp = [0.0, 0.0, 0.0] if dT_jump is None else [float(x) for x in dT_jump]
+    wl = bte_boundaries((ct.c_int * 6)(*[int(x) for x in bc]), (ct.c_double * 6)(*[float(x) for x in T_wall]),
+                        (ct.c_double * 3)(*jmp))
     st = _current_stream() if stream is None else ct.c_void_p(stream)
     o = bte_options(float(dt), int(storage), int(limiter), float(T_scale), int(rounding), st, int(seed), int(kernel))
     h_ = ct.c_void_p()
@@ -192,6 +199,8 @@ def bte_create(dim, n, h, C, vabs, tau, quad, bc, T_wall, dt, storage=BTE_STORE_
 
 def bte_from_workload(cfg, **opts):
     """bte_create for a workload dict of ``paper_2306_14181_gb300.inputs``."""
+    if cfg.get("jump") is not None:
+        opts.setdefault("dT_jump", cfg["jump"])
     return bte_create(cfg["dim"], cfg["n"], cfg["h"], cfg["C"], cfg["v"], cfg["tau"], cfg["quad"], cfg["bc"],
                       cfg["Tw"], opts.pop("dt", cfg["dt"]), **opts)
 
@@ -233,9 +242,27 @@ def bte_synchronize(ctx):
     _check(load().bte_synchronize(ctx.handle), ctx.handle)
 
 
-def bte_set_wait_limit(ctx, limit_ns=0):
-    """Limit (ns) of the tiled forward kernel's bounded waits; 0 restores the default 2 s."""
-    _check(load().bte_set_wait_limit(ctx.handle, int(limit_ns)), ctx.handle)
+def bte_set_wait_limit(ctx, limit_ns=0, stall_test=0):
+    """Limit (ns) of the tiled forward kernel's bounded waits (0: the default 2 s); stall_test 1/2/3
+    makes the consumers'/producer's/both first waits of the next launch wait on a barrier nothing
+    completes (a failure-detection test)."""
+    _check(load().bte_set_wait_limit(ctx.handle, int(limit_ns), int(stall_test)), ctx.handle)
+
+
+def bte_residuals(ctx, nsteps=1):
+    """Run nsteps steps; (eps_T, eps_q) of Algorithm 2 between the last two states."""
+    eT, eq = ct.c_double(), ct.c_double()
+    _check(load().bte_residuals(ctx.handle, int(nsteps), ct.byref(eT), ct.byref(eq)), ctx.handle)
+    return eT.value, eq.value
+
+
+def bte_run_steady(ctx, max_steps, check_every, tol_T, tol_q):
+    """Step until eps_T < tol_T and eps_q < tol_q (checked every check_every steps) or max_steps:
+    returns (steps run, eps_T, eps_q)."""
+    n, eT, eq = ct.c_longlong(), ct.c_double(), ct.c_double()
+    _check(load().bte_run_steady(ctx.handle, int(max_steps), int(check_every), float(tol_T), float(tol_q),
+                                 ct.byref(n), ct.byref(eT), ct.byref(eq)), ctx.handle)
+    return n.value, eT.value, eq.value
 
 
 def bte_lattice_temperature(ctx, out=None):

@@ -36,6 +36,8 @@ struct bte_ctx {
     std::vector<int> mirror;  // [3][nd], -1 = none
     int bc[6] = {0, 0, 0, 0, 0, 0};
     double Tw[6] = {0, 0, 0, 0, 0, 0};
+    double jump[3] = {0, 0, 0};  // temperature difference across each periodic pair (Sec. 2.2 (iv))
+    bool has_jump = false;
     double dt = 0, T_scale = 1;
     int storage = 0, limiter = 0, rounding = 0, kernel = 0;
     uint64_t seed = 0;
@@ -55,13 +57,14 @@ struct bte_ctx {
     int wc_max = 1;
     float inv_den[6] = {0, 0, 0, 0, 0, 0};
     // device tables
-    float *nu = nullptr, *wmom = nullptr, *wdiff = nullptr, *iso = nullptr;
+    float *nu = nullptr, *wmom = nullptr, *wdiff = nullptr, *iso = nullptr, *jmp = nullptr;
     int *mirror_d = nullptr;
     BandConst *band = nullptr;
     double *d_w = nullptr, *d_s = nullptr, *d_v = nullptr, *d_invtau = nullptr;
     // diagnostics scratch (allocated on first use)
     double *dg = nullptr;
     int *dflag = nullptr;
+    double *rs = nullptr;  // residuals: T^n, |q|^n [2 ncell], block partials [4 kResidBlocks], results [4]
     // tiled-kernel plan
     TiledPlan plan;
     bool tiled = false;
@@ -272,6 +275,7 @@ static StepArgs make_args(const bte_ctx *c) {
     a.mirror = c->mirror_d;
     a.band = c->band;
     a.iso = c->iso;
+    a.jmp = c->jmp;
     a.TL = c->TL;
     a.R = c->R;
     a.invTs = (float)(1.0 / c->T_scale);
@@ -300,7 +304,8 @@ static bte_status refresh_moments(bte_ctx *c) {
 
 static void free_all(bte_ctx *c) {
     void *ptrs[] = {c->d_amp, c->wf, c->e[0], c->e[1], c->TL, c->R, c->Q, c->P, c->ediff[0], c->ediff[1], c->nu, c->wmom, c->wdiff,
-                    c->iso, c->mirror_d, c->band, c->d_w, c->d_s, c->d_v, c->d_invtau, c->dg, c->dflag};
+                    c->iso, c->jmp, c->mirror_d, c->band, c->d_w, c->d_s, c->d_v, c->d_invtau, c->dg, c->dflag,
+                    c->rs};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     tiled_free(c->plan);
@@ -379,10 +384,17 @@ extern "C" bte_status bte_create(const bte_grid *grid, const bte_bands *bands, c
     for (int a = 0; a < 3; ++a) {
         if (a >= c->dim) {
             c->bc[2 * a] = c->bc[2 * a + 1] = BTE_BC_PERIODIC;  // unused
+            if (walls->dT_jump[a] != 0.0) return fail(nullptr, BTE_EINVAL, "inactive axis %d: dT_jump must be 0", a);
             continue;
         }
         if ((c->bc[2 * a] == BTE_BC_PERIODIC) != (c->bc[2 * a + 1] == BTE_BC_PERIODIC))
             return fail(nullptr, BTE_EINVAL, "axis %d: a periodic wall needs a periodic partner", a);
+        const double jp = walls->dT_jump[a];
+        if (!std::isfinite(jp)) return fail(nullptr, BTE_EINVAL, "axis %d: non-finite dT_jump", a);
+        if (jp != 0.0 && c->bc[2 * a] != BTE_BC_PERIODIC)
+            return fail(nullptr, BTE_EINVAL, "axis %d: dT_jump needs a periodic pair", a);
+        c->jump[a] = jp;
+        if (jp != 0.0) c->has_jump = true;
         for (int side = 0; side < 2; ++side)
             if (c->bc[2 * a + side] == BTE_BC_SPECULAR)
                 for (int d = 0; d < c->nd; ++d)
@@ -446,17 +458,20 @@ extern "C" bte_status bte_create(const bte_grid *grid, const bte_bands *bands, c
             cudaGetLastError();
             optin = 0;
         }
-        const bool fits = c->dim == 1 && c->storage == BTE_STORE_F32 && ps <= (size_t)optin;
+        const bool fits = c->dim == 1 && c->storage == BTE_STORE_F32 && ps <= (size_t)optin && !c->has_jump;
         if (c->kernel == BTE_KERNEL_PERSISTENT && !fits) {
-            c->err = "persistent kernel unavailable: it needs a 1-D FP32 state that fits in shared memory";
+            c->err = "persistent kernel unavailable: it needs a 1-D FP32 state that fits in shared memory and no "
+                     "periodic temperature jump";
             return bail(BTE_EUNSUPPORTED);
         }
         c->persist = fits && (c->kernel == BTE_KERNEL_AUTO || c->kernel == BTE_KERNEL_PERSISTENT);
     }
     if (c->kernel != BTE_KERNEL_GENERIC && !c->persist) {
         std::string why;
-        c->tiled = tiled_plan(c->dim, c->n, c->nb, c->nd, c->storage, c->limiter,
-                              c->rounding == BTE_ROUND_STOCHASTIC, c->bc, c->plan, why);
+        // the tiled kernel takes periodic ghosts as plain wrapped rows (no jump offset)
+        c->tiled = !c->has_jump && tiled_plan(c->dim, c->n, c->nb, c->nd, c->storage, c->limiter,
+                                              c->rounding == BTE_ROUND_STOCHASTIC, c->bc, c->plan, why);
+        if (c->has_jump) why = "a periodic temperature jump runs the generic kernel";
         if (!c->tiled && c->kernel == BTE_KERNEL_TILED) {
             c->err = "tiled kernel unavailable: " + why;
             return bail(BTE_EUNSUPPORTED);
@@ -485,7 +500,8 @@ extern "C" bte_status bte_create(const bte_grid *grid, const bte_bands *bands, c
         }
     }
     // host tables
-    std::vector<float> nu(3 * nplanes, 0.f), wmom(nplanes), wdiff(6 * c->nd, 0.f), iso(6 * c->nb, 0.f);
+    std::vector<float> nu(3 * nplanes, 0.f), wmom(nplanes), wdiff(6 * c->nd, 0.f), iso(6 * c->nb, 0.f),
+        jmp(3 * c->nb, 0.f);
     std::vector<BandConst> band(c->nb);
     for (int k = 0; k < c->nb; ++k) {
         BandConst &b = band[k];
@@ -504,6 +520,7 @@ extern "C" bte_status bte_create(const bte_grid *grid, const bte_bands *bands, c
         }
         for (int wl = 0; wl < 2 * c->dim; ++wl)
             if (c->bc[wl] == BTE_BC_ISOTHERMAL) iso[wl * c->nb + k] = (float)(c->C[k] * c->Tw[wl] / c->W);
+        for (int a = 0; a < 3; ++a) jmp[a * c->nb + k] = (float)(c->C[k] * c->jump[a] / c->W);
     }
     for (int wl = 0; wl < 2 * c->dim; ++wl) {
         const int a = wl >> 1;
@@ -539,6 +556,7 @@ extern "C" bte_status bte_create(const bte_grid *grid, const bte_bands *bands, c
     if ((st = dalloc(c, &c->wmom, wmom.size())) != BTE_OK) return bail(st);
     if ((st = dalloc(c, &c->wdiff, wdiff.size())) != BTE_OK) return bail(st);
     if ((st = dalloc(c, &c->iso, iso.size())) != BTE_OK) return bail(st);
+    if ((st = dalloc(c, &c->jmp, jmp.size())) != BTE_OK) return bail(st);
     if ((st = dalloc(c, &c->mirror_d, mir.size())) != BTE_OK) return bail(st);
     if ((st = dalloc(c, &c->band, band.size())) != BTE_OK) return bail(st);
     if ((st = dalloc(c, &c->d_w, c->w.size())) != BTE_OK) return bail(st);
@@ -550,6 +568,7 @@ extern "C" bte_status bte_create(const bte_grid *grid, const bte_bands *bands, c
     if ((st = upload(c, c->wmom, wmom.data(), wmom.size())) != BTE_OK) return bail(st);
     if ((st = upload(c, c->wdiff, wdiff.data(), wdiff.size())) != BTE_OK) return bail(st);
     if ((st = upload(c, c->iso, iso.data(), iso.size())) != BTE_OK) return bail(st);
+    if ((st = upload(c, c->jmp, jmp.data(), jmp.size())) != BTE_OK) return bail(st);
     if ((st = upload(c, c->mirror_d, mir.data(), mir.size())) != BTE_OK) return bail(st);
     if ((st = upload(c, c->band, band.data(), band.size())) != BTE_OK) return bail(st);
     if ((st = upload(c, c->d_w, c->w.data(), c->w.size())) != BTE_OK) return bail(st);
@@ -706,8 +725,12 @@ extern "C" bte_status bte_step(bte_ctx *c, int nsteps) {
         cudaError_t e;
         cudaEvent_t ev;
         if (c->prof) TRY(prof_event(c, &ev));
-        if (c->tiled) e = launch_step_tiled(a, c->plan, c->stream);
-        else e = launch_step_generic(a, c->storage, c->limiter, c->stream);
+        if (c->tiled) {
+            e = launch_step_tiled(a, c->plan, c->stream);
+            c->plan.stall = 0;
+        } else {
+            e = launch_step_generic(a, c->storage, c->limiter, c->stream);
+        }
         if (e != cudaSuccess) return fail(c, BTE_ECUDA, "forward step launch: %s", cudaGetErrorString(e));
         if (c->prof) TRY(prof_event(c, &ev));
         // T_L^{n+1} goes to the buffer of the old code reference; T_L^n becomes the reference of
@@ -747,9 +770,11 @@ extern "C" bte_status bte_synchronize(bte_ctx *c) {
     return check_device_flags(c);
 }
 
-extern "C" bte_status bte_set_wait_limit(bte_ctx *c, long long limit_ns) {
+extern "C" bte_status bte_set_wait_limit(bte_ctx *c, long long limit_ns, int stall_test) {
     if (!c) return fail(nullptr, BTE_EINVAL, "ctx is NULL");
+    if (stall_test < 0 || stall_test > 3) return fail(c, BTE_EINVAL, "stall_test must be 0..3");
     c->plan.wait_ns = limit_ns > 0 ? (unsigned long long)limit_ns : 2000000000ull;
+    c->plan.stall = stall_test;
     return BTE_OK;
 }
 
@@ -832,6 +857,65 @@ extern "C" bte_status bte_energy(bte_ctx *c, double *E_total, double wall_flux[6
     if (wall_flux)
         for (int wl = 0; wl < 6; ++wl) wall_flux[wl] = (wl < 2 * c->dim) ? (V / L[wl >> 1]) * res[1 + wl] : 0.0;
     if (flag) return fail(c, BTE_ENONFINITE, "the state holds a non-finite value");
+    return BTE_OK;
+}
+
+// T and q of the current state (Eq. getTQ, FP64) into the diagnostic buffers; the non-finite
+// flag is cleared first and read by the caller.
+static bte_status moments_on_device(bte_ctx *c, const DiagOut &o) {
+    StepArgs a = make_args(c);
+    a.e_in = c->e[c->cur];
+    DiagOut o2 = o;
+    o2.TL = nullptr;
+    o2.cellE = nullptr;
+    CU(c, launch_moments64(a, c->storage, c->d_w, c->d_s, c->d_v, c->d_invtau, c->sumC, c->D, o2, c->stream));
+    return BTE_OK;
+}
+
+extern "C" bte_status bte_residuals(bte_ctx *c, int nsteps, double *eps_T, double *eps_q) {
+    if (!c) return fail(nullptr, BTE_EINVAL, "ctx is NULL");
+    if (nsteps < 1) return fail(c, BTE_EINVAL, "nsteps must be >= 1");
+    TRY(diag_buffers(c));
+    if (!c->rs) TRY(dalloc(c, &c->rs, (size_t)2 * c->ncell + 4 * kResidBlocks + 4));
+    double *Tp = c->rs, *qp = c->rs + c->ncell, *part = c->rs + 2 * c->ncell, *res = part + 4 * kResidBlocks;
+    const DiagOut o = diag_layout(c);
+    TRY(bte_step(c, nsteps - 1));
+    CU(c, cudaMemsetAsync(c->dflag, 0, sizeof(int), c->stream));
+    TRY(moments_on_device(c, o));
+    CU(c, launch_resid_keep(o.T, o.q, c->ncell, Tp, qp, c->stream));
+    TRY(bte_step(c, 1));
+    TRY(moments_on_device(c, o));
+    CU(c, launch_residuals(o.T, o.q, Tp, qp, c->ncell, c->Tref, part, res, c->stream));
+    double r[4];
+    int flag = 0;
+    CU(c, cudaMemcpyAsync(r, res, sizeof r, cudaMemcpyDeviceToHost, c->stream));
+    CU(c, cudaMemcpyAsync(&flag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CU(c, cudaStreamSynchronize(c->stream));
+    TRY(check_device_flags(c));
+    if (flag) return fail(c, BTE_ENONFINITE, "the state holds a non-finite value");
+    const double N = (double)c->ncell;
+    auto ratio = [](double rms, double mx) { return rms == 0.0 ? 0.0 : (mx > 0.0 ? rms / mx : HUGE_VAL); };
+    if (eps_T) *eps_T = ratio(std::sqrt(r[0] / N), r[2]);
+    if (eps_q) *eps_q = ratio(std::sqrt(r[1] / N), r[3]);
+    return BTE_OK;
+}
+
+extern "C" bte_status bte_run_steady(bte_ctx *c, long long max_steps, int check_every, double tol_T, double tol_q,
+                                     long long *steps_done, double *eps_T, double *eps_q) {
+    if (!c) return fail(nullptr, BTE_EINVAL, "ctx is NULL");
+    if (max_steps < 1 || check_every < 1) return fail(c, BTE_EINVAL, "max_steps and check_every must be >= 1");
+    if (!(tol_T >= 0.0) || !(tol_q >= 0.0)) return fail(c, BTE_EINVAL, "tolerances must be >= 0");
+    long long done = 0;
+    double eT = HUGE_VAL, eq = HUGE_VAL;
+    while (done < max_steps) {
+        const int n = (int)std::min<long long>(check_every, max_steps - done);
+        TRY(bte_residuals(c, n, &eT, &eq));
+        done += n;
+        if (eT < tol_T && eq < tol_q) break;
+    }
+    if (steps_done) *steps_done = done;
+    if (eps_T) *eps_T = eT;
+    if (eps_q) *eps_q = eq;
     return BTE_OK;
 }
 

@@ -123,7 +123,8 @@ __device__ __forceinline__ void cell_coords(const StepArgs &a, long long i, int 
 // be a ghost (-2, -1, n, n+1).  Ghosts follow Sec. 2.2: periodic wrap; thermalizing wall
 // emission C_k T_w / W for incoming directions; diffuse wall value e_diff for incoming
 // directions; the wall cell itself for directions leaving through a thermalizing or diffuse
-// wall; the mirrored direction at the mirrored cell for a specular wall.
+// wall; the mirrored direction at the mirrored cell for a specular wall; periodic ghosts carry
+// the pair's temperature jump (+C_k dT / W on the -a side, minus it on the +a side).
 template <class Cd>
 __device__ __forceinline__ float ext_value(const StepArgs &a, const typename Cd::T *e, const BandConst &b, int k,
                                            int d, long long base, long long i, const int c[3], int ax, int pos,
@@ -138,8 +139,10 @@ __device__ __forceinline__ float ext_value(const StepArgs &a, const typename Cd:
     const int wall = 2 * ax + side;
     const int bc = a.bc[wall];
     if (bc == kBcPeriodic) {
+        // Sec. 2.2 (iv): the wrapped value, shifted by the pair's temperature difference
         const long long j = i + (long long)((side ? pos - n : pos + n) - c[ax]) * st;
-        return Cd::ld(e, base + j, b, rho_at<Cd>(a.R, a.invTs, j));
+        const float off = a.jmp[ax * a.nb + k];
+        return Cd::ld(e, base + j, b, rho_at<Cd>(a.R, a.invTs, j)) + (side ? -off : off);
     }
     if (bc == kBcSpecular) {
         const int layer = side ? pos - n + 1 : -pos;

@@ -56,6 +56,7 @@ struct StepArgs {
     const int *mirror;     // [3][nd]
     const BandConst *band; // [nb]
     const float *iso;      // [6][nb]     C_k T_wall / W, rounded to a value the storage format holds
+    const float *jmp;      // [3][nb]     C_k dT_jump[a] / W: offset of the -a wall's periodic ghosts (+a: minus it)
     // fields
     const void *e_in;
     void *e_out;
@@ -99,6 +100,13 @@ cudaError_t launch_wallflux64(const StepArgs &a, int storage, int limiter, const
                               const double *v, DiagOut o, cudaStream_t s);
 // Deterministic FP64 sum of n values into *out (device); scratch holds >= 1024 doubles.
 cudaError_t launch_sum64(const double *x, long long n, double *scratch, double *out, cudaStream_t s);
+// Residuals of the transient loop condition (Algorithm 2) between two states: keep T^n, |q|^n
+// (FP64, from launch_moments64's T and q) into Tp, qp; then out4 = {sum (T^n - T^{n+1})^2,
+// sum (|q|^n - |q|^{n+1})^2, max (T_ref + T^{n+1}), max |q^{n+1}|}; scratch >= 4 kResidBlocks.
+constexpr int kResidBlocks = 512;
+cudaError_t launch_resid_keep(const double *T, const double *q, long long n, double *Tp, double *qp, cudaStream_t s);
+cudaError_t launch_residuals(const double *T, const double *q, const double *Tp, const double *qp, long long n,
+                             double Tref, double *scratch, double *out4, cudaStream_t s);
 // Energy and wall flows into host7[7] with no device allocation (file-scope device scratch).
 // Returns 0, 1 (grid larger than the scratch covers) or 2 (CUDA error in *err).
 int launch_energy_noalloc(const StepArgs &a, int storage, int limiter, const double *w, const double *sv,

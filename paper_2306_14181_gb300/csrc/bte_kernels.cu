@@ -267,7 +267,8 @@ __device__ double ext64(const StepArgs &a, const typename Cd::T *e, const BandCo
     const int bc = a.bc[wall];
     if (bc == kBcPeriodic) {
         const long long j = i + (long long)((side ? pos - n : pos + n) - c[ax]) * st;
-        return Cd::ld64(e, base + j, b, rho_at<Cd>(a.R, a.invTs, j));
+        const double off = (double)a.jmp[ax * a.nb + k];  // the step's FP32 jump offset
+        return Cd::ld64(e, base + j, b, rho_at<Cd>(a.R, a.invTs, j)) + (side ? -off : off);
     }
     if (bc == kBcSpecular) {
         const int layer = side ? pos - n + 1 : -pos;
@@ -384,6 +385,91 @@ cudaError_t launch_sum64(const double *x, long long n, double *scratch, double *
     const int np = 1024;
     k_sum64_a<<<np, 256, 0, s>>>(x, n, scratch);
     k_sum64_b<<<1, 256, 0, s>>>(scratch, np, out);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// Residuals of the transient solver's loop condition (Algorithm 2) between consecutive states:
+//   eps_T = sqrt(sum_i (T_i^n - T_i^{n+1})^2 / N) / T_max,
+//   eps_q = sqrt(sum_i (|q|_i^n - |q|_i^{n+1})^2 / N) / |q|_max,
+// T and q of Eq. (getTQ) in FP64.  k_resid_keep stores T^n and |q|^n; k_resid_a forms per-block
+// partials of the two sums and the two maxima (T_max = max_i (T_ref + T_i^{n+1}), the absolute
+// temperature; |q|_max = max_i |q_i^{n+1}|) in a fixed order; k_resid_b combines them.
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_resid_keep(const double *T, const double *q, long long n, double *Tp,
+                                                    double *qp) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Tp[i] = T[i];
+    qp[i] = sqrt(q[i] * q[i] + q[n + i] * q[n + i] + q[2 * n + i] * q[2 * n + i]);
+}
+
+__global__ void __launch_bounds__(256) k_resid_a(const double *T, const double *q, const double *Tp, const double *qp,
+                                                 long long n, double Tref, double *part) {
+    __shared__ double sm[4][256];
+    const long long nb = gridDim.x;
+    const long long chunk = (n + nb - 1) / nb;
+    const long long lo = blockIdx.x * chunk;
+    const long long hi = lo + chunk < n ? lo + chunk : n;
+    double s1 = 0.0, s2 = 0.0, m1 = 0.0, m2 = 0.0;
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const double qm = sqrt(q[i] * q[i] + q[n + i] * q[n + i] + q[2 * n + i] * q[2 * n + i]);
+        const double dT = Tp[i] - T[i], dq = qp[i] - qm;
+        s1 += dT * dT;
+        s2 += dq * dq;
+        m1 = fmax(m1, fabs(Tref + T[i]));
+        m2 = fmax(m2, qm);
+    }
+    sm[0][threadIdx.x] = s1;
+    sm[1][threadIdx.x] = s2;
+    sm[2][threadIdx.x] = m1;
+    sm[3][threadIdx.x] = m2;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            sm[0][threadIdx.x] += sm[0][threadIdx.x + h];
+            sm[1][threadIdx.x] += sm[1][threadIdx.x + h];
+            sm[2][threadIdx.x] = fmax(sm[2][threadIdx.x], sm[2][threadIdx.x + h]);
+            sm[3][threadIdx.x] = fmax(sm[3][threadIdx.x], sm[3][threadIdx.x + h]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) part[threadIdx.x * nb + blockIdx.x] = sm[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(256) k_resid_b(const double *part, int np, double *out) {
+    __shared__ double sm[4][256];
+    double r[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int t = threadIdx.x; t < np; t += blockDim.x) {
+        r[0] += part[t];
+        r[1] += part[np + t];
+        r[2] = fmax(r[2], part[2 * np + t]);
+        r[3] = fmax(r[3], part[3 * np + t]);
+    }
+    for (int j = 0; j < 4; ++j) sm[j][threadIdx.x] = r[j];
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            sm[0][threadIdx.x] += sm[0][threadIdx.x + h];
+            sm[1][threadIdx.x] += sm[1][threadIdx.x + h];
+            sm[2][threadIdx.x] = fmax(sm[2][threadIdx.x], sm[2][threadIdx.x + h]);
+            sm[3][threadIdx.x] = fmax(sm[3][threadIdx.x], sm[3][threadIdx.x + h]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) out[threadIdx.x] = sm[threadIdx.x][0];
+}
+
+cudaError_t launch_resid_keep(const double *T, const double *q, long long n, double *Tp, double *qp, cudaStream_t s) {
+    k_resid_keep<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(T, q, n, Tp, qp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residuals(const double *T, const double *q, const double *Tp, const double *qp, long long n,
+                             double Tref, double *scratch, double *out4, cudaStream_t s) {
+    const int np = kResidBlocks;
+    k_resid_a<<<np, 256, 0, s>>>(T, q, Tp, qp, n, Tref, scratch);
+    k_resid_b<<<1, 256, 0, s>>>(scratch, np, out4);
     return cudaGetLastError();
 }
 

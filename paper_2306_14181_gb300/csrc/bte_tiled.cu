@@ -202,7 +202,8 @@ bool tiled_plan(int dim, const int n[3], int nb, int nd, int storage, int limite
     plan.hdr_off = plan.side_off + (int)((side_bytes + 15) / 16 * 16);
     plan.stage_bytes = (int)((plan.hdr_off + kHdrFloats * sizeof(float) + 127) / 128 * 128);
     plan.stage0 = 128;  // 2 ns mbarriers (ns <= 6) and the abort word at byte kAbortOff
-    static_assert(kAbortOff >= 2 * 6 * 8 && kAbortOff + 4 <= 128, "abort word after the barriers");
+    static_assert(kStallOff >= 2 * 6 * 8 && kAbortOff >= kStallOff + 8 && kAbortOff + 4 <= 128,
+                  "test barrier and abort word after the stage barriers");
     const size_t budget = 227 * 1024;
     for (int w = 0; w < 2 * dim; ++w)
         if (bc[w] == kBcDiffuse) plan.wslot[w] = plan.nwd++;
@@ -360,6 +361,7 @@ TiledArgs tiled_device_args(const TiledPlan &plan) {
     t.tcells = plan.tcells;
     t.chunk = plan.chunk;
     t.wait_ns = plan.wait_ns;
+    t.stall = plan.stall;
     return t;
 }
 

@@ -27,6 +27,7 @@ struct TiledArgs {
     int tcells;            // cells of a full tile (row length of P)
     int chunk;             // rows per bulk copy of a box slice
     unsigned long long wait_ns;  // limit of a bounded mbarrier wait (ns)
+    int stall;                   // failure-detection test: 1 the consumers', 2 the producer's first wait never completes
 };
 
 // Plane-synchronous schedule of the tiled forward kernel.  The plane list (k*nd + d) of every
@@ -58,6 +59,7 @@ struct TiledPlan {
     int storage = 0, nx = 0, chunk = 4;
     int *err = nullptr;
     unsigned long long wait_ns = 2000000000ull;  // bounded-wait limit (bte_set_wait_limit)
+    int stall = 0;                               // one-shot stall test of the next launch (bte_set_wait_limit)
 };
 
 // Shape check, tile geometry and the schedule (queries the current device for its SM count

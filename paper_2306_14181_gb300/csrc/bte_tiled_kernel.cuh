@@ -11,6 +11,7 @@ namespace bte {
 namespace tiled {
 
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s: the drain limit, and the default of TiledArgs::wait_ns
+constexpr int kStallOff = 96;   // byte offset of an mbarrier nothing arrives on (failure-detection test)
 constexpr int kAbortOff = 112;  // byte offset of the CTA's abort word in shared memory (after <= 6 + 6 mbarriers)
 constexpr int kHdrFloats = 16;                        // per-plane constants written by the producer
 
@@ -426,6 +427,12 @@ __device__ void producer(const StepArgs &a, const TiledArgs &p, char *smem, uint
     int issued = 0;    // plane-tiles whose copies were issued
     for (int i = 0; more; ++i, more = cur.next(a, p)) {
         if (cta_aborted(smem)) break;
+        // failure-detection test: a wait on a barrier that nothing completes gives up
+        if (i == 0 && (p.stall & 2) && !__all_sync(0xffffffffu, mbar_wait(reinterpret_cast<uint64_t *>(smem + kStallOff), 0u,
+                                                                        p.err, 2, p.wait_ns))) {
+            cta_abort(smem);
+            break;
+        }
         if (i >= p.ns) {
             // the consumers released the stage, and the copies of its previous use have landed
             // (at once in a normal run: the consumers waited for them; after an abort they may not)
@@ -965,15 +972,14 @@ __device__ void consumer(const StepArgs &a, const TiledArgs &p, char *smem, uint
                 }
             }
         }
-        // warp-uniform: the stage's copies landed (fast path), else wait unless a warp of the
-        // CTA has given up.  After an abort a stage may pass the test with stale contents; the
-        // arithmetic on it reads only in-bounds addresses and the step is reported invalid.
-        bool ok = __all_sync(0xffffffffu, mbar_try_wait(&full[s], ph));
-        if (!ok) {
-            ok = !cta_aborted(smem);
-            if (ok) ok = __all_sync(0xffffffffu, mbar_wait(&full[s], ph, p.err, 1, p.wait_ns));
-            if (!ok && lane == 0) cta_abort(smem);
-        }
+        // warp-uniform: no warp of the CTA has given up, and the stage's copies landed (a
+        // bounded wait unless the first try succeeds)
+        bool ok = !cta_aborted(smem);
+        if (ok && i == 0 && (p.stall & 1))  // failure-detection test: a wait that nothing completes
+            ok = __all_sync(0xffffffffu, mbar_wait(reinterpret_cast<uint64_t *>(smem + kStallOff), 0u, p.err, 1, p.wait_ns));
+        if (ok && !__all_sync(0xffffffffu, mbar_try_wait(&full[s], ph)))
+            ok = __all_sync(0xffffffffu, mbar_wait(&full[s], ph, p.err, 1, p.wait_ns));
+        if (!ok && lane == 0) cta_abort(smem);
         const char *stage = smem + p.stage0 + (size_t)s * p.stage_bytes;
         if constexpr (REF) {
             if (ok) wsum += reinterpret_cast<const float *>(stage + p.hdr_off)[3];
@@ -1015,6 +1021,7 @@ __global__ void __launch_bounds__((Geo<DIM, WPR>::NCW + kProducerWarps) * 32, 1)
             mbar_init(&empty[s], Geo<DIM, WPR>::NCW);
         }
         *reinterpret_cast<int *>(smem + kAbortOff) = 0;
+        mbar_init(reinterpret_cast<uint64_t *>(smem + kStallOff), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     float *wsm = reinterpret_cast<float *>(smem + p.wall_off);

@@ -17,10 +17,11 @@ def oracle_problem(cfg, limiter=LIM_VANALBADA, **over):
     c.update(over)
     s, w, mirror = oracle_quadrature(c["quad"])
     return Problem(c["dim"], c["n"], c["h"], c["C"], c["v"], c["tau"], s, w, mirror, c["bc"], c["Tw"], c["dt"],
-                   limiter)
+                   limiter, jump=c.get("jump"))
 
 
-def small_cfg(dim, n, bc, Tw=(0, 0, 0, 0, 0, 0), nb=3, quad=None, h=2e-9, seed=7, beta=0.5, tau=None, v=None):
+def small_cfg(dim, n, bc, Tw=(0, 0, 0, 0, 0, 0), nb=3, quad=None, h=2e-9, seed=7, beta=0.5, tau=None, v=None,
+              jump=None):
     """A small synthetic problem for pins."""
     from paper_2306_14181_gb300 import inputs
     C, vv, tt = inputs.bands(seed, nb)
@@ -31,8 +32,11 @@ def small_cfg(dim, n, bc, Tw=(0, 0, 0, 0, 0, 0), nb=3, quad=None, h=2e-9, seed=7
     if quad is None:
         quad = ("gl1d", 8) if dim == 1 else ("octant", 2, 2)
     hh = (h, h, h)
-    return dict(dim=dim, n=tuple(n), h=hh, nb=nb, C=C, v=vv, tau=tt, quad=quad, bc=list(bc), Tw=list(Tw),
-                dt=inputs.cfl_time_step(hh[:dim], vv, beta))
+    cfg = dict(dim=dim, n=tuple(n), h=hh, nb=nb, C=C, v=vv, tau=tt, quad=quad, bc=list(bc), Tw=list(Tw),
+               dt=inputs.cfl_time_step(hh[:dim], vv, beta))
+    if jump is not None:
+        cfg["jump"] = list(jump)
+    return cfg
 
 
 def rel_linf(a, b):
@@ -44,6 +48,8 @@ def rel_linf(a, b):
 def gpu_ctx(cfg, **opts):
     """A GPU context for a workload/small-config dict (imports the binding lazily)."""
     from paper_2306_14181_gb300 import bte
+    if cfg.get("jump") is not None:
+        opts.setdefault("dT_jump", cfg["jump"])
     return bte.bte_create(cfg["dim"], cfg["n"], cfg["h"], cfg["C"], cfg["v"], cfg["tau"], cfg["quad"], cfg["bc"],
                           cfg["Tw"], opts.pop("dt", cfg["dt"]), **opts)
 

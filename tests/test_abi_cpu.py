@@ -59,6 +59,9 @@ def _create(**over):
     (dict(limiter=5), "limiter"),
     (dict(quad=("explicit", np.array([[1.0, 0, 0], [0.0, 1, 0]]), np.array([1.0, 1.0])), bc=[2, 2, 0, 0, 3, 3]),
      "mirror"),
+    (dict(dT_jump=(0.5, 0.0, 0.0)), "dT_jump needs a periodic pair"),        # x walls are diffuse
+    (dict(bc=[3, 3, 0, 1, 3, 3], dT_jump=(0.5, 0.0, 0.2)), "inactive axis 2"),
+    (dict(bc=[3, 3, 0, 1, 3, 3], dT_jump=(float("inf"), 0.0, 0.0)), "non-finite dT_jump"),
 ])
 def test_host_validation_rejects_bad_input(lib, over, frag):
     with pytest.raises(bte.BteError) as ei:

@@ -117,3 +117,32 @@ def test_uniform_source_gradient_is_the_summed_gradient():
     Qu = np.full((P.nz, P.ny, P.nx), hq, np.float32)
     fd = (_J(P, e0, 1, probe, Qu, None) - _J(P, e0, 1, probe, -Qu, None)) / (2 * float(np.float32(hq)))
     assert abs(fd - gQ.sum()) <= 1e-10 * abs(fd)
+
+
+# A periodic pair with a temperature difference (Sec. 2.2 (iv)) shifts the pair's ghosts by a
+# constant: the step stays affine in e with the same Jacobian structure, the limiter's partials
+# being taken at the shifted ghost values.
+JUMP_GRIDS = [
+    (1, (12, 1, 1), [PER] * 6, (0.7, 0, 0)),
+    (2, (7, 6, 1), [PER, PER, DIF, ISO, PER, PER], (-0.4, 0, 0)),
+    (3, (5, 4, 4), [PER, PER, PER, PER, DIF, ISO], (0.3, 0.6, 0)),
+]
+
+
+@pytest.mark.parametrize("limiter", [0, 1, 2])
+@pytest.mark.parametrize("dim,n,bc,jump", JUMP_GRIDS)
+def test_adjoint_and_tangent_with_periodic_jump(dim, n, bc, jump, limiter):
+    cfg = small_cfg(dim, n, bc, Tw=TW, nb=2, jump=jump)
+    P = oracle_problem(cfg, limiter)
+    # a state on the scale of the jump's ghost offset C_k dT / W (~1e4), so that the limiter's
+    # arguments are not dominated by the offset (central differences would straddle its kink)
+    e = inputs.random_state(P.shape, 23) * 1e4
+    de = inputs.random_state(P.shape, 24, smooth=False)
+    lam = inputs.random_state(P.shape, 25, smooth=False)
+    t = P.step_tangent(e, de)
+    a = float(np.vdot(lam, t))
+    b = float(np.vdot(P.adjoint_step(e, lam), de))
+    assert abs(a - b) <= 1e-13 * max(abs(a), np.linalg.norm(lam) * np.linalg.norm(de))
+    h = 1e-2 if limiter == 0 else 1e-5
+    fd = (P.step(e + h * de) - P.step(e - h * de)) / (2 * h)
+    assert np.max(np.abs(fd - t)) <= (1e-9 if limiter == 0 else 1e-5) * np.max(np.abs(fd))

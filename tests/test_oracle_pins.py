@@ -426,3 +426,109 @@ def test_step_points_equal_whole_step(dim, n, bc, limiter):
     got = P.step_points(e, pts, Q, amp)
     want = full[pts[:, 0] * P.nd + pts[:, 1], pts[:, 2]]
     assert np.array_equal(got, want)
+
+
+# ---------------------------------------------------------------------------------------
+# Periodic pair with a temperature difference (Sec. 2.2 (iv)): e(r_B1) = e(r_B2) + C dT/W.
+# A uniform gradient G = dT/L along x in an unbounded (periodic) medium has the exact
+# solution e_{k,d}(x) = C_k/W (T(x) + tau_k v_k s_x G), T(x) = -G x: the advection of the
+# linear profile, -v s_x de/dx = v s_x C G/W, cancels the relaxation (e - e0)/tau =
+# C tau v s_x G/W / tau (sum_d w s_x = 0 leaves T_L = T).  Every limiter reproduces a linear
+# profile's face values exactly, so the discrete step keeps this state, and its heat flux is
+# q_x = sum_k C_k v_k^2 tau_k G sum_d w s_x^2 / W = G sum_k C_k v_k^2 tau_k / 3, the bulk
+# conductivity of Sec. 2.1 times the gradient, at any Knudsen number.
+# ---------------------------------------------------------------------------------------
+def _gradient_state(P, G):
+    xc = (np.arange(P.nx) + 0.5) * P.dx
+    T = -G * xc
+    e = np.empty(P.shape)
+    for k in range(P.nb):
+        for d in range(P.nd):
+            e[k, d] = (P.C[k] / P.W) * (T + P.tau[k] * P.v[k] * P.s[d, 0] * G)[None, None, :]
+    return e, T
+
+
+@pytest.mark.parametrize("limiter", [LIM_FIRST_ORDER, LIM_MINMOD, LIM_VANALBADA])
+@pytest.mark.parametrize("dim,n,quad", [(1, (24, 1, 1), ("gl1d", 16)), (2, (20, 5, 1), ("octant", 2, 3)),
+                                        (3, (16, 4, 3), ("octant", 2, 2))])
+def test_p13_periodic_jump_uniform_gradient_is_stationary(dim, n, quad, limiter):
+    dT = 0.8
+    cfg = small_cfg(dim, n, [PER] * 6, nb=4, quad=quad, jump=(dT, 0.0, 0.0))
+    P = oracle_problem(cfg, limiter)
+    G = dT / (P.nx * P.dx)
+    e, T = _gradient_state(P, G)
+    e1 = P.step(e)
+    scale = np.max(np.abs(e))
+    assert np.max(np.abs(e1 - e)) <= 1e-12 * scale
+    Tm, TL, q = P.moments(e1)
+    kappa = float(np.sum(P.C * P.v ** 2 * P.tau) / 3.0)
+    assert np.max(np.abs(q[0] - kappa * G)) <= 1e-12 * kappa * G
+    assert np.max(np.abs(q[1:])) <= 1e-12 * kappa * G
+    assert np.max(np.abs(TL - T[None, None, :])) <= 1e-12 * dT
+
+
+def test_p13_jump_sign_and_size():
+    """A uniform state in a periodic box with a jump: only the cells next to the two walls see
+    the ghost offset, +C dT/W at the -x wall for directions entering there, with the sign
+    that makes heat flow towards +x."""
+    dT = 0.5
+    cfg = small_cfg(1, (12, 1, 1), [PER] * 6, nb=2, quad=("gl1d", 8), jump=(dT, 0.0, 0.0))
+    P = oracle_problem(cfg, LIM_FIRST_ORDER)
+    e = P.equilibrium(0.0)
+    e1 = P.step(e)
+    k, W = 1, P.W
+    for d in range(P.nd):
+        nu = P.dt * P.v[k] * P.s[d, 0] / P.dx
+        if nu > 0:   # enters through -x: first-order inflow e_ghost = C dT / W at cell 0
+            assert e1[k, d, 0, 0, 0] == pytest.approx(nu * P.C[k] * dT / W, rel=1e-12)
+            assert e1[k, d, 0, 0, -1] == 0.0
+        else:        # enters through +x from the -x side: ghost = -C dT / W
+            assert e1[k, d, 0, 0, -1] == pytest.approx(nu * P.C[k] * dT / W, rel=1e-12)
+            assert e1[k, d, 0, 0, 0] == 0.0
+    # the net flow through the pair moves energy towards +x: the -x wall takes energy in
+    E0, F0 = P.energy(e)
+    assert F0[0] < 0 and F0[1] > 0
+
+
+@pytest.mark.parametrize("limiter", [LIM_FIRST_ORDER, LIM_MINMOD, LIM_VANALBADA])
+@pytest.mark.parametrize("dim,n,bc,jump", [
+    (1, (11, 1, 1), [PER] * 6, (0.4, 0, 0)),
+    (2, (9, 7, 1), [PER, PER, DIF, SPE, PER, PER], (-0.3, 0, 0)),
+    (3, (6, 5, 4), [PER, PER, PER, PER, ISO, DIF], (0.2, 0.5, 0)),
+])
+def test_p2_energy_balance_with_periodic_jump(dim, n, bc, jump, limiter):
+    """The discrete energy balance holds with the jump's ghost values in the wall face values."""
+    cfg = small_cfg(dim, n, bc, Tw=[0.3, -0.2, 0.1, 0.4, -0.3, 0.2], jump=jump)
+    P = oracle_problem(cfg, limiter)
+    e = inputs.random_state(P.shape, 12) * 1e3
+    Q = (np.random.default_rng(3).random((P.nz, P.ny, P.nx)) * 1e17).astype(np.float32)
+    E0, F0 = P.energy(e)
+    e1 = P.step(e, Q, 0.9)
+    E1, _ = P.energy(e1)
+    rhs = P.dt * (P.cell_volume * 0.9 * float(Q.astype(np.float64).sum()) - F0.sum())
+    scale = max(abs(E0), abs(E1), P.dt * np.abs(F0).sum())
+    assert abs((E1 - E0) - rhs) <= 1e-12 * scale
+    # the jump shifts every ghost of the pair by the same C dT/W with opposite signs on the two
+    # sides, so it moves heat through the pair but adds no energy (sum_d w v s_x = 0)
+    assert abs(F0[0] + F0[1]) <= 1e-12 * scale / P.dt
+
+
+# ---------------------------------------------------------------------------------------
+# Residuals of the transient loop condition (Sec. 4.1, Algorithm 2)
+# ---------------------------------------------------------------------------------------
+def test_residuals_closed_forms():
+    """A uniform temperature shift delta between the two states gives eps_T = |delta| / T_max
+    exactly; doubling a state of uniform flux (the uniform gradient of P13) gives eps_q = 1/2;
+    that gradient state is stationary, so one step gives eps_T = eps_q = 0 to round-off."""
+    cfg = small_cfg(2, (8, 6, 1), [PER] * 6, nb=3, quad=("octant", 2, 2))
+    P = oracle_problem(cfg)
+    eT, _ = P.residuals(P.equilibrium(0.25), P.equilibrium(0.25 + 0.125), 300.0)
+    assert eT == pytest.approx(0.125 / 300.375, rel=1e-12)
+    dT = 0.6
+    cfg = small_cfg(1, (20, 1, 1), [PER] * 6, nb=3, quad=("gl1d", 8), jump=(dT, 0, 0))
+    P = oracle_problem(cfg)
+    e, _ = _gradient_state(P, dT / (P.nx * P.dx))
+    _, eq = P.residuals(e, 2.0 * e, 300.0)
+    assert eq == pytest.approx(0.5, rel=1e-12)
+    eT, eq = P.residuals(e, P.step(e), 300.0)
+    assert eT <= 1e-15 and eq <= 1e-12
