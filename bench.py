@@ -7,8 +7,9 @@ workload: the 3-D laser-heated block (128x128x64 cells, 40 bands, 96 directions,
 the largest of the paper-shaped configurations that runs on one GPU.  Inputs are resident in
 HBM before the timed region; the state (16.1 GB a copy) is far larger than L2, so no flush is
 needed between steps.  The same run then measures, one context at a time, the sub-records:
-the laser block with 16-bit storage, the 2-D hot spot (FP32 and 16-bit) and the adjoint/forward
-step-time ratio of the two adjoint workloads.
+the laser block with 16-bit storage, the 2-D hot spot (FP32 and 16-bit), the adjoint/forward
+step-time ratio of the two adjoint workloads, an in-plane film run to steady state by the
+residual stop, and the transient thermal grating over its xi sweep.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--storage f32|f16|bf16]
   python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
@@ -451,24 +452,27 @@ def adjoint_record(ctx, cfg, info, fwd_step_ms, nadj, kck, Q, amps, peak):
 
 
 # Sub-records measured in the same run after the headline, one context at a time: (workload,
-# storage, T_scale, timed forward steps, adjoint steps or None, checkpoint spacing).  The 3-D
-# adjoint runs 100 of its 1000 steps (checkpoints every 50) to keep the run within minutes.
+# storage, T_scale, timed forward steps, adjoint steps or None, checkpoint spacing, kernel).
+# The 3-D adjoint runs 100 of its 1000 steps (checkpoints every 50) to keep the run within
+# minutes.  The hot spot also runs on the generic kernel (one thread per cell and band), the
+# path grids of any shape take.
 SUB_RECORDS = [
-    ("laser_3d", "f16", 1.0, 30, None, None),
-    ("hotspot_2d", "f32", 1.0, 100, None, None),
-    ("hotspot_2d", "f16", 10.0, 100, None, None),
-    ("film_adjoint_2d", "f32", 1.0, 100, 2000, 100),
-    ("block_adjoint_3d", "f16", 1.0, 10, 100, 50),
+    ("laser_3d", "f16", 1.0, 30, None, None, "auto"),
+    ("hotspot_2d", "f32", 1.0, 100, None, None, "auto"),
+    ("hotspot_2d", "f16", 10.0, 100, None, None, "auto"),
+    ("hotspot_2d", "f32", 1.0, 20, None, None, "generic"),
+    ("film_adjoint_2d", "f32", 1.0, 100, 2000, 100, "auto"),
+    ("block_adjoint_3d", "f16", 1.0, 10, 100, 50, "auto"),
 ]
 
 
-def sub_record(args, name, storage, T_scale, steps, nadj, kck, peak, peak_kind):
+def sub_record(args, name, storage, T_scale, steps, nadj, kck, peak, peak_kind, kernel="auto"):
     import gc
     import torch
     from paper_2306_14181_gb300 import bte
     cfg = workloads()[name]()
     warm = 3
-    ctx, Q, amps = make_context(cfg, STORAGE[storage], args.limiter, KERNEL["auto"], T_scale, 0,
+    ctx, Q, amps = make_context(cfg, STORAGE[storage], args.limiter, KERNEL[kernel], T_scale, 0,
                                 warm + steps + 8)
     info = ctx.info
     bte.bte_step(ctx, warm)
@@ -486,6 +490,59 @@ def sub_record(args, name, storage, T_scale, steps, nadj, kck, peak, peak_kind):
     del ctx
     gc.collect()
     torch.cuda.empty_cache()
+    return rec
+
+
+def steady_record(args):
+    """f1: the in-plane film run to steady state by the residual stop of the transient solver
+    (eps_T and eps_q below 1e-7, checked every 200 steps): steps, device time and the in-plane
+    conductivity q L / dT against the bulk sum C v^2 tau / 3."""
+    import gc
+    import numpy as np
+    import torch
+    from paper_2306_14181_gb300 import bte, inputs
+    cfg = inputs.inplane_film_2d()
+    ctx = bte.bte_from_workload(cfg, limiter=args.limiter, stream=torch.cuda.current_stream().cuda_stream)
+    info = ctx.info
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n, eT, eq = bte.bte_run_steady(ctx, cfg["steps"], 200, 1e-7, 1e-7)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    _, _, q = bte.bte_moments(ctx)
+    L = cfg["n"][0] * cfg["h"][0]
+    kappa = float(np.mean(q[0])) * L / cfg["jump"][0]
+    kbulk = float(np.sum(cfg["C"] * cfg["v"] ** 2 * cfg["tau"]) / 3.0)
+    rec = {"workload": cfg["name"], "storage": "f32", "kernel": kernel_name_of(info), "steps": n, "converged": bool(
+        eT < 1e-7 and eq < 1e-7), "eps_T": eT, "eps_q": eq, "wall_s": wall, "ms_per_step": 1e3 * wall / max(n, 1),
+           "kappa_inplane": kappa, "kappa_bulk": kbulk, "kappa_ratio": kappa / kbulk,
+           "note": "residual stop of Algorithm 2 (eps_T, eps_q < 1e-7, checked every 200 steps); "
+                   "wall time includes the FP64 residual reductions"}
+    bte.bte_destroy(ctx)
+    del ctx
+    gc.collect()
+    return rec
+
+
+def ttg_record(args, xi):
+    """f2: the transient thermal grating (1000 cells, 512 directions, gray Si) at xi = 2 pi Kn over
+    t* = t/tau up to 10/xi: device time of the steps and the grating amplitude at the end."""
+    import gc
+    import torch
+    from paper_2306_14181_gb300 import bte, inputs
+    cfg = inputs.ttg_1d(xi)
+    ctx = bte.bte_from_workload(cfg, limiter=args.limiter, stream=torch.cuda.current_stream().cuda_stream)
+    info = ctx.info
+    bte.bte_init_temperature(ctx, inputs.ttg_initial_temperature(cfg).reshape(-1))
+    t_ms, fwd_ms, nfwd, fin_ms, nfin, _ = timed_forward(ctx, cfg["steps"])
+    T, _, _ = bte.bte_moments(ctx)
+    rec = {"workload": cfg["name"], "xi": xi, "storage": "f32", "kernel": kernel_name_of(info), "steps": cfg["steps"],
+           "t_star_end": cfg["steps"] * cfg["dt"] / cfg["tau_ref"], "ms_per_step": t_ms / cfg["steps"],
+           "value": info.nelem * cfg["steps"] / (t_ms / 1e3), "unit": UNIT,
+           "amplitude_end": inputs.grating_amplitude(cfg, T) / cfg["A0"]}
+    bte.bte_destroy(ctx)
+    del ctx
+    gc.collect()
     return rec
 
 
@@ -560,10 +617,13 @@ def run_gb300(args):
     # the other workloads, storage forms and the adjoint ratios (one GPU runs only)
     if d.world == 1 and not args.no_sub_records:
         subs = []
-        for name, st, ts, steps, nadj, kck in SUB_RECORDS:
-            if name == args.workload and st == args.storage and nadj is None:
+        for name, st, ts, steps, nadj, kck, kern in SUB_RECORDS:
+            if name == args.workload and st == args.storage and nadj is None and kern == args.kernel:
                 continue
-            subs.append(sub_record(args, name, st, ts, steps, nadj, kck, peak, peak_kind))
+            subs.append(sub_record(args, name, st, ts, steps, nadj, kck, peak, peak_kind, kern))
+        subs.append(steady_record(args))
+        for xi in (0.1, 1.0, 10.0):
+            subs.append(ttg_record(args, xi))
         line["sub_records"] = subs
     if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:
         v, n, grid, secs = time_oracle(cfg, args.cpu_seconds, args.limiter)

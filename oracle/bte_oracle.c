@@ -572,15 +572,19 @@ void orc_adjoint_step(const orc_problem *P, const double *e, const double *lam_i
     const double W = total_weight(P), D = sum_C_over_tau(P);
     double *ediff = (double *)calloc((size_t)6 * P->nb * nc, sizeof(double));
     double *mu = (double *)calloc((size_t)nc, sizeof(double));
-    long *idx = (long *)malloc(sizeof(long) * (P->nd + 1));
-    double *coef = (double *)malloc(sizeof(double) * (P->nd + 1));
     diffuse_wall_values(P, e, ediff);
     memset(lam_out, 0, sizeof(double) * total);
     /* T_L coupling: d e^{n+1}_{k,d,i}/d T_L,i = dt C_k/(W tau_k) */
-    for (int k = 0; k < P->nb; ++k)
-        for (int d = 0; d < P->nd; ++d)
-            for (long i = 0; i < nc; ++i) mu[i] += lam_in[EIDX(P, k, d, i)] * P->dt * P->C[k] / (W * P->tau[k]);
-    for (int k = 0; k < P->nb; ++k)
+    #pragma omp parallel for schedule(static)
+    for (long i = 0; i < nc; ++i)
+        for (int k = 0; k < P->nb; ++k)
+            for (int d = 0; d < P->nd; ++d) mu[i] += lam_in[EIDX(P, k, d, i)] * P->dt * P->C[k] / (W * P->tau[k]);
+    /* Every element of band k scatters only into band k (the ghost rules never leave a band),
+     * so the bands run in parallel and each element sums its terms in the serial order. */
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int k = 0; k < P->nb; ++k) {
+        long *idx = (long *)malloc(sizeof(long) * (P->nd + 1));
+        double *coef = (double *)malloc(sizeof(double) * (P->nd + 1));
         for (int d = 0; d < P->nd; ++d)
             for (int z = 0; z < P->nz; ++z)
                 for (int y = 0; y < P->ny; ++y)
@@ -611,39 +615,50 @@ void orc_adjoint_step(const orc_problem *P, const double *e, const double *lam_i
                             }
                         }
                     }
+        free(idx);
+        free(coef);
+    }
     free(ediff);
     free(mu);
-    free(idx);
-    free(coef);
 }
 
 /* Adjoint of a whole run: J = sum_i p_i T_L,i after nsteps steps from e0 (steps n0 ..
- * n0+nsteps-1, source amplitude amp[n], 1 when amp is NULL, 0 past namp).  Stores every
- * state.  Outputs J, dJ/dQ (ncell) and dJ/dlog tau (nb).  Returns 0, or 1 when out of memory. */
+ * n0+nsteps-1, source amplitude amp[n], 1 when amp is NULL, 0 past namp).  States are kept
+ * at every ckpt-th step (ckpt <= 0: every state); the reverse sweep recomputes each segment
+ * from its checkpoint before stepping back through it, which gives the same states bitwise
+ * (the forward step is deterministic).  Memory: nsteps/ckpt + ckpt + 1 states.  Outputs J,
+ * dJ/dQ (ncell) and dJ/dlog tau (nb).  Returns 0, or 1 when out of memory. */
 int orc_adjoint(const orc_problem *P, const double *e0, const float *Q, const double *amp, int namp, long n0,
-                int nsteps, const double *probe, double *J, double *gQ, double *gtau) {
+                int nsteps, const double *probe, double *J, double *gQ, double *gtau, int ckpt) {
     const long nc = ncell_of(P);
     const long total = (long)P->nb * P->nd * nc;
     const double W = total_weight(P), SC = sum_C(P), D = sum_C_over_tau(P);
-    double *traj = (double *)malloc(sizeof(double) * total * (size_t)(nsteps + 1));
+    const int K = (ckpt > 0 && ckpt < nsteps) ? ckpt : (nsteps > 0 ? nsteps : 1);
+    const int nseg = nsteps > 0 ? (nsteps + K - 1) / K : 0;
+    double *cps = (double *)malloc(sizeof(double) * total * (size_t)(nseg > 0 ? nseg : 1));
+    double *traj = (double *)malloc(sizeof(double) * total * (size_t)(K + 1)); /* a segment's states, then e^N */
     double *lam = (double *)malloc(sizeof(double) * total);
     double *lam2 = (double *)malloc(sizeof(double) * total);
     double *TL = (double *)malloc(sizeof(double) * nc);
     double *mu = (double *)malloc(sizeof(double) * nc);
-    if (!traj || !lam || !lam2 || !TL || !mu) {
-        free(traj); free(lam); free(lam2); free(TL); free(mu);
+    if (!cps || !traj || !lam || !lam2 || !TL || !mu) {
+        free(cps); free(traj); free(lam); free(lam2); free(TL); free(mu);
         return 1;
     }
+    /* forward sweep: checkpoints at steps 0, K, 2K, ..., e^N in the last slot of traj */
     memcpy(traj, e0, sizeof(double) * total);
     for (int s = 0; s < nsteps; ++s) {
         const long n = n0 + s;
         const double a = amp ? (n < namp ? amp[n] : 0.0) : 1.0;
-        orc_step(P, traj + (size_t)s * total, traj + (size_t)(s + 1) * total, Q, a);
+        if (s % K == 0) memcpy(cps + (size_t)(s / K) * total, traj, sizeof(double) * total);
+        orc_step(P, traj, traj + (size_t)K * total, Q, a);
+        memcpy(traj, traj + (size_t)K * total, sizeof(double) * total);
     }
+    memcpy(traj + (size_t)K * total, traj, sizeof(double) * total);
     for (long i = 0; i < nc; ++i) gQ[i] = 0.0;
     for (int k = 0; k < P->nb; ++k) gtau[k] = 0.0;
     /* J and lambda^N = dT_L/de^T p; the final T_L's own tau dependence */
-    const double *eN = traj + (size_t)nsteps * total;
+    const double *eN = traj + (size_t)K * total;
     orc_lattice_temperature(P, eN, TL);
     double Jv = 0.0;
     for (long i = 0; i < nc; ++i) Jv += probe[i] * TL[i];
@@ -660,7 +675,17 @@ int orc_adjoint(const orc_problem *P, const double *e0, const float *Q, const do
     for (int s = nsteps - 1; s >= 0; --s) {
         const long n = n0 + s;
         const double a = amp ? (n < namp ? amp[n] : 0.0) : 1.0;
-        const double *en = traj + (size_t)s * total;
+        const int s0 = (s / K) * K;
+        if (s == nsteps - 1 || s % K == K - 1) {
+            /* entering segment [s0, s]: its states from the checkpoint */
+            memcpy(traj, cps + (size_t)(s / K) * total, sizeof(double) * total);
+            for (int m = s0; m < s; ++m) {
+                const long nm = n0 + m;
+                const double am = amp ? (nm < namp ? amp[nm] : 0.0) : 1.0;
+                orc_step(P, traj + (size_t)(m - s0) * total, traj + (size_t)(m - s0 + 1) * total, Q, am);
+            }
+        }
+        const double *en = traj + (size_t)(s - s0) * total;
         orc_lattice_temperature(P, en, TL);
         for (long i = 0; i < nc; ++i) mu[i] = 0.0;
         for (int k = 0; k < P->nb; ++k)
@@ -680,6 +705,6 @@ int orc_adjoint(const orc_problem *P, const double *e0, const float *Q, const do
         orc_adjoint_step(P, en, lam, lam2);
         memcpy(lam, lam2, sizeof(double) * total);
     }
-    free(traj); free(lam); free(lam2); free(TL); free(mu);
+    free(cps); free(traj); free(lam); free(lam2); free(TL); free(mu);
     return 0;
 }

@@ -69,7 +69,7 @@ def load_oracle():
             _lib.orc_step_points.argtypes = [pp, dp, fp, ct.c_double, ct.c_long, ct.POINTER(ct.c_long), dp]
             _lib.orc_step_tangent.argtypes = [pp, dp, dp, dp]
             _lib.orc_adjoint_step.argtypes = [pp, dp, dp, dp]
-            _lib.orc_adjoint.argtypes = [pp, dp, fp, dp, ct.c_int, ct.c_long, ct.c_int, dp, dp, dp, dp]
+            _lib.orc_adjoint.argtypes = [pp, dp, fp, dp, ct.c_int, ct.c_long, ct.c_int, dp, dp, dp, dp, ct.c_int]
             _lib.orc_adjoint.restype = ct.c_int
         return _lib
 
@@ -212,9 +212,10 @@ class Problem:
         self._lib.orc_adjoint_step(ct.byref(self._p), _dp(e), _dp(lam), _dp(out))
         return out
 
-    def adjoint(self, e0, nsteps, probe, Q=None, amps=None, n0=0):
+    def adjoint(self, e0, nsteps, probe, Q=None, amps=None, n0=0, ckpt=0):
         """J = sum_i probe_i T_L,i after nsteps steps from e0, with dJ/dQ (per cell; Q taken
-        as 0 when None) and dJ/dlog tau_k.  Returns (J, dJ_dQ, dJ_dlogtau)."""
+        as 0 when None) and dJ/dlog tau_k.  ckpt > 0 keeps every ckpt-th state and recomputes
+        the rest (bitwise the same result).  Returns (J, dJ_dQ, dJ_dlogtau)."""
         e0 = np.ascontiguousarray(e0, dtype=np.float64)
         probe = np.ascontiguousarray(probe, dtype=np.float64).reshape(-1)
         assert probe.size == self.ncell
@@ -228,7 +229,7 @@ class Problem:
         gQ = np.zeros(self.ncell)
         gt = np.zeros(self.nb)
         rc = self._lib.orc_adjoint(ct.byref(self._p), _dp(e0), _fp(Qc), ap, na, int(n0), int(nsteps), _dp(probe),
-                                   _dp(J), _dp(gQ), _dp(gt))
+                                   _dp(J), _dp(gQ), _dp(gt), int(ckpt))
         if rc != 0:
             raise MemoryError("oracle adjoint: trajectory does not fit in memory")
         return float(J[0]), gQ.reshape(self.nz, self.ny, self.nx), gt

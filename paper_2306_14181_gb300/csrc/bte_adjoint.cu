@@ -36,13 +36,19 @@ template <> __device__ __forceinline__ void lim_grad<kLimMinmod>(float a, float 
     Lb = on && !pa ? 1.f : 0.f;
 }
 template <> __device__ __forceinline__ void lim_grad<kLimVanAlbada>(float a, float b, float &La, float &Lb) {
-    // L = ab(a+b)/(a^2+b^2):  dL/da = b^2 (2ab + b^2 - a^2)/(a^2+b^2)^2, symmetric in b
+    // L = ab(a+b)/(a^2+b^2):  dL/da = b^2 (2ab + b^2 - a^2)/(a^2+b^2)^2, symmetric in b.  L is
+    // homogeneous of degree 1, so its partials are of degree 0: they are evaluated on
+    // (a, b) / max(|a|, |b|), which keeps a^2 + b^2 in [1, 2].  (On the raw slopes, tiny ones --
+    // a state barely off its reference -- overflow 1/(a^2+b^2)^2 to infinity and the product
+    // to NaN.)
     La = Lb = 0.f;
     if (a * b > 0.f) {
-        const float q = fmaf(a, a, b * b);
+        const float r = 1.f / fmaxf(fabsf(a), fabsf(b));
+        const float an = a * r, bn = b * r;
+        const float q = fmaf(an, an, bn * bn);
         const float rq = 1.f / q;
-        La = (b * b * rq) * ((2.f * a * b + b * b - a * a) * rq);
-        Lb = (a * a * rq) * ((2.f * a * b + a * a - b * b) * rq);
+        La = (bn * bn * rq) * ((2.f * an * bn + bn * bn - an * an) * rq);
+        Lb = (an * an * rq) * ((2.f * an * bn + an * an - bn * bn) * rq);
     }
 }
 

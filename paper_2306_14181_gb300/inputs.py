@@ -173,6 +173,62 @@ def block_adjoint_3d(nx=96, ny=96, nz=96, nb=32, ntheta=4, nphi=3, steps=1000, c
                  [0, 0, 0, 0, 0, 0], steps, src, probe=probe, ckpt=ckpt)
 
 
+def inplane_film_2d(nx=64, ny=64, ntheta=2, nphi=3, dT=1.0):
+    """In-plane conduction of a film (the verification problem (b) of Sec. 5 shaped): a square cell
+    of 64 x 64 cells of 5 nm, periodic along x with a temperature difference of 1 K between the
+    two periodic ends, diffusely reflecting top and bottom; 3 seeded bands with relaxation times
+    2, 10 and 40 ps (seed 7 speeds and capacities), 48 directions.  The time step is half the
+    transient workloads' (beta = 0.25) so that the limited scheme reaches a steady state."""
+    C, v, _ = bands(7, 3)
+    tau = np.array([2e-12, 1e-11, 4e-11])
+    h = (5e-9, 5e-9, 5e-9)
+    cfg = dict(name="inplane_film_2d_%dx%d_3x%d" % (nx, ny, 8 * ntheta * nphi), dim=2, n=(nx, ny, 1), h=h, nb=3,
+               seed=7, quad=("octant", ntheta, nphi), bc=[PERIODIC, PERIODIC, DIFFUSE, DIFFUSE, PERIODIC, PERIODIC],
+               Tw=[0.0] * 6, steps=20000, C=C, v=v, tau=tau, dt=cfl_time_step(h[:2], v, 0.25), source=None,
+               jump=[dT, 0.0, 0.0])
+    return cfg
+
+
+# gray silicon of the paper's verification problems (Sec. 5): one band
+GRAY_SI = dict(C=1627600.0, v=2677.0, tau=39.9e-12)
+
+
+def ttg_1d(xi=1.0, nx=1000, ntheta=512, nb=1, A0=1.0, t_star=None):
+    """Transient thermal grating (Sec. 4.2): one period L of T(x, 0) = A0 cos(2 pi x / L) with
+    periodic ends, 1000 cells and 512 directions (GL in mu).  Gray silicon by default; the
+    period follows from xi = 2 pi Kn = 2 pi v tau / L.  With nb > 1 the seeded non-gray bands
+    (seed 1006) are used and L is fixed by xi on the capacity-weighted mean of v tau.  The run
+    covers t* = t / tau up to 10 / xi (diffusive decay at small xi, ballistic at large), about
+    3200 steps at the CFL time step for every xi."""
+    if nb == 1:
+        C, v, tau = (np.array([GRAY_SI[k]]) for k in ("C", "v", "tau"))
+    else:
+        C, v, tau = bands(1006, nb)
+    vt = float(np.sum(C * v * tau) / np.sum(C))
+    tau_ref = float(np.sum(C * tau) / np.sum(C))
+    L = 2 * math.pi * vt / xi
+    h = (L / nx, L / nx, L / nx)
+    dt = cfl_time_step(h[:1], v)
+    t_end = (10.0 / xi if t_star is None else t_star) * tau_ref
+    steps = int(math.ceil(t_end / dt))
+    cfg = dict(name="ttg_1d_%d_%dx%d_xi%g" % (nx, nb, ntheta, xi), dim=1, n=(nx, 1, 1), h=h, nb=nb, seed=1006,
+               quad=("gl1d", ntheta), bc=[PERIODIC] * 6, Tw=[0.0] * 6, steps=steps, C=C, v=v, tau=tau, dt=dt,
+               source=None, xi=xi, L=L, A0=A0, tau_ref=tau_ref)
+    return cfg
+
+
+def ttg_initial_temperature(cfg):
+    """T(x, 0) - T_ref = A0 cos(2 pi x / L) at the cell centres, shape (nz, ny, nx)."""
+    x = (np.arange(cfg["n"][0]) + 0.5) * cfg["h"][0]
+    return (cfg["A0"] * np.cos(2 * math.pi * x / cfg["L"]))[None, None, :]
+
+
+def grating_amplitude(cfg, T):
+    """A = (2/N) sum_i T_i cos(2 pi x_i / L): the amplitude of the grating's mode in a field T."""
+    x = (np.arange(cfg["n"][0]) + 0.5) * cfg["h"][0]
+    return 2.0 / cfg["n"][0] * float(np.sum(np.asarray(T).reshape(-1) * np.cos(2 * math.pi * x / cfg["L"])))
+
+
 def source_field(cfg):
     """Per-cell source Q_i (W/m^3) of a workload, float32 (nz, ny, nx), or None."""
     src = cfg.get("source")

@@ -135,15 +135,27 @@ def test_two_level_recomputation(monkeypatch):
     assert two[0] == ref[0] and np.array_equal(two[1], ref[1]) and np.array_equal(two[2], ref[2])
 
 
-@pytest.mark.parametrize("storage,tol", [(1, 2e-3), (2, 1e-2)])
-def test_adjoint_with_16bit_state(storage, tol):
+@pytest.mark.parametrize("storage,rounding", [(1, 0), (1, 1), (2, 0), (2, 1)])
+def test_adjoint_with_16bit_state(storage, rounding):
     """FP16/BF16 coded state (FP32 adjoint): the gradients of the rounded trajectory against
-    the FP64 oracle's, within the storage's own accuracy."""
+    the FP64 oracle's.  The adjoint is exact for the trajectory it differentiates, so its error
+    is the storage's own: the bound is the 16-bit bar 2e-3 or, for codes whose forward T_L error
+    on this run exceeds 5e-4, four times that error (measured on GB300: gradient errors 2-3x
+    the forward error, e.g. BF16 to nearest 1.3e-3 forward, 2.5e-3 gradient)."""
+    from paper_2306_14181_gb300 import bte
     nsteps = 16
-    cfg, P, ctx, Q, amps, dT0, p = _setup(3, (96, 9, 7), [DIF, ISO, SPE, SPE, PER, PER], 2, 2, nsteps, storage=storage)
-    J, gQ, gt = _gpu_adjoint(ctx, Q, amps, dT0, p, nsteps)
+    cfg, P, _, Q, amps, dT0, p = _setup(3, (96, 9, 7), [DIF, ISO, SPE, SPE, PER, PER], 2, 2, nsteps, storage=storage)
+    ctx = gpu_ctx(cfg, limiter=2, kernel=2, storage=storage, rounding=rounding, seed=3)
     e0 = P.equilibrium(np.asarray(dT0, np.float32).astype(np.float64))
     Jo, gQo, gto = P.adjoint(e0, nsteps, p, Q, amps)
+    bte.bte_init_temperature(ctx, dT0.reshape(-1))
+    bte.bte_set_source(ctx, Q, amps)
+    bte.bte_step(ctx, nsteps)
+    _, TL, _ = bte.bte_moments(ctx)
+    TLo = P.lattice_temperature(P.run(e0, nsteps, Q, amps))
+    fwd = float(np.max(np.abs(TL - TLo)) / np.max(np.abs(TLo)))
+    tol = max(2e-3, 4.0 * fwd)
+    J, gQ, gt = _gpu_adjoint(ctx, Q, amps, dT0, p, nsteps)
     assert np.max(np.abs(gQ - gQo)) <= tol * np.max(np.abs(gQo))
     assert np.max(np.abs(gt - gto)) <= tol * np.max(np.abs(gto))
 
@@ -186,3 +198,134 @@ def test_autograd_function():
     assert abs(J.item() - Jo) <= 1e-5 * abs(Jo)
     assert np.max(np.abs(Q.grad.cpu().numpy() - 2 * gQo)) <= TOL * np.max(np.abs(2 * gQo))
     assert np.max(np.abs(log_tau.grad.numpy() - 2 * gto)) <= TOL * np.max(np.abs(2 * gto))
+
+
+def test_film_adjoint_full_grid():
+    """The 2-D film adjoint workload on its full grid (128 x 128 cells, 20 bands, 64 directions,
+    specular sides, isothermal bottom, diffuse top, the centred Gaussian source; J = mean T_L
+    over the top-centre 16 x 16 probe): 100 steps with checkpoints every 25 (the workload's 2000
+    steps are out of the oracle's reach), tiled kernels, against the oracle's checkpointed FP64
+    adjoint at 1e-4, and against oracle central differences (h = 1e-4 of the cell's own source,
+    so that the limited scheme responds linearly) on the cell of the largest gradient within the
+    heated region (source above 1 % of its peak) and on the log tau_k of the largest gradient."""
+    from paper_2306_14181_gb300 import bte
+    nsteps, ck = 100, 25
+    cfg = inputs.film_adjoint_2d()
+    P = oracle_problem(cfg)
+    Q = inputs.source_field(cfg)
+    probe = inputs.probe_weights(cfg)
+    ctx = gpu_ctx(cfg)
+    assert ctx.info.kernel == bte.BTE_KERNEL_TILED
+    bte.bte_set_source(ctx, Q)
+    J, gQ, gt = bte.bte_adjoint(ctx, nsteps, probe, ck)
+    del ctx
+    e0 = P.equilibrium(0.0)
+    Jo, gQo, gto = P.adjoint(e0, nsteps, probe, Q, ckpt=ck)
+    assert abs(J - Jo) <= 1e-5 * abs(Jo)
+    assert np.max(np.abs(gQ - gQo)) <= TOL * np.max(np.abs(gQo))
+    assert np.max(np.abs(gt - gto)) <= TOL * np.max(np.abs(gto))
+
+    def Jrun(Pp, Qq):
+        return float(np.sum(probe * Pp.lattice_temperature(Pp.run(e0, nsteps, Qq))))
+
+    heated = Q.reshape(-1) >= 0.01 * float(Q.max())
+    ci = int(np.flatnonzero(heated)[np.argmax(np.abs(gQ.reshape(-1)[heated]))])
+    hq = 1e-4 * float(Q.reshape(-1)[ci])
+    Qp, Qm = Q.copy().reshape(-1), Q.copy().reshape(-1)
+    Qp[ci] = np.float32(Qp[ci] + hq)
+    Qm[ci] = np.float32(Qm[ci] - hq)
+    fd = (Jrun(P, Qp.reshape(Q.shape)) - Jrun(P, Qm.reshape(Q.shape))) / (float(Qp[ci]) - float(Qm[ci]))
+    assert abs(fd - gQ.reshape(-1)[ci]) <= TOL * np.max(np.abs(gQ))
+    k = int(np.argmax(np.abs(gt)))
+    Js = []
+    for sgn in (1, -1):
+        tau = np.array(cfg["tau"], float)
+        tau[k] *= np.exp(sgn * 1e-4)
+        Js.append(Jrun(oracle_problem(dict(cfg, tau=tau)), Q))
+    assert abs((Js[0] - Js[1]) / 2e-4 - gt[k]) <= TOL * np.max(np.abs(gt))
+
+
+_BLOCK_FD = {}
+
+
+def _block_fd():
+    """Oracle central differences of J for the reduced 3-D adjoint block (computed once): 20
+    source cells drawn with rng(1005) among the heated ones (source above 1 % of its peak; h =
+    1e-4 of the largest source) and every log tau_k (h = 1e-4).  Cells the pulse has not reached
+    are left out: there the state still sits exactly on its reference, where the limited face
+    value (homogeneous of degree 1 in the two slopes) has a kink at a = b = 0, so a finite
+    difference measures the scheme's nonlinear response, not a derivative."""
+    if not _BLOCK_FD:
+        nsteps = 20
+        cfg = inputs.block_adjoint_3d(nx=96, ny=8, nz=8, nb=4)
+        P = oracle_problem(cfg)
+        Q = inputs.source_field(cfg)
+        amps = inputs.source_amplitudes(cfg, nsteps)
+        probe = inputs.probe_weights(cfg)
+        e0 = P.equilibrium(0.0)
+
+        def Jrun(Pp, Qq):
+            return float(np.sum(probe * Pp.lattice_temperature(Pp.run(e0, nsteps, Qq, amps))))
+
+        heated = np.flatnonzero(Q.reshape(-1) >= 1e-2 * float(Q.max()))
+        cells = np.random.default_rng(1005).choice(heated, 20, replace=False)
+        hq = 1e-4 * float(Q.max())
+        fdQ = []
+        for ci in cells:
+            Qp, Qm = Q.copy().reshape(-1), Q.copy().reshape(-1)
+            Qp[ci] = np.float32(Qp[ci] + hq)
+            Qm[ci] = np.float32(Qm[ci] - hq)
+            fdQ.append((Jrun(P, Qp.reshape(Q.shape)) - Jrun(P, Qm.reshape(Q.shape))) / (float(Qp[ci]) - float(Qm[ci])))
+        fdt = []
+        for k in range(P.nb):
+            Js = []
+            for sgn in (1, -1):
+                tau = np.array(cfg["tau"], float)
+                tau[k] *= np.exp(sgn * 1e-4)
+                Js.append(Jrun(oracle_problem(dict(cfg, tau=tau)), Q))
+            fdt.append((Js[0] - Js[1]) / 2e-4)
+        _BLOCK_FD.update(cfg=cfg, Q=Q, amps=amps, probe=probe, nsteps=nsteps, cells=cells, fdQ=np.array(fdQ),
+                         fdt=np.array(fdt), J=Jrun(P, Q))
+    return _BLOCK_FD
+
+
+@pytest.mark.parametrize("storage,tol", [(0, TOL), (1, 2e-3)])
+def test_block_adjoint_finite_difference_spot_checks(storage, tol):
+    """The 3-D adjoint block (specular sides, isothermal bottom, diffuse top, the laser pulse
+    on the symmetry edge, J = mean T_L of the top layer) reduced to 96 x 8 x 8 cells and 4 bands
+    (96 directions, nx = 96 so the tiled kernels run), 20 steps from equilibrium: the GPU's FP32
+    adjoint of an FP32 or FP16 state against oracle central differences on 20 heated source
+    cells drawn with rng(1005) and on every log tau_k.  FP16 storage: the gradient of the
+    rounded trajectory, within the 16-bit bar 2e-3."""
+    from paper_2306_14181_gb300 import bte
+    f = _block_fd()
+    ctx = gpu_ctx(f["cfg"], storage=storage, T_scale=1.0)
+    assert ctx.info.kernel == bte.BTE_KERNEL_TILED
+    bte.bte_set_source(ctx, f["Q"], f["amps"])
+    J, gQ, gt = bte.bte_adjoint(ctx, f["nsteps"], f["probe"], 5)
+    assert abs(J - f["J"]) <= (1e-5 if storage == 0 else 2e-3) * abs(f["J"])
+    assert np.max(np.abs(gQ.reshape(-1)[f["cells"]] - f["fdQ"])) <= tol * np.max(np.abs(gQ))
+    assert np.max(np.abs(gt - f["fdt"])) <= tol * np.max(np.abs(gt))
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_block_adjoint_from_equilibrium_matches_oracle_adjoint(kernel):
+    """From an exactly uniform start the pulse's far field carries slopes of 1e-20 and below;
+    the limiter's partials (homogeneous of degree 0) must stay finite there.  The reduced block,
+    20 steps, generic and tiled adjoints, against the oracle's adjoint on every cell."""
+    from paper_2306_14181_gb300 import bte
+    nsteps = 20
+    cfg = inputs.block_adjoint_3d(nx=96, ny=8, nz=8, nb=4)
+    P = oracle_problem(cfg)
+    Q = inputs.source_field(cfg)
+    amps = inputs.source_amplitudes(cfg, nsteps)
+    probe = inputs.probe_weights(cfg)
+    ctx = gpu_ctx(cfg, kernel=kernel)
+    assert ctx.info.kernel == kernel
+    bte.bte_set_source(ctx, Q, amps)
+    J, gQ, gt = bte.bte_adjoint(ctx, nsteps, probe, 5)
+    assert np.all(np.isfinite(gQ)) and np.all(np.isfinite(gt))
+    Jo, gQo, gto = P.adjoint(P.equilibrium(0.0), nsteps, probe, Q, amps, ckpt=5)
+    assert abs(J - Jo) <= 1e-5 * abs(Jo)
+    assert np.max(np.abs(gQ - gQo)) <= TOL * np.max(np.abs(gQo))
+    assert np.max(np.abs(gt - gto)) <= TOL * np.max(np.abs(gto))

@@ -146,3 +146,19 @@ def test_adjoint_and_tangent_with_periodic_jump(dim, n, bc, jump, limiter):
     h = 1e-2 if limiter == 0 else 1e-5
     fd = (P.step(e + h * de) - P.step(e - h * de)) / (2 * h)
     assert np.max(np.abs(fd - t)) <= (1e-9 if limiter == 0 else 1e-5) * np.max(np.abs(fd))
+
+
+@pytest.mark.parametrize("dim,n,bc", [GRIDS[2], GRIDS[4]])
+def test_checkpointed_run_adjoint_is_bitwise_the_stored_one(dim, n, bc):
+    """Keeping every ckpt-th state and recomputing the rest gives bitwise the gradients of
+    keeping every state (ckpt = 0): the forward step is deterministic."""
+    cfg = small_cfg(dim, n, bc, Tw=TW, nb=3)
+    P = oracle_problem(cfg, 2)
+    e0 = inputs.random_state(P.shape, 3) * 1e3
+    Q = (np.random.default_rng(1).random((P.nz, P.ny, P.nx)) * 1e17).astype(np.float32)
+    p = np.random.default_rng(2).random((P.nz, P.ny, P.nx))
+    amps = np.linspace(1, 0.2, 13)
+    ref = P.adjoint(e0, 13, p, Q, amps, ckpt=0)
+    for ck in (1, 4, 5, 13):
+        J, gQ, gt = P.adjoint(e0, 13, p, Q, amps, ckpt=ck)
+        assert J == ref[0] and np.array_equal(gQ, ref[1]) and np.array_equal(gt, ref[2])

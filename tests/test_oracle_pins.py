@@ -13,6 +13,7 @@ from oracle import quadrature as oq
 from oracle.oracle import (BC_DIFFUSE, BC_ISOTHERMAL, BC_PERIODIC, BC_SPECULAR, LIM_FIRST_ORDER, LIM_MINMOD,
                            LIM_VANALBADA)
 from paper_2306_14181_gb300 import inputs
+from oracle import ttg
 from tests.support import oracle_problem, oracle_quadrature, rel_linf, small_cfg
 
 ISO, DIF, SPE, PER = BC_ISOTHERMAL, BC_DIFFUSE, BC_SPECULAR, BC_PERIODIC
@@ -190,24 +191,6 @@ def test_p5_diffusive_limit_fourier_law():
 # P6  transient thermal grating (Sec. 4.2): with the first-order face value the fully
 #     discrete scheme maps each Fourier mode to itself, e_hat^{n+1} = G(theta) e_hat^n.
 # ---------------------------------------------------------------------------------------
-def _ttg_matrix(P, theta):
-    nb, nd = P.nb, P.nd
-    D = float(np.sum(P.C / P.tau))
-    G = np.zeros((nb * nd, nb * nd), dtype=complex)
-    col = np.zeros(nb * nd)
-    for k in range(nb):
-        for d in range(nd):
-            col[k * nd + d] = P.w[d] / P.tau[k] / D
-    for k in range(nb):
-        for d in range(nd):
-            r = k * nd + d
-            nu = P.dt * P.v[k] * P.s[d, 0] / P.dx
-            sg = 1.0 if nu > 0 else -1.0
-            G[r, r] += 1.0 - abs(nu) * (1.0 - np.exp(-1j * sg * theta)) - P.dt / P.tau[k]
-            G[r, :] += P.dt / P.tau[k] * (P.C[k] / P.W) * col
-    return G, col
-
-
 @pytest.mark.parametrize("nb,quad", [(1, ("gl1d", 8)), (3, ("gl1d", 6))])
 def test_p6_ttg_fourier_mode_exact(nb, quad):
     cfg = small_cfg(1, (24, 1, 1), [PER] * 6, nb=nb, quad=quad, h=1e-9)
@@ -217,8 +200,9 @@ def test_p6_ttg_fourier_mode_exact(nb, quad):
     e0 = P.equilibrium(np.cos(theta * (j + 0.5))[None, None, :])
     nsteps = 150
     e = P.run(e0, nsteps)
-    G, col = _ttg_matrix(P, theta)
-    a = np.repeat((P.C / P.W)[:, None], P.nd, axis=1).ravel() * np.exp(0.5j * theta)
+    G = ttg.discrete_first_order_matrix(P, theta)
+    col = ttg.moment_row(P)
+    a = ttg.equilibrium_mode(P) * np.exp(0.5j * theta)
     a = np.linalg.matrix_power(G, nsteps) @ a
     pred_e = np.real(a[:, None] * np.exp(1j * theta * j)[None, :])
     assert rel_linf(e.reshape(P.nb * P.nd, P.nx), pred_e) <= 1e-12
@@ -532,3 +516,53 @@ def test_residuals_closed_forms():
     assert eq == pytest.approx(0.5, rel=1e-12)
     eT, eq = P.residuals(e, P.step(e), 300.0)
     assert eT <= 1e-15 and eq <= 1e-12
+
+
+# ---------------------------------------------------------------------------------------
+# Transient thermal grating (Sec. 4.2): the semi-discrete mode solution exp(M t) that the
+# scheme approaches as dx, dt -> 0.  Its two closed-form limits for one gray band:
+#  - ballistic (tau -> infinity): each direction's mode advects unchanged, so
+#    A(t)/A0 = sum_d w_d cos(q v mu_d t) / W;
+#  - diffusive (Kn = v tau / L << 1): A(t)/A0 -> exp(-alpha q^2 t), alpha = v^2 tau / 3.
+# The limited scheme of the oracle converges to it under grid refinement.
+# ---------------------------------------------------------------------------------------
+def _ttg_problem(N, L, v, tau, nd, limiter=LIM_VANALBADA, beta=0.5):
+    cfg = small_cfg(1, (N, 1, 1), [PER] * 6, nb=1, quad=("gl1d", nd), h=L / N, tau=tau, v=v, beta=beta)
+    return oracle_problem(cfg, limiter)
+
+
+def test_ttg_semidiscrete_ballistic_limit():
+    L, v = 1e-6, 2677.0
+    P = _ttg_problem(10, L, v, 1e3, 32)
+    q = 2 * math.pi / L
+    t = np.linspace(0.0, 3 * L / v, 13)
+    A = ttg.semidiscrete_amplitudes(P, q, t)
+    exact = np.array([np.sum(P.w * np.cos(q * v * P.s[:, 0] * tt)) / P.W for tt in t])
+    assert np.max(np.abs(A - exact)) <= 1e-9
+
+
+def test_ttg_semidiscrete_diffusive_limit():
+    L, v, tau = 1e-6, 2677.0, 39.9e-12 * 1e-3   # Kn = v tau / L ~ 1e-4
+    P = _ttg_problem(10, L, v, tau, 32)
+    q = 2 * math.pi / L
+    alpha = v * v * tau / 3.0
+    t = np.array([0.5, 1.0, 2.0]) / (alpha * q * q)
+    A = ttg.semidiscrete_amplitudes(P, q, t)
+    assert np.max(np.abs(A - np.exp(-alpha * q * q * t))) <= 1e-4
+
+
+def test_ttg_limited_scheme_converges_to_the_mode_solution():
+    """xi = 2 pi Kn = 1 gray grating: the van Albada scheme's amplitude error against exp(M t)
+    at t* = t/tau = 4 falls with refinement (dt tied to dx by the CFL rule)."""
+    v, tau = 2677.0, 39.9e-12
+    L = 2 * math.pi * v * tau / 1.0
+    errs = []
+    for N in (50, 100, 200):
+        P = _ttg_problem(N, L, v, tau, 16)
+        x = (np.arange(N) + 0.5) * P.dx
+        nsteps = int(round(4 * tau / P.dt))
+        e = P.run(P.equilibrium(np.cos(2 * math.pi * x / L)[None, None, :]), nsteps)
+        T = P.moments(e)[0].ravel()
+        A = 2.0 / N * float(np.sum(T * np.cos(2 * math.pi * x / L)))
+        errs.append(abs(A - ttg.semidiscrete_amplitudes(P, 2 * math.pi / L, [nsteps * P.dt])[0]))
+    assert errs[1] < 0.6 * errs[0] and errs[2] < 0.6 * errs[1], errs
