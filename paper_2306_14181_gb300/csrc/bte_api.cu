@@ -1161,7 +1161,8 @@ extern "C" bte_status bte_adjoint(bte_ctx *c, int nsteps, int ckpt_every, const 
     // tiled adjoint: segment partials, wall corrections, block partials of sum mu T_L
     float *Pm = nullptr, *Pq = nullptr, *Ps = nullptr, *corr[3] = {nullptr, nullptr, nullptr};
     double *mtp = nullptr;
-    const bool tiled_adj = c->tiled && c->nd <= adj_walls_max_dirs();
+    // the tiled adjoint takes rows that fill the forward kernel's row capacity exactly
+    const bool tiled_adj = c->tiled && c->nd <= adj_walls_max_dirs() && c->plan.nx == c->n[0];
     float *wscr = nullptr;
     if (tiled_adj) {
         const size_t gt_rows = (size_t)std::max(1, c->plan.G);

@@ -40,7 +40,8 @@ __global__ void __launch_bounds__(256) k_finalize_tiled(const StepArgs a, const 
     const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long long)nx * ny));
     const int ty = y / p.ty, tz = z / p.tz;
     const int tile = tz * p.nty + ty;
-    const int li = ((z - tz * p.tz) * p.ty + (y - ty * p.ty)) * nx + x;
+    // the tile arrays keep rows of p.nxt cells (the kernel's row capacity, >= nx)
+    const int li = ((z - tz * p.tz) * p.ty + (y - ty * p.ty)) * p.nxt + x;
     // the tile's segments: its units in part order, each unit's bands in order
     const int g0 = p.tile_seg0[tile], g1 = p.tile_seg0[tile + 1];
     const float *P = a.P + li;
@@ -82,7 +83,7 @@ __global__ void __launch_bounds__(256) k_ediff_tiled(const StepArgs a, const Til
         const int ty = y / p.ty, tz = z / p.tz;
         const int tile = tz * p.nty + ty;
         const int yl = y - ty * p.ty, zl = z - tz * p.tz;
-        const int slot = ax == 0 ? zl * p.ty + yl : (ax == 1 ? zl * nx + x : yl * nx + x);
+        const int slot = ax == 0 ? zl * p.ty + yl : (ax == 1 ? zl * p.nxt + x : yl * p.nxt + x);
         float s = 0.f;
         for (int jj = 0; jj < p.J; ++jj) {
             const int u = jj * p.ntiles + tile;
@@ -167,12 +168,30 @@ bool tiled_plan(int dim, const int n[3], int nb, int nd, int storage, int limite
         why = "the tiled kernel covers 2-D and 3-D grids";
         return false;
     }
-    const int nx = n[0];
-    if (!(nx == 96 || nx == 128 || (nx == 256 && dim == 2))) {
-        why = "the tiled kernel needs nx = 96, 128 or 256 (2-D) or nx = 96 or 128 (3-D)";
+    // Row capacity NX of the kernel instance: the smallest of 64, 96, 128 and (2-D) 256 cells that
+    // holds the grid's rows, such that a row is a whole number of 16-byte units (its bulk copies
+    // start and end on 16-byte boundaries), a whole number of lanes (VL = NX / 32 / warps per row
+    // cells a lane), and every warp of the row keeps at least two lanes of cells.
+    const int gxn = n[0];
+    const int esz = storage == kStoreF32 ? 4 : 2;
+    int nx = 0;
+    {
+        const int caps[4] = {64, 96, 128, 256};
+        for (int cap : caps) {
+            if (cap == 256 && dim != 2) continue;
+            const int w = cap == 256 ? 2 : 1, vl = cap / (32 * w);
+            const int lo = w == 2 ? 128 + 2 * vl : 2 * vl;
+            if (gxn <= cap && gxn >= lo && gxn % vl == 0 && (gxn * esz) % 16 == 0) {
+                nx = cap;
+                break;
+            }
+        }
+    }
+    if (nx == 0) {
+        why = "the tiled kernel needs rows of a multiple of 16 bytes and of the cells a lane holds, at most 256 "
+              "(2-D) or 128 (3-D) cells";
         return false;
     }
-    const int esz = storage == kStoreF32 ? 4 : 2;
     const int wpr = nx == 256 ? 2 : 1;
     const int ncw = dim == 2 ? Geo<2, 1>::NCW : Geo<3, 1>::NCW;
     const int TZ = dim == 2 ? Geo<2, 1>::TZ : Geo<3, 1>::TZ;
@@ -187,6 +206,9 @@ bool tiled_plan(int dim, const int n[3], int nb, int nd, int storage, int limite
         const int c = std::atoi(env);
         if (c >= 1 && c <= 1024) plan.chunk = c;
     }
+    // rows shorter than the capacity lie at another stride in global memory than in the box:
+    // one bulk copy a row
+    if (gxn != nx) plan.chunk = 1;
     plan.ty = TY;
     plan.tz = TZ;
     plan.threads = (ncw + kProducerWarps) * 32;
@@ -362,6 +384,7 @@ TiledArgs tiled_device_args(const TiledPlan &plan) {
     t.chunk = plan.chunk;
     t.wait_ns = plan.wait_ns;
     t.stall = plan.stall;
+    t.nxt = plan.nx;
     return t;
 }
 

@@ -28,6 +28,7 @@ struct TiledArgs {
     int chunk;             // rows per bulk copy of a box slice
     unsigned long long wait_ns;  // limit of a bounded mbarrier wait (ns)
     int stall;                   // failure-detection test: 1 the consumers', 2 the producer's first wait never completes
+    int nxt;                     // row capacity of the kernel instance (tile arrays' row length, >= nx)
 };
 
 // Plane-synchronous schedule of the tiled forward kernel.  The plane list (k*nd + d) of every
@@ -56,7 +57,7 @@ struct TiledPlan {
     float *PW = nullptr;
     float *hdr = nullptr;
     void *isorow = nullptr;
-    int storage = 0, nx = 0, chunk = 4;
+    int storage = 0, nx = 0, chunk = 4;  // nx: the instance's row capacity NX (>= the grid's nx)
     int *err = nullptr;
     unsigned long long wait_ns = 2000000000ull;  // bounded-wait limit (bte_set_wait_limit)
     int stall = 0;                               // one-shot stall test of the next launch (bte_set_wait_limit)

@@ -356,7 +356,7 @@ template <int S, int NX>
 __device__ __forceinline__ const typename St<S>::T *ghost_row_src(const StepArgs &a, const TiledArgs &p, const PT &q,
                                                                   int ax, int pos, int other, float nu) {
     using T = typename St<S>::T;
-    const int ny = a.n[1];
+    const int gx = a.n[0], ny = a.n[1];
     const int n = a.n[ax];
     const int side = pos < 0 ? 0 : 1;
     const int wall = 2 * ax + side;
@@ -364,7 +364,7 @@ __device__ __forceinline__ const typename St<S>::T *ghost_row_src(const StepArgs
     const T *e = static_cast<const T *>(a.e_in);
     auto row_at = [&](int plane, int along) {
         const int yy = ax == 1 ? along : other, zz = ax == 1 ? other : along;
-        return e + (long long)plane * a.ncell + ((long long)zz * ny + yy) * NX;
+        return e + (long long)plane * a.ncell + ((long long)zz * ny + yy) * gx;
     };
     if (bc == kBcPeriodic) return row_at(q.plane, side ? pos - n : pos + n);
     if (bc == kBcSpecular) {
@@ -379,7 +379,7 @@ __device__ __forceinline__ const typename St<S>::T *ghost_row_src(const StepArgs
     // diffuse wall (and with 16-bit storage the thermalizing wall, whose emission is coded
     // against each wall cell's reference): wall cells of a y-wall are indexed z*nx + x, those
     // of a z-wall y*nx + x
-    return static_cast<const T *>(a.ediff_in) + ((long long)wall * a.nb + q.k) * a.wc_max + (long long)other * NX;
+    return static_cast<const T *>(a.ediff_in) + ((long long)wall * a.nb + q.k) * a.wc_max + (long long)other * gx;
 }
 
 // Shared-memory side arrays of a stage for the x-wall ghosts (storage format, bulk-copied):
@@ -411,10 +411,11 @@ __device__ void producer(const StepArgs &a, const TiledArgs &p, char *smem, uint
     using T = typename St<S>::T;
     using SD = Side<S, WPR, DIM>;
     constexpr int NX = 32 * VL * WPR, TY = Geo<DIM, WPR>::TY;
-    constexpr uint32_t rowb = NX * sizeof(T);
     constexpr int V = SD::V;
     const int lane = threadIdx.x & 31;
-    const int ny = a.n[1], nz = a.n[2];
+    const int gx = a.n[0], ny = a.n[1], nz = a.n[2];
+    // a row of the grid is gx <= NX cells (a multiple of 16 bytes); box rows keep the stride NX
+    const uint32_t rowb = (uint32_t)gx * sizeof(T);
     const T *e = static_cast<const T *>(a.e_in);
     const T *ed = static_cast<const T *>(a.ediff_in);
     const int bx[2] = {a.bc[0], a.bc[1]};
@@ -492,7 +493,7 @@ __device__ void producer(const StepArgs &a, const TiledArgs &p, char *smem, uint
             if (it < nch) {
                 const int y = ya + it * p.chunk;
                 if (y < yb)
-                    bulk_g2s(slice + (size_t)(y - ybox0) * NX, e + pbase + ((long long)z * ny + y) * NX,
+                    bulk_g2s(slice + (size_t)(y - ybox0) * NX, e + pbase + ((long long)z * ny + y) * gx,
                              (uint32_t)min(p.chunk, yb - y) * rowb, &full[s]);
             } else if (it < nch + 4) {
                 const int g = it - nch;  // 0, 1: below the domain; 2, 3: above it
@@ -505,10 +506,10 @@ __device__ void producer(const StepArgs &a, const TiledArgs &p, char *smem, uint
         // the diffuse values of the tile's rows (incoming directions only)
         for (int sd = 0; sd < 2; ++sd) {
             if (spec[sd]) {
-                const long long mb = ((long long)q.k * a.nd + a.mirror[q.d]) * a.ncell + (sd ? NX - V : 0);
+                const long long mb = ((long long)q.k * a.nd + a.mirror[q.d]) * a.ncell + (sd ? gx - V : 0);
                 for (int j = lane; j < ncore; j += 32) {
                     const int yl = j % q.nyt, zl = j / q.nyt;
-                    bulk_g2s(SD::spec(side, sd, zl, yl), e + mb + ((long long)(q.z0 + zl) * ny + q.y0 + yl) * NX, 16, &full[s]);
+                    bulk_g2s(SD::spec(side, sd, zl, yl), e + mb + ((long long)(q.z0 + zl) * ny + q.y0 + yl) * gx, 16, &full[s]);
                 }
             }
             if (dif[sd])
@@ -528,7 +529,7 @@ __device__ void producer(const StepArgs &a, const TiledArgs &p, char *smem, uint
             const int zlo = DIM == 3 ? max(qp.z0 - (pnuz > 0.f ? 2 : 1), 0) : 0;
             const int zhi = DIM == 3 ? min(qp.z0 + qp.nzt + (pnuz > 0.f ? 1 : 2), nz) : 1;
             for (int z = zlo + lane; z < zhi; z += 32)
-                bulk_prefetch_l2(e + (long long)qp.plane * a.ncell + ((long long)z * ny + ylo) * NX, (uint32_t)(yhi - ylo) * rowb);
+                bulk_prefetch_l2(e + (long long)qp.plane * a.ncell + ((long long)z * ny + ylo) * gx, (uint32_t)(yhi - ylo) * rowb);
             ahead_ok = ahead.next(a, p);
         }
         if (++s == p.ns) {
@@ -558,7 +559,12 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
     constexpr bool REF = St<S>::kRef;
     constexpr int NX = 32 * VL * WPR, TY = Geo<DIM, WPR>::TY, RY = TY + 4;
     const int lane = threadIdx.x & 31, x0 = (half * 32 + lane) * VL;
-    const int ny = a.n[1], nz = a.n[2];
+    const int rowlen = a.n[0], ny = a.n[1], nz = a.n[2];
+    // The grid's rows hold rowlen <= NX cells (a multiple of VL): lanes past the row's end compute
+    // on unused box columns and store nothing.  The right end lane of this warp's part of the row
+    // holds its last cell (lane 31 unless the row ends inside this warp's part).
+    const bool active = x0 < rowlen;
+    const int rend = min(31, (rowlen - half * 32 * VL) / VL - 1);
     const float *hd = reinterpret_cast<const float *>(stage + p.hdr_off);  // per-plane constants
     const float4 h0 = reinterpret_cast<const float4 *>(hd)[0];
     const float nux = h0.x, nuy = h0.y, nuz = h0.z, wm = h0.w;
@@ -598,11 +604,12 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
             }
         }
     }
-    T *eo = static_cast<T *>(a.e_out) + (long long)q.plane * a.ncell + ((long long)z * ny + q.y0 + yl0) * NX + x0;
+    T *eo = static_cast<T *>(a.e_out) + (long long)q.plane * a.ncell + ((long long)z * ny + q.y0 + yl0) * rowlen + x0;
+    const int dyg = sy * rowlen;                   // next row in streaming order (global elements)
     using SD = Side<S, WPR, DIM>;
     char *side = const_cast<char *>(stage) + p.side_off;
     // x ghosts of the two end lanes, decided once per plane-tile
-    const bool xlo = lane == 0 && half == 0, xhi = lane == 31 && half == WPR - 1;
+    const bool xlo = lane == 0 && half == 0, xhi = x0 + VL == rowlen;
     // Ghost sources of the two end lanes, decided once per plane-tile.  Every lane then reads two
     // values g0 (next to its end) and g1 (second ghost) per row from gptr + j * gstep at gi0 / gi1
     // (other lanes read their own cells), and the mode picks between them, a constant and the
@@ -612,14 +619,14 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
     int gstep = dy, gi0 = 0, gi1 = 0;
     int rx0 = x0, rx1 = x0;  // the two ghosts' cells in the reference box row
     float gc = 0.f;
-    if (lane == 0 || lane == 31) {
+    if (lane == 0 || lane == rend) {
         const int sd = lane == 0 ? 0 : 1;
         const int bc = a.bc[sd];
         const bool wall_lane = sd == 0 ? xlo : xhi;
         const bool leaving = sd == 0 ? nux <= 0.f : nux >= 0.f;
         gmode = kGhSmem;
         if (!wall_lane || bc == kBcPeriodic) {
-            const int gi = !wall_lane ? (sd == 0 ? x0 - 2 : x0 + VL) : (sd == 0 ? NX - 2 : 0);
+            const int gi = !wall_lane ? (sd == 0 ? x0 - 2 : x0 + VL) : (sd == 0 ? rowlen - 2 : 0);
             gptr = box + o + gi;
             gi0 = sd == 0 ? 1 : 0;
             gi1 = sd == 0 ? 0 : 1;
@@ -630,8 +637,8 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
             gstep = sy * SD::V;
             gi0 = sd == 0 ? 0 : SD::V - 1;
             gi1 = sd == 0 ? 1 : SD::V - 2;
-            rx0 = (sd == 0 ? 0 : NX - SD::V) + gi0;
-            rx1 = (sd == 0 ? 0 : NX - SD::V) + gi1;
+            rx0 = (sd == 0 ? 0 : rowlen - SD::V) + gi0;
+            rx1 = (sd == 0 ? 0 : rowlen - SD::V) + gi1;
         } else if (leaving) {
             gmode = kGhOwn;
             // FP32: read the lane's own end cell from the box row (same value, no select)
@@ -647,7 +654,7 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
         } else {
             gptr = SD::dcol(side, sd, zl) + (int)(dcol_src(a, sd, q.k, z, q.y0) & (SD::V - 1)) + yl0;
             gstep = sy;
-            rx0 = rx1 = sd == 0 ? 0 : NX - 1;
+            rx0 = rx1 = sd == 0 ? 0 : rowlen - 1;
         }
     }
     // diffuse-wall sums of Eq. (diff_bound) for the next step: cells next to a diffuse wall add
@@ -700,7 +707,7 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
                 g0 = gmode == kGhConst ? gc : (gmode == kGhOwn ? own : g0);
                 g1 = gmode == kGhConst ? gc : (gmode == kGhOwn ? own : g1);
             }
-            const bool l0 = gmode != kGhShfl && lane == 0, l31 = gmode != kGhShfl && lane == 31;
+            const bool l0 = gmode != kGhShfl && lane == 0, l31 = gmode != kGhShfl && lane == rend;
             ex[1] = l0 ? g0 : ex[1];
             ex[0] = l0 ? g1 : ex[0];
             ex[VL + 2] = l31 ? g0 : ex[VL + 2];
@@ -743,7 +750,7 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
         }
         typename St<S>::C h[VL];
         float en[VL], es[VL];
-        const long long grow = ((long long)z * ny + y) * NX;  // global index of the row's first cell
+        const long long grow = ((long long)z * ny + y) * rowlen;  // global index of the row's first cell
         // FP32: e^{n+1} = e - dt/tau e + bt - |nu_y| (F_out - F_in) - nu_x (F_{v+1} - F_v)
         // [- |nu_z| (F_zout - F_zin)].  16-bit: bt carries -rho_new, so en is already the new code's
         // value.  Two cells at a time.
@@ -789,7 +796,7 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
             #pragma unroll
             for (int v = 0; v < VL; ++v) accsm[c + v] = ac[v];
         }
-        st_row<S, VL>(eo, h);
+        if (active) st_row<S, VL>(eo, h);
         // the stored values at the walls: 16-bit codes are decoded against the new reference
         // (T_L^n of the cell, read from global memory for wall cells only)
         // x walls: only the two end lanes have a non-zero weight (a predicated update)
@@ -799,7 +806,7 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
             if constexpr (REF) ev = sc * (ev + a.TL[grow + x0 + xe] * a.invTs);
             wxp[j * sy] += wx * ev;
         }
-        if (j == jw0 || j == jw1) {  // uniform across the warp
+        if (active && (j == jw0 || j == jw1)) {
             const float wy = j == jw0 ? wy0 : wy1;
             float *w = j == jw0 ? wy0p : wy1p;
             #pragma unroll
@@ -809,7 +816,7 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
                 w[v] += wy * ev;
             }
         }
-        if (DIM == 3 && wz != 0.f) {
+        if (DIM == 3 && wz != 0.f && active) {
             #pragma unroll
             for (int v = 0; v < VL; ++v) {
                 float ev = es[v];
@@ -826,7 +833,7 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
         }
         o += dy;
         c += dy;
-        eo += dy;
+        eo += dyg;
         ro += dyR;
     }
 }
@@ -852,6 +859,7 @@ __device__ __forceinline__ void flush_segment(const StepArgs &a, const TiledArgs
     int zl, rb, half;
     warp_place<VL, WPR, DIM>(zl, rb, half);
     const int x0 = (half * 32 + (threadIdx.x & 31)) * VL;
+    const int gx = a.n[0];
     float *P = a.P + (size_t)seg * p.tcells;
     float sc = 1.f, wck = 0.f;
     if constexpr (REF) {
@@ -863,8 +871,8 @@ __device__ __forceinline__ void flush_segment(const StepArgs &a, const TiledArgs
     for (int r = 0; r < Geo<DIM, WPR>::KR; ++r) {
         const int yl = rb + r;
         const int c = (zl * TY + yl) * NX + x0;
-        if (yl < q.nyt && zl < q.nzt) {
-            const long long g = ((long long)(q.z0 + zl) * a.n[1] + q.y0 + yl) * NX + x0;
+        if (yl < q.nyt && zl < q.nzt && x0 < gx) {
+            const long long g = ((long long)(q.z0 + zl) * a.n[1] + q.y0 + yl) * gx + x0;
             #pragma unroll
             for (int v = 0; v < VL; ++v) {
                 const float m = kAccRegs<DIM> ? acc[r][v] : accsm[c + v];
@@ -902,12 +910,12 @@ template <int VL, int WPR, int DIM>
 __device__ __forceinline__ void fill_ref_box(const StepArgs &a, const PT &q, float *rbox) {
     constexpr int NX = 32 * VL * WPR, TY = Geo<DIM, WPR>::TY, TZ = Geo<DIM, WPR>::TZ, NCW = Geo<DIM, WPR>::NCW;
     constexpr int RY = TY + 4, RZ = DIM == 3 ? TZ + 4 : 1;
-    const int ny = a.n[1], nz = a.n[2];
+    const int gx = a.n[0], ny = a.n[1], nz = a.n[2];
     for (int idx = threadIdx.x; idx < RZ * RY * NX; idx += NCW * 32) {
         const int x = idx % NX, ry = (idx / NX) % RY, rz = idx / (NX * RY);
         const int y = ref_row(q.y0 - 2 + ry, ny, a.bc[2], a.bc[3]);
         const int z = DIM == 3 ? ref_row(q.z0 - 2 + rz, nz, a.bc[4], a.bc[5]) : 0;
-        rbox[idx] = a.R[((long long)z * ny + y) * NX + x] * a.invTs;
+        rbox[idx] = x < gx ? a.R[((long long)z * ny + y) * gx + x] * a.invTs : 0.f;
     }
 }
 
@@ -919,7 +927,7 @@ __device__ void consumer(const StepArgs &a, const TiledArgs &p, char *smem, uint
     int zl, rb, half;
     warp_place<VL, WPR, DIM>(zl, rb, half);
     const int x0 = (half * 32 + lane) * VL;
-    const int ny = a.n[1];
+    const int gx = a.n[0], ny = a.n[1];
     float *wsm = reinterpret_cast<float *>(smem + p.wall_off);
     float *btsm = reinterpret_cast<float *>(smem + p.bt_off);
     float *accsm = reinterpret_cast<float *>(smem + p.acc_off);
@@ -958,8 +966,8 @@ __device__ void consumer(const StepArgs &a, const TiledArgs &p, char *smem, uint
             #pragma unroll
             for (int r = 0; r < Geo<DIM, WPR>::KR; ++r) {
                 const int yl = rb + r;
-                if (yl < q.nyt && zl < q.nzt) {
-                    const long long i0 = ((long long)(q.z0 + zl) * ny + (q.y0 + yl)) * NX + x0;
+                if (yl < q.nyt && zl < q.nzt && x0 < gx) {
+                    const long long i0 = ((long long)(q.z0 + zl) * ny + (q.y0 + yl)) * gx + x0;
                     float *bp = btsm + (zl * TY + yl) * NX + x0;
                     #pragma unroll
                     for (int v = 0; v < VL; ++v) {
@@ -1043,9 +1051,11 @@ __global__ void __launch_bounds__((Geo<DIM, WPR>::NCW + kProducerWarps) * 32, 1)
 
 typedef void (*StepKernel)(const StepArgs, const TiledArgs);
 
-// nx = 96: VL 3, one warp per row; nx = 128: VL 4, one warp; nx = 256 (2-D only): VL 4, two warps
+// row capacity 64: VL 2, one warp per row; 96: VL 3, one warp; 128: VL 4, one warp; 256 (2-D
+// only): VL 4, two warps
 template <int S, int LIM, int DIM, bool SR>
 StepKernel pick_nx(int nx) {
+    if (nx == 64) return k_step_tiled<S, LIM, 2, 1, DIM, SR>;
     if (nx == 96) return k_step_tiled<S, LIM, 3, 1, DIM, SR>;
     if (nx == 128) return k_step_tiled<S, LIM, 4, 1, DIM, SR>;
     if constexpr (DIM == 2) {

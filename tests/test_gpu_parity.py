@@ -242,6 +242,61 @@ def test_tiled_kernel_elementwise(dim, n, bc, limiter):
     assert rel_linf(fused_TL(ctx), oTL) <= TOL
 
 
+# Rows shorter than the kernel instance's capacity (64, 96, 128 or, in 2-D, 256 cells): lanes past
+# the row's end store nothing and the lane holding the last cell takes the right wall's ghosts.
+ANY_ROW = [
+    (2, (100, 21, 1), [PER, PER, ISO, DIF, PER, PER]),    # capacity 128, wrap at the short end
+    (2, (200, 13, 1), [SPE, DIF, SPE, ISO, PER, PER]),    # capacity 256: two warps, the second one short
+    (2, (72, 17, 1), [DIF, ISO, PER, PER, PER, PER]),     # capacity 96
+    (2, (40, 9, 1), [ISO, SPE, DIF, SPE, PER, PER]),      # capacity 64 (two cells a lane)
+    (3, (100, 9, 7), [SPE, SPE, PER, PER, ISO, DIF]),
+    (3, (60, 10, 8), [PER, PER, SPE, DIF, DIF, ISO]),
+]
+
+
+@pytest.mark.parametrize("limiter", [0, 2])
+@pytest.mark.parametrize("dim,n,bc", ANY_ROW)
+def test_tiled_kernel_any_row_length(dim, n, bc, limiter):
+    from paper_2306_14181_gb300 import bte
+    cfg = small_cfg(dim, n, bc, Tw=[0.3, -0.2, 0.1, 0.4, -0.3, 0.2], nb=3)
+    P = oracle_problem(cfg)
+    e0 = inputs.random_state(P.shape, 203) * 1e4
+    Q = (np.random.default_rng(7).random((P.nz, P.ny, P.nx)) * 1e17).astype(np.float32)
+    ctx, g, gTL, eo, oTL = run_both(cfg, e0, 10, Q, None, limiter=limiter, kernel=bte.BTE_KERNEL_TILED)
+    assert ctx.info.kernel == bte.BTE_KERNEL_TILED
+    assert rel_linf(g, eo) <= TOL
+    assert rel_linf(gTL, oTL) <= TOL
+    assert rel_linf(fused_TL(ctx), oTL) <= TOL
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+@pytest.mark.parametrize("dim,n,bc", [(2, (200, 13, 1), [SPE, DIF, SPE, ISO, PER, PER]),
+                                      (3, (104, 9, 7), [PER, PER, SPE, DIF, ISO, DIF])])
+def test_tiled_kernel_any_row_length_16bit(dim, n, bc, storage):
+    """16-bit codes on short rows: the 60-step run from equilibrium with a source, within 2e-3."""
+    from paper_2306_14181_gb300 import bte
+    cfg = small_cfg(dim, n, bc, Tw=[0.3, -0.2, 0.1, 0.4, -0.3, 0.2], nb=3)
+    P = oracle_problem(cfg)
+    Q = (np.random.default_rng(9).random((P.nz, P.ny, P.nx)) * 2e17).astype(np.float32)
+    ctx, g, gTL, eo, oTL = run_both(cfg, np.zeros(P.shape), 60, Q, None, storage=storage, kernel=bte.BTE_KERNEL_TILED)
+    assert ctx.info.kernel == bte.BTE_KERNEL_TILED
+    assert rel_linf(gTL, oTL) <= TOL16
+
+
+def test_rows_the_tiled_kernel_cannot_take():
+    """257 FP32 cells a row is not a whole number of 16-byte units: AUTO runs the generic kernel
+    (and still matches the oracle), an explicit request for the tiled one is refused."""
+    from paper_2306_14181_gb300 import bte
+    cfg = small_cfg(2, (257, 5, 1), [PER, PER, ISO, DIF, PER, PER], nb=2)
+    with pytest.raises(bte.BteError) as ei:
+        gpu_ctx(cfg, kernel=bte.BTE_KERNEL_TILED)
+    assert ei.value.status == bte.BTE_EUNSUPPORTED
+    P = oracle_problem(cfg)
+    ctx, g, gTL, eo, oTL = run_both(cfg, inputs.random_state(P.shape, 4) * 1e4, 5)
+    assert ctx.info.kernel == bte.BTE_KERNEL_GENERIC
+    assert rel_linf(gTL, oTL) <= TOL
+
+
 @pytest.mark.parametrize("dim,n,bc", [TILED[0], TILED[4]])
 def test_tiled_kernel_is_deterministic(dim, n, bc):
     """Two runs from the same state give bitwise equal states (no atomics in the moment)."""
