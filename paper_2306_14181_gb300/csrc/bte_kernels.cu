@@ -20,47 +20,73 @@ namespace bte {
 // The same pass accumulates the T_L moment sum_d w_d e^{n+1}/tau_k (Eq. BTE_get_e0) into
 // P[k][i] and, at diffuse walls, the outgoing sums of Eq. (diff_bound) for the next step.
 // ------------------------------------------------------------------------------------------
+// Threads of a block: blockDim.x cells by blockDim.y direction groups (256 in all); group g
+// takes the directions g, g + blockDim.y, ...  Small grids (few cells and bands) split a band's
+// directions over up to 32 groups so that the launch still fills the GPU; the groups' moment and
+// diffuse-wall partials are then summed in group order in shared memory, so the result is
+// deterministic for a given grid.
 template <int S, int LIM>
 __global__ void __launch_bounds__(256) k_step_generic(const StepArgs a) {
     using Cd = Codec<S>;
     using T = typename Cd::T;
+    __shared__ float red[4][256];  // moment and up to three diffuse walls (one per axis) per thread
+    const int ng = blockDim.y, grp = threadIdx.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.ncell) return;
+    const bool valid = i < a.ncell;
     const int k = blockIdx.y;
-    int c[3];
-    cell_coords(a, i, c);
+    int c[3] = {0, 0, 0};
     const BandConst b = a.band[k];
-    const T *ein = static_cast<const T *>(a.e_in);
-    T *eout = static_cast<T *>(a.e_out);
-    const float eq = b.ck * a.TL[i];
-    const float rho_i = rho_at<Cd>(a.R, a.invTs, i), rho_new = rho_at<Cd>(a.TL, a.invTs, i);
-    const float src = a.Q ? b.srck * (a.amp * a.Q[i]) : 0.f;
     int wl[6];
-    const int nw = diffuse_walls_of(a, c, wl);
+    int nw = 0;
     float wacc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float acc = 0.f;
-    for (int d = 0; d < a.nd; ++d) {
-        const int plane = k * a.nd + d;
-        const long long base = (long long)plane * a.ncell;
-        const float e0 = Cd::ld(ein, base + i, b, rho_i);
-        float div = 0.f;
-        for (int ax = 0; ax < a.dim; ++ax) {
-            const float nu = a.nu[plane * 3 + ax];
-            if (nu == 0.f) continue;
-            const int sg = nu > 0.f ? 1 : -1;
-            const float um2 = ext_value<Cd>(a, ein, b, k, d, base, i, c, ax, c[ax] - 2 * sg, nu);
-            const float um1 = ext_value<Cd>(a, ein, b, k, d, base, i, c, ax, c[ax] - sg, nu);
-            const float up1 = ext_value<Cd>(a, ein, b, k, d, base, i, c, ax, c[ax] + sg, nu);
-            const float fo = e0 + 0.5f * limit<LIM>(e0 - um1, up1 - e0);
-            const float fi = um1 + 0.5f * limit<LIM>(um1 - um2, e0 - um1);
-            div += fabsf(nu) * (fo - fi);
+    float rho_new = 0.f;
+    if (valid) {
+        cell_coords(a, i, c);
+        const T *ein = static_cast<const T *>(a.e_in);
+        T *eout = static_cast<T *>(a.e_out);
+        const float eq = b.ck * a.TL[i];
+        const float rho_i = rho_at<Cd>(a.R, a.invTs, i);
+        rho_new = rho_at<Cd>(a.TL, a.invTs, i);
+        const float src = a.Q ? b.srck * (a.amp * a.Q[i]) : 0.f;
+        nw = diffuse_walls_of(a, c, wl);
+        for (int d = grp; d < a.nd; d += ng) {
+            const int plane = k * a.nd + d;
+            const long long base = (long long)plane * a.ncell;
+            const float e0 = Cd::ld(ein, base + i, b, rho_i);
+            float div = 0.f;
+            for (int ax = 0; ax < a.dim; ++ax) {
+                const float nu = a.nu[plane * 3 + ax];
+                if (nu == 0.f) continue;
+                const int sg = nu > 0.f ? 1 : -1;
+                const float um2 = ext_value<Cd>(a, ein, b, k, d, base, i, c, ax, c[ax] - 2 * sg, nu);
+                const float um1 = ext_value<Cd>(a, ein, b, k, d, base, i, c, ax, c[ax] - sg, nu);
+                const float up1 = ext_value<Cd>(a, ein, b, k, d, base, i, c, ax, c[ax] + sg, nu);
+                const float fo = e0 + 0.5f * limit<LIM>(e0 - um1, up1 - e0);
+                const float fi = um1 + 0.5f * limit<LIM>(um1 - um2, e0 - um1);
+                div += fabsf(nu) * (fo - fi);
+            }
+            const float en = e0 - div + b.dtinv * (eq - e0) + src;
+            const float es = a.sr ? Cd::st_sr(eout, base + i, en, b, rho_new, mix32(plane_key(a.srkey, plane) ^ (uint32_t)i))
+                                  : Cd::st(eout, base + i, en, b, rho_new);
+            acc += a.wmom[plane] * es;
+            for (int j = 0; j < nw; ++j) wacc[j] += a.wdiff[wl[j] * a.nd + d] * es;
         }
-        const float en = e0 - div + b.dtinv * (eq - e0) + src;
-        const float es = a.sr ? Cd::st_sr(eout, base + i, en, b, rho_new, mix32(plane_key(a.srkey, plane) ^ (uint32_t)i))
-                              : Cd::st(eout, base + i, en, b, rho_new);
-        acc += a.wmom[plane] * es;
-        for (int j = 0; j < nw; ++j) wacc[j] += a.wdiff[wl[j] * a.nd + d] * es;
     }
+    if (ng > 1) {
+        // group partials, summed in group order by group 0
+        red[0][tid] = acc;
+        for (int j = 0; j < 3; ++j) red[1 + j][tid] = j < nw ? wacc[j] : 0.f;
+        __syncthreads();
+        if (grp == 0) {
+            for (int g = 1; g < ng; ++g) {
+                const int t = g * blockDim.x + threadIdx.x;
+                acc += red[0][t];
+                for (int j = 0; j < nw && j < 3; ++j) wacc[j] += red[1 + j][t];
+            }
+        }
+    }
+    if (!valid || grp != 0) return;
     a.P[(long long)k * a.ncell + i] = acc;
     for (int j = 0; j < nw; ++j) {
         const int w = wl[j];
@@ -186,12 +212,23 @@ cudaError_t launch_moment_only(const StepArgs &a, int storage, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Direction groups of the generic step: one while cells x bands give at least 4096 blocks of 256
+// threads' worth of work, else more (up to 32, no more than the directions), so that small grids
+// still spread over the GPU's SMs.
+static int generic_direction_groups(long long ncell, int nb, int nd) {
+    int ng = 1;
+    while (ng < 32 && 2 * ng <= nd && ncell * nb * ng < 4096LL * 256) ng *= 2;
+    return ng;
+}
+
 template <int S>
 static void step_generic_s(const StepArgs &a, int limiter, cudaStream_t s) {
-    const dim3 g = cell_grid(a.ncell, a.nb);
-    if (limiter == kLimFirst) k_step_generic<S, kLimFirst><<<g, 256, 0, s>>>(a);
-    else if (limiter == kLimMinmod) k_step_generic<S, kLimMinmod><<<g, 256, 0, s>>>(a);
-    else k_step_generic<S, kLimVanAlbada><<<g, 256, 0, s>>>(a);
+    const int ng = generic_direction_groups(a.ncell, a.nb, a.nd);
+    const dim3 blk(256 / ng, ng);
+    const dim3 g((unsigned)((a.ncell + blk.x - 1) / blk.x), (unsigned)a.nb);
+    if (limiter == kLimFirst) k_step_generic<S, kLimFirst><<<g, blk, 0, s>>>(a);
+    else if (limiter == kLimMinmod) k_step_generic<S, kLimMinmod><<<g, blk, 0, s>>>(a);
+    else k_step_generic<S, kLimVanAlbada><<<g, blk, 0, s>>>(a);
 }
 
 cudaError_t launch_step_generic(const StepArgs &a, int storage, int limiter, cudaStream_t s) {

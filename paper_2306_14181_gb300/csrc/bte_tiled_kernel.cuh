@@ -425,25 +425,14 @@ __device__ void producer(const StepArgs &a, const TiledArgs &p, char *smem, uint
     for (int j = 0; j < p.ns && ahead_ok; ++j) ahead_ok = ahead.next(a, p);  // the plane-tile ns later
     int s = 0;         // stage of plane-tile i = i mod ns
     uint32_t ph = 0u;  // its use count parity = (i / ns) mod 2
-    int issued = 0;    // plane-tiles whose copies were issued
-    for (int i = 0; more; ++i, more = cur.next(a, p)) {
+    // failure-detection test: a first wait on a barrier that nothing completes
+    if ((p.stall & 2) &&
+        !__all_sync(0xffffffffu, mbar_wait(reinterpret_cast<uint64_t *>(smem + kStallOff), 0u, p.err, 2, p.wait_ns)))
+        cta_abort(smem);
+    int i = 0;         // plane-tiles whose copies were issued
+    for (; more; ++i, more = cur.next(a, p)) {
+        if (i >= p.ns && !__all_sync(0xffffffffu, mbar_wait(&empty[s], ph ^ 1u, p.err, 2, p.wait_ns))) cta_abort(smem);
         if (cta_aborted(smem)) break;
-        // failure-detection test: a wait on a barrier that nothing completes gives up
-        if (i == 0 && (p.stall & 2) && !__all_sync(0xffffffffu, mbar_wait(reinterpret_cast<uint64_t *>(smem + kStallOff), 0u,
-                                                                        p.err, 2, p.wait_ns))) {
-            cta_abort(smem);
-            break;
-        }
-        if (i >= p.ns) {
-            // the consumers released the stage, and the copies of its previous use have landed
-            // (at once in a normal run: the consumers waited for them; after an abort they may not)
-            bool ok = mbar_wait(&empty[s], ph ^ 1u, p.err, 2, p.wait_ns);
-            ok = ok && mbar_wait(&full[s], ph ^ 1u, p.err, 2, kWaitLimitNs);
-            if (!__all_sync(0xffffffffu, ok)) {
-                cta_abort(smem);
-                break;
-            }
-        }
         fence_proxy_async();
         __syncwarp();
         const PT &q = cur.q;
@@ -519,7 +508,6 @@ __device__ void producer(const StepArgs &a, const TiledArgs &p, char *smem, uint
                 }
         }
         mbar_arrive(&full[s]);
-        issued = i + 1;
         // pull the rows of a later plane-tile towards L2 (no shared memory involved)
         if (ahead_ok) {
             const PT &qp = ahead.q;
@@ -538,8 +526,10 @@ __device__ void producer(const StepArgs &a, const TiledArgs &p, char *smem, uint
         }
     }
     // Before the CTA exits, every bulk copy it issued has landed: the last use of each stage
-    // (bounded; a copy that never lands leaves the error flag set).
-    for (int j = max(issued - p.ns, 0); j < issued; ++j) mbar_wait(&full[j % p.ns], (uint32_t)(j / p.ns) & 1u, p.err, 2, kWaitLimitNs);
+    // (bounded; a copy that never lands leaves the error flag set).  A stage is reused only after
+    // the empty wait, and that is followed by the abort check, so no copy is issued into a stage
+    // whose previous copies may still be in flight.
+    for (int j = max(i - p.ns, 0); j < i; ++j) mbar_wait(&full[j % p.ns], (uint32_t)(j / p.ns) & 1u, p.err, 2, kWaitLimitNs);
 }
 
 // ---- consumer warps -----------------------------------------------------------------------
@@ -942,6 +932,12 @@ __device__ void consumer(const StepArgs &a, const TiledArgs &p, char *smem, uint
     uint32_t ph = 0u;  // its use count parity = (i / ns) mod 2
     float wsum = 0.f;  // sum of w_d / tau_k over the segment's planes (16-bit storage)
     PT cur{};
+    // failure-detection test: a first wait on a barrier that nothing completes (the CTA then gives
+    // up at its first wait for data that does not come)
+    if ((p.stall & 1) &&
+        !__all_sync(0xffffffffu, mbar_wait(reinterpret_cast<uint64_t *>(smem + kStallOff), 0u, p.err, 1, p.wait_ns)) &&
+        lane == 0)
+        cta_abort(smem);
     Cursor<DIM, WPR> c;
     bool more = c.start(a, p);
     for (int i = 0; more; ++i, more = c.next(a, p)) {
@@ -980,19 +976,27 @@ __device__ void consumer(const StepArgs &a, const TiledArgs &p, char *smem, uint
                 }
             }
         }
-        // warp-uniform: no warp of the CTA has given up, and the stage's copies landed (a
-        // bounded wait unless the first try succeeds)
-        bool ok = !cta_aborted(smem);
-        if (ok && i == 0 && (p.stall & 1))  // failure-detection test: a wait that nothing completes
-            ok = __all_sync(0xffffffffu, mbar_wait(reinterpret_cast<uint64_t *>(smem + kStallOff), 0u, p.err, 1, p.wait_ns));
-        if (ok && !__all_sync(0xffffffffu, mbar_try_wait(&full[s], ph)))
-            ok = __all_sync(0xffffffffu, mbar_wait(&full[s], ph, p.err, 1, p.wait_ns));
-        if (!ok && lane == 0) cta_abort(smem);
-        const char *stage = smem + p.stage0 + (size_t)s * p.stage_bytes;
-        if constexpr (REF) {
-            if (ok) wsum += reinterpret_cast<const float *>(stage + p.hdr_off)[3];
+        // warp-uniform: the stage's copies landed, else a bounded wait unless a warp gave up
+        bool ok = __all_sync(0xffffffffu, mbar_try_wait(&full[s], ph));
+        if (!ok) {
+            ok = !cta_aborted(smem);
+            if (ok) ok = __all_sync(0xffffffffu, mbar_wait(&full[s], ph, p.err, 1, p.wait_ns));
         }
-        if (ok && zl < q.nzt && rb < q.nyt) {
+        if (!ok) {
+            // release the stage unread and walk on through the schedule
+            if (lane == 0) {
+                cta_abort(smem);
+                mbar_arrive(&empty[s]);
+            }
+            if (++s == p.ns) {
+                s = 0;
+                ph ^= 1u;
+            }
+            continue;
+        }
+        const char *stage = smem + p.stage0 + (size_t)s * p.stage_bytes;
+        if constexpr (REF) wsum += reinterpret_cast<const float *>(stage + p.hdr_off)[3];
+        if (zl < q.nzt && rb < q.nyt) {
             const float *hd = reinterpret_cast<const float *>(stage + p.hdr_off);
             const bool px = hd[0] > 0.f, py = hd[1] > 0.f;  // the signs rows_of_warp takes
             const bool full = rb + Geo<DIM, WPR>::KR <= q.nyt;
