@@ -280,13 +280,12 @@ static double step_element(const orc_problem *P, const double *e, const double *
 /* T_L^n and the diffuse-wall values are formed from e^n first.              */
 /* Q may be NULL (no source).                                                  */
 /* ------------------------------------------------------------------------- */
-void orc_step(const orc_problem *P, const double *e_in, double *e_out, const float *Q, double amp) {
+static void step_with(const orc_problem *P, const double *e_in, const double *ediff, double *e_out, const float *Q,
+                      double amp) {
     const long nc = ncell_of(P);
     const double W = total_weight(P), SC = sum_C(P);
     double *TL = (double *)malloc(sizeof(double) * nc);
-    double *ediff = (double *)calloc((size_t)6 * P->nb * nc, sizeof(double));
     orc_lattice_temperature(P, e_in, TL);
-    diffuse_wall_values(P, e_in, ediff);
     const long nplanes = (long)P->nb * P->nd;
     #pragma omp parallel for schedule(static)
     for (long pl = 0; pl < nplanes; ++pl) {
@@ -299,6 +298,12 @@ void orc_step(const orc_problem *P, const double *e_in, double *e_out, const flo
                 }
     }
     free(TL);
+}
+
+void orc_step(const orc_problem *P, const double *e_in, double *e_out, const float *Q, double amp) {
+    double *ediff = (double *)calloc((size_t)6 * P->nb * ncell_of(P), sizeof(double));
+    diffuse_wall_values(P, e_in, ediff);
+    step_with(P, e_in, ediff, e_out, Q, amp);
     free(ediff);
 }
 
@@ -347,7 +352,8 @@ void orc_step_points(const orc_problem *P, const double *e_in, const float *Q, d
 /* with e_face the wall-face value the step uses.  For one step,              */
 /*   E^{n+1} - E^n = dt ( V amp sum_i Q_i - sum_walls F_wall^n ).             */
 /* ------------------------------------------------------------------------- */
-void orc_energy(const orc_problem *P, const double *e, double *E_total, double *wall_flux) {
+static void energy_with(const orc_problem *P, const double *e, const double *ediff, double *E_total,
+                        double *wall_flux) {
     const long nc = ncell_of(P);
     const double V = cell_volume(P);
     double E = 0.0;
@@ -355,8 +361,6 @@ void orc_energy(const orc_problem *P, const double *e, double *E_total, double *
         for (int d = 0; d < P->nd; ++d)
             for (long i = 0; i < nc; ++i) E += P->w[d] * e[EIDX(P, k, d, i)];
     *E_total = V * E;
-    double *ediff = (double *)calloc((size_t)6 * P->nb * nc, sizeof(double));
-    diffuse_wall_values(P, e, ediff);
     for (int wall = 0; wall < 6; ++wall) wall_flux[wall] = 0.0;
     for (int a = 0; a < P->dim; ++a) {
         const double S = V / length_of(P, a);
@@ -382,7 +386,97 @@ void orc_energy(const orc_problem *P, const double *e, double *E_total, double *
             wall_flux[wall] = S * F;
         }
     }
+}
+
+void orc_energy(const orc_problem *P, const double *e, double *E_total, double *wall_flux) {
+    double *ediff = (double *)calloc((size_t)6 * P->nb * ncell_of(P), sizeof(double));
+    diffuse_wall_values(P, e, ediff);
+    energy_with(P, e, ediff, E_total, wall_flux);
     free(ediff);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Interface between two materials, Sec. 2.2 (v): wall wa of problem A (the   */
+/* material-A side) faces wall wb of problem B, both declared DIFFUSE, with   */
+/* the same axis, opposite sides and the same cells along the other two axes. */
+/* A phonon of band k reaching the interface from A is transmitted into B     */
+/* with probability bAB[k] and diffusely reflected otherwise; from B,         */
+/* bBA[k].  The incoming value at each interface cell is therefore            */
+/*   e_in,A = bBA S_B + (1 - bAB) S_A,   e_in,B = bAB S_A + (1 - bBA) S_B,     */
+/* with S_X the diffuse value of side X's outgoing directions at its cell     */
+/* (the integral of e |s.n| over the directions reaching the interface over   */
+/* the integral of |s.n| over the other half, Eq. (diff_bound)'s discrete     */
+/* normaliser: the 1/pi of the paper's formula).  Transmitted energy is taken */
+/* with |s.n|; the paper's integral over B's directions carries s.n < 0.      */
+/* ediffA, ediffB: [6][nb][ncell] of each problem, filled at every DIFFUSE    */
+/* wall (plain diffuse values) and then mixed at the interface cells.         */
+/* ------------------------------------------------------------------------- */
+static int interface_ok(const orc_problem *A, int wa, const orc_problem *B, int wb) {
+    if (A->dim != B->dim || A->nb != B->nb || wa < 0 || wb < 0 || wa >= 2 * A->dim || wb >= 2 * B->dim) return 0;
+    if ((wa >> 1) != (wb >> 1) || (wa & 1) == (wb & 1)) return 0;
+    if (A->bc[wa] != ORC_BC_DIFFUSE || B->bc[wb] != ORC_BC_DIFFUSE) return 0;
+    for (int a = 0; a < 3; ++a)
+        if (a != (wa >> 1) && extent(A, a) != extent(B, a)) return 0;
+    return 1;
+}
+
+int orc_interface_values(const orc_problem *A, const double *eA, int wa, const orc_problem *B, const double *eB, int wb,
+                         const double *bAB, const double *bBA, double *ediffA, double *ediffB) {
+    if (!interface_ok(A, wa, B, wb)) return 1;
+    const long ncA = ncell_of(A), ncB = ncell_of(B);
+    diffuse_wall_values(A, eA, ediffA);
+    diffuse_wall_values(B, eB, ediffB);
+    const int a = wa >> 1;
+    const int posA = (wa & 1) ? extent(A, a) - 1 : 0, posB = (wb & 1) ? extent(B, a) - 1 : 0;
+    for (int z = 0; z < A->nz; ++z)
+        for (int y = 0; y < A->ny; ++y)
+            for (int x = 0; x < A->nx; ++x) {
+                int c[3] = {x, y, z};
+                if (c[a] != posA) continue;
+                const long iA = cidx(A, c);
+                c[a] = posB;
+                const long iB = cidx(B, c);
+                for (int k = 0; k < A->nb; ++k) {
+                    double *pa = &ediffA[((long)wa * A->nb + k) * ncA + iA];
+                    double *pb = &ediffB[((long)wb * B->nb + k) * ncB + iB];
+                    const double SA = *pa, SB = *pb;
+                    *pa = bBA[k] * SB + (1.0 - bAB[k]) * SA;
+                    *pb = bAB[k] * SA + (1.0 - bBA[k]) * SB;
+                }
+            }
+    return 0;
+}
+
+/* One step of both materials (Algorithm 2 for each, with the interface values above). */
+int orc_interface_step(const orc_problem *A, const double *eA, double *eA_out, const float *QA, double ampA, int wa,
+                       const orc_problem *B, const double *eB, double *eB_out, const float *QB, double ampB, int wb,
+                       const double *bAB, const double *bBA) {
+    double *ediffA = (double *)calloc((size_t)6 * A->nb * ncell_of(A), sizeof(double));
+    double *ediffB = (double *)calloc((size_t)6 * B->nb * ncell_of(B), sizeof(double));
+    const int rc = orc_interface_values(A, eA, wa, B, eB, wb, bAB, bBA, ediffA, ediffB);
+    if (rc == 0) {
+        step_with(A, eA, ediffA, eA_out, QA, ampA);
+        step_with(B, eB, ediffB, eB_out, QB, ampB);
+    }
+    free(ediffA);
+    free(ediffB);
+    return rc;
+}
+
+/* Energy and wall heat flows of both materials; the flows through wa and wb are the */
+/* interface heat flows (outward from each side).                                    */
+int orc_interface_energy(const orc_problem *A, const double *eA, int wa, const orc_problem *B, const double *eB, int wb,
+                         const double *bAB, const double *bBA, double *EA, double *fluxA, double *EB, double *fluxB) {
+    double *ediffA = (double *)calloc((size_t)6 * A->nb * ncell_of(A), sizeof(double));
+    double *ediffB = (double *)calloc((size_t)6 * B->nb * ncell_of(B), sizeof(double));
+    const int rc = orc_interface_values(A, eA, wa, B, eB, wb, bAB, bBA, ediffA, ediffB);
+    if (rc == 0) {
+        energy_with(A, eA, ediffA, EA, fluxA);
+        energy_with(B, eB, ediffB, EB, fluxB);
+    }
+    free(ediffA);
+    free(ediffB);
+    return rc;
 }
 
 /* ========================================================================= */

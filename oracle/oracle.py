@@ -71,6 +71,11 @@ def load_oracle():
             _lib.orc_adjoint_step.argtypes = [pp, dp, dp, dp]
             _lib.orc_adjoint.argtypes = [pp, dp, fp, dp, ct.c_int, ct.c_long, ct.c_int, dp, dp, dp, dp, ct.c_int]
             _lib.orc_adjoint.restype = ct.c_int
+            for f in (_lib.orc_interface_step, _lib.orc_interface_energy):
+                f.restype = ct.c_int
+            _lib.orc_interface_step.argtypes = [pp, dp, dp, fp, ct.c_double, ct.c_int, pp, dp, dp, fp, ct.c_double,
+                                                ct.c_int, dp, dp]
+            _lib.orc_interface_energy.argtypes = [pp, dp, ct.c_int, pp, dp, ct.c_int, dp, dp, dp, dp, dp, dp]
         return _lib
 
 
@@ -256,3 +261,48 @@ class Problem:
     def cell_volume(self):
         L = [self.dx, self.dy, self.dz]
         return float(np.prod([L[a] if a < self.dim else 1.0 for a in range(3)]))
+
+
+# -- interface between two materials (Sec. 2.2 (v)) -----------------------------------------
+def _betas(b, nb):
+    b = np.ascontiguousarray(np.broadcast_to(np.asarray(b, dtype=np.float64), (nb,)))
+    assert np.all((b >= 0.0) & (b <= 1.0))
+    return b
+
+
+def interface_step(A, eA, wa, B, eB, wb, bAB, bBA, QA=None, QB=None, ampA=1.0, ampB=1.0):
+    """One step of both materials of a diffuse-mismatch interface: wall ``wa`` of problem A
+    faces wall ``wb`` of problem B (both DIFFUSE, same axis, opposite sides, same cells across);
+    a band-k phonon crossing from A into B is transmitted with probability ``bAB[k]``, from B
+    into A with ``bBA[k]``, and diffusely reflected otherwise.  Returns (eA', eB')."""
+    eA = np.ascontiguousarray(eA, dtype=np.float64)
+    eB = np.ascontiguousarray(eB, dtype=np.float64)
+    oA, oB = np.empty_like(eA), np.empty_like(eB)
+    bAB, bBA = _betas(bAB, A.nb), _betas(bBA, A.nb)
+    rc = A._lib.orc_interface_step(ct.byref(A._p), _dp(eA), _dp(oA), _fp(A._src(QA)), float(ampA), int(wa),
+                                   ct.byref(B._p), _dp(eB), _dp(oB), _fp(B._src(QB)), float(ampB), int(wb),
+                                   _dp(bAB), _dp(bBA))
+    if rc != 0:
+        raise ValueError("walls do not form an interface")
+    return oA, oB
+
+
+def interface_run(A, eA, wa, B, eB, wb, bAB, bBA, nsteps, QA=None, QB=None):
+    """nsteps interface steps from (eA, eB); returns the final pair."""
+    for _ in range(nsteps):
+        eA, eB = interface_step(A, eA, wa, B, eB, wb, bAB, bBA, QA, QB)
+    return eA, eB
+
+
+def interface_energy(A, eA, wa, B, eB, wb, bAB, bBA):
+    """(E_A, flows_A[6], E_B, flows_B[6]): each side's energy and outward wall heat flows, the
+    interface walls' flows being the heat crossing the interface."""
+    eA = np.ascontiguousarray(eA, dtype=np.float64)
+    eB = np.ascontiguousarray(eB, dtype=np.float64)
+    bAB, bBA = _betas(bAB, A.nb), _betas(bBA, A.nb)
+    EA, EB, FA, FB = np.zeros(1), np.zeros(1), np.zeros(6), np.zeros(6)
+    rc = A._lib.orc_interface_energy(ct.byref(A._p), _dp(eA), int(wa), ct.byref(B._p), _dp(eB), int(wb), _dp(bAB),
+                                     _dp(bBA), _dp(EA), _dp(FA), _dp(EB), _dp(FB))
+    if rc != 0:
+        raise ValueError("walls do not form an interface")
+    return float(EA[0]), FA, float(EB[0]), FB
