@@ -546,6 +546,56 @@ def ttg_record(args, xi):
     return rec
 
 
+def interface_record(args, peak, peak_kind):
+    """f3: the two-material interface pair (both sides' forward steps and the interface kernel
+    each step), timed with CUDA events over 100 coupled steps after 3 warm-up ones; the
+    roofline counts both sides' algorithmic bytes over the pair step."""
+    import gc
+    import torch
+    from paper_2306_14181_gb300 import bte, inputs
+    cfg = inputs.interface_2d()
+    stream = torch.cuda.current_stream()
+    ctxs = []
+    for side, w in (("A", cfg["wall_a"]), ("B", cfg["wall_b"])):
+        c = dict(cfg[side])
+        c["bc"] = [bte.BTE_BC_INTERFACE if j == w else b for j, b in enumerate(c["bc"])]
+        ctxs.append(bte.bte_from_workload(c, limiter=args.limiter, stream=stream.cuda_stream))
+    A, B = ctxs
+    Q = inputs.source_field(cfg["A"])
+    bte.bte_set_source(A, torch.from_numpy(Q.reshape(-1)).cuda())
+    bte.bte_interface(A, cfg["wall_a"], B, cfg["wall_b"], cfg["beta_ab"], cfg["beta_ba"])
+    bte.bte_step_pair(A, B, 3)
+    steps = 100
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    bte.bte_step_pair(A, B, steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    bte.bte_synchronize(A)
+    bte.bte_synchronize(B)
+    t_ms = ev0.elapsed_time(ev1)
+    n = A.info.nelem + B.info.nelem
+    bytes_step = n * 2 * A.info.elem_bytes
+    achieved = bytes_step / (t_ms / steps / 1e3) / 1e9
+    _, FA = bte.bte_energy(A)
+    _, FB = bte.bte_energy(B)
+    rec = {"workload": cfg["name"], "storage": "f32", "kernel": kernel_name_of(A.info), "steps": steps, "warmup": 3,
+           "ms_per_step": t_ms / steps, "value": n * steps / (t_ms / 1e3), "unit": UNIT, "updates_per_step": n,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "kernel": "pair step (two forward steps, two finalizes, the interface kernel)",
+                        "peak_source": peak_kind, "bytes_per_step": bytes_step},
+           "interface_flow_w_per_m": [FA[cfg["wall_a"]], FB[cfg["wall_b"]]],
+           "launches_per_step": A.info.launches_per_step + B.info.launches_per_step + 1}
+    bte.bte_destroy(B)
+    bte.bte_destroy(A)
+    del A, B, ctxs
+    gc.collect()
+    torch.cuda.empty_cache()
+    return rec
+
+
 def run_gb300(args):
     import gc
     import numpy as np
@@ -622,6 +672,7 @@ def run_gb300(args):
                 continue
             subs.append(sub_record(args, name, st, ts, steps, nadj, kck, peak, peak_kind, kern))
         subs.append(steady_record(args))
+        subs.append(interface_record(args, peak, peak_kind))
         for xi in (0.1, 1.0, 10.0):
             subs.append(ttg_record(args, xi))
         line["sub_records"] = subs

@@ -65,7 +65,9 @@ enum {
     BTE_BC_ISOTHERMAL = 0, /* thermalizing wall, Eq. (thermal): emits C_k T_wall / W */
     BTE_BC_DIFFUSE = 1,    /* diffusely reflecting wall, Eq. (diff_bound) */
     BTE_BC_SPECULAR = 2,   /* specularly reflecting wall, Sec. 2.2 (ii) */
-    BTE_BC_PERIODIC = 3    /* periodic pair, Eq. (periodic); both walls of the axis */
+    BTE_BC_PERIODIC = 3,   /* periodic pair, Eq. (periodic); both walls of the axis */
+    BTE_BC_INTERFACE = 4   /* one side of an interface between two materials, Sec. 2.2 (v): the
+                              wall faces a wall of another context (see bte_interface) */
 };
 
 /* Storage of e in device memory.  All arithmetic is FP32 in every mode. */
@@ -332,6 +334,37 @@ bte_status bte_synchronize(bte_ctx *ctx);
  * the producer warp (3: both); that wait gives up after limit_ns and the launch ends as above.
  * It applies to one launch only and is then cleared.  BTE_EINVAL for stall_test outside 0..3. */
 bte_status bte_set_wait_limit(bte_ctx *ctx, long long limit_ns, int stall_test);
+
+/* Interface between two materials (Sec. 2.2 (v), diffuse mismatch).  Wall wall_a of ctx_a (the
+ * material-A side) and wall wall_b of ctx_b (material B) must both have been created as
+ * BTE_BC_INTERFACE, on the same axis and opposite sides (A's +x against B's -x, say), with the
+ * same cell counts along the other two axes (wall cells correspond one to one, same coordinates
+ * across) and the same number of bands.  beta_ab[k] (host, nbands doubles in [0, 1]) is the
+ * probability that a band-k phonon reaching the interface from A is transmitted into B,
+ * beta_ba[k] the same from B into A; the rest is reflected diffusely.  At every interface cell
+ * the incoming value of band k (every direction entering the material) is
+ *   A: beta_ba S_B + (1 - beta_ab) S_A,     B: beta_ab S_A + (1 - beta_ba) S_B,
+ * S_X being what a diffuse wall (Eq. diff_bound) would return on side X: the sum of w_d |s_d.n| e
+ * over X's directions reaching the interface over the sum of w_d |s_d.n| over the others.  A
+ * uniform temperature is stationary when beta_ba C_B = beta_ab C_A band by band (detailed
+ * balance); with equal group speeds the heat that leaves one side enters the other.
+ * Both contexts need FP32 storage (their interface walls are refused at bte_create otherwise), a
+ * context has at most one interface wall, and ctx_a != ctx_b.  The pair then advances only
+ * through bte_step_pair: bte_step, bte_residuals, bte_run_steady and bte_adjoint on either
+ * context return BTE_ESTATE.  bte_init_temperature and bte_set_state of either context keep the
+ * coupling (the interface values are formed again from both current states).  bte_energy's flow
+ * through the interface wall is the heat crossing the interface, outward from that side.  The
+ * coupling holds until either context is destroyed; a context that is destroyed leaves its
+ * partner uncoupled (its interface wall then behaves as a diffuse wall of Eq. diff_bound).
+ * Stream ordered with respect to both contexts' streams.  BTE_EINVAL on any mismatch. */
+bte_status bte_interface(bte_ctx *ctx_a, int wall_a, bte_ctx *ctx_b, int wall_b, const double *beta_ab,
+                         const double *beta_ba);
+
+/* Advance both contexts of an interface n >= 0 steps together: per step, one forward step of
+ * each (as bte_step, on each context's own stream), then one short kernel that forms both
+ * sides' interface values of the new states.  BTE_ESTATE unless ctx_a and ctx_b are coupled
+ * with each other.  Non-blocking. */
+bte_status bte_step_pair(bte_ctx *ctx_a, bte_ctx *ctx_b, int n);
 
 /* Kernel tracing with CUDA events on the context's stream.  bte_profile(ctx, 1) clears the
  * counters and starts recording an event pair around every forward-step launch and every

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libbte_gb300.so")
 
 BTE_OK, BTE_EINVAL, BTE_ENOMEM, BTE_ECUDA, BTE_ESTATE, BTE_ENONFINITE, BTE_ETIMEOUT, BTE_EUNSUPPORTED = range(8)
 BTE_QUAD_GL1D_POLAR, BTE_QUAD_OCTANT, BTE_QUAD_EXPLICIT = 0, 1, 2
-BTE_BC_ISOTHERMAL, BTE_BC_DIFFUSE, BTE_BC_SPECULAR, BTE_BC_PERIODIC = 0, 1, 2, 3
+BTE_BC_ISOTHERMAL, BTE_BC_DIFFUSE, BTE_BC_SPECULAR, BTE_BC_PERIODIC, BTE_BC_INTERFACE = 0, 1, 2, 3, 4
 BTE_STORE_F32, BTE_STORE_F16, BTE_STORE_BF16 = 0, 1, 2
 BTE_LIM_FIRST_ORDER, BTE_LIM_MINMOD, BTE_LIM_VANALBADA = 0, 1, 2
 BTE_ROUND_NEAREST, BTE_ROUND_STOCHASTIC = 0, 1
@@ -28,7 +28,7 @@ EXPORTS = ["bte_create", "bte_destroy", "bte_last_error", "bte_init_temperature"
            "bte_lattice_temperature", "bte_moments", "bte_energy", "bte_get_state", "bte_set_state",
            "bte_get_values", "bte_adjoint", "bte_adjoint_profile_read",
            "bte_get_info", "bte_get_quadrature", "bte_synchronize", "bte_profile", "bte_profile_read", "bte_energy_noalloc",
-           "bte_set_wait_limit", "bte_residuals", "bte_run_steady"]
+           "bte_set_wait_limit", "bte_residuals", "bte_run_steady", "bte_interface", "bte_step_pair"]
 
 _STATUS = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESTATE", 5: "ENONFINITE", 6: "ETIMEOUT", 7: "EUNSUPPORTED"}
 
@@ -109,6 +109,8 @@ def load():
     lib.bte_residuals.argtypes = [P, ct.c_int, dp, dp]
     lib.bte_run_steady.argtypes = [P, ct.c_longlong, ct.c_int, ct.c_double, ct.c_double,
                                    ct.POINTER(ct.c_longlong), dp, dp]
+    lib.bte_interface.argtypes = [P, ct.c_int, P, ct.c_int, dp, dp]
+    lib.bte_step_pair.argtypes = [P, P, ct.c_int]
     lib.bte_profile.argtypes = [P, ct.c_int]
     lib.bte_profile_read.argtypes = [P, dp, ct.POINTER(ct.c_longlong), dp, ct.POINTER(ct.c_longlong)]
     for name in EXPORTS:
@@ -236,6 +238,21 @@ def bte_set_source(ctx, Q, amp=None):
 
 def bte_step(ctx, n=1):
     _check(load().bte_step(ctx.handle, int(n)), ctx.handle)
+
+
+def bte_interface(ctx_a, wall_a, ctx_b, wall_b, beta_ab, beta_ba):
+    """Couple wall wall_a of ctx_a (material A) with wall wall_b of ctx_b (material B) as a
+    diffuse-mismatch interface; beta_ab[k] / beta_ba[k] are the band transmissions A->B / B->A
+    (scalars are broadcast over the bands)."""
+    nb = ctx_a.info.nbands
+    bab = np.ascontiguousarray(np.broadcast_to(np.asarray(beta_ab, dtype=np.float64), (nb,)))
+    bba = np.ascontiguousarray(np.broadcast_to(np.asarray(beta_ba, dtype=np.float64), (nb,)))
+    _check(load().bte_interface(ctx_a.handle, int(wall_a), ctx_b.handle, int(wall_b), _dp(bab), _dp(bba)),
+           ctx_a.handle)
+
+
+def bte_step_pair(ctx_a, ctx_b, n=1):
+    _check(load().bte_step_pair(ctx_a.handle, ctx_b.handle, int(n)), ctx_a.handle)
 
 
 def bte_synchronize(ctx):

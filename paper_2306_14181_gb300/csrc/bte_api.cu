@@ -86,6 +86,16 @@ struct bte_ctx {
     float *wf = nullptr;
     double adj_ms = 0, adj_recompute_ms = 0;
     long long adj_steps = 0, adj_recompute_steps = 0;
+    // interface between two materials (Sec. 2.2 (v)): the wall created as BTE_BC_INTERFACE (-1:
+    // none; the kernels treat it as diffuse), the coupled context, this side's plain diffuse
+    // values at that wall [nb][wall cells] once mixed, and (side A only) the transmissions
+    int iwall = -1;
+    bte_ctx *peer = nullptr;
+    bool iface_a = false;
+    bool iface_pure = true;  // e_diff at iwall holds plain diffuse values (not the mixed ones)
+    float *ipure = nullptr;
+    float *ibeta = nullptr;  // [4][nb]: beta_ab, 1 - beta_ab, beta_ba, 1 - beta_ba
+    cudaEvent_t iev = nullptr;
     // tracing: event triples (before forward, after forward, after finalize) per step
     bool prof = false;
     std::vector<cudaEvent_t> ev;
@@ -292,6 +302,8 @@ static double amplitude_at(const bte_ctx *c, long long n) {
 }
 
 // T_L and the diffuse-wall values of the current state (after a fill or an upload).
+static bte_status iface_mix(bte_ctx *c);
+
 static bte_status refresh_moments(bte_ctx *c) {
     StepArgs a = make_args(c);
     a.e_in = c->e[c->cur];
@@ -299,10 +311,35 @@ static bte_status refresh_moments(bte_ctx *c) {
     CU(c, launch_moment_only(a, c->storage, c->stream));
     c->ecur ^= 1;
     CU(c, launch_finalize(a, c->nb, c->TL, c->stream));
+    c->iface_pure = true;
+    if (c->peer) TRY(iface_mix(c));
+    return BTE_OK;
+}
+
+// Interface values of a coupled pair from both sides' current states (Sec. 2.2 (v)).  The mix
+// runs on side B's stream after the work queued on side A's, and side A's stream waits for it.
+static bte_status iface_mix(bte_ctx *c) {
+    bte_ctx *A = c->iface_a ? c : c->peer, *B = c->iface_a ? c->peer : c;
+    const int ax = A->iwall >> 1;
+    const int ncw = (int)(A->ncell / A->n[ax]);
+    CU(A, cudaEventRecord(A->iev, A->stream));
+    CU(B, cudaStreamWaitEvent(B->stream, A->iev, 0));
+    float *eA = static_cast<float *>(A->ediff[A->ecur]) + (size_t)A->iwall * A->nb * A->wc_max;
+    float *eB = static_cast<float *>(B->ediff[B->ecur]) + (size_t)B->iwall * B->nb * B->wc_max;
+    CU(B, launch_iface_mix(eA, A->ipure, A->iface_pure, A->wc_max, eB, B->ipure, B->iface_pure, B->wc_max, A->ibeta,
+                           A->nb, ncw, B->stream));
+    CU(B, cudaEventRecord(B->iev, B->stream));
+    CU(A, cudaStreamWaitEvent(A->stream, B->iev, 0));
+    A->iface_pure = B->iface_pure = false;
     return BTE_OK;
 }
 
 static void free_all(bte_ctx *c) {
+    if (c->iev) cudaEventDestroy(c->iev);
+    c->iev = nullptr;
+    cudaFree(c->ipure);
+    cudaFree(c->ibeta);
+    c->ipure = c->ibeta = nullptr;
     void *ptrs[] = {c->d_amp, c->wf, c->e[0], c->e[1], c->TL, c->R, c->Q, c->P, c->ediff[0], c->ediff[1], c->nu, c->wmom, c->wdiff,
                     c->iso, c->jmp, c->mirror_d, c->band, c->d_w, c->d_s, c->d_v, c->d_invtau, c->dg, c->dflag,
                     c->rs};
@@ -376,9 +413,16 @@ extern "C" bte_status bte_create(const bte_grid *grid, const bte_bands *bands, c
     // walls
     for (int wl = 0; wl < 6; ++wl) {
         const int t = walls->type[wl];
-        if (t < BTE_BC_ISOTHERMAL || t > BTE_BC_PERIODIC) return fail(nullptr, BTE_EINVAL, "wall %d: bad type %d", wl, t);
+        if (t < BTE_BC_ISOTHERMAL || t > BTE_BC_INTERFACE) return fail(nullptr, BTE_EINVAL, "wall %d: bad type %d", wl, t);
         if (!std::isfinite(walls->T_wall[wl])) return fail(nullptr, BTE_EINVAL, "wall %d: non-finite T_wall", wl);
         c->bc[wl] = t;
+        if (t == BTE_BC_INTERFACE) {
+            // the kernels see a diffuse wall; bte_interface supplies its incoming values
+            if (c->iwall >= 0) return fail(nullptr, BTE_EINVAL, "at most one interface wall a context");
+            if ((wl >> 1) >= c->dim) return fail(nullptr, BTE_EINVAL, "wall %d: interface on an inactive axis", wl);
+            c->iwall = wl;
+            c->bc[wl] = BTE_BC_DIFFUSE;
+        }
         c->Tw[wl] = walls->T_wall[wl];
     }
     for (int a = 0; a < 3; ++a) {
@@ -409,6 +453,8 @@ extern "C" bte_status bte_create(const bte_grid *grid, const bte_bands *bands, c
     if (opts->kernel < BTE_KERNEL_AUTO || opts->kernel > BTE_KERNEL_PERSISTENT) return fail(nullptr, BTE_EINVAL, "bad kernel");
     if (opts->rounding != BTE_ROUND_NEAREST && opts->rounding != BTE_ROUND_STOCHASTIC)
         return fail(nullptr, BTE_EINVAL, "bad rounding");
+    if (c->iwall >= 0 && opts->storage != BTE_STORE_F32)
+        return fail(nullptr, BTE_EUNSUPPORTED, "interface walls need FP32 storage");
     c->dt = opts->dt;
     c->storage = opts->storage;
     c->limiter = opts->limiter;
@@ -458,10 +504,11 @@ extern "C" bte_status bte_create(const bte_grid *grid, const bte_bands *bands, c
             cudaGetLastError();
             optin = 0;
         }
-        const bool fits = c->dim == 1 && c->storage == BTE_STORE_F32 && ps <= (size_t)optin && !c->has_jump;
+        const bool fits = c->dim == 1 && c->storage == BTE_STORE_F32 && ps <= (size_t)optin && !c->has_jump &&
+                          c->iwall < 0;
         if (c->kernel == BTE_KERNEL_PERSISTENT && !fits) {
-            c->err = "persistent kernel unavailable: it needs a 1-D FP32 state that fits in shared memory and no "
-                     "periodic temperature jump";
+            c->err = "persistent kernel unavailable: it needs a 1-D FP32 state that fits in shared memory, no "
+                     "periodic temperature jump and no interface wall";
             return bail(BTE_EUNSUPPORTED);
         }
         c->persist = fits && (c->kernel == BTE_KERNEL_AUTO || c->kernel == BTE_KERNEL_PERSISTENT);
@@ -601,6 +648,13 @@ extern "C" void bte_destroy(bte_ctx *ctx) {
     if (!ctx) return;
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
+    if (bte_ctx *p = ctx->peer) {
+        // the partner keeps a plain diffuse wall: its diffuse values of the current state again
+        if (p->stream) cudaStreamSynchronize(p->stream);
+        p->peer = nullptr;
+        ctx->peer = nullptr;
+        refresh_moments(p);
+    }
     free_all(ctx);
     delete ctx;
 }
@@ -706,11 +760,69 @@ static bte_status step_persistent(bte_ctx *c, int nsteps) {
     return BTE_OK;
 }
 
+static bte_status step_one(bte_ctx *c);
+
 extern "C" bte_status bte_step(bte_ctx *c, int nsteps) {
     if (!c) return fail(nullptr, BTE_EINVAL, "ctx is NULL");
     if (nsteps < 0) return fail(c, BTE_EINVAL, "n must be >= 0");
+    if (c->peer) return fail(c, BTE_ESTATE, "the context is coupled at an interface: it steps through bte_step_pair");
     if (c->persist) return nsteps > 0 ? step_persistent(c, nsteps) : BTE_OK;
+    for (int s = 0; s < nsteps; ++s) TRY(step_one(c));
+    return BTE_OK;
+}
+
+extern "C" bte_status bte_step_pair(bte_ctx *a, bte_ctx *b, int nsteps) {
+    if (!a || !b) return fail(a ? a : b, BTE_EINVAL, "ctx is NULL");
+    if (nsteps < 0) return fail(a, BTE_EINVAL, "n must be >= 0");
+    if (a->peer != b || b->peer != a) return fail(a, BTE_ESTATE, "the two contexts are not coupled with each other");
     for (int s = 0; s < nsteps; ++s) {
+        TRY(step_one(a));
+        TRY(step_one(b));
+        a->iface_pure = b->iface_pure = true;
+        TRY(iface_mix(a));
+    }
+    return BTE_OK;
+}
+
+extern "C" bte_status bte_interface(bte_ctx *a, int wa, bte_ctx *b, int wb, const double *bab, const double *bba) {
+    if (!a || !b) return fail(a ? a : b, BTE_EINVAL, "ctx is NULL");
+    if (a == b) return fail(a, BTE_EINVAL, "an interface couples two contexts");
+    if (!bab || !bba) return fail(a, BTE_EINVAL, "beta arrays are NULL");
+    if (a->peer || b->peer) return fail(a, BTE_EINVAL, "a context is already coupled");
+    if (wa < 0 || wa > 5 || wb < 0 || wb > 5 || a->iwall != wa || b->iwall != wb)
+        return fail(a, BTE_EINVAL, "walls %d and %d are not the contexts' interface walls", wa, wb);
+    if (a->dim != b->dim || a->nb != b->nb) return fail(a, BTE_EINVAL, "dimension or band count differ");
+    const int ax = wa >> 1;
+    if ((wb >> 1) != ax || (wa & 1) == (wb & 1))
+        return fail(a, BTE_EINVAL, "the walls must lie on the same axis and on opposite sides");
+    for (int x = 0; x < 3; ++x)
+        if (x != ax && a->n[x] != b->n[x]) return fail(a, BTE_EINVAL, "cell counts across the interface differ (axis %d)", x);
+    std::vector<float> beta(4 * (size_t)a->nb);
+    for (int k = 0; k < a->nb; ++k) {
+        if (!(bab[k] >= 0.0 && bab[k] <= 1.0) || !(bba[k] >= 0.0 && bba[k] <= 1.0))
+            return fail(a, BTE_EINVAL, "band %d: transmissions must lie in [0, 1]", k);
+        beta[k] = (float)bab[k];
+        beta[a->nb + k] = (float)(1.0 - bab[k]);
+        beta[2 * a->nb + k] = (float)bba[k];
+        beta[3 * a->nb + k] = (float)(1.0 - bba[k]);
+    }
+    const size_t ncw = (size_t)(a->ncell / a->n[ax]);
+    for (bte_ctx *c : {a, b}) {
+        if (!c->ipure) TRY(dalloc(c, &c->ipure, (size_t)c->nb * ncw));
+        if (!c->iev) CU(c, cudaEventCreateWithFlags(&c->iev, cudaEventDisableTiming));
+    }
+    if (!a->ibeta) TRY(dalloc(a, &a->ibeta, beta.size()));
+    TRY(upload(a, a->ibeta, beta.data(), beta.size()));
+    CU(a, cudaStreamSynchronize(a->stream));
+    a->peer = b;
+    b->peer = a;
+    a->iface_a = true;
+    b->iface_a = false;
+    return iface_mix(a);
+}
+
+static bte_status step_one(bte_ctx *c) {
+    {
         StepArgs a = make_args(c);
         a.amp = (float)amplitude_at(c, c->step);
         if (c->rounding == BTE_ROUND_STOCHASTIC && c->storage != BTE_STORE_F32) {
@@ -1114,6 +1226,7 @@ extern "C" bte_status bte_adjoint(bte_ctx *c, int nsteps, int ckpt_every, const 
     if (!probe) return fail(c, BTE_EINVAL, "probe is NULL");
     if (nsteps < 0) return fail(c, BTE_EINVAL, "nsteps must be >= 0");
     if (ckpt_every < 0) return fail(c, BTE_EINVAL, "ckpt_every must be >= 0");
+    if (c->peer) return fail(c, BTE_ESTATE, "the context is coupled at an interface (no adjoint of the pair)");
     for (long long i = 0; i < c->ncell; ++i)
         if (!std::isfinite(probe[i])) return fail(c, BTE_EINVAL, "probe holds a non-finite value at cell %lld", i);
     const long long nc = c->ncell, nel = c->nelem;

@@ -107,6 +107,14 @@ constexpr int kResidBlocks = 512;
 cudaError_t launch_resid_keep(const double *T, const double *q, long long n, double *Tp, double *qp, cudaStream_t s);
 cudaError_t launch_residuals(const double *T, const double *q, const double *Tp, const double *qp, long long n,
                              double Tref, double *scratch, double *out4, cudaStream_t s);
+// Interface between two materials (Sec. 2.2 (v)): for every band k and interface cell j, with
+// S_A, S_B the two sides' plain diffuse values (from eA / eB where pure_a / pure_b, else from the
+// copies pa / pb an earlier call kept), writes S_A, S_B to pa, pb and the incoming values
+// eA = beta_ba S_B + (1 - beta_ab) S_A, eB = beta_ab S_A + (1 - beta_ba) S_B.  eA, eB: the
+// interface wall's rows of each side's e_diff (band stride sa / sb); pa, pb: [nb][ncw];
+// beta: [4][nb] = beta_ab, 1 - beta_ab, beta_ba, 1 - beta_ba.
+cudaError_t launch_iface_mix(float *eA, float *pa, int pure_a, int sa, float *eB, float *pb, int pure_b, int sb,
+                             const float *beta, int nb, int ncw, cudaStream_t s);
 // Energy and wall flows into host7[7] with no device allocation (file-scope device scratch).
 // Returns 0, 1 (grid larger than the scratch covers) or 2 (CUDA error in *err).
 int launch_energy_noalloc(const StepArgs &a, int storage, int limiter, const double *w, const double *sv,

@@ -497,6 +497,28 @@ __global__ void __launch_bounds__(256) k_resid_b(const double *part, int np, dou
     if (threadIdx.x < 4) out[threadIdx.x] = sm[threadIdx.x][0];
 }
 
+// ---- interface between two materials (Sec. 2.2 (v)) ------------------------------------------
+__global__ void __launch_bounds__(256) k_iface_mix(float *__restrict__ eA, float *__restrict__ pa, int pure_a, int sa,
+                                                   float *__restrict__ eB, float *__restrict__ pb, int pure_b, int sb,
+                                                   const float *__restrict__ beta, int nb, int ncw) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+    if (j >= ncw) return;
+    float *a = eA + (size_t)k * sa + j, *b = eB + (size_t)k * sb + j;
+    float *qa = pa + (size_t)k * ncw + j, *qb = pb + (size_t)k * ncw + j;
+    const float SA = pure_a ? *a : *qa, SB = pure_b ? *b : *qb;
+    *qa = SA;
+    *qb = SB;
+    *a = fmaf(beta[2 * nb + k], SB, beta[nb + k] * SA);
+    *b = fmaf(beta[k], SA, beta[3 * nb + k] * SB);
+}
+
+cudaError_t launch_iface_mix(float *eA, float *pa, int pure_a, int sa, float *eB, float *pb, int pure_b, int sb,
+                             const float *beta, int nb, int ncw, cudaStream_t s) {
+    const dim3 g((unsigned)((ncw + 255) / 256), (unsigned)nb);
+    k_iface_mix<<<g, 256, 0, s>>>(eA, pa, pure_a, sa, eB, pb, pure_b, sb, beta, nb, ncw);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_resid_keep(const double *T, const double *q, long long n, double *Tp, double *qp, cudaStream_t s) {
     k_resid_keep<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(T, q, n, Tp, qp);
     return cudaGetLastError();

@@ -262,7 +262,20 @@ bool tiled_plan(int dim, const int n[3], int nb, int nd, int storage, int limite
         return false;
     }
     StepKernel kf = (StepKernel)plan.kernel;
-    if (cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.smem) != cudaSuccess ||
+    // The dynamic shared-memory cap is an attribute of the kernel instance, shared by every context
+    // that runs it, so it is set to the device's opt-in limit (not to this plan's size, which a
+    // later context with a smaller plan would lower below ours).
+    int optin = 0;
+    cudaFuncAttributes fa;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, kf) != cudaSuccess) {
+        cudaGetLastError();
+        why = "kernel attributes unavailable";
+        return false;
+    }
+    const int smem_cap = optin - (int)fa.sharedSizeBytes;
+    if (plan.smem > smem_cap ||
+        cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, plan.threads, plan.smem) != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         why = "kernel does not fit on an SM";

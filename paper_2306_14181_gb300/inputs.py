@@ -189,6 +189,28 @@ def inplane_film_2d(nx=64, ny=64, ntheta=2, nphi=3, dT=1.0):
     return cfg
 
 
+def interface_2d(nx=256, ny=128, nb=40, ntheta=4, nphi=4):
+    """Two materials side by side (an interface problem of Sec. 2.2 (v) shaped like the Ge-Si
+    verification problem of Sec. 5): material A (seed 1002 bands) on 256 x 128 cells of 2 nm, its
+    +x wall against the -x wall of material B (seed 2002 bands) on another 256 x 128 cells; 40
+    bands and 128 directions on both sides; thermalizing outer x walls at T_ref, diffuse top and
+    bottom; the hot spot's Gaussian source (sigma = 20 nm, 1e18 W/m^3) in A, 40 nm from the
+    interface.  Band transmissions of the diffuse-mismatch form beta_AB = C_B / (C_A + C_B),
+    beta_BA = C_A / (C_A + C_B) (they sum to one and keep a uniform temperature stationary).
+    One time step: the smaller CFL step of the two."""
+    h = (2e-9, 2e-9, 2e-9)
+    quad = ("octant", ntheta, nphi)
+    name = "interface_2d_2x%dx%d_%dx%d" % (nx, ny, nb, 8 * ntheta * nphi)
+    src = dict(kind="gaussian", centre=((nx - 20) * h[0], 0.5 * ny * h[1]), sigma=20e-9, q0=1e18)
+    A = _base(name + "_A", 2, (nx, ny, 1), h, nb, 1002, quad, [ISOTHERMAL, DIFFUSE, DIFFUSE, DIFFUSE, PERIODIC, PERIODIC],
+              [0] * 6, 1000, src)
+    B = _base(name + "_B", 2, (nx, ny, 1), h, nb, 2002, quad, [DIFFUSE, ISOTHERMAL, DIFFUSE, DIFFUSE, PERIODIC, PERIODIC],
+              [0] * 6, 1000, None)
+    A["dt"] = B["dt"] = min(A["dt"], B["dt"])
+    return dict(name=name, A=A, B=B, wall_a=1, wall_b=0, beta_ab=B["C"] / (A["C"] + B["C"]),
+                beta_ba=A["C"] / (A["C"] + B["C"]))
+
+
 # gray silicon of the paper's verification problems (Sec. 5): one band
 GRAY_SI = dict(C=1627600.0, v=2677.0, tau=39.9e-12)
 

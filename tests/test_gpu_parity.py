@@ -572,3 +572,20 @@ def test_persistent_matches_generic_kernel():
         bte.bte_step(ctx, 200)
         out.append(bte.bte_lattice_temperature(ctx))
     assert rel_linf(out[0], out[1]) <= 2e-6
+
+
+def test_contexts_sharing_a_kernel_instance():
+    """Two contexts on the same tiled kernel instance with different shared-memory plans (two
+    diffuse walls against one): the one created first still runs after the second is created."""
+    from paper_2306_14181_gb300 import bte
+    cA = small_cfg(3, (32, 12, 6), [PER, PER, SPE, DIF, ISO, DIF], Tw=[0.3] * 6, nb=3)
+    cB = small_cfg(3, (32, 12, 6), [PER, PER, ISO, SPE, DIF, SPE], Tw=[0.3] * 6, nb=3)
+    A = gpu_ctx(cA, kernel=bte.BTE_KERNEL_TILED)
+    B = gpu_ctx(cB, kernel=bte.BTE_KERNEL_TILED)
+    PA = oracle_problem(cA, 2)
+    e0 = (PA.equilibrium(0.1) * (1 + 0.2 * np.random.default_rng(3).standard_normal(PA.shape))).astype(np.float32)
+    for ctx in (A, B, A):
+        bte.bte_set_state(ctx, e0)
+        bte.bte_step(ctx, 3)
+    eo = PA.run(e0.astype(np.float64), 3)
+    assert rel_linf(bte.bte_get_state(A), eo) <= TOL

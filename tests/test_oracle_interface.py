@@ -161,3 +161,17 @@ def test_walls_that_do_not_face_are_refused():
     C = oracle_problem(cC, LIM_VANALBADA)
     with pytest.raises(ValueError):                          # 6 rows against 5
         interface_step(C, C.equilibrium(0.0), 1, B, eB, 0, 0.5, 0.5)
+
+
+def test_interface_workload_transmissions():
+    """The benchmark's two-material workload: transmissions in [0, 1] that sum to one band by
+    band and satisfy detailed balance, facing walls on one axis, one time step for both sides."""
+    from paper_2306_14181_gb300 import inputs
+    cfg = inputs.interface_2d(nx=128, ny=24, nb=4, ntheta=2, nphi=2)
+    A, B = cfg["A"], cfg["B"]
+    bab, bba = cfg["beta_ab"], cfg["beta_ba"]
+    assert np.all((bab > 0) & (bab < 1)) and np.allclose(bab + bba, 1.0, rtol=0, atol=1e-15)
+    assert np.allclose(bba * B["C"], bab * A["C"], rtol=1e-15, atol=0)
+    assert A["dt"] == B["dt"] and A["n"][1:] == B["n"][1:]
+    assert A["bc"][cfg["wall_a"]] == BC_DIFFUSE and B["bc"][cfg["wall_b"]] == BC_DIFFUSE
+    assert (cfg["wall_a"] >> 1) == (cfg["wall_b"] >> 1) and cfg["wall_a"] != cfg["wall_b"]
