@@ -75,6 +75,7 @@ def load_oracle():
                 f.restype = ct.c_int
             _lib.orc_interface_step.argtypes = [pp, dp, dp, fp, ct.c_double, ct.c_int, pp, dp, dp, fp, ct.c_double,
                                                 ct.c_int, dp, dp]
+            _lib.orc_sis_iteration.argtypes = [pp, dp, dp, fp, ct.c_double]
             _lib.orc_interface_energy.argtypes = [pp, dp, ct.c_int, pp, dp, ct.c_int, dp, dp, dp, dp, dp, dp]
         return _lib
 
@@ -238,6 +239,29 @@ class Problem:
         if rc != 0:
             raise MemoryError("oracle adjoint: trajectory does not fit in memory")
         return float(J[0]), gQ.reshape(self.nz, self.ny, self.nx), gt
+
+    def sis_iteration(self, e, Q=None, amp=1.0):
+        """One sequential iteration of the steady implicit DOM (Sec. 3.3-3.5, Eq. disretized_BTE
+        in delta form, first-order upwind on the left, the step's limited faces on the right,
+        walls lagged by one iteration): e^{n+1} = e^n + De."""
+        e = np.ascontiguousarray(e, dtype=np.float64)
+        out = np.empty_like(e)
+        self._lib.orc_sis_iteration(ct.byref(self._p), _dp(e), _dp(out), _fp(self._src(Q)), float(amp))
+        return out
+
+    def run_sis(self, e, max_iters, tol_T, tol_q, Q=None, Tref=300.0):
+        """Sequential iterations until eps_T < tol_T and eps_q < tol_q between consecutive
+        iterates (the loop condition of Sec. 3.5) or max_iters: (e, iterations, eps_T, eps_q)."""
+        eT = eq = math.inf
+        n = 0
+        while n < max_iters:
+            e1 = self.sis_iteration(e, Q)
+            eT, eq = self.residuals(e, e1, Tref)
+            e = e1
+            n += 1
+            if eT < tol_T and eq < tol_q:
+                break
+        return e, n, eT, eq
 
     def residuals(self, e_n, e_n1, Tref):
         """The loop condition of the transient solver (Sec. 4.1, Algorithm 2) between consecutive
