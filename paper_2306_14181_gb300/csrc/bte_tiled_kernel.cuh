@@ -615,7 +615,11 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
         const bool wall_lane = sd == 0 ? xlo : xhi;
         const bool leaving = sd == 0 ? nux <= 0.f : nux >= 0.f;
         gmode = kGhSmem;
-        if (!wall_lane || bc == kBcPeriodic) {
+        if (wall_lane && bc == kBcPeriodic && WPR == 1 && rowlen == NX) {
+            // one warp holds the whole row: the plain shuffle wraps around it, which is the
+            // periodic image
+            gmode = kGhShfl;
+        } else if (!wall_lane || bc == kBcPeriodic) {
             const int gi = !wall_lane ? (sd == 0 ? x0 - 2 : x0 + VL) : (sd == 0 ? rowlen - 2 : 0);
             gptr = box + o + gi;
             gi0 = sd == 0 ? 1 : 0;
@@ -647,6 +651,9 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
             rx0 = rx1 = sd == 0 ? 0 : rowlen - 1;
         }
     }
+    // whether any end lane of the warp takes its ghosts other than by the plain shuffle (always,
+    // when two warps share a row: each has an inner end)
+    const bool need_gh = WPR == 2 || __any_sync(0xffffffffu, gmode != kGhShfl);
     // diffuse-wall sums of Eq. (diff_bound) for the next step: cells next to a diffuse wall add
     // w_d (s_d.n) e for the directions leaving through it (weight 0 otherwise)
     const float wx = xlo ? hd[9] : (xhi ? hd[10] : 0.f);
@@ -684,7 +691,7 @@ __device__ __forceinline__ void rows_of_warp(const StepArgs &a, const TiledArgs 
         ex[1] = __shfl_sync(0xffffffffu, w0[VL - 1], (lane + 31) & 31);
         ex[VL + 2] = __shfl_sync(0xffffffffu, w0[0], (lane + 1) & 31);
         ex[VL + 3] = __shfl_sync(0xffffffffu, w0[1], (lane + 1) & 31);
-        {
+        if (need_gh) {
             const T *gp = gptr + j * gstep;
             float r0 = 0.f, r1 = 0.f;
             if constexpr (REF) {

@@ -502,6 +502,20 @@ def test_hotspot_2d_16bit_storage(storage, kernel):
     assert rel_linf(gTL, oTL) <= TOL16
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_hotspot_2d_bf16_nearest_stall_is_bounded(kernel):
+    """BF16 codes rounded to nearest on the same 300-step hot spot: a per-step change below half
+    a code step is lost, so the run stalls short of the oracle as the rise slows (6.4e-3 at step
+    300, above the 2e-3 bar that stochastic rounding meets).  This pins that known error at 1e-2
+    so that it cannot grow unnoticed; BF16 runs that need the bar use stochastic rounding."""
+    cfg = inputs.hotspot_2d(nx=128, ny=64, nb=8, ntheta=2, nphi=2)
+    P = oracle_problem(cfg)
+    Q = inputs.source_field(cfg)
+    ctx, g, gTL, eo, oTL = run_both(cfg, np.zeros(P.shape), 300, Q, storage=2, kernel=kernel, T_scale=10.0)
+    assert ctx.info.kernel == kernel
+    assert rel_linf(gTL, oTL) <= 1e-2
+
+
 @pytest.mark.parametrize("storage", [1, 2])
 @pytest.mark.parametrize("kernel", [1, 2])
 def test_hotspot_2d_16bit_stochastic_rounding(storage, kernel):
