@@ -546,6 +546,47 @@ def ttg_record(args, xi):
     return rec
 
 
+def implicit_record(args, explicit):
+    """f4: the in-plane film solved by the steady implicit DOM (sequential iterations, Sec.
+    3.3-3.5) to eps_T, eps_q < 1e-6 (checked every 5 iterations; the FP32 right-hand side keeps
+    the change between iterates near 1e-7): iterations, device time per
+    iteration (CUDA events over the whole solve, residual checks included) and the in-plane
+    conductivity, beside the time-marched solve of the same problem."""
+    import gc
+    import numpy as np
+    import torch
+    from paper_2306_14181_gb300 import bte, inputs
+    cfg = inputs.inplane_film_2d()
+    stream = torch.cuda.current_stream()
+    ctx = bte.bte_from_workload(cfg, limiter=args.limiter, stream=stream.cuda_stream)
+    info = ctx.info
+    bte.bte_sis_iterate(ctx, 2)  # warm-up (module load, first launches)
+    bte.bte_init_temperature(ctx, None)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    n, eT, eq = bte.bte_run_steady_implicit(ctx, 2000, 5, 1e-6, 1e-6)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_ms = ev0.elapsed_time(ev1)
+    _, _, q = bte.bte_moments(ctx)
+    L = cfg["n"][0] * cfg["h"][0]
+    kappa = float(np.mean(q[0])) * L / cfg["jump"][0]
+    rec = {"workload": cfg["name"], "method": "steady implicit DOM, sequential iterations", "storage": "f32",
+           "forward_kernel": kernel_name_of(info), "iterations": n, "converged": bool(eT < 1e-6 and eq < 1e-6),
+           "eps_T": eT, "eps_q": eq, "ms_total": t_ms, "ms_per_iteration": t_ms / max(n, 1),
+           "kappa_inplane": kappa}
+    if explicit is not None and explicit.get("steps"):
+        rec["time_marching"] = {"steps": explicit["steps"], "wall_s": explicit["wall_s"],
+                                "kappa_inplane": explicit["kappa_inplane"]}
+        rec["speedup_vs_time_marching"] = explicit["wall_s"] * 1e3 / t_ms
+    bte.bte_destroy(ctx)
+    del ctx
+    gc.collect()
+    return rec
+
+
 def interface_record(args, peak, peak_kind):
     """f3: the two-material interface pair (both sides' forward steps and the interface kernel
     each step), timed with CUDA events over 100 coupled steps after 3 warm-up ones; the
@@ -672,6 +713,7 @@ def run_gb300(args):
                 continue
             subs.append(sub_record(args, name, st, ts, steps, nadj, kck, peak, peak_kind, kern))
         subs.append(steady_record(args))
+        subs.append(implicit_record(args, subs[-1]))
         subs.append(interface_record(args, peak, peak_kind))
         for xi in (0.1, 1.0, 10.0):
             subs.append(ttg_record(args, xi))

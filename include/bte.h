@@ -335,6 +335,27 @@ bte_status bte_synchronize(bte_ctx *ctx);
  * It applies to one launch only and is then cleared.  BTE_EINVAL for stall_test outside 0..3. */
 bte_status bte_set_wait_limit(bte_ctx *ctx, long long limit_ns, int stall_test);
 
+/* Steady state by the implicit discrete-ordinates method with the sequential iterative scheme
+ * (Sec. 3.3-3.5, Eq. disretized_BTE in delta form).  One iteration forms the steady equation's
+ * right-hand side R of the current state with the forward step's own faces (second order,
+ * limited), walls and source (at the current step's amplitude), then solves for every band k and
+ * direction d the first-order upwind system of the increment
+ *   (1/tau_k + sum_a v_k |s_a| / h_a) De_i - sum_a (v_k |s_a| / h_a) De_{upwind neighbour along a} = R_i
+ * by one sweep from the upwind corner (the upwind De across a wall, periodic pairs included, is
+ * 0: the boundary values move at the next iteration), sets e = e + De, and forms T_L and the
+ * diffuse-wall values of the new state.  A fixed point solves the steady discrete equation of
+ * bte_step exactly.  bte_sis_iterate runs n >= 0 iterations (stream ordered, non-blocking; the
+ * step counter is not advanced).  FP32 storage only (BTE_EUNSUPPORTED otherwise); BTE_ESTATE on
+ * a context coupled at an interface. */
+bte_status bte_sis_iterate(bte_ctx *ctx, int n);
+
+/* Iterate until the loop condition of Sec. 3.5 holds between consecutive iterates, eps_T <
+ * tol_T and eps_q < tol_q (as bte_residuals defines them), checked every check_every iterations,
+ * or max_iters iterations have run.  Outputs (any may be NULL): the iterations run and the last
+ * eps_T, eps_q.  Synchronises at every check. */
+bte_status bte_run_steady_implicit(bte_ctx *ctx, long long max_iters, int check_every, double tol_T, double tol_q,
+                                   long long *iters, double *eps_T, double *eps_q);
+
 /* Interface between two materials (Sec. 2.2 (v), diffuse mismatch).  Wall wall_a of ctx_a (the
  * material-A side) and wall wall_b of ctx_b (material B) must both have been created as
  * BTE_BC_INTERFACE, on the same axis and opposite sides (A's +x against B's -x, say), with the

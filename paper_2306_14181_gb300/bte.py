@@ -28,7 +28,8 @@ EXPORTS = ["bte_create", "bte_destroy", "bte_last_error", "bte_init_temperature"
            "bte_lattice_temperature", "bte_moments", "bte_energy", "bte_get_state", "bte_set_state",
            "bte_get_values", "bte_adjoint", "bte_adjoint_profile_read",
            "bte_get_info", "bte_get_quadrature", "bte_synchronize", "bte_profile", "bte_profile_read", "bte_energy_noalloc",
-           "bte_set_wait_limit", "bte_residuals", "bte_run_steady", "bte_interface", "bte_step_pair"]
+           "bte_set_wait_limit", "bte_residuals", "bte_run_steady", "bte_interface", "bte_step_pair",
+           "bte_sis_iterate", "bte_run_steady_implicit"]
 
 _STATUS = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESTATE", 5: "ENONFINITE", 6: "ETIMEOUT", 7: "EUNSUPPORTED"}
 
@@ -109,6 +110,9 @@ def load():
     lib.bte_residuals.argtypes = [P, ct.c_int, dp, dp]
     lib.bte_run_steady.argtypes = [P, ct.c_longlong, ct.c_int, ct.c_double, ct.c_double,
                                    ct.POINTER(ct.c_longlong), dp, dp]
+    lib.bte_sis_iterate.argtypes = [P, ct.c_int]
+    lib.bte_run_steady_implicit.argtypes = [P, ct.c_longlong, ct.c_int, ct.c_double, ct.c_double,
+                                            ct.POINTER(ct.c_longlong), dp, dp]
     lib.bte_interface.argtypes = [P, ct.c_int, P, ct.c_int, dp, dp]
     lib.bte_step_pair.argtypes = [P, P, ct.c_int]
     lib.bte_profile.argtypes = [P, ct.c_int]
@@ -279,6 +283,20 @@ def bte_run_steady(ctx, max_steps, check_every, tol_T, tol_q):
     n, eT, eq = ct.c_longlong(), ct.c_double(), ct.c_double()
     _check(load().bte_run_steady(ctx.handle, int(max_steps), int(check_every), float(tol_T), float(tol_q),
                                  ct.byref(n), ct.byref(eT), ct.byref(eq)), ctx.handle)
+    return n.value, eT.value, eq.value
+
+
+def bte_sis_iterate(ctx, n=1):
+    """n iterations of the steady implicit DOM's sequential scheme."""
+    _check(load().bte_sis_iterate(ctx.handle, int(n)), ctx.handle)
+
+
+def bte_run_steady_implicit(ctx, max_iters, check_every, tol_T, tol_q):
+    """Implicit iterations until eps_T < tol_T and eps_q < tol_q (checked every check_every
+    iterations) or max_iters: returns (iterations run, eps_T, eps_q)."""
+    n, eT, eq = ct.c_longlong(), ct.c_double(), ct.c_double()
+    _check(load().bte_run_steady_implicit(ctx.handle, int(max_iters), int(check_every), float(tol_T), float(tol_q),
+                                          ct.byref(n), ct.byref(eT), ct.byref(eq)), ctx.handle)
     return n.value, eT.value, eq.value
 
 

@@ -984,18 +984,84 @@ static bte_status moments_on_device(bte_ctx *c, const DiagOut &o) {
     return BTE_OK;
 }
 
+// One sequential iteration of the steady implicit DOM (Sec. 3.3-3.5): the forward step writes
+// e^n + dt R, the sweep turns it into e^n + De, and T_L and the diffuse-wall values follow from
+// the new state.
+static bte_status sis_one(bte_ctx *c) {
+    StepArgs a = make_args(c);
+    a.amp = (float)amplitude_at(c, c->step);
+    a.e_in = c->e[c->cur];
+    a.e_out = c->e[c->cur ^ 1];
+    a.ediff_in = c->ediff[c->ecur];
+    a.ediff_out = c->ediff[c->ecur ^ 1];
+    cudaError_t e;
+    if (c->tiled) {
+        e = launch_step_tiled(a, c->plan, c->stream);
+        c->plan.stall = 0;
+    } else {
+        e = launch_step_generic(a, c->storage, c->limiter, c->stream);
+    }
+    if (e != cudaSuccess) return fail(c, BTE_ECUDA, "forward step launch: %s", cudaGetErrorString(e));
+    CU(c, launch_sis_sweep(a, static_cast<const float *>(c->e[c->cur]), static_cast<float *>(c->e[c->cur ^ 1]),
+                           c->stream));
+    c->cur ^= 1;
+    return refresh_moments(c);
+}
+
+static bte_status sis_check(bte_ctx *c) {
+    if (c->storage != BTE_STORE_F32) return fail(c, BTE_EUNSUPPORTED, "the implicit iteration needs FP32 storage");
+    if (c->peer) return fail(c, BTE_ESTATE, "the context is coupled at an interface");
+    return BTE_OK;
+}
+
+extern "C" bte_status bte_sis_iterate(bte_ctx *c, int n) {
+    if (!c) return fail(nullptr, BTE_EINVAL, "ctx is NULL");
+    if (n < 0) return fail(c, BTE_EINVAL, "n must be >= 0");
+    TRY(sis_check(c));
+    for (int s = 0; s < n; ++s) TRY(sis_one(c));
+    return BTE_OK;
+}
+
+// eps_T and eps_q of Algorithm 2's loop condition between the last two of n more steps (or
+// implicit iterations).
+static bte_status residuals_after(bte_ctx *c, int nsteps, bool implicit, double *eps_T, double *eps_q);
+
 extern "C" bte_status bte_residuals(bte_ctx *c, int nsteps, double *eps_T, double *eps_q) {
     if (!c) return fail(nullptr, BTE_EINVAL, "ctx is NULL");
+    return residuals_after(c, nsteps, false, eps_T, eps_q);
+}
+
+extern "C" bte_status bte_run_steady_implicit(bte_ctx *c, long long max_iters, int check_every, double tol_T,
+                                              double tol_q, long long *iters, double *eps_T, double *eps_q) {
+    if (!c) return fail(nullptr, BTE_EINVAL, "ctx is NULL");
+    if (max_iters < 1 || check_every < 1) return fail(c, BTE_EINVAL, "max_iters and check_every must be >= 1");
+    if (!(tol_T >= 0.0) || !(tol_q >= 0.0)) return fail(c, BTE_EINVAL, "tolerances must be >= 0");
+    TRY(sis_check(c));
+    long long done = 0;
+    double eT = HUGE_VAL, eq = HUGE_VAL;
+    while (done < max_iters) {
+        const int n = (int)std::min<long long>(check_every, max_iters - done);
+        TRY(residuals_after(c, n, true, &eT, &eq));
+        done += n;
+        if (eT < tol_T && eq < tol_q) break;
+    }
+    if (iters) *iters = done;
+    if (eps_T) *eps_T = eT;
+    if (eps_q) *eps_q = eq;
+    return BTE_OK;
+}
+
+static bte_status residuals_after(bte_ctx *c, int nsteps, bool implicit, double *eps_T, double *eps_q) {
     if (nsteps < 1) return fail(c, BTE_EINVAL, "nsteps must be >= 1");
     TRY(diag_buffers(c));
     if (!c->rs) TRY(dalloc(c, &c->rs, (size_t)2 * c->ncell + 4 * kResidBlocks + 4));
     double *Tp = c->rs, *qp = c->rs + c->ncell, *part = c->rs + 2 * c->ncell, *res = part + 4 * kResidBlocks;
     const DiagOut o = diag_layout(c);
-    TRY(bte_step(c, nsteps - 1));
+    TRY(implicit ? bte_sis_iterate(c, nsteps - 1) : bte_step(c, nsteps - 1));
     CU(c, cudaMemsetAsync(c->dflag, 0, sizeof(int), c->stream));
     TRY(moments_on_device(c, o));
     CU(c, launch_resid_keep(o.T, o.q, c->ncell, Tp, qp, c->stream));
-    TRY(bte_step(c, 1));
+    TRY(implicit ? bte_sis_iterate(c, 1) : bte_step(c, 1));
     TRY(moments_on_device(c, o));
     CU(c, launch_residuals(o.T, o.q, Tp, qp, c->ncell, c->Tref, part, res, c->stream));
     double r[4];

@@ -115,6 +115,10 @@ cudaError_t launch_residuals(const double *T, const double *q, const double *Tp,
 // beta: [4][nb] = beta_ab, 1 - beta_ab, beta_ba, 1 - beta_ba.
 cudaError_t launch_iface_mix(float *eA, float *pa, int pure_a, int sa, float *eB, float *pb, int pure_b, int sb,
                              const float *beta, int nb, int ncw, cudaStream_t s);
+// Steady implicit DOM, sequential iteration (Sec. 3.3-3.5): e_io holds the forward step's output
+// e^n + dt R on entry and e^{n+1} = e^n + De on exit, De solving each plane's first-order upwind
+// system (dt/tau + sum|nu_a|) De_i - sum_a |nu_a| De_{up_a(i)} = dt R_i (0 across walls).  FP32.
+cudaError_t launch_sis_sweep(const StepArgs &a, const float *e_in, float *e_io, cudaStream_t s);
 // Energy and wall flows into host7[7] with no device allocation (file-scope device scratch).
 // Returns 0, 1 (grid larger than the scratch covers) or 2 (CUDA error in *err).
 int launch_energy_noalloc(const StepArgs &a, int storage, int limiter, const double *w, const double *sv,
