@@ -584,6 +584,30 @@ def implicit_record(args, explicit):
     bte.bte_destroy(ctx)
     del ctx
     gc.collect()
+    # one iteration at the hot spot's size (5120 planes of 256 x 256 cells): forward step (8 B an
+    # update), sweep (12 B) and moment pass (4 B) over the iteration's device time
+    hcfg = inputs.hotspot_2d()
+    hctx = bte.bte_from_workload(hcfg, limiter=args.limiter, stream=stream.cuda_stream)
+    Q = inputs.source_field(hcfg)
+    bte.bte_set_source(hctx, torch.from_numpy(Q.reshape(-1)).cuda())
+    bte.bte_sis_iterate(hctx, 2)
+    torch.cuda.synchronize()
+    its = 10
+    ev0.record(stream)
+    bte.bte_sis_iterate(hctx, its)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    it_ms = ev0.elapsed_time(ev1) / its
+    nel = hctx.info.nelem
+    gbs = nel * 24 / (it_ms / 1e3) / 1e9
+    rec["hotspot_iteration"] = {"workload": hcfg["name"], "iterations": its, "ms_per_iteration": it_ms,
+                                "bytes_per_iteration": nel * 24, "achieved_gbs": gbs,
+                                "frac": gbs / hbm_peak()[0], "unit": "GB/s",
+                                "note": "forward step 8 B + sweep 12 B + moment pass 4 B per update"}
+    bte.bte_destroy(hctx)
+    del hctx
+    gc.collect()
+    torch.cuda.empty_cache()
     return rec
 
 
