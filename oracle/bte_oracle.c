@@ -427,12 +427,13 @@ static double residual_element(const orc_problem *P, const double *e, const doub
     return -div + (e0 - en) / P->tau[k] + src;
 }
 
-void orc_sis_iteration(const orc_problem *P, const double *e_in, double *e_out, const float *Q, double amp) {
+/* The same iteration with the equilibrium e0 = C_k TL / W of a given lattice temperature TL (the
+ * synthetic scheme of Sec. 3.5 corrects T_L between iterations). */
+void orc_sis_iteration_tl(const orc_problem *P, const double *e_in, const double *TL, double *e_out, const float *Q,
+                          double amp) {
     const long nc = ncell_of(P);
     const double W = total_weight(P), SC = sum_C(P);
-    double *TL = (double *)malloc(sizeof(double) * nc);
     double *ediff = (double *)calloc((size_t)6 * P->nb * nc, sizeof(double));
-    orc_lattice_temperature(P, e_in, TL);
     diffuse_wall_values(P, e_in, ediff);
     const long nplanes = (long)P->nb * P->nd;
     #pragma omp parallel for schedule(dynamic, 1)
@@ -466,8 +467,14 @@ void orc_sis_iteration(const orc_problem *P, const double *e_in, double *e_out, 
                 }
         free(De);
     }
-    free(TL);
     free(ediff);
+}
+
+void orc_sis_iteration(const orc_problem *P, const double *e_in, double *e_out, const float *Q, double amp) {
+    double *TL = (double *)malloc(sizeof(double) * ncell_of(P));
+    orc_lattice_temperature(P, e_in, TL);
+    orc_sis_iteration_tl(P, e_in, TL, e_out, Q, amp);
+    free(TL);
 }
 
 /* ------------------------------------------------------------------------- */

@@ -76,6 +76,7 @@ def load_oracle():
             _lib.orc_interface_step.argtypes = [pp, dp, dp, fp, ct.c_double, ct.c_int, pp, dp, dp, fp, ct.c_double,
                                                 ct.c_int, dp, dp]
             _lib.orc_sis_iteration.argtypes = [pp, dp, dp, fp, ct.c_double]
+            _lib.orc_sis_iteration_tl.argtypes = [pp, dp, dp, dp, fp, ct.c_double]
             _lib.orc_interface_energy.argtypes = [pp, dp, ct.c_int, pp, dp, ct.c_int, dp, dp, dp, dp, dp, dp]
         return _lib
 
@@ -248,6 +249,117 @@ class Problem:
         out = np.empty_like(e)
         self._lib.orc_sis_iteration(ct.byref(self._p), _dp(e), _dp(out), _fp(self._src(Q)), float(amp))
         return out
+
+    def sis_iteration_tl(self, e, TL, Q=None, amp=1.0):
+        """The sequential iteration with the equilibrium of a given lattice temperature TL."""
+        e = np.ascontiguousarray(e, dtype=np.float64)
+        TL = np.ascontiguousarray(np.broadcast_to(np.asarray(TL, dtype=np.float64), (self.nz, self.ny, self.nx)))
+        out = np.empty_like(e)
+        self._lib.orc_sis_iteration_tl(ct.byref(self._p), _dp(e), _dp(TL), _dp(out), _fp(self._src(Q)), float(amp))
+        return out
+
+    # -- synthetic iterative scheme (Sec. 3.5) ------------------------------------------------
+    @property
+    def k_bulk(self):
+        """Bulk conductivity sum_k C_k v_k^2 tau_k / 3 (Sec. 3.5)."""
+        return float(np.sum(self.C * self.v ** 2 * self.tau)) / 3.0
+
+    def energy_residual(self, e, Q=None, amp=1.0):
+        """r_i = sum_k sum_d w_d R_{k,d,i}: the energy the steady equation's right-hand side R
+        (with e0 of T_L(e)) leaves in cell i per unit time and volume (W/m^3); R = (step(e) - e)/dt."""
+        R = (self.step(e, Q, amp) - e) / self.dt
+        return np.einsum("d,kdzyx->zyx", self.w, R)
+
+    def laplacian(self):
+        """The cell-centred 2*dim+1-point Laplacian (1/m^2) of a temperature correction on the
+        grid, as a sparse matrix over the cells (x fastest), with the walls' conditions on the
+        correction: a thermalizing wall holds the temperature (zero at the wall face: the ghost
+        is minus the wall cell), reflecting walls pass no heat (the ghost equals the wall cell),
+        periodic pairs wrap (the jump is in the state, not in the correction)."""
+        import scipy.sparse as sp
+        n = (self.nx, self.ny, self.nz)
+        h = (self.dx, self.dy, self.dz)
+        N = self.ncell
+        rows, cols, vals = [], [], []
+        for z in range(self.nz):
+            for y in range(self.ny):
+                for x in range(self.nx):
+                    i = (z * self.ny + y) * self.nx + x
+                    c = [x, y, z]
+                    for a in range(self.dim):
+                        w2 = 1.0 / (h[a] * h[a])
+                        for side, step in ((0, -1), (1, 1)):
+                            nb = list(c)
+                            nb[a] += step
+                            rows.append(i)
+                            cols.append(i)
+                            vals.append(-w2)
+                            if 0 <= nb[a] < n[a]:
+                                j = (nb[2] * self.ny + nb[1]) * self.nx + nb[0]
+                                rows.append(i)
+                                cols.append(j)
+                                vals.append(w2)
+                                continue
+                            bc = self.bc[2 * a + side]
+                            if bc == BC_PERIODIC:
+                                nb[a] %= n[a]
+                                j = (nb[2] * self.ny + nb[1]) * self.nx + nb[0]
+                                rows.append(i)
+                                cols.append(j)
+                                vals.append(w2)
+                            elif bc == BC_ISOTHERMAL:
+                                rows.append(i)
+                                cols.append(i)
+                                vals.append(-w2)
+                            else:
+                                rows.append(i)
+                                cols.append(i)
+                                vals.append(w2)
+        return sp.csr_matrix((vals, (rows, cols)), shape=(N, N))
+
+    def synthetic_correction(self, r):
+        """dT solving k_bulk L dT = -r (the macroscopic equation of Sec. 3.5 for the correction of
+        T_L); with no thermalizing wall L is singular and dT is the mean-free least-squares
+        solution of the mean-free r."""
+        import scipy.sparse.linalg as spl
+        if getattr(self, "_klap", None) is None:
+            self._klap = (self.laplacian() * self.k_bulk).tocsc()
+            self._klap_lu = (spl.splu(self._klap) if any(self.bc[w] == BC_ISOTHERMAL for w in range(2 * self.dim))
+                             else None)
+        L = self._klap
+        b = -np.asarray(r, dtype=np.float64).reshape(-1)
+        if self._klap_lu is not None:
+            dT = self._klap_lu.solve(b)
+        else:
+            b = b - b.mean()
+            dT = spl.lsqr(L, b, atol=1e-15, btol=1e-15, iter_lim=20 * self.ncell)[0]
+            dT -= dT.mean()
+        return dT.reshape(self.nz, self.ny, self.nx)
+
+    def synthetic_iteration(self, e, TL, Q=None, amp=1.0):
+        """One iteration of the synthetic scheme (Sec. 3.5, Steps 2-4): the sweep with e0 of TL,
+        then the macroscopic equation for the lattice temperature of the next sweep.  The
+        equation's right-hand side div q_nonFourier - sum Q, with the scheme's own face fluxes
+        for q, is k_bulk L T_L(e) - r(e) (r: the energy residual), so the new lattice temperature
+        is T_L(e) + dT with k_bulk L dT = -r(e).  Returns (e', TL')."""
+        e1 = self.sis_iteration_tl(e, TL, Q, amp)
+        dT = self.synthetic_correction(self.energy_residual(e1, Q, amp))
+        return e1, self.lattice_temperature(e1) + dT
+
+    def run_synthetic(self, e, max_iters, tol_T, tol_q, Q=None, Tref=300.0):
+        """Synthetic iterations until the loop condition of Sec. 3.5 holds between consecutive
+        states: (e, iterations, eps_T, eps_q)."""
+        TL = self.lattice_temperature(e)
+        eT = eq = math.inf
+        n = 0
+        while n < max_iters:
+            e1, TL = self.synthetic_iteration(e, TL, Q)
+            eT, eq = self.residuals(e, e1, Tref)
+            e = e1
+            n += 1
+            if eT < tol_T and eq < tol_q:
+                break
+        return e, n, eT, eq
 
     def run_sis(self, e, max_iters, tol_T, tol_q, Q=None, Tref=300.0):
         """Sequential iterations until eps_T < tol_T and eps_q < tol_q between consecutive
