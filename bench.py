@@ -608,6 +608,26 @@ def implicit_record(args, explicit):
     del hctx
     gc.collect()
     torch.cuda.empty_cache()
+    # the near-diffusive film: sequential against synthetic iterations (Sec. 3.5) to 1e-5
+    dcfg = inputs.diffusive_film_1d()
+    schemes = {}
+    for name, scheme in (("sequential", bte.BTE_SCHEME_SEQUENTIAL), ("synthetic", bte.BTE_SCHEME_SYNTHETIC)):
+        dctx = bte.bte_from_workload(dcfg, limiter=args.limiter, stream=stream.cuda_stream)
+        bte.bte_set_steady_scheme(dctx, scheme)
+        bte.bte_sis_iterate(dctx, 2)
+        bte.bte_init_temperature(dctx, None)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        n, eT, eq = bte.bte_run_steady_implicit(dctx, 20000, 5, 1e-5, 1e-5)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        _, _, q = bte.bte_moments(dctx)
+        schemes[name] = {"iterations": n, "converged": bool(eT < 1e-5 and eq < 1e-5), "ms_total": ev0.elapsed_time(ev1),
+                         "q_mean_w_m2": float(np.mean(q[0]))}
+        bte.bte_destroy(dctx)
+        del dctx
+    rec["diffusive_film"] = {"workload": dcfg["name"], "tol": 1e-5, **schemes}
+    gc.collect()
     return rec
 
 

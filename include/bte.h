@@ -349,6 +349,26 @@ bte_status bte_set_wait_limit(bte_ctx *ctx, long long limit_ns, int stall_test);
  * a context coupled at an interface. */
 bte_status bte_sis_iterate(bte_ctx *ctx, int n);
 
+/* Iterative scheme of bte_sis_iterate and bte_run_steady_implicit (Sec. 3.5). */
+enum {
+    BTE_SCHEME_SEQUENTIAL = 0, /* the lattice temperature of each sweep is that of the state (default) */
+    BTE_SCHEME_SYNTHETIC = 1   /* after each sweep the lattice temperature is corrected by the macroscopic
+                                  (diffusion-type) equation of Eq. disretized_macro: with the scheme's own face
+                                  fluxes for q its right-hand side is k_bulk L T_L(e) - r(e), so the next sweep
+                                  relaxes towards T_L(e) + dT with k_bulk L dT = -r, r_i = sum_k sum_d w_d R the
+                                  energy residual of the new state, k_bulk = sum_k C_k v_k^2 tau_k / 3, L the cell
+                                  Laplacian (thermalizing walls hold the temperature, reflecting walls pass no
+                                  heat, periodic pairs wrap; the mean-free solution when no wall is thermalizing),
+                                  solved by conjugate gradients in FP64 to 1e-10.  Its fixed point is the
+                                  sequential scheme's; it converges in far fewer iterations near the diffusive
+                                  limit.  An iteration costs a second forward step and the solve */
+};
+
+/* Select the scheme of the steady implicit iterations (BTE_EINVAL for another value).  After a
+ * synthetic iteration bte_lattice_temperature returns the corrected lattice temperature the next
+ * sweep uses; bte_moments' dTL is always that of the state. */
+bte_status bte_set_steady_scheme(bte_ctx *ctx, int scheme);
+
 /* Iterate until the loop condition of Sec. 3.5 holds between consecutive iterates, eps_T <
  * tol_T and eps_q < tol_q (as bte_residuals defines them), checked every check_every iterations,
  * or max_iters iterations have run.  Outputs (any may be NULL): the iterations run and the last

@@ -22,6 +22,7 @@ BTE_STORE_F32, BTE_STORE_F16, BTE_STORE_BF16 = 0, 1, 2
 BTE_LIM_FIRST_ORDER, BTE_LIM_MINMOD, BTE_LIM_VANALBADA = 0, 1, 2
 BTE_ROUND_NEAREST, BTE_ROUND_STOCHASTIC = 0, 1
 BTE_KERNEL_AUTO, BTE_KERNEL_GENERIC, BTE_KERNEL_TILED, BTE_KERNEL_PERSISTENT = 0, 1, 2, 3
+BTE_SCHEME_SEQUENTIAL, BTE_SCHEME_SYNTHETIC = 0, 1
 
 # every entry point include/bte.h declares
 EXPORTS = ["bte_create", "bte_destroy", "bte_last_error", "bte_init_temperature", "bte_set_source", "bte_step",
@@ -29,7 +30,7 @@ EXPORTS = ["bte_create", "bte_destroy", "bte_last_error", "bte_init_temperature"
            "bte_get_values", "bte_adjoint", "bte_adjoint_profile_read",
            "bte_get_info", "bte_get_quadrature", "bte_synchronize", "bte_profile", "bte_profile_read", "bte_energy_noalloc",
            "bte_set_wait_limit", "bte_residuals", "bte_run_steady", "bte_interface", "bte_step_pair",
-           "bte_sis_iterate", "bte_run_steady_implicit"]
+           "bte_sis_iterate", "bte_run_steady_implicit", "bte_set_steady_scheme"]
 
 _STATUS = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESTATE", 5: "ENONFINITE", 6: "ETIMEOUT", 7: "EUNSUPPORTED"}
 
@@ -111,6 +112,7 @@ def load():
     lib.bte_run_steady.argtypes = [P, ct.c_longlong, ct.c_int, ct.c_double, ct.c_double,
                                    ct.POINTER(ct.c_longlong), dp, dp]
     lib.bte_sis_iterate.argtypes = [P, ct.c_int]
+    lib.bte_set_steady_scheme.argtypes = [P, ct.c_int]
     lib.bte_run_steady_implicit.argtypes = [P, ct.c_longlong, ct.c_int, ct.c_double, ct.c_double,
                                             ct.POINTER(ct.c_longlong), dp, dp]
     lib.bte_interface.argtypes = [P, ct.c_int, P, ct.c_int, dp, dp]
@@ -289,6 +291,11 @@ def bte_run_steady(ctx, max_steps, check_every, tol_T, tol_q):
 def bte_sis_iterate(ctx, n=1):
     """n iterations of the steady implicit DOM's sequential scheme."""
     _check(load().bte_sis_iterate(ctx.handle, int(n)), ctx.handle)
+
+
+def bte_set_steady_scheme(ctx, scheme):
+    """BTE_SCHEME_SEQUENTIAL or BTE_SCHEME_SYNTHETIC for the steady implicit iterations."""
+    _check(load().bte_set_steady_scheme(ctx.handle, int(scheme)), ctx.handle)
 
 
 def bte_run_steady_implicit(ctx, max_iters, check_every, tol_T, tol_q):

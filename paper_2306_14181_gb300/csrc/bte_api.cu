@@ -86,6 +86,13 @@ struct bte_ctx {
     float *wf = nullptr;
     double adj_ms = 0, adj_recompute_ms = 0;
     long long adj_steps = 0, adj_recompute_steps = 0;
+    // steady solver's iterative scheme (Sec. 3.5): 0 sequential, 1 synthetic; the synthetic
+    // scheme's scratch (allocated on first use) and the conjugate-gradient count of its last
+    // correction
+    int scheme = 0;
+    float *syn_pr = nullptr;
+    double *syn_x = nullptr;
+    int syn_cg = 0;
     // interface between two materials (Sec. 2.2 (v)): the wall created as BTE_BC_INTERFACE (-1:
     // none; the kernels treat it as diffuse), the coupled context, this side's plain diffuse
     // values at that wall [nb][wall cells] once mixed, and (side A only) the transmissions
@@ -335,6 +342,10 @@ static bte_status iface_mix(bte_ctx *c) {
 }
 
 static void free_all(bte_ctx *c) {
+    cudaFree(c->syn_pr);
+    cudaFree(c->syn_x);
+    c->syn_pr = nullptr;
+    c->syn_x = nullptr;
     if (c->iev) cudaEventDestroy(c->iev);
     c->iev = nullptr;
     cudaFree(c->ipure);
@@ -1005,7 +1016,40 @@ static bte_status sis_one(bte_ctx *c) {
     CU(c, launch_sis_sweep(a, static_cast<const float *>(c->e[c->cur]), static_cast<float *>(c->e[c->cur ^ 1]),
                            c->stream));
     c->cur ^= 1;
-    return refresh_moments(c);
+    TRY(refresh_moments(c));
+    if (c->scheme != BTE_SCHEME_SYNTHETIC) return BTE_OK;
+    // synthetic scheme: the forward step of the new state (e0 of its own T_L) gives the energy
+    // residual, and the macroscopic equation corrects the T_L the next sweep relaxes towards
+    if (!c->syn_pr) TRY(dalloc(c, &c->syn_pr, (size_t)c->nb * c->ncell));
+    if (!c->syn_x) TRY(dalloc(c, &c->syn_x, synthetic_scratch_doubles(c->ncell)));
+    StepArgs b = make_args(c);
+    b.amp = a.amp;
+    b.e_in = c->e[c->cur];
+    b.e_out = c->e[c->cur ^ 1];
+    b.ediff_in = c->ediff[c->ecur];
+    b.ediff_out = c->ediff[c->ecur ^ 1];
+    if (c->tiled) {
+        e = launch_step_tiled(b, c->plan, c->stream);
+        c->plan.stall = 0;
+    } else {
+        e = launch_step_generic(b, c->storage, c->limiter, c->stream);
+    }
+    if (e != cudaSuccess) return fail(c, BTE_ECUDA, "forward step launch: %s", cudaGetErrorString(e));
+    double kb = 0.0;
+    for (int k = 0; k < c->nb; ++k) kb += c->C[k] * c->v[k] * c->v[k] * c->tau[k];
+    kb /= 3.0;
+    const int max_cg = 40 * (c->n[0] + c->n[1] + c->n[2]);
+    CU(c, synthetic_correct(b, c->h, c->wf, static_cast<const float *>(c->e[c->cur]),
+                            static_cast<const float *>(c->e[c->cur ^ 1]), c->syn_pr, c->syn_x, kb, c->dt, max_cg, 1e-10,
+                            c->TL, c->stream, &c->syn_cg));
+    return BTE_OK;
+}
+
+extern "C" bte_status bte_set_steady_scheme(bte_ctx *c, int scheme) {
+    if (!c) return fail(nullptr, BTE_EINVAL, "ctx is NULL");
+    if (scheme != BTE_SCHEME_SEQUENTIAL && scheme != BTE_SCHEME_SYNTHETIC) return fail(c, BTE_EINVAL, "bad scheme");
+    c->scheme = scheme;
+    return BTE_OK;
 }
 
 static bte_status sis_check(bte_ctx *c) {

@@ -119,6 +119,17 @@ cudaError_t launch_iface_mix(float *eA, float *pa, int pure_a, int sa, float *eB
 // e^n + dt R on entry and e^{n+1} = e^n + De on exit, De solving each plane's first-order upwind
 // system (dt/tau + sum|nu_a|) De_i - sum_a |nu_a| De_{up_a(i)} = dt R_i (0 across walls).  FP32.
 cudaError_t launch_sis_sweep(const StepArgs &a, const float *e_in, float *e_io, cudaStream_t s);
+// Synthetic iterative scheme (Sec. 3.5): from e_in (the state) and e_out (the forward step's
+// e_in + dt R, R with e0 of T_L(e_in)), the energy residual r = sum_k sum_d w_d R, then
+// conjugate gradients on k_bulk L dT = -r (L: the cell Laplacian, thermalizing walls hold the
+// temperature, reflecting walls pass no heat, periodic pairs wrap; mean-free when no wall is
+// thermalizing), and TL += dT.  Pr: nb * ncell floats; scratch: synthetic_scratch_doubles(ncell).
+// Synchronises the stream every 16 CG iterations to test |r_cg| <= rel_tol |b|.
+constexpr int kSynthParts = 304;
+size_t synthetic_scratch_doubles(long long ncell);
+cudaError_t synthetic_correct(const StepArgs &a, const double h[3], const float *w, const float *e_in,
+                              const float *e_out, float *Pr, double *scratch, double k_bulk, double dt, int max_cg,
+                              double rel_tol, float *TL, cudaStream_t s, int *cg_iters);
 // Energy and wall flows into host7[7] with no device allocation (file-scope device scratch).
 // Returns 0, 1 (grid larger than the scratch covers) or 2 (CUDA error in *err).
 int launch_energy_noalloc(const StepArgs &a, int storage, int limiter, const double *w, const double *sv,

@@ -215,6 +215,18 @@ def interface_2d(nx=256, ny=128, nb=40, ntheta=4, nphi=4):
 GRAY_SI = dict(C=1627600.0, v=2677.0, tau=39.9e-12)
 
 
+def diffusive_film_1d(nx=100, h=40e-9, ntheta=16):
+    """A gray-silicon film 4 um thick (100 cells of 40 nm, about 37 mean free paths) between
+    thermalizing walls 0.5 K above and below T_ref, 16 Gauss-Legendre directions: the
+    near-diffusive steady problem on which the sequential iterations of the steady solver slow
+    down and the synthetic scheme of Sec. 3.5 is meant to help."""
+    hh = (h, h, h)
+    C, v, tau = (np.array([GRAY_SI[k]]) for k in ("C", "v", "tau"))
+    return dict(name="diffusive_film_1d_%d_1x%d" % (nx, ntheta), dim=1, n=(nx, 1, 1), h=hh, nb=1, seed=0,
+                quad=("gl1d", ntheta), bc=[ISOTHERMAL, ISOTHERMAL, PERIODIC, PERIODIC, PERIODIC, PERIODIC],
+                Tw=[0.5, -0.5, 0, 0, 0, 0], steps=0, C=C, v=v, tau=tau, dt=cfl_time_step(hh[:1], v), source=None)
+
+
 def ttg_1d(xi=1.0, nx=1000, ntheta=512, nb=1, A0=1.0, t_star=None):
     """Transient thermal grating (Sec. 4.2): one period L of T(x, 0) = A0 cos(2 pi x / L) with
     periodic ends, 1000 cells and 512 directions (GL in mu).  Gray silicon by default; the

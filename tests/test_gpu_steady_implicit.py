@@ -133,3 +133,63 @@ def test_implicit_uses_that_are_refused():
     with pytest.raises(bte.BteError) as ei:
         bte.bte_run_steady_implicit(ctx, 0, 1, 1e-6, 1e-6)
     assert ei.value.status == bte.BTE_EINVAL
+
+
+@pytest.mark.parametrize("limiter", [0, 2])
+@pytest.mark.parametrize("case", CASES)
+def test_synthetic_iterations_elementwise(case, limiter):
+    """Synthetic iterations (Sec. 3.5): one and then three more from a seeded start with a source
+    (none when no wall is thermalizing, the macroscopic equation then being singular), the state
+    element by element and the corrected lattice temperature against the oracle within 1e-5."""
+    from paper_2306_14181_gb300 import bte
+    dim, n, bc, quad, jump, kern = case
+    cfg = small_cfg(dim, n, bc, Tw=TW, nb=3, quad=quad, jump=jump)
+    P = oracle_problem(cfg, limiter)
+    ctx = gpu_ctx(cfg, limiter=limiter)
+    bte.bte_set_steady_scheme(ctx, bte.BTE_SCHEME_SYNTHETIC)
+    e0 = _start(P, 33)
+    regular = ISO in bc[:2 * dim]
+    Q = (np.random.default_rng(6).random((P.nz, P.ny, P.nx)) * 2e17).astype(np.float32) if regular else None
+    bte.bte_set_state(ctx, e0)
+    if Q is not None:
+        bte.bte_set_source(ctx, Q)
+    eo = e0.astype(np.float64)
+    TLo = P.lattice_temperature(eo)
+    for m in (1, 3):
+        bte.bte_sis_iterate(ctx, m)
+        for _ in range(m):
+            eo, TLo = P.synthetic_iteration(eo, TLo, Q)
+        g = bte.bte_get_state(ctx)
+        assert np.max(np.abs(g - eo)) <= 1e-5 * np.max(np.abs(eo))
+        gTL = bte.bte_lattice_temperature(ctx).reshape(TLo.shape)
+        assert np.max(np.abs(gTL - TLo)) <= 1e-5 * np.max(np.abs(TLo))
+
+
+def test_synthetic_scheme_near_the_diffusive_limit():
+    """A film between two walls 1 K apart with relaxation times far below a cell's flight time:
+    the sequential scheme needs hundreds of iterations to eps_T, eps_q < 1e-6, the synthetic one a
+    few tens to 1e-5 (in FP32 its change between iterates settles near 1e-6: a correction from the
+    energy residual of an FP32 state), and both land on the oracle's steady lattice temperature
+    within 1e-4."""
+    from paper_2306_14181_gb300 import bte
+    cfg = small_cfg(1, (30, 1, 1), [ISO, ISO, PER, PER, PER, PER], Tw=[0.5, -0.5, 0, 0, 0, 0], nb=1,
+                    quad=("gl1d", 16), h=1e-9, tau=1e-12, v=1e3)
+    cfg["C"] = np.array([1.66e6])
+    P = oracle_problem(cfg, 2)
+    eo, _, _, _ = P.run_synthetic(P.equilibrium(0.0), 500, 1e-12, 1e-12)
+    oTL = P.lattice_temperature(eo)
+    its = {}
+    for scheme in (bte.BTE_SCHEME_SEQUENTIAL, bte.BTE_SCHEME_SYNTHETIC):
+        ctx = gpu_ctx(cfg, limiter=2)
+        bte.bte_set_steady_scheme(ctx, scheme)
+        bte.bte_init_temperature(ctx, None)
+        tol = 1e-6 if scheme == bte.BTE_SCHEME_SEQUENTIAL else 1e-5
+        it, eT, eq = bte.bte_run_steady_implicit(ctx, 5000, 5, tol, tol)
+        assert eT < tol and eq < tol
+        _, gTL, _ = bte.bte_moments(ctx)
+        assert np.max(np.abs(gTL.ravel() - oTL.ravel())) <= 1e-4 * np.max(np.abs(oTL))
+        its[scheme] = it
+    assert its[bte.BTE_SCHEME_SYNTHETIC] <= 60 and its[bte.BTE_SCHEME_SEQUENTIAL] >= 4 * its[bte.BTE_SCHEME_SYNTHETIC]
+    with pytest.raises(bte.BteError) as ei:
+        bte.bte_set_steady_scheme(ctx, 2)
+    assert ei.value.status == bte.BTE_EINVAL
