@@ -359,7 +359,8 @@ enum {
                                   energy residual of the new state, k_bulk = sum_k C_k v_k^2 tau_k / 3, L the cell
                                   Laplacian (thermalizing walls hold the temperature, reflecting walls pass no
                                   heat, periodic pairs wrap; the mean-free solution when no wall is thermalizing),
-                                  solved by conjugate gradients in FP64 to 1e-10.  Its fixed point is the
+                                  solved in FP64 (1-D with a thermalizing wall: the Thomas algorithm; else
+                                  conjugate gradients to a relative residual of 1e-8).  Its fixed point is the
                                   sequential scheme's; it converges in far fewer iterations near the diffusive
                                   limit.  An iteration costs a second forward step and the solve */
 };

@@ -1040,7 +1040,7 @@ static bte_status sis_one(bte_ctx *c) {
     kb /= 3.0;
     const int max_cg = 40 * (c->n[0] + c->n[1] + c->n[2]);
     CU(c, synthetic_correct(b, c->h, c->wf, static_cast<const float *>(c->e[c->cur]),
-                            static_cast<const float *>(c->e[c->cur ^ 1]), c->syn_pr, c->syn_x, kb, c->dt, max_cg, 1e-10,
+                            static_cast<const float *>(c->e[c->cur ^ 1]), c->syn_pr, c->syn_x, kb, c->dt, max_cg, 1e-8,
                             c->TL, c->stream, &c->syn_cg));
     return BTE_OK;
 }

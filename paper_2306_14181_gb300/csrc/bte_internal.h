@@ -124,7 +124,8 @@ cudaError_t launch_sis_sweep(const StepArgs &a, const float *e_in, float *e_io, 
 // conjugate gradients on k_bulk L dT = -r (L: the cell Laplacian, thermalizing walls hold the
 // temperature, reflecting walls pass no heat, periodic pairs wrap; mean-free when no wall is
 // thermalizing), and TL += dT.  Pr: nb * ncell floats; scratch: synthetic_scratch_doubles(ncell).
-// Synchronises the stream every 16 CG iterations to test |r_cg| <= rel_tol |b|.
+// 1-D grids with a thermalizing wall and no periodic pair are solved directly (Thomas); else
+// CG, synchronising the stream every 16 iterations to test |r_cg| <= rel_tol |b|.
 constexpr int kSynthParts = 304;
 size_t synthetic_scratch_doubles(long long ncell);
 cudaError_t synthetic_correct(const StepArgs &a, const double h[3], const float *w, const float *e_in,

@@ -13,9 +13,10 @@
 // the solution is the mean-free one.
 //
 // Here: the energy residual from the forward step's output (two passes: a band's directions,
-// then the bands), and conjugate gradients in FP64 on the cells, each iteration five short
-// launches with the scalars on the device (no host synchronisation but a convergence check every
-// few iterations); the dot products are block partials summed in a fixed order.
+// then the bands), then on 1-D grids with a thermalizing wall the Thomas algorithm (one thread),
+// else conjugate gradients in FP64 on the cells, each iteration short launches with the scalars
+// on the device (no host synchronisation but a convergence check every 16 iterations); the dot
+// products are block partials summed in a fixed order.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -176,6 +177,29 @@ __global__ void __launch_bounds__(kThreads) k_tl_correct(const double *__restric
     TL[i] = (float)((double)TL[i] + (project ? x[i] - scal[kMEAN] : x[i]));
 }
 
+// 1-D grids with a thermalizing wall and no periodic pair: L is tridiagonal and regular; one
+// thread solves L x = b by the Thomas algorithm (forward elimination, back substitution), the
+// elimination's ratios kept in cp.
+__global__ void k_thomas_1d(const double *__restrict__ b, long long n, double ih2, int lo_iso, int hi_iso,
+                            double *__restrict__ cp, double *__restrict__ x) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    auto diag = [&](long long i) {
+        double d = -2.0 * ih2;
+        if (i == 0) d += lo_iso ? -ih2 : ih2;
+        if (i == n - 1) d += hi_iso ? -ih2 : ih2;
+        return d;
+    };
+    double m = diag(0);
+    cp[0] = ih2 / m;
+    x[0] = b[0] / m;
+    for (long long i = 1; i < n; ++i) {
+        m = diag(i) - ih2 * cp[i - 1];
+        cp[i] = ih2 / m;
+        x[i] = (b[i] - ih2 * x[i - 1]) / m;
+    }
+    for (long long i = n - 2; i >= 0; --i) x[i] -= cp[i] * x[i + 1];
+}
+
 }  // namespace
 
 size_t synthetic_scratch_doubles(long long ncell) { return (size_t)5 * ncell + kSynthParts + 8; }
@@ -198,6 +222,12 @@ cudaError_t synthetic_correct(const StepArgs &a, const double h[3], const float 
     for (int q = 0; q < a.dim; ++q)
         if (a.bc[2 * q] == kBcIsothermal || a.bc[2 * q + 1] == kBcIsothermal) singular = false;
     for (int q = 0; q < 3; ++q) g.ih2[q] = 1.0 / (h[q] * h[q]);
+    if (a.dim == 1 && !singular && a.bc[0] != kBcPeriodic) {
+        k_thomas_1d<<<1, 1, 0, s>>>(b, n, g.ih2[0], a.bc[0] == kBcIsothermal, a.bc[1] == kBcIsothermal, r, x);
+        k_tl_correct<<<nblk, kThreads, 0, s>>>(x, scal, 0, n, TL);
+        if (cg_iters) *cg_iters = 0;
+        return cudaGetLastError();
+    }
     if (singular) {
         k_partial_sum<<<kSynthParts, kThreads, 0, s>>>(b, nullptr, n, part);
         k_finish<<<1, kThreads, 0, s>>>(part, kSynthParts, scal, kMEAN, 1, n);
