@@ -534,7 +534,18 @@ def ttg_record(args, xi):
     ctx = bte.bte_from_workload(cfg, limiter=args.limiter, stream=torch.cuda.current_stream().cuda_stream)
     info = ctx.info
     bte.bte_init_temperature(ctx, inputs.ttg_initial_temperature(cfg).reshape(-1))
-    t_ms, fwd_ms, nfwd, fin_ms, nfin, _ = timed_forward(ctx, cfg["steps"])
+    # CUDA events around the one bte_step call, without per-launch tracing: a long call replays
+    # captured step graphs, which tracing would turn off
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    bte.bte_step(ctx, cfg["steps"])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    bte.bte_synchronize(ctx)
+    t_ms = ev0.elapsed_time(ev1)
     T, _, _ = bte.bte_moments(ctx)
     rec = {"workload": cfg["name"], "xi": xi, "storage": "f32", "kernel": kernel_name_of(info), "steps": cfg["steps"],
            "t_star_end": cfg["steps"] * cfg["dt"] / cfg["tau_ref"], "ms_per_step": t_ms / cfg["steps"],

@@ -86,6 +86,14 @@ struct bte_ctx {
     float *wf = nullptr;
     double adj_ms = 0, adj_recompute_ms = 0;
     long long adj_steps = 0, adj_recompute_steps = 0;
+    // CUDA graph of kGraphSteps forward steps for long bte_step calls (see step_graphs), its
+    // private stream and ordering events, and the context state it was captured from
+    cudaStream_t gstream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaEvent_t gev[2] = {nullptr, nullptr};
+    int gkey_cur = -1, gkey_ecur = -1, gkey_src = -1;
+    const float *gkey_tl = nullptr;
+    unsigned long long gkey_wait = 0;
     // steady solver's iterative scheme (Sec. 3.5): 0 sequential, 1 synthetic; the synthetic
     // scheme's scratch (allocated on first use) and the conjugate-gradient count of its last
     // correction
@@ -342,6 +350,12 @@ static bte_status iface_mix(bte_ctx *c) {
 }
 
 static void free_all(bte_ctx *c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    for (cudaEvent_t &e : c->gev)
+        if (e) cudaEventDestroy(e), e = nullptr;
+    if (c->gstream) cudaStreamDestroy(c->gstream);
+    c->gstream = nullptr;
     cudaFree(c->syn_pr);
     cudaFree(c->syn_x);
     c->syn_pr = nullptr;
@@ -771,14 +785,85 @@ static bte_status step_persistent(bte_ctx *c, int nsteps) {
     return BTE_OK;
 }
 
-static bte_status step_one(bte_ctx *c);
+static bte_status step_one(bte_ctx *c, cudaStream_t s);
+
+// A long bte_step call replays a CUDA graph of kGraphSteps steps (an even number, so that the
+// two state buffers, the two wall-value buffers and the T_L / code-reference pair are back where
+// they were) instead of launching every kernel of every step.  That is exact when the steps differ
+// only in those buffers: a constant source amplitude, no stochastic rounding (its key depends on
+// the step index), no kernel tracing and no pending failure-detection test.  The graph runs on a
+// private stream ordered after and before the context's stream by events; it is captured again
+// when the buffers' parity, the source's presence or the wait limit differ from its capture.
+constexpr int kGraphSteps = 32;
+
+static bool graph_eligible(const bte_ctx *c) {
+    const bool sr = c->rounding == BTE_ROUND_STOCHASTIC && c->storage != BTE_STORE_F32;
+    return !c->persist && !c->has_amp && !sr && !c->prof && !(c->tiled && c->plan.stall);
+}
+
+static bte_status step_graphs(bte_ctx *c, int chunks) {
+    const unsigned long long wait = c->tiled ? c->plan.wait_ns : 0ull;
+    const int src = c->has_source ? 1 : 0;
+    if (!c->gexec || c->gkey_cur != c->cur || c->gkey_ecur != c->ecur || c->gkey_tl != c->TL || c->gkey_src != src ||
+        c->gkey_wait != wait) {
+        if (c->gexec) cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+        if (!c->gstream) CU(c, cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+        for (cudaEvent_t &e : c->gev)
+            if (!e) CU(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        const int cur = c->cur, ecur = c->ecur;
+        float *TL = c->TL, *R = c->R;
+        const long long step = c->step;
+        CU(c, cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal));
+        bte_status st = BTE_OK;
+        for (int i = 0; i < kGraphSteps && st == BTE_OK; ++i) st = step_one(c, c->gstream);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(c->gstream, &graph);
+        c->cur = cur;
+        c->ecur = ecur;
+        c->TL = TL;
+        c->R = R;
+        c->step = step;
+        if (st != BTE_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (ec != cudaSuccess) return fail(c, BTE_ECUDA, "step graph capture: %s", cudaGetErrorString(ec));
+        const cudaError_t ei = cudaGraphInstantiate(&c->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            c->gexec = nullptr;
+            return fail(c, BTE_ECUDA, "step graph instantiation: %s", cudaGetErrorString(ei));
+        }
+        c->gkey_cur = cur;
+        c->gkey_ecur = ecur;
+        c->gkey_tl = TL;
+        c->gkey_src = src;
+        c->gkey_wait = wait;
+    }
+    CU(c, cudaEventRecord(c->gev[0], c->stream));
+    CU(c, cudaStreamWaitEvent(c->gstream, c->gev[0], 0));
+    for (int i = 0; i < chunks; ++i) {
+        CU(c, cudaGraphLaunch(c->gexec, c->gstream));
+        c->step += kGraphSteps;
+    }
+    CU(c, cudaEventRecord(c->gev[1], c->gstream));
+    CU(c, cudaStreamWaitEvent(c->stream, c->gev[1], 0));
+    return BTE_OK;
+}
 
 extern "C" bte_status bte_step(bte_ctx *c, int nsteps) {
     if (!c) return fail(nullptr, BTE_EINVAL, "ctx is NULL");
     if (nsteps < 0) return fail(c, BTE_EINVAL, "n must be >= 0");
     if (c->peer) return fail(c, BTE_ESTATE, "the context is coupled at an interface: it steps through bte_step_pair");
     if (c->persist) return nsteps > 0 ? step_persistent(c, nsteps) : BTE_OK;
-    for (int s = 0; s < nsteps; ++s) TRY(step_one(c));
+    int s = 0;
+    if (nsteps >= 2 * kGraphSteps && graph_eligible(c)) {
+        const int chunks = nsteps / kGraphSteps;
+        TRY(step_graphs(c, chunks));
+        s = chunks * kGraphSteps;
+    }
+    for (; s < nsteps; ++s) TRY(step_one(c, c->stream));
     return BTE_OK;
 }
 
@@ -787,8 +872,8 @@ extern "C" bte_status bte_step_pair(bte_ctx *a, bte_ctx *b, int nsteps) {
     if (nsteps < 0) return fail(a, BTE_EINVAL, "n must be >= 0");
     if (a->peer != b || b->peer != a) return fail(a, BTE_ESTATE, "the two contexts are not coupled with each other");
     for (int s = 0; s < nsteps; ++s) {
-        TRY(step_one(a));
-        TRY(step_one(b));
+        TRY(step_one(a, a->stream));
+        TRY(step_one(b, b->stream));
         a->iface_pure = b->iface_pure = true;
         TRY(iface_mix(a));
     }
@@ -832,7 +917,7 @@ extern "C" bte_status bte_interface(bte_ctx *a, int wa, bte_ctx *b, int wb, cons
     return iface_mix(a);
 }
 
-static bte_status step_one(bte_ctx *c) {
+static bte_status step_one(bte_ctx *c, cudaStream_t strm) {
     {
         StepArgs a = make_args(c);
         a.amp = (float)amplitude_at(c, c->step);
@@ -849,18 +934,18 @@ static bte_status step_one(bte_ctx *c) {
         cudaEvent_t ev;
         if (c->prof) TRY(prof_event(c, &ev));
         if (c->tiled) {
-            e = launch_step_tiled(a, c->plan, c->stream);
+            e = launch_step_tiled(a, c->plan, strm);
             c->plan.stall = 0;
         } else {
-            e = launch_step_generic(a, c->storage, c->limiter, c->stream);
+            e = launch_step_generic(a, c->storage, c->limiter, strm);
         }
         if (e != cudaSuccess) return fail(c, BTE_ECUDA, "forward step launch: %s", cudaGetErrorString(e));
         if (c->prof) TRY(prof_event(c, &ev));
         // T_L^{n+1} goes to the buffer of the old code reference; T_L^n becomes the reference of
         // the new state
         float *TL_next = c->R;
-        if (c->tiled) e = launch_finalize_tiled(a, c->plan, c->storage, TL_next, c->stream);
-        else e = launch_finalize(a, c->G, TL_next, c->stream);
+        if (c->tiled) e = launch_finalize_tiled(a, c->plan, c->storage, TL_next, strm);
+        else e = launch_finalize(a, c->G, TL_next, strm);
         if (e != cudaSuccess) return fail(c, BTE_ECUDA, "finalize launch: %s", cudaGetErrorString(e));
         if (c->prof) TRY(prof_event(c, &ev));
         c->R = c->TL;

@@ -603,3 +603,33 @@ def test_contexts_sharing_a_kernel_instance():
         bte.bte_step(ctx, 3)
     eo = PA.run(e0.astype(np.float64), 3)
     assert rel_linf(bte.bte_get_state(A), eo) <= TOL
+
+
+@pytest.mark.parametrize("dim,n,bc,storage", [(2, (96, 40, 1), [DIF, SPE, ISO, DIF, PER, PER], 0),
+                                              (2, (37, 23, 1), [PER, PER, ISO, DIF, PER, PER], 0),
+                                              (3, (64, 9, 7), [PER, PER, SPE, DIF, ISO, DIF], 0),
+                                              (2, (96, 40, 1), [DIF, SPE, ISO, DIF, PER, PER], 1)])
+def test_graph_replayed_steps_equal_single_steps(dim, n, bc, storage):
+    """A long bte_step call replays a CUDA graph of captured steps: 150 steps in one call (graph
+    chunks and a remainder) are bitwise the 150 steps of single calls, and so are the next 70
+    after the source is removed (the graph is captured again)."""
+    from paper_2306_14181_gb300 import bte
+    cfg = small_cfg(dim, n, bc, Tw=[0.3, -0.2, 0.1, 0.4, -0.3, 0.2], nb=3)
+    P = oracle_problem(cfg)
+    Q = (np.random.default_rng(8).random((P.nz, P.ny, P.nx)) * 2e17).astype(np.float32)
+    ctxs = [gpu_ctx(cfg, storage=storage, T_scale=1.0) for _ in range(2)]
+    for ctx in ctxs:
+        bte.bte_init_temperature(ctx, None)
+        bte.bte_set_source(ctx, Q)
+    bte.bte_step(ctxs[0], 150)
+    for _ in range(150):
+        bte.bte_step(ctxs[1], 1)
+    assert np.array_equal(bte.bte_get_state(ctxs[0]), bte.bte_get_state(ctxs[1]))
+    assert np.array_equal(bte.bte_lattice_temperature(ctxs[0]), bte.bte_lattice_temperature(ctxs[1]))
+    for ctx in ctxs:
+        bte.bte_set_source(ctx, None)
+    bte.bte_step(ctxs[0], 70)
+    for _ in range(70):
+        bte.bte_step(ctxs[1], 1)
+    assert np.array_equal(bte.bte_get_state(ctxs[0]), bte.bte_get_state(ctxs[1]))
+
