@@ -367,7 +367,8 @@ enum {
 
 /* Select the scheme of the steady implicit iterations (BTE_EINVAL for another value).  After a
  * synthetic iteration bte_lattice_temperature returns the corrected lattice temperature the next
- * sweep uses; bte_moments' dTL is always that of the state. */
+ * sweep uses; bte_moments' dTL is always that of the state, and bte_step, bte_adjoint and a
+ * sequential iteration that follow start from the state's own T_L again. */
 bte_status bte_set_steady_scheme(bte_ctx *ctx, int scheme);
 
 /* Iterate until the loop condition of Sec. 3.5 holds between consecutive iterates, eps_T <

@@ -98,6 +98,7 @@ struct bte_ctx {
     // scheme's scratch (allocated on first use) and the conjugate-gradient count of its last
     // correction
     int scheme = 0;
+    bool tl_corrected = false;  // TL holds a synthetic correction, not the T_L of the state
     float *syn_pr = nullptr;
     double *syn_x = nullptr;
     int syn_cg = 0;
@@ -326,6 +327,7 @@ static bte_status refresh_moments(bte_ctx *c) {
     CU(c, launch_moment_only(a, c->storage, c->stream));
     c->ecur ^= 1;
     CU(c, launch_finalize(a, c->nb, c->TL, c->stream));
+    c->tl_corrected = false;
     c->iface_pure = true;
     if (c->peer) TRY(iface_mix(c));
     return BTE_OK;
@@ -856,6 +858,8 @@ extern "C" bte_status bte_step(bte_ctx *c, int nsteps) {
     if (!c) return fail(nullptr, BTE_EINVAL, "ctx is NULL");
     if (nsteps < 0) return fail(c, BTE_EINVAL, "n must be >= 0");
     if (c->peer) return fail(c, BTE_ESTATE, "the context is coupled at an interface: it steps through bte_step_pair");
+    // after synthetic iterations the step starts from the state's own T_L (Eq. BTE_get_e0)
+    if (c->tl_corrected && nsteps > 0) TRY(refresh_moments(c));
     if (c->persist) return nsteps > 0 ? step_persistent(c, nsteps) : BTE_OK;
     int s = 0;
     if (nsteps >= 2 * kGraphSteps && graph_eligible(c)) {
@@ -1084,6 +1088,8 @@ static bte_status moments_on_device(bte_ctx *c, const DiagOut &o) {
 // e^n + dt R, the sweep turns it into e^n + De, and T_L and the diffuse-wall values follow from
 // the new state.
 static bte_status sis_one(bte_ctx *c) {
+    // a sequential iteration after synthetic ones relaxes towards the state's own T_L again
+    if (c->tl_corrected && c->scheme != BTE_SCHEME_SYNTHETIC) TRY(refresh_moments(c));
     StepArgs a = make_args(c);
     a.amp = (float)amplitude_at(c, c->step);
     a.e_in = c->e[c->cur];
@@ -1127,6 +1133,7 @@ static bte_status sis_one(bte_ctx *c) {
     CU(c, synthetic_correct(b, c->h, c->wf, static_cast<const float *>(c->e[c->cur]),
                             static_cast<const float *>(c->e[c->cur ^ 1]), c->syn_pr, c->syn_x, kb, c->dt, max_cg, 1e-8,
                             c->TL, c->stream, &c->syn_cg));
+    c->tl_corrected = true;
     return BTE_OK;
 }
 
@@ -1422,6 +1429,7 @@ extern "C" bte_status bte_adjoint(bte_ctx *c, int nsteps, int ckpt_every, const 
     if (nsteps < 0) return fail(c, BTE_EINVAL, "nsteps must be >= 0");
     if (ckpt_every < 0) return fail(c, BTE_EINVAL, "ckpt_every must be >= 0");
     if (c->peer) return fail(c, BTE_ESTATE, "the context is coupled at an interface (no adjoint of the pair)");
+    if (c->tl_corrected) TRY(refresh_moments(c));
     for (long long i = 0; i < c->ncell; ++i)
         if (!std::isfinite(probe[i])) return fail(c, BTE_EINVAL, "probe holds a non-finite value at cell %lld", i);
     const long long nc = c->ncell, nel = c->nelem;

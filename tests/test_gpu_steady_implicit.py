@@ -193,3 +193,20 @@ def test_synthetic_scheme_near_the_diffusive_limit():
     with pytest.raises(bte.BteError) as ei:
         bte.bte_set_steady_scheme(ctx, 2)
     assert ei.value.status == bte.BTE_EINVAL
+
+
+def test_time_steps_after_synthetic_iterations():
+    """Time steps that follow synthetic iterations start from the state's own T_L (the corrected
+    one is only the next sweep's): they match the oracle's steps from the same state."""
+    from paper_2306_14181_gb300 import bte
+    dim, n, bc, quad, jump, kern = CASES[1]
+    cfg = small_cfg(dim, n, bc, Tw=TW, nb=3, quad=quad, jump=jump)
+    P = oracle_problem(cfg, 2)
+    ctx = gpu_ctx(cfg, limiter=2)
+    bte.bte_set_steady_scheme(ctx, bte.BTE_SCHEME_SYNTHETIC)
+    bte.bte_set_state(ctx, _start(P, 35))
+    bte.bte_sis_iterate(ctx, 3)
+    e3 = bte.bte_get_state(ctx).astype(np.float64)
+    bte.bte_step(ctx, 2)
+    eo = P.run(e3, 2)
+    assert np.max(np.abs(bte.bte_get_state(ctx) - eo)) <= 1e-5 * np.max(np.abs(eo))
