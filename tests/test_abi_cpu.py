@@ -62,12 +62,29 @@ def _create(**over):
     (dict(dT_jump=(0.5, 0.0, 0.0)), "dT_jump needs a periodic pair"),        # x walls are diffuse
     (dict(bc=[3, 3, 0, 1, 3, 3], dT_jump=(0.5, 0.0, 0.2)), "inactive axis 2"),
     (dict(bc=[3, 3, 0, 1, 3, 3], dT_jump=(float("inf"), 0.0, 0.0)), "non-finite dT_jump"),
+    (dict(bc=[4, 4, 0, 1, 3, 3]), "at most one interface wall"),
+    (dict(bc=[0, 1, 0, 1, 4, 3]), "interface on an inactive axis"),
 ])
 def test_host_validation_rejects_bad_input(lib, over, frag):
     with pytest.raises(bte.BteError) as ei:
         _create(**over)
     assert ei.value.status == bte.BTE_EINVAL
     assert frag in str(ei.value)
+
+
+def test_interface_walls_need_fp32_storage(lib):
+    with pytest.raises(bte.BteError) as ei:
+        _create(bc=[0, 4, 0, 1, 3, 3], storage=bte.BTE_STORE_F16)
+    assert ei.value.status == bte.BTE_EUNSUPPORTED
+
+
+def test_null_arguments_are_rejected_by_the_newer_calls(lib):
+    assert lib.bte_interface(None, 1, None, 0, None, None) == bte.BTE_EINVAL
+    assert lib.bte_step_pair(None, None, 1) == bte.BTE_EINVAL
+    assert lib.bte_sis_iterate(None, 1) == bte.BTE_EINVAL
+    assert lib.bte_run_steady_implicit(None, 10, 1, 1e-6, 1e-6, None, None, None) == bte.BTE_EINVAL
+    assert lib.bte_set_steady_scheme(None, 0) == bte.BTE_EINVAL
+    assert lib.bte_set_wait_limit(None, 0, 0) == bte.BTE_EINVAL
 
 
 def test_null_arguments_are_rejected(lib):
