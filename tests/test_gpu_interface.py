@@ -61,6 +61,7 @@ CASES = [
     (3, (32, 12, 6), (32, 12, 4), 5, 4, [PER, PER, SPE, DIF, ISO, None], [PER, PER, ISO, SPE, None, SPE], "tiled"),
     (2, (13, 9, 1), (7, 9, 1), 1, 0, [ISO, None, DIF, SPE, PER, PER], [None, SPE, ISO, DIF, PER, PER], "generic"),
     (1, (40, 1, 1), (25, 1, 1), 0, 1, [None, ISO, PER, PER, PER, PER], [DIF, None, PER, PER, PER, PER], "generic"),
+    (3, (9, 6, 5), (9, 6, 4), 5, 4, [ISO, DIF, SPE, SPE, DIF, None], [SPE, ISO, DIF, SPE, None, ISO], "generic"),
 ]
 
 
@@ -217,5 +218,24 @@ def test_interface_workload_reduced():
         oA, oB = interface_step(PA, oA, wa, PB, oB, wb, cfg["beta_ab"], cfg["beta_ba"], QA=Q)
     sc = max(np.max(np.abs(oA)), np.max(np.abs(oB)))
     assert np.max(np.abs(oB)) > 1e-3 * sc  # heat reached B through the interface
+    assert np.max(np.abs(bte.bte_get_state(A) - oA)) <= 1e-5 * sc
+    assert np.max(np.abs(bte.bte_get_state(B) - oB)) <= 1e-5 * sc
+
+
+def test_interface_with_a_periodic_jump_across():
+    """The interface on x while y is a periodic pair with a temperature difference in A (Sec. 2.2
+    (iv) and (v) together): 20 coupled steps against the oracle within 1e-5."""
+    from paper_2306_14181_gb300 import bte
+    cA, cB = pair(2, (40, 12, 1), (24, 12, 1), 1, 0, [ISO, None, PER, PER, PER, PER], [None, ISO, PER, PER, PER, PER])
+    cA["jump"] = [0.0, 0.4, 0.0]
+    PA, PB = oracle_problem(cA, 2), oracle_problem(cB, 2)
+    A, B = gpu_pair(cA, cB, 1, 0, BAB, BBA, 2)
+    eA, eB = start_states(PA, PB, 44)
+    bte.bte_set_state(A, eA)
+    bte.bte_set_state(B, eB)
+    bte.bte_interface(A, 1, B, 0, BAB, BBA)
+    bte.bte_step_pair(A, B, 20)
+    oA, oB = interface_run(PA, eA.astype(np.float64), 1, PB, eB.astype(np.float64), 0, BAB, BBA, 20)
+    sc = max(np.max(np.abs(oA)), np.max(np.abs(oB)))
     assert np.max(np.abs(bte.bte_get_state(A) - oA)) <= 1e-5 * sc
     assert np.max(np.abs(bte.bte_get_state(B) - oB)) <= 1e-5 * sc

@@ -135,8 +135,16 @@ def test_implicit_uses_that_are_refused():
     assert ei.value.status == bte.BTE_EINVAL
 
 
+# closed boxes (no thermalizing wall): the macroscopic equation is singular
+SINGULAR = [
+    (2, (96, 20, 1), [SPE, DIF, PER, PER, PER, PER], None, None, "tiled"),
+    (3, (32, 8, 6), [PER, PER, SPE, DIF, SPE, DIF], None, None, "tiled"),
+    (3, (7, 5, 4), [DIF, SPE, PER, PER, SPE, DIF], None, None, "generic"),
+]
+
+
 @pytest.mark.parametrize("limiter", [0, 2])
-@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("case", CASES + SINGULAR)
 def test_synthetic_iterations_elementwise(case, limiter):
     """Synthetic iterations (Sec. 3.5): one and then three more from a seeded start with a source
     (none when no wall is thermalizing, the macroscopic equation then being singular), the state
