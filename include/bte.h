@@ -216,7 +216,10 @@ bte_status bte_set_source(bte_ctx *ctx, const float *Q, int on_device, const dou
 /* Advance n >= 0 steps of Eq. (disretized_transientBTE).  Each step is one fused pass of the
  * forward kernel over all (band, direction, cell) (flux, relaxation, source, walls, moment
  * partials), then one short pass that finishes T_L and the diffuse-wall values.  Stream
- * ordered, non-blocking. */
+ * ordered, non-blocking.  A call of 64 steps or more replays a captured CUDA graph of 32 steps
+ * (on a private stream ordered after and before the context's stream) when the steps differ only
+ * in the ping-pong buffers: no source amplitudes, no stochastic rounding, no tracing; the result
+ * is bitwise that of single steps. */
 bte_status bte_step(bte_ctx *ctx, int n);
 
 /* The lattice temperature the last step formed (FP32 on the device), as doubles into dTL
@@ -393,8 +396,9 @@ bte_status bte_run_steady_implicit(bte_ctx *ctx, long long max_iters, int check_
  * balance); with equal group speeds the heat that leaves one side enters the other.
  * Both contexts need FP32 storage (their interface walls are refused at bte_create otherwise), a
  * context has at most one interface wall, and ctx_a != ctx_b.  The pair then advances only
- * through bte_step_pair: bte_step, bte_residuals, bte_run_steady and bte_adjoint on either
- * context return BTE_ESTATE.  bte_init_temperature and bte_set_state of either context keep the
+ * through bte_step_pair: bte_step, bte_residuals, bte_run_steady, bte_sis_iterate,
+ * bte_run_steady_implicit and bte_adjoint on either context return BTE_ESTATE.  Before the
+ * coupling (and after the partner's destruction) an interface wall is a diffuse wall.  bte_init_temperature and bte_set_state of either context keep the
  * coupling (the interface values are formed again from both current states).  bte_energy's flow
  * through the interface wall is the heat crossing the interface, outward from that side.  The
  * coupling holds until either context is destroyed; a context that is destroyed leaves its
