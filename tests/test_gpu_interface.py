@@ -239,3 +239,28 @@ def test_interface_with_a_periodic_jump_across():
     sc = max(np.max(np.abs(oA)), np.max(np.abs(oB)))
     assert np.max(np.abs(bte.bte_get_state(A) - oA)) <= 1e-5 * sc
     assert np.max(np.abs(bte.bte_get_state(B) - oB)) <= 1e-5 * sc
+
+
+def test_ballistic_flux_through_the_interface():
+    """The series law on the GPU: ballistic transport between thermalizing walls 1 K apart
+    through an interface of transmission 0.3 carries 0.3 of the wall-to-wall ballistic flux,
+    within 1e-5 (FP32 state)."""
+    from paper_2306_14181_gb300 import bte
+    t = 0.3
+    cA = small_cfg(1, (12, 1, 1), [ISO, DIF, PER, PER, PER, PER], Tw=[0.5, 0, 0, 0, 0, 0], nb=1, quad=("gl1d", 16),
+                   h=1e-9, tau=1e3, v=1e3)
+    cB = small_cfg(1, (12, 1, 1), [DIF, ISO, PER, PER, PER, PER], Tw=[0, -0.5, 0, 0, 0, 0], nb=1, quad=("gl1d", 16),
+                   h=1e-9, tau=1e3, v=1e3)
+    for c in (cA, cB):
+        c["C"] = np.array([1.66e6])
+    A, B = gpu_pair(cA, cB, 1, 0, t, t, 2)
+    bte.bte_init_temperature(A, None)
+    bte.bte_init_temperature(B, None)
+    bte.bte_interface(A, 1, B, 0, t, t)
+    bte.bte_step_pair(A, B, 3000)
+    PA = oracle_problem(cA, 2)
+    half = float((PA.w * np.clip(PA.s[:, 0], 0, None)).sum()) / PA.W
+    expect = t * 1.66e6 * 1e3 * 1.0 * half
+    for ctx in (A, B):
+        _, _, q = bte.bte_moments(ctx)
+        assert np.max(np.abs(q[0] - expect)) <= 1e-5 * expect

@@ -175,3 +175,24 @@ def test_interface_workload_transmissions():
     assert A["dt"] == B["dt"] and A["n"][1:] == B["n"][1:]
     assert A["bc"][cfg["wall_a"]] == BC_DIFFUSE and B["bc"][cfg["wall_b"]] == BC_DIFFUSE
     assert (cfg["wall_a"] >> 1) == (cfg["wall_b"] >> 1) and cfg["wall_a"] != cfg["wall_b"]
+
+
+@pytest.mark.parametrize("t", [0.25, 0.5, 0.8])
+def test_ballistic_flux_through_the_interface(t):
+    """Ballistic limit (relaxation times far beyond the flight time), one gray material on both
+    sides, thermalizing outer walls 1 K apart and an interface that transmits a share t both ways:
+    every emitter is diffuse, so the steady flux is the ballistic flux between the two walls times
+    t (the series law of diffuse transmitters: 1 / tau_eff = 1 + 1 + (1 / t - 1) - 1)."""
+    cA = small_cfg(1, (10, 1, 1), [ISO, DIF, PER, PER, PER, PER], Tw=[0.5, 0, 0, 0, 0, 0], nb=1, quad=("gl1d", 16),
+                   h=1e-9, tau=1e3, v=1e3)
+    cB = small_cfg(1, (10, 1, 1), [DIF, ISO, PER, PER, PER, PER], Tw=[0, -0.5, 0, 0, 0, 0], nb=1, quad=("gl1d", 16),
+                   h=1e-9, tau=1e3, v=1e3)
+    for c in (cA, cB):
+        c["C"] = np.array([1.66e6])
+    A, B = oracle_problem(cA, LIM_VANALBADA), oracle_problem(cB, LIM_VANALBADA)
+    eA, eB = interface_run(A, A.equilibrium(0.0), 1, B, B.equilibrium(0.0), 0, t, t, 3000)
+    half = float((A.w * np.clip(A.s[:, 0], 0, None)).sum()) / A.W
+    expect = t * 1.66e6 * 1e3 * 1.0 * half
+    for P, e in ((A, eA), (B, eB)):
+        q = P.moments(e)[2][0].ravel()
+        assert np.max(np.abs(q - expect)) <= 1e-10 * expect
