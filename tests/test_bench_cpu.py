@@ -29,3 +29,13 @@ def test_warmup_below_three_is_refused():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--warmup", "2"],
                        capture_output=True, text=True, timeout=120, cwd=ROOT)
     assert r.returncode != 0 and "warmup" in r.stderr
+
+
+def test_traffic_table_matches_the_forward_kernel_source():
+    """The committed DRAM-traffic table was taken on the current forward-kernel source for the
+    headline and the bench's other tiled forms (a kernel change turns the bench's traffic null
+    until it is measured again)."""
+    import bench
+    for workload, storage in (("laser_3d", "f32"), ("laser_3d", "f16"), ("hotspot_2d", "f32"), ("hotspot_2d", "f16")):
+        t = bench.measured_traffic(workload, storage, "tiled")
+        assert t is not None and t > 0, (workload, storage)
