@@ -94,3 +94,11 @@ def test_null_arguments_are_rejected(lib):
     assert lib.bte_step(None, 1) == bte.BTE_EINVAL
     lib.bte_destroy(None)   # ignored
     assert b"NULL" in lib.bte_last_error(None)
+
+
+def test_binding_declares_argument_types_of_every_export(lib):
+    """Every entry point the binding calls has its argument types declared (a pointer passed
+    without them would be truncated to a C int)."""
+    for name in bte.EXPORTS:
+        f = getattr(lib, name)
+        assert f.argtypes is not None, name
