@@ -136,3 +136,49 @@ def test_diffusive_limit_fourier_law():
     assert np.max(np.abs(TL[sl] - (slope * xs[sl] + icpt))) <= 1e-3 * np.ptp(TL)
     kappa = float(np.sum(P.C * P.v ** 2 * P.tau)) / 3.0
     assert abs(np.mean(q[0].ravel()[sl]) / (-kappa * slope) - 1.0) <= 1e-2
+
+
+@pytest.mark.parametrize("dim,n,bc,quad", [CASES[0], CASES[2], CASES[4]])
+def test_iteration_with_a_given_lattice_temperature(dim, n, bc, quad):
+    """The iteration that relaxes towards a given T_L (the synthetic scheme's corrected one):
+    with T_L of the state it is the plain iteration bit for bit; raising T_L by dT in one cell
+    adds to that cell's right-hand side C_k dT / (W tau_k) in every direction, so the increment
+    changes by the dense upwind solve of that source."""
+    cfg = small_cfg(dim, n, bc, Tw=TW, nb=3, quad=quad)
+    P = oracle_problem(cfg, LIM_VANALBADA)
+    rng = np.random.default_rng(21)
+    e = P.equilibrium(rng.uniform(-0.5, 0.5, (P.nz, P.ny, P.nx))) * (1 + 0.3 * rng.standard_normal(P.shape))
+    TL = P.lattice_temperature(e)
+    base = P.sis_iteration_tl(e, TL)
+    assert np.array_equal(base, P.sis_iteration(e))
+    cell = (P.nz // 2, P.ny // 2, P.nx // 2)
+    dT = 0.25
+    TL2 = TL.copy()
+    TL2[cell] += dT
+    change = P.sis_iteration_tl(e, TL2) - base
+    # the same change from the dense upwind solve of a source C_k dT / (W tau_k) in that cell
+    h = (P.dx, P.dy, P.dz)
+    nn = (P.nx, P.ny, P.nz)
+    idx = np.arange(P.ncell).reshape(P.nz, P.ny, P.nx)
+    for k in range(P.nb):
+        for d in range(P.nd):
+            M = np.zeros((P.ncell, P.ncell))
+            M[np.arange(P.ncell), np.arange(P.ncell)] = 1.0 / P.tau[k]
+            for a in range(P.dim):
+                sa = P.s[d, a]
+                c = P.v[k] * abs(sa) / h[a]
+                M[np.arange(P.ncell), np.arange(P.ncell)] += c
+                if sa == 0.0:
+                    continue
+                step = 1 if sa > 0 else -1
+                for z in range(P.nz):
+                    for y in range(P.ny):
+                        for x in range(P.nx):
+                            up = [x, y, z]
+                            up[a] -= step
+                            if 0 <= up[a] < nn[a]:
+                                M[idx[z, y, x], idx[up[2], up[1], up[0]]] -= c
+            rhs = np.zeros(P.ncell)
+            rhs[idx[cell]] = P.C[k] * dT / (P.W * P.tau[k])
+            expect = np.linalg.solve(M, rhs).reshape(P.nz, P.ny, P.nx)
+            assert np.max(np.abs(change[k, d] - expect)) <= 1e-9 * np.max(np.abs(expect)) + 1e-12 * np.max(np.abs(base))
